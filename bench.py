@@ -1,0 +1,322 @@
+"""Benchmark: exact betweenness centrality, BC edges/s (sources x m / s).
+
+Default workload: R-MAT scale 16, edge factor 16, (a,b,c,d) =
+(0.57,0.19,0.19,0.05), symmetrised, largest connected component; every LCC
+vertex is a source, batches of 256. One step = one bc_run over all sources
+plus its device-side result (the whole hot path: batch init, forward
+counting, backward sweep with the FP64 BC reduction, per-source summaries).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0). See the design doc for the roofline model.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0809_1906_gb300 import graphs as G  # noqa: E402
+
+METRIC = "BC edges/sec (sources x m / s)"
+UNIT = "edges/s"
+BATCH = 256
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload():
+    g = G.rmat_lcc(16, 16)
+    return g, f"rmat_s16_ef16_lcc (n={g.n}, m={g.m}), all {g.n} sources, batch {BATCH}"
+
+
+def algorithmic_bytes(n, m, arcs_total, nsrc, B):
+    """Bytes Brandes must move, per pass (one look per arc per pass):
+    forward  2m x 1 B level probe + 8 B sigma x a + 9 B (sigma + level) x n
+    backward 2m x 1 B level probe + 4 B c x a + 13 B (sigma + level read, c write) x n
+    per batch: BC 16 B x n, CSR 2 x (8m + 4n) B (read by each pass)."""
+    nb = -(-nsrc // B)
+    fwd = nsrc * (2 * m + 9 * n) + 8 * arcs_total + nb * (8 * m + 4 * n)
+    bwd = nsrc * (2 * m + 13 * n) + 4 * arcs_total + nb * (8 * m + 4 * n + 16 * n)
+    return fwd, bwd
+
+
+def cpu_oracle_rate(g, seconds: float):
+    """Oracle (as it stands) on the host cores over a bounded sample of sources."""
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    probe = G.sample_sources(g.n, min(g.n, 2 * threads), 901)
+    t0 = time.perf_counter()
+    oracle.bc(g, probe, threads=threads)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    k = int(min(g.n, max(len(probe), len(probe) * seconds / dt)))
+    src = G.sample_sources(g.n, k, 902)
+    t0 = time.perf_counter()
+    oracle.bc(g, src, threads=threads)
+    dt = time.perf_counter() - t0
+    return k * g.m / dt, threads, k, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    g, desc = workload()
+    per_step = max(2.0, 20.0 / max(args.steps, 1))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, cores, k, dt = cpu_oracle_rate(g, per_step if i >= args.warmup else 1.0)
+        if i >= args.warmup:
+            vals.append((v, k, dt))
+    v = statistics.median([x[0] for x in vals])
+    ms = 1000.0 * statistics.median([x[2] / x[1] * g.n for x in vals])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u128+f64", "data": "synthetic",
+            "config": {"workload": desc, "n": g.n, "m": g.m, "sources": g.n},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{vals[0][1]} seeded sources per step (bounded sample of the all-sources job); "
+                                       "ms_per_step extrapolated to all sources"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--plain-sources", type=int, default=1024)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_0809_1906_gb300 import native
+    native.load()
+    g, desc = workload()
+    n, m = g.n, g.m
+    # weak scaling: every rank runs the whole all-sources job, sources rotated by rank
+    src = ((np.arange(n, dtype=np.int64) + rank * (n // max(world, 1))) % n).astype(np.int32)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    h = native.Graph.from_csr(g, trust_input=True)
+    src_d = torch.from_numpy(src).cuda()
+    out_d = torch.empty(n, dtype=torch.float64, device="cuda")
+
+    def step(flags):
+        h.run(src_d, batch=BATCH, flags=flags, stream=stream)
+        h.result(out_d)
+
+    for _ in range(args.warmup):
+        step(0)
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: inputs resident in HBM, L2 flushed between steps
+    times, launches = [], 0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(0)
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+            launches += h.launch_count()
+    torch.cuda.synchronize()
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * n * m / (ms_per_step / 1000.0)
+    arcs, depth_sum = h.run_stats()
+
+    # ---- per-launch CUDA events of every kernel (same steps, BC_TIMING)
+    ktime = {}
+    for _ in range(2):
+        flush.fill_(1.0)
+        step(native.BC_TIMING)
+        for kind, name in native.KERNEL_NAMES.items():
+            cnt, tot = h.kernel_time(kind)
+            ktime[name] = (cnt, tot)
+    fwd_b, bwd_b = algorithmic_bytes(n, m, arcs, n, BATCH)
+    peak, peak_kind = peaks()
+    f_ms = ktime["forward"][1]
+    b_ms = ktime["backward"][1]
+    dom, dom_bytes, dom_ms, dom_cnt = ("backward", bwd_b, b_ms, ktime["backward"][0]) if b_ms >= f_ms else \
+        ("forward", fwd_b, f_ms, ktime["forward"][0])
+    achieved = dom_bytes / (dom_ms / 1000.0) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            with open(tr_path) as f:
+                tr = json.load(f)
+            if tr.get("kernel") == dom:
+                traffic = tr.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+    col_h = torch.from_numpy(g.col).pin_memory()
+    src_h = torch.from_numpy(src).pin_memory()
+    out_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for i in range(1 + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        he = native.Graph(n, rp_h, col_h, trust_input=True)
+        he.run(src_h, batch=BATCH, stream=stream)
+        he.result(out_h)
+        he.close()
+        dt = (time.perf_counter() - t0) * 1000.0
+        if i > 0:
+            e2e_ms.append(dt)
+    e2e_value = world * n * m / (statistics.median(e2e_ms) / 1000.0)
+    h2d = (g.row_ptr.nbytes + g.col.nbytes + src.nbytes)
+    d2h = n * 8 + 4
+
+    # ---- plain one-source-per-launch GPU Brandes on a bounded sample
+    plain_k = min(args.plain_sources, n)
+    psrc = torch.from_numpy(src[:plain_k]).cuda()
+    h.run(psrc, flags=native.BC_PLAIN, stream=stream)
+    h.result(out_d)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    h.run(psrc, flags=native.BC_PLAIN, stream=stream)
+    h.result(out_d)
+    b.record(stream)
+    b.synchronize()
+    plain_value = plain_k * m / (a.elapsed_time(b) / 1000.0)
+
+    line = None
+    if rank == 0:
+        cpu_v, cores, k, dt = cpu_oracle_rate(g, args.cpu_seconds) if world == 1 or rank == 0 else (None,) * 4
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64+f32 (BC f64)", "data": "synthetic",
+            "config": {"workload": desc, "n": n, "m": m, "sources_per_rank": n, "batch": BATCH,
+                       "parallelism": f"sources replicated per rank x{world}",
+                       "l2": "flushed (512 MB write) between timed steps",
+                       "dag_arcs_per_source": arcs / n, "depth_sum": depth_sum},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind,
+                         "traffic": traffic, "algorithmic_bytes_per_launch": dom_bytes / max(dom_cnt, 1),
+                         "avg_launch_ms": dom_ms / max(dom_cnt, 1), "launches": dom_cnt},
+            "kernels_ms": {k2: {"launches": v[0], "total_ms": v[1]} for k2, v in ktime.items()},
+            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{k} seeded sources of the same graph ({dt:.1f} s, OpenMP over sources)"},
+            "vs_plain_gpu": {"value": plain_value, "unit": UNIT, "speedup": value / plain_value,
+                             "sample": f"first {plain_k} sources, one source per launch sequence"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "ms_per_step": statistics.median(e2e_ms)},
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

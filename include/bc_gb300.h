@@ -1,0 +1,202 @@
+/*
+ * bc_gb300.h -- C ABI of the exact betweenness-centrality library for one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Problem (Kintali, "Betweenness Centrality: Algorithms and Lower Bounds",
+ * Section 1.1): an undirected graph G(V,E), vertices 0..n-1, each edge with a
+ * positive integer weight (unweighted = all 1). For a source s, d(s,v) is the
+ * shortest-path length, sigma_s(v) (lambda_sv in the paper) the number of
+ * shortest s-v paths, P_s(v) = {u : (u,v) in E, d(s,v) = d(s,u) + w(u,v)} the
+ * predecessors, and delta_s*(v) the dependency given by Theorem 1.1:
+ *     delta_s*(v) = sum_{w : v in P_s(w)} sigma_s(v)/sigma_s(w) * (1 + delta_s*(w)).
+ * The library returns BC(v) = sum_{s in S, s != v} delta_s*(v) over a source
+ * set S (all vertices by default), i.e. the sum over ORDERED pairs of the
+ * paper's definition; flag BC_HALVE divides by two (unordered pairs, as the
+ * paper does for undirected graphs at the end of Section 1.1).
+ *
+ * Arithmetic: sigma is exact uint64 (wrapping mod 2^64, with a status flag
+ * when any count reaches 2^64); distances are int32; dependencies are FP32 per
+ * (source, vertex); BC is summed in FP64 in a fixed order, so a run is
+ * deterministic. Vertices unreachable from s contribute nothing.
+ *
+ * Conventions for every call:
+ *   - Returns a status: 0 (BC_OK), a positive warning, or a negative error.
+ *     No call throws or aborts; bc_last_error() gives a message for the last
+ *     failing call on the calling thread.
+ *   - Pointer arguments marked "host or device" may be either: copies use
+ *     unified addressing (cudaMemcpyDefault).
+ *   - cuda_stream: a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). All device work of a call is ordered on it.
+ *   - The library allocates the device memory it needs (cudaMalloc) and frees
+ *     it in bc_destroy_graph. Caller buffers stay owned by the caller.
+ *   - A graph handle may be used by one thread at a time.
+ */
+#ifndef BC_GB300_H
+#define BC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define BC_OK 0
+#define BC_WARN_SIGMA_OVERFLOW 1 /* results returned; some sigma reached 2^64 */
+#define BC_ERR_ARG (-1)          /* bad argument (NULL, size, id out of range) */
+#define BC_ERR_NOT_SYMMETRIC (-2)/* CSR is not an undirected graph (missing reverse arc, self-loop, duplicate) */
+#define BC_ERR_WEIGHT (-3)       /* weight <= 0, or n * max weight >= 2^31 */
+#define BC_ERR_OOM (-4)          /* device or host allocation failed */
+#define BC_ERR_CUDA (-5)         /* a CUDA runtime call failed */
+#define BC_ERR_TIMEOUT (-6)      /* a bounded wait gave up (see bc_options.wait_limit_ms) */
+#define BC_ERR_BOUNDS (-7)       /* a device-side bounds check fired */
+#define BC_ERR_UNSUPPORTED (-8)  /* option combination not supported for this graph */
+#define BC_ERR_STATE (-9)        /* call out of order (e.g. bc_result before bc_run) */
+
+/* ---- bits of the status_flags word returned by bc_result -------------- */
+#define BC_STATUS_SIGMA_OVERFLOW 0x1u
+#define BC_STATUS_BOUNDS 0x2u
+#define BC_STATUS_LEVEL_CAP 0x4u /* internal: a batch needed more BFS levels (re-run automatically) */
+
+/* ---- bc_create_graph flags --------------------------------------------- */
+#define BC_GRAPH_TRUST_INPUT 0x1u /* skip the host-side symmetry/duplicate check */
+
+/* ---- bc_options.flags ---------------------------------------------------- */
+#define BC_HALVE 0x1u        /* divide BC by 2 (unordered pairs, Section 1.1) */
+#define BC_ACCUMULATE 0x2u   /* add to the previous run's BC instead of starting from 0 */
+#define BC_PLAIN 0x4u        /* one source per launch sequence (the unbatched GPU Brandes) */
+#define BC_TIMING 0x8u       /* record CUDA events around every kernel launch (bc_kernel_time) */
+#define BC_NO_HASH 0x10u     /* skip the per-source summary values */
+
+/*
+ * Run options. Zero-initialise and set what you need; bc_run(..., NULL, ...)
+ * uses the same defaults.
+ *   batch          sources per batch for the unweighted multi-source path:
+ *                  32, 64, 128 or 256 (0 = 256).
+ *   flags          BC_* option bits above.
+ *   chunk          arcs per work item for high-degree vertices (0 = 256).
+ *   wait_limit_ms  bound on every host-side wait for device progress
+ *                  (0 = 600000). Expiry returns BC_ERR_TIMEOUT.
+ */
+typedef struct bc_options {
+    int32_t batch;
+    uint32_t flags;
+    int32_t chunk;
+    int32_t reserved0;
+    int64_t wait_limit_ms;
+    int64_t reserved1[4];
+} bc_options;
+
+typedef struct bc_graph bc_graph;
+
+/*
+ * Copy a CSR graph to the device (Section 1.1's graph model).
+ *   n        vertex count, 0 <= n < 2^31.
+ *   row_ptr  int32[n+1] (host or device), row_ptr[0] = 0, non-decreasing.
+ *   col      int32[row_ptr[n]] (host or device): neighbours of each vertex.
+ *            Every undirected edge appears as both arcs.
+ *   weights  int32[row_ptr[n]] arc weights (host or device), NULL = unweighted.
+ *            Both arcs of an edge carry the same weight.
+ *   flags    BC_GRAPH_* bits.
+ *   out      receives the handle (NULL on failure).
+ * Errors: BC_ERR_ARG (sizes, ids), BC_ERR_NOT_SYMMETRIC (missing reverse arc,
+ * mismatched weight, self-loop, duplicate arc), BC_ERR_WEIGHT, BC_ERR_OOM,
+ * BC_ERR_CUDA. The caller's arrays are not kept.
+ */
+int bc_create_graph(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *weights,
+                    uint32_t flags, bc_graph **out);
+
+/*
+ * Betweenness over a source set: the forward pass (distances and exact path
+ * counts over P_s, Section 1.1), the backward pass (Theorem 1.1) and the sum
+ * over sources, all on the device.
+ *   sources      int32[num_sources] (host or device), NULL = all n vertices.
+ *                Ids in [0, n); repeats are allowed and counted each time.
+ *   num_sources  >= 0 (ignored when sources == NULL).
+ *   opt          NULL = defaults.
+ * Without BC_ACCUMULATE the result starts from zero. Returns when all work is
+ * enqueued on cuda_stream, except for the bounded host waits the level loop
+ * needs to learn each batch's depth. Errors: BC_ERR_ARG, BC_ERR_OOM,
+ * BC_ERR_CUDA, BC_ERR_TIMEOUT, BC_ERR_UNSUPPORTED.
+ */
+int bc_run(bc_graph *g, const int32_t *sources, int32_t num_sources, const bc_options *opt,
+           void *cuda_stream);
+
+/*
+ * Copy the result of the last bc_run.
+ *   bc            double[n] (host or device), may be NULL.
+ *   status_flags  receives BC_STATUS_* bits (may be NULL).
+ * Synchronises the run's stream. Returns BC_OK, BC_WARN_SIGMA_OVERFLOW when
+ * some path count reached 2^64 (BC is then not trustworthy), or an error
+ * (BC_ERR_STATE before any run, BC_ERR_BOUNDS, BC_ERR_CUDA).
+ */
+int bc_result(bc_graph *g, double *bc, uint32_t *status_flags);
+
+/*
+ * Per-source summary values of the last bc_run, in source-list order
+ * (length = number of sources run). Any pointer may be NULL; all are host or
+ * device. For source s:
+ *   h_sigma[i]  = sum_v (sigma_s(v) mod 2^64) * (v+1)            mod 2^64
+ *   h_dist[i]   = sum_{v reachable} (d(s,v) + 1) * (v+1)         mod 2^64
+ *   dist_sum[i] = sum_{v reachable} d(s,v)
+ *   reach[i]    = number of vertices reachable from s (s included)
+ * Errors: BC_ERR_STATE if the run used BC_NO_HASH or no run happened.
+ */
+int bc_source_hashes(bc_graph *g, uint64_t *h_sigma, uint64_t *h_dist, int64_t *dist_sum,
+                     int64_t *reach);
+
+/*
+ * Forward-pass rows for k sources (Section 3's D and Lambda rows), computed by
+ * the same kernels bc_run uses.
+ *   sources  int32[k] (host or device), 0 <= k.
+ *   sigma    uint64[k*n] (host or device): row i = sigma_{sources[i]}(.), 0 where unreachable.
+ *   dist     int32[k*n] (host or device): d(sources[i], .), -1 where unreachable.
+ * Either output may be NULL. Synchronises cuda_stream. Returns BC_OK or
+ * BC_WARN_SIGMA_OVERFLOW, or an error.
+ */
+int bc_forward_rows(bc_graph *g, const int32_t *sources, int32_t k, uint64_t *sigma, int32_t *dist,
+                    const bc_options *opt, void *cuda_stream);
+
+/*
+ * Kernel timing of the last run made with BC_TIMING: for kernel class `kind`
+ * (BC_KERNEL_*), the number of launches and their summed CUDA-event durations
+ * in milliseconds (events recorded on the run's stream around each launch).
+ * Synchronises the stream. Errors: BC_ERR_ARG, BC_ERR_STATE.
+ */
+#define BC_KERNEL_INIT 0
+#define BC_KERNEL_FORWARD 1
+#define BC_KERNEL_BACKWARD 2
+#define BC_KERNEL_HASH 3
+#define BC_KERNEL_PLAIN 4
+#define BC_KERNEL_KINDS 5
+int bc_kernel_time(bc_graph *g, int32_t kind, int64_t *launches, double *total_ms);
+
+/*
+ * Work counters of the last bc_run (synchronises its stream):
+ *   dag_arcs   sum over the run's sources s of the number of arcs (u,v) with
+ *              u in P_s(v), i.e. the size of each shortest-path DAG (Section 1.1)
+ *   depth_sum  sum over batches (one-source path: over sources) of the BFS depth
+ * Either pointer may be NULL (host pointers). Errors: BC_ERR_ARG, BC_ERR_STATE.
+ */
+int bc_run_stats(bc_graph *g, int64_t *dag_arcs, int64_t *depth_sum);
+
+/* Number of kernel launches the last bc_run issued (all kinds). */
+int64_t bc_launch_count(const bc_graph *g);
+
+/* Vertex and undirected edge counts of a graph handle. */
+int bc_graph_size(const bc_graph *g, int32_t *n, int64_t *m, int32_t *weighted);
+
+/* Free the handle and its device memory. NULL is ignored. */
+void bc_destroy_graph(bc_graph *g);
+
+/* Static text for a status code. */
+const char *bc_status_string(int status);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *bc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BC_GB300_H */

@@ -1,0 +1,646 @@
+// bc_api.cu -- the C ABI (include/bc_gb300.h): graph upload and checks,
+// work-item plan, device memory plan, and the batch scheduler that drives the
+// level loop of the multi-source path.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "bc_internal.cuh"
+#include "plain.cuh"
+#include "sched.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? BC_ERR_OOM : BC_ERR_CUDA,           \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    } while (0)
+
+template <class T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    cudaError_t ensure(size_t count) {
+        if (count <= n && p) return cudaSuccess;
+        release();
+        size_t c = count ? count : 1;
+        cudaError_t e = cudaMalloc((void **)&p, c * sizeof(T));
+        if (e == cudaSuccess) n = c;
+        return e;
+    }
+};
+
+// Copy `count` elements from a host-or-device pointer into a host vector.
+template <class T>
+cudaError_t fetch(std::vector<T> &dst, const T *src, size_t count) {
+    dst.resize(count);
+    if (count == 0) return cudaSuccess;
+    return cudaMemcpy(dst.data(), src, count * sizeof(T), cudaMemcpyDefault);
+}
+
+}  // namespace
+
+struct bc_graph {
+    int32_t n = 0;
+    int64_t narcs = 0;
+    bool weighted = false;
+    std::vector<int32_t> h_row_ptr;  // host copy (work-item plan)
+    DevBuf<int32_t> row_ptr, col, w;
+
+    // work items for the current chunk size
+    int32_t chunk = 0, nitems = 0, nslots = 0;
+    DevBuf<int32_t> item_v, item_beg, item_end, item_slot, slot_first, slot_nch;
+
+    // multi-source batch state for (W, Lcap)
+    int32_t W = 0, Lcap = 0;
+    DevBuf<uint64_t> sigma, part;
+    DevBuf<float> cval;
+    DevBuf<uint32_t> F, ufr, V, pmask, cnt;
+
+    // results
+    DevBuf<double> bc;
+    DevBuf<int32_t> sources;
+    DevBuf<uint64_t> h_sigma, h_dist;
+    DevBuf<int64_t> dist_sum, reach;
+    int32_t last_nsrc = 0;
+    bool has_run = false, has_hash = false;
+    cudaStream_t last_stream = nullptr;
+
+    bcgb::DevCtl *ctl = nullptr;
+    bcgb::HostCtl *hctl = nullptr;    // host view
+    bcgb::HostCtl *hctl_d = nullptr;  // device view
+    uint32_t seq = 0;
+
+    // timing
+    struct Ev {
+        cudaEvent_t a, b;
+        int kind;
+    };
+    std::vector<Ev> evpool;
+    size_t evused = 0;
+    bool timing = false;
+    int64_t launches = 0;
+
+    bcgb::PlainState plain;
+};
+
+namespace {
+
+void free_graph(bc_graph *g) {
+    for (auto *b : {&g->row_ptr, &g->col, &g->w, &g->item_v, &g->item_beg, &g->item_end, &g->item_slot,
+                    &g->slot_first, &g->slot_nch, &g->sources})
+        b->release();
+    g->sigma.release();
+    g->part.release();
+    g->cval.release();
+    for (auto *b : {&g->F, &g->ufr, &g->V, &g->pmask, &g->cnt}) b->release();
+    g->bc.release();
+    g->h_sigma.release();
+    g->h_dist.release();
+    g->dist_sum.release();
+    g->reach.release();
+    if (g->ctl) cudaFree(g->ctl);
+    if (g->hctl) cudaFreeHost(g->hctl);
+    for (auto &e : g->evpool) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    bcgb::plain_free(g->plain);
+    delete g;
+}
+
+// Host check of the paper's graph model: every arc has its reverse with the
+// same weight, no self-loops, no duplicate arcs, positive weights.
+int check_graph(int32_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &col,
+                const std::vector<int32_t> *w) {
+    if (rp[0] != 0) return fail(BC_ERR_ARG, "row_ptr[0] != 0");
+    for (int32_t v = 0; v < n; ++v)
+        if (rp[v + 1] < rp[v]) return fail(BC_ERR_ARG, "row_ptr not non-decreasing");
+    const int64_t m = rp[n];
+    int64_t maxw = 1;
+    for (int64_t e = 0; e < m; ++e) {
+        if (col[e] < 0 || col[e] >= n) return fail(BC_ERR_ARG, "col id out of range");
+        if (w) {
+            if ((*w)[e] <= 0) return fail(BC_ERR_WEIGHT, "non-positive weight");
+            maxw = std::max<int64_t>(maxw, (*w)[e]);
+        }
+    }
+    if (w && (int64_t)n * maxw >= (int64_t(1) << 31))
+        return fail(BC_ERR_WEIGHT, "n * max weight >= 2^31 (distances would not fit int32)");
+    // sorted copy of every row (with weights) for reverse-arc lookups
+    std::vector<std::pair<int32_t, int32_t>> arcs(m);
+    for (int32_t v = 0; v < n; ++v) {
+        for (int64_t e = rp[v]; e < rp[v + 1]; ++e) arcs[e] = {col[e], w ? (*w)[e] : 1};
+        std::sort(arcs.begin() + rp[v], arcs.begin() + rp[v + 1]);
+        for (int64_t e = rp[v]; e < rp[v + 1]; ++e) {
+            if (arcs[e].first == v) return fail(BC_ERR_NOT_SYMMETRIC, "self-loop at vertex " + std::to_string(v));
+            if (e > rp[v] && arcs[e].first == arcs[e - 1].first)
+                return fail(BC_ERR_NOT_SYMMETRIC, "duplicate arc at vertex " + std::to_string(v));
+        }
+    }
+    for (int32_t v = 0; v < n; ++v) {
+        for (int64_t e = rp[v]; e < rp[v + 1]; ++e) {
+            const int32_t u = arcs[e].first;
+            auto lo = arcs.begin() + rp[u], hi = arcs.begin() + rp[u + 1];
+            auto it = std::lower_bound(lo, hi, std::make_pair(v, INT32_MIN));
+            if (it == hi || it->first != v) return fail(BC_ERR_NOT_SYMMETRIC, "missing reverse arc");
+            if (it->second != arcs[e].second) return fail(BC_ERR_NOT_SYMMETRIC, "asymmetric weight");
+        }
+    }
+    return BC_OK;
+}
+
+// Work items: one per vertex, except vertices with more than `chunk` arcs,
+// which are split into chunks that combine through partial slots. Heavy
+// chunks come first, then vertices by descending degree.
+int build_items(bc_graph *g, int32_t chunk) {
+    if (g->chunk == chunk && g->item_v.p) return BC_OK;
+    const int32_t n = g->n;
+    const auto &rp = g->h_row_ptr;
+    std::vector<int32_t> iv, ib, ie, is, sf, sn;
+    std::vector<int32_t> light;
+    for (int32_t v = 0; v < n; ++v) {
+        const int64_t deg = rp[v + 1] - rp[v];
+        const int64_t nch = std::max<int64_t>(1, (deg + chunk - 1) / chunk);
+        if (nch == 1) {
+            light.push_back(v);
+            continue;
+        }
+        const int32_t first = (int32_t)sf.size();
+        for (int64_t c = 0; c < nch; ++c) {
+            iv.push_back(v);
+            ib.push_back((int32_t)(rp[v] + c * chunk));
+            ie.push_back((int32_t)std::min<int64_t>(rp[v + 1], rp[v] + (c + 1) * chunk));
+            is.push_back((int32_t)sf.size());
+            sf.push_back(first);
+            sn.push_back((int32_t)nch);
+        }
+    }
+    std::stable_sort(light.begin(), light.end(),
+                     [&](int32_t a, int32_t b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
+    for (int32_t v : light) {
+        iv.push_back(v);
+        ib.push_back(rp[v]);
+        ie.push_back(rp[v + 1]);
+        is.push_back(-1);
+    }
+    g->nitems = (int32_t)iv.size();
+    g->nslots = (int32_t)sf.size();
+    for (auto pr : {std::make_pair(&g->item_v, &iv), std::make_pair(&g->item_beg, &ib),
+                    std::make_pair(&g->item_end, &ie), std::make_pair(&g->item_slot, &is),
+                    std::make_pair(&g->slot_first, &sf), std::make_pair(&g->slot_nch, &sn)}) {
+        CK(pr.first->ensure(pr.second->size()));
+        if (!pr.second->empty())
+            CK(cudaMemcpy(pr.first->p, pr.second->data(), pr.second->size() * sizeof(int32_t),
+                          cudaMemcpyHostToDevice));
+    }
+    g->chunk = chunk;
+    // partial slots depend on the plan: force the state to be re-sized
+    g->W = 0;
+    return BC_OK;
+}
+
+int ensure_state(bc_graph *g, int W, int Lcap) {
+    if (g->W == W && g->Lcap >= Lcap && g->sigma.p) return BC_OK;
+    const size_t n = (size_t)std::max(g->n, 1);
+    const size_t B = 32 * (size_t)W;
+    const size_t nw32 = (n + 31) / 32;
+    CK(g->sigma.ensure(n * B));
+    CK(g->cval.ensure(n * B));
+    CK(g->F.ensure((size_t)Lcap * n * W));
+    CK(g->ufr.ensure((size_t)Lcap * nw32));
+    CK(g->V.ensure(2 * n * W));
+    CK(g->part.ensure((size_t)std::max(g->nslots, 1) * B));
+    CK(g->pmask.ensure((size_t)std::max(g->nslots, 1) * W));
+    CK(g->cnt.ensure((size_t)std::max(g->nslots, 1)));
+    CK(cudaMemset(g->cnt.p, 0, g->cnt.n * sizeof(uint32_t)));
+    g->W = W;
+    g->Lcap = Lcap;
+    return BC_OK;
+}
+
+size_t timer_begin(bc_graph *g, cudaStream_t st, int kind) {
+    g->launches++;
+    if (!g->timing) return SIZE_MAX;
+    if (g->evused == g->evpool.size()) {
+        bc_graph::Ev e{};
+        cudaEventCreate(&e.a);
+        cudaEventCreate(&e.b);
+        g->evpool.push_back(e);
+    }
+    const size_t idx = g->evused++;
+    g->evpool[idx].kind = kind;
+    cudaEventRecord(g->evpool[idx].a, st);
+    return idx;
+}
+
+void timer_end(bc_graph *g, cudaStream_t st, size_t idx) {
+    if (idx != SIZE_MAX) cudaEventRecord(g->evpool[idx].b, st);
+}
+
+// Scoped launch accounting: counts the launch and, with BC_TIMING, brackets
+// it with CUDA events on the launching stream.
+struct Timer {
+    bc_graph *g;
+    cudaStream_t st;
+    size_t idx;
+    Timer(bc_graph *g_, cudaStream_t s, int k) : g(g_), st(s), idx(timer_begin(g_, s, k)) {}
+    ~Timer() { timer_end(g, st, idx); }
+    Timer(const Timer &) = delete;
+    Timer &operator=(const Timer &) = delete;
+};
+
+size_t hook_begin(void *ctx, int kind) {
+    auto *c = static_cast<std::pair<bc_graph *, cudaStream_t> *>(ctx);
+    return timer_begin(c->first, c->second, kind);
+}
+void hook_end(void *ctx, size_t idx) {
+    auto *c = static_cast<std::pair<bc_graph *, cudaStream_t> *>(ctx);
+    timer_end(c->first, c->second, idx);
+}
+
+bcgb::MsParams make_params(bc_graph *g) {
+    bcgb::MsParams p{};
+    p.n = g->n;
+    p.nitems = g->nitems;
+    p.nw32 = (std::max(g->n, 1) + 31) / 32;
+    p.Lcap = g->Lcap;
+    p.row_ptr = g->row_ptr.p;
+    p.col = g->col.p;
+    p.item_v = g->item_v.p;
+    p.item_beg = g->item_beg.p;
+    p.item_end = g->item_end.p;
+    p.item_slot = g->item_slot.p;
+    p.slot_first = g->slot_first.p;
+    p.slot_nch = g->slot_nch.p;
+    p.sigma = g->sigma.p;
+    p.cval = g->cval.p;
+    p.F = g->F.p;
+    p.ufr = g->ufr.p;
+    p.V = g->V.p;
+    p.part = g->part.p;
+    p.pmask = g->pmask.p;
+    p.cnt = g->cnt.p;
+    p.bc = g->bc.p;
+    p.ctl = g->ctl;
+    p.hctl = g->hctl_d;
+    return p;
+}
+
+int resolve_batch(const bc_options *opt, int *W) {
+    int b = (opt && opt->batch) ? opt->batch : 256;
+    if (b % 32 != 0 || !bcgb::ms_supported_width(b / 32)) return fail(BC_ERR_ARG, "batch must be 32, 64, 128 or 256");
+    *W = b / 32;
+    return BC_OK;
+}
+
+// Upload (or copy) a source list; returns its length.
+int stage_sources(bc_graph *g, const int32_t *sources, int32_t num, int32_t *count) {
+    std::vector<int32_t> hs;
+    if (!sources) {
+        hs.resize(g->n);
+        for (int32_t i = 0; i < g->n; ++i) hs[i] = i;
+    } else {
+        if (num < 0) return fail(BC_ERR_ARG, "num_sources < 0");
+        CK(fetch(hs, sources, (size_t)num));
+        for (int32_t s : hs)
+            if (s < 0 || s >= g->n) return fail(BC_ERR_ARG, "source id out of range");
+    }
+    CK(g->sources.ensure(hs.size()));
+    if (!hs.empty()) CK(cudaMemcpy(g->sources.p, hs.data(), hs.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    *count = (int32_t)hs.size();
+    return BC_OK;
+}
+
+// The multi-source driver shared by bc_run and bc_forward_rows.
+int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStream_t st, bool backward,
+                bool hash, uint64_t *rows_sig, int32_t *rows_dist) {
+    const int64_t wait_ms = (opt && opt->wait_limit_ms > 0) ? opt->wait_limit_ms : 600000;
+    const int32_t chunk = (opt && opt->chunk > 0) ? opt->chunk : 256;
+    int r = build_items(g, chunk);
+    if (r) return r;
+    r = ensure_state(g, W, std::max(g->Lcap, 32));
+    if (r) return r;
+    const int B = 32 * W;
+    for (int32_t b0 = 0; b0 < nsrc;) {
+        const int32_t nb = std::min<int32_t>(B, nsrc - b0);
+        bcgb::MsParams p = make_params(g);
+        p.nb = nb;
+        p.seq = ++g->seq;
+        p.sources = g->sources.p + b0;
+        if (hash) {
+            p.h_sigma = g->h_sigma.p + b0;
+            p.h_dist = g->h_dist.p + b0;
+            p.dist_sum = g->dist_sum.p + b0;
+            p.reach = g->reach.p + b0;
+        }
+        {
+            Timer t(g, st, BC_KERNEL_INIT);
+            bcgb::ms_launch_init(W, p, st);
+        }
+        int L = 0;
+        auto launch = [&](int level) {
+            Timer t(g, st, BC_KERNEL_FORWARD);
+            bcgb::ms_launch_forward(W, p, level, st);
+        };
+        r = bcgb::drive_forward(g->hctl, p.seq, g->Lcap - 2, launch, wait_ms, st, &g_err, &L);
+        if (r) return r;
+        if (L < 0) {  // deeper than the level capacity: grow it and redo this batch
+            CK(cudaStreamSynchronize(st));
+            r = ensure_state(g, W, g->Lcap * 2);
+            if (r) return r;
+            continue;
+        }
+        if (backward) {
+            for (int l = L; l >= 1; --l) {
+                Timer t(g, st, BC_KERNEL_BACKWARD);
+                bcgb::ms_launch_backward(W, p, l, st);
+            }
+        }
+        if (hash) {
+            Timer t(g, st, BC_KERNEL_HASH);
+            bcgb::ms_launch_hash(W, p, L, st);
+        }
+        if (rows_sig || rows_dist) {
+            Timer t(g, st, BC_KERNEL_HASH);
+            bcgb::ms_launch_rows(W, p, L, rows_sig ? rows_sig + (size_t)b0 * g->n : nullptr,
+                                 rows_dist ? rows_dist + (size_t)b0 * g->n : nullptr, st);
+        }
+        CK(cudaGetLastError());
+        b0 += nb;
+    }
+    return BC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bc_create_graph(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *weights,
+                    uint32_t flags, bc_graph **out) {
+    g_err.clear();
+    if (!out) return fail(BC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 0) return fail(BC_ERR_ARG, "n < 0");
+    if (!row_ptr) return fail(BC_ERR_ARG, "row_ptr is NULL");
+    std::vector<int32_t> rp, cl, ww;
+    CK(fetch(rp, row_ptr, (size_t)n + 1));
+    const int64_t m2 = rp[n];
+    if (m2 < 0) return fail(BC_ERR_ARG, "row_ptr[n] < 0");
+    if (m2 > 0 && !col) return fail(BC_ERR_ARG, "col is NULL");
+    CK(fetch(cl, col, (size_t)m2));
+    if (weights) CK(fetch(ww, weights, (size_t)m2));
+    if (!(flags & BC_GRAPH_TRUST_INPUT)) {
+        int r = check_graph(n, rp, cl, weights ? &ww : nullptr);
+        if (r) return r;
+    }
+    bc_graph *g = new (std::nothrow) bc_graph();
+    if (!g) return fail(BC_ERR_OOM, "host allocation failed");
+    g->n = n;
+    g->narcs = m2;
+    g->weighted = weights != nullptr;
+    g->h_row_ptr = rp;
+    auto up = [&](DevBuf<int32_t> &d, const std::vector<int32_t> &h) -> int {
+        CK(d.ensure(h.size()));
+        if (!h.empty()) CK(cudaMemcpy(d.p, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        return BC_OK;
+    };
+    int r = up(g->row_ptr, rp);
+    if (!r) r = up(g->col, cl);
+    if (!r && weights) r = up(g->w, ww);
+    if (!r) {
+        cudaError_t e = g->bc.ensure((size_t)std::max(n, 1));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&g->ctl, sizeof(bcgb::DevCtl));
+        if (e == cudaSuccess) e = cudaMemset(g->ctl, 0, sizeof(bcgb::DevCtl));
+        if (e == cudaSuccess) e = cudaMemset(g->bc.p, 0, g->bc.n * sizeof(double));
+        if (e == cudaSuccess)
+            e = cudaHostAlloc((void **)&g->hctl, sizeof(bcgb::HostCtl), cudaHostAllocMapped | cudaHostAllocPortable);
+        if (e == cudaSuccess) {
+            std::memset(g->hctl, 0, sizeof(bcgb::HostCtl));
+            e = cudaHostGetDevicePointer((void **)&g->hctl_d, g->hctl, 0);
+        }
+        if (e != cudaSuccess)
+            r = fail(e == cudaErrorMemoryAllocation ? BC_ERR_OOM : BC_ERR_CUDA,
+                     std::string("graph allocation: ") + cudaGetErrorString(e));
+    }
+    if (r) {
+        free_graph(g);
+        return r;
+    }
+    *out = g;
+    return BC_OK;
+}
+
+int bc_run(bc_graph *g, const int32_t *sources, int32_t num_sources, const bc_options *opt, void *cuda_stream) {
+    g_err.clear();
+    if (!g) return fail(BC_ERR_ARG, "graph is NULL");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const uint32_t flags = opt ? opt->flags : 0u;
+    int W = 0;
+    int r = resolve_batch(opt, &W);
+    if (r) return r;
+    if (g->weighted && !(flags & BC_PLAIN)) return fail(BC_ERR_UNSUPPORTED, "weighted graphs need the delta-stepping path");
+    int32_t nsrc = 0;
+    r = stage_sources(g, sources, num_sources, &nsrc);
+    if (r) return r;
+    g->timing = (flags & BC_TIMING) != 0;
+    g->evused = 0;
+    g->launches = 0;
+    g->has_run = false;
+    const bool hash = !(flags & BC_NO_HASH);
+    if (!(flags & BC_ACCUMULATE)) CK(cudaMemsetAsync(g->bc.p, 0, g->bc.n * sizeof(double), st));
+    CK(cudaMemsetAsync(&g->ctl->status, 0, sizeof(uint32_t), st));
+    CK(cudaMemsetAsync(&g->ctl->dag_arcs, 0, 2 * sizeof(unsigned long long), st));
+    if (hash) {
+        CK(g->h_sigma.ensure(nsrc));
+        CK(g->h_dist.ensure(nsrc));
+        CK(g->dist_sum.ensure(nsrc));
+        CK(g->reach.ensure(nsrc));
+        if (nsrc) {
+            CK(cudaMemsetAsync(g->h_sigma.p, 0, nsrc * sizeof(uint64_t), st));
+            CK(cudaMemsetAsync(g->h_dist.p, 0, nsrc * sizeof(uint64_t), st));
+            CK(cudaMemsetAsync(g->dist_sum.p, 0, nsrc * sizeof(int64_t), st));
+            CK(cudaMemsetAsync(g->reach.p, 0, nsrc * sizeof(int64_t), st));
+        }
+    }
+    if (flags & BC_PLAIN) {
+        std::pair<bc_graph *, cudaStream_t> ctx{g, st};
+        bcgb::LaunchHook hook{&ctx, hook_begin, hook_end};
+        const int64_t wait_ms = (opt && opt->wait_limit_ms > 0) ? opt->wait_limit_ms : 600000;
+        r = bcgb::plain_run(g->plain, g->n, g->row_ptr.p, g->col.p, g->sources.p, nsrc, g->bc.p,
+                            hash ? g->h_sigma.p : nullptr, hash ? g->h_dist.p : nullptr,
+                            hash ? g->dist_sum.p : nullptr, hash ? g->reach.p : nullptr, g->ctl, g->hctl,
+                            g->hctl_d, &g->seq, st, hook, wait_ms, &g_err);
+        if (r) return r;
+    } else {
+        r = run_batches(g, nsrc, W, opt, st, true, hash, nullptr, nullptr);
+        if (r) return r;
+    }
+    if (flags & BC_HALVE) {
+        Timer t(g, st, BC_KERNEL_HASH);
+        bcgb::launch_scale(g->bc.p, g->n, 0.5, st);
+    }
+    CK(cudaGetLastError());
+    g->last_nsrc = nsrc;
+    g->has_run = true;
+    g->has_hash = hash;
+    g->last_stream = st;
+    return BC_OK;
+}
+
+int bc_result(bc_graph *g, double *bc, uint32_t *status_flags) {
+    g_err.clear();
+    if (!g) return fail(BC_ERR_ARG, "graph is NULL");
+    if (!g->has_run) return fail(BC_ERR_STATE, "no completed bc_run");
+    uint32_t status = 0;
+    if (bc && g->n) CK(cudaMemcpyAsync(bc, g->bc.p, (size_t)g->n * sizeof(double), cudaMemcpyDefault, g->last_stream));
+    CK(cudaMemcpyAsync(&status, &g->ctl->status, sizeof(uint32_t), cudaMemcpyDefault, g->last_stream));
+    CK(cudaStreamSynchronize(g->last_stream));
+    if (status_flags) *status_flags = status;
+    if (status & BC_STATUS_BOUNDS) return fail(BC_ERR_BOUNDS, "device bounds check fired");
+    if (status & BC_STATUS_SIGMA_OVERFLOW) return BC_WARN_SIGMA_OVERFLOW;
+    return BC_OK;
+}
+
+int bc_source_hashes(bc_graph *g, uint64_t *h_sigma, uint64_t *h_dist, int64_t *dist_sum, int64_t *reach) {
+    g_err.clear();
+    if (!g) return fail(BC_ERR_ARG, "graph is NULL");
+    if (!g->has_run || !g->has_hash) return fail(BC_ERR_STATE, "no bc_run with per-source summaries");
+    const size_t k = (size_t)g->last_nsrc;
+    cudaStream_t st = g->last_stream;
+    if (k) {
+        if (h_sigma) CK(cudaMemcpyAsync(h_sigma, g->h_sigma.p, k * 8, cudaMemcpyDefault, st));
+        if (h_dist) CK(cudaMemcpyAsync(h_dist, g->h_dist.p, k * 8, cudaMemcpyDefault, st));
+        if (dist_sum) CK(cudaMemcpyAsync(dist_sum, g->dist_sum.p, k * 8, cudaMemcpyDefault, st));
+        if (reach) CK(cudaMemcpyAsync(reach, g->reach.p, k * 8, cudaMemcpyDefault, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    return BC_OK;
+}
+
+int bc_forward_rows(bc_graph *g, const int32_t *sources, int32_t k, uint64_t *sigma, int32_t *dist,
+                    const bc_options *opt, void *cuda_stream) {
+    g_err.clear();
+    if (!g) return fail(BC_ERR_ARG, "graph is NULL");
+    if (k < 0 || (k > 0 && !sources)) return fail(BC_ERR_ARG, "bad source list");
+    if (g->weighted) return fail(BC_ERR_UNSUPPORTED, "weighted graphs need the delta-stepping path");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int W = 0;
+    int r = resolve_batch(opt, &W);
+    if (r) return r;
+    int32_t nsrc = 0;
+    r = stage_sources(g, sources, k, &nsrc);
+    if (r) return r;
+    if (nsrc == 0) return BC_OK;
+    const size_t cells = (size_t)nsrc * g->n;
+    DevBuf<uint64_t> ds;
+    DevBuf<int32_t> dd;
+    if (sigma) CK(ds.ensure(cells));
+    if (dist) CK(dd.ensure(cells));
+    CK(cudaMemsetAsync(&g->ctl->status, 0, sizeof(uint32_t), st));
+    g->timing = false;
+    r = run_batches(g, nsrc, W, opt, st, false, false, sigma ? ds.p : nullptr, dist ? dd.p : nullptr);
+    uint32_t status = 0;
+    if (!r) {
+        cudaError_t e = cudaSuccess;
+        if (sigma) e = cudaMemcpyAsync(sigma, ds.p, cells * 8, cudaMemcpyDefault, st);
+        if (e == cudaSuccess && dist) e = cudaMemcpyAsync(dist, dd.p, cells * 4, cudaMemcpyDefault, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&status, &g->ctl->status, 4, cudaMemcpyDefault, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) r = fail(BC_ERR_CUDA, std::string("forward rows: ") + cudaGetErrorString(e));
+    }
+    cudaStreamSynchronize(st);
+    ds.release();
+    dd.release();
+    if (r) return r;
+    return (status & BC_STATUS_SIGMA_OVERFLOW) ? BC_WARN_SIGMA_OVERFLOW : BC_OK;
+}
+
+int bc_kernel_time(bc_graph *g, int32_t kind, int64_t *launches, double *total_ms) {
+    g_err.clear();
+    if (!g || kind < 0 || kind >= BC_KERNEL_KINDS) return fail(BC_ERR_ARG, "bad graph or kernel kind");
+    if (!g->has_run) return fail(BC_ERR_STATE, "no completed bc_run");
+    CK(cudaStreamSynchronize(g->last_stream));
+    int64_t cnt = 0;
+    double tot = 0.0;
+    for (size_t i = 0; i < g->evused; ++i) {
+        if (g->evpool[i].kind != kind) continue;
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, g->evpool[i].a, g->evpool[i].b));
+        tot += ms;
+        ++cnt;
+    }
+    if (launches) *launches = cnt;
+    if (total_ms) *total_ms = tot;
+    return BC_OK;
+}
+
+int64_t bc_launch_count(const bc_graph *g) { return g ? g->launches : 0; }
+
+int bc_run_stats(bc_graph *g, int64_t *dag_arcs, int64_t *depth_sum) {
+    g_err.clear();
+    if (!g) return fail(BC_ERR_ARG, "graph is NULL");
+    if (!g->has_run) return fail(BC_ERR_STATE, "no completed bc_run");
+    unsigned long long v[2] = {0, 0};
+    CK(cudaMemcpyAsync(v, &g->ctl->dag_arcs, sizeof(v), cudaMemcpyDeviceToHost, g->last_stream));
+    CK(cudaStreamSynchronize(g->last_stream));
+    if (dag_arcs) *dag_arcs = (int64_t)v[0];
+    if (depth_sum) *depth_sum = (int64_t)v[1];
+    return BC_OK;
+}
+
+int bc_graph_size(const bc_graph *g, int32_t *n, int64_t *m, int32_t *weighted) {
+    if (!g) return fail(BC_ERR_ARG, "graph is NULL");
+    if (n) *n = g->n;
+    if (m) *m = g->narcs / 2;
+    if (weighted) *weighted = g->weighted ? 1 : 0;
+    return BC_OK;
+}
+
+void bc_destroy_graph(bc_graph *g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    free_graph(g);
+}
+
+const char *bc_status_string(int status) {
+    switch (status) {
+        case BC_OK: return "ok";
+        case BC_WARN_SIGMA_OVERFLOW: return "warning: a shortest-path count reached 2^64 (sigma wrapped)";
+        case BC_ERR_ARG: return "invalid argument";
+        case BC_ERR_NOT_SYMMETRIC: return "graph is not undirected (missing reverse arc, self-loop or duplicate)";
+        case BC_ERR_WEIGHT: return "invalid weight";
+        case BC_ERR_OOM: return "out of memory";
+        case BC_ERR_CUDA: return "CUDA error";
+        case BC_ERR_TIMEOUT: return "timed out waiting for the device";
+        case BC_ERR_BOUNDS: return "device bounds check failed";
+        case BC_ERR_UNSUPPORTED: return "unsupported option for this graph";
+        case BC_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+const char *bc_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// bc_internal.cuh -- structures shared by the library's translation units.
+//
+// Layout of the multi-source state in HBM (B = 32*W sources per batch, n
+// vertices; every per-vertex row is contiguous so a warp reads a neighbour's
+// row in one coalesced access):
+//   sigma  uint64 [n][B]        exact path counts sigma_s(v)        (Section 1.1)
+//   cval   float  [n][B]        c_s(v) = (1 + delta_s*(v)) / sigma_s(v)
+//   F      uint32 [Lcap][n][W]  frontier bit of source b at level l (d(s_b, v) = l)
+//   ufr    uint32 [Lcap][n/32]  bit v set iff F[l][v] has any bit (union frontier)
+//   V      uint32 [2][n][W]     visited bits through level l-1 / l (ping-pong)
+//   part   uint64 [slots][B]    partial sums of high-degree vertices split in chunks
+//   pmask  uint32 [slots][W]    partial next-frontier words of those chunks
+//   cnt    uint32 [slots]       arrival counters (indexed by a vertex's first slot)
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/bc_gb300.h"
+
+namespace bcgb {
+
+// Device-side control block of a graph (device memory).
+struct DevCtl {
+    uint32_t status;       // BC_STATUS_* bits, sticky for one bc_run
+    uint32_t fwd_done;     // 1 once the running batch's forward pass ended
+    int32_t nlevels;       // deepest non-empty level of the running batch
+    uint32_t nonempty;     // OR over blocks: next frontier not empty
+    uint32_t blocks_done;  // arrival counter for last-block detection
+    uint32_t seq;          // batch sequence number
+    uint32_t pad[2];
+    unsigned long long dag_arcs;  // sum over the run's sources of |{(u,v): u in P_s(v)}|
+    unsigned long long depth_sum; // sum over batches (or sources) of the BFS depth
+};
+
+// Host-mapped mirror the host polls while the level loop runs (pinned,
+// written by the device with system-scope fences).
+struct HostCtl {
+    uint32_t done_seq;      // == batch seq once its forward pass ended
+    int32_t nlevels;        // its depth L, or -1 when the level capacity was hit
+    uint32_t progress_seq;  // batch seq of the last completed forward level
+    int32_t progress;       // number of forward levels completed
+    uint32_t pad[4];
+};
+
+struct MsParams {
+    int32_t n;
+    int32_t nitems;
+    int32_t nw32;  // words of one union-frontier bitmap
+    int32_t Lcap;  // level slots in F / ufr
+    int32_t nb;    // sources in this batch (<= B)
+    uint32_t seq;
+    const int32_t *row_ptr;
+    const int32_t *col;
+    const int32_t *item_v;
+    const int32_t *item_beg;
+    const int32_t *item_end;
+    const int32_t *item_slot;   // -1: whole vertex; else partial slot of a chunk
+    const int32_t *slot_first;  // first slot of the chunk's vertex
+    const int32_t *slot_nch;    // number of chunks of that vertex
+    const int32_t *sources;     // this batch's source ids [nb]
+    uint64_t *sigma;
+    float *cval;
+    uint32_t *F;
+    uint32_t *ufr;
+    uint32_t *V;
+    uint64_t *part;
+    uint32_t *pmask;
+    uint32_t *cnt;
+    double *bc;
+    uint64_t *h_sigma;  // per-source summaries, indexed from this batch's first source
+    uint64_t *h_dist;
+    int64_t *dist_sum;
+    int64_t *reach;
+    DevCtl *ctl;
+    HostCtl *hctl;  // device pointer of the host-mapped block
+};
+
+// Launchers (msbfs.cu). W = words per vertex row (B = 32 W).
+bool ms_supported_width(int W);
+void ms_launch_init(int W, const MsParams &p, cudaStream_t st);
+void ms_launch_forward(int W, const MsParams &p, int level, cudaStream_t st);
+void ms_launch_backward(int W, const MsParams &p, int level, cudaStream_t st);
+void ms_launch_hash(int W, const MsParams &p, int nlevels, cudaStream_t st);
+void ms_launch_rows(int W, const MsParams &p, int nlevels, uint64_t *sig_out, int32_t *dist_out,
+                    cudaStream_t st);
+void launch_scale(double *x, int32_t n, double f, cudaStream_t st);
+
+}  // namespace bcgb

@@ -1,0 +1,534 @@
+// msbfs.cu -- batched multi-source Brandes for unweighted graphs.
+//
+// One batch runs B = 32*W sources in lockstep, level by level (Section 4's
+// "nodes are visited level by level", applied to many sources at once):
+//
+//   forward, level l -> l+1 (pull):  for every vertex v still unvisited by
+//     some source, sigma_s(v) = sum over neighbours u with d(s,u) = l of
+//     sigma_s(u), i.e. the sum over P_s(v) of Section 1.1; v joins frontier
+//     l+1 for every source whose sum is non-zero.
+//   backward, level l (pull over successors, Theorem 1.1): with
+//     c_s(w) = (1 + delta_s*(w)) / sigma_s(w) stored for level l+1,
+//     delta_s*(v) = sigma_s(v) * sum_{w adjacent, d(s,w) = l+1} c_s(w),
+//     which is Lemma 3.5's ((D_l + Delta_l) div Lambda) . A masked to level
+//     l-1 and multiplied by Lambda, one row per source.
+//   BC(v) += sum over the batch of delta_s*(v) (FP64, fixed order), fused
+//     into the backward step; the source itself (level 0) is never summed.
+//
+// Thread mapping: one warp per work item (a vertex, or a chunk of a
+// high-degree vertex's arcs). Lanes first probe 32 arcs at once against the
+// union-frontier bitmap (one bit per vertex, cache resident) and the
+// neighbour's frontier words; then, for each neighbour that contributes, the
+// warp switches to lanes-over-sources and reads the neighbour's sigma (or c)
+// row with coalesced 256-byte accesses. Chunks of one vertex combine through
+// partial buffers: the last chunk to arrive (atomic counter) sums them in
+// chunk order, so every result is deterministic and no wait is needed.
+#include <cuda_runtime.h>
+
+#include "bc_internal.cuh"
+
+namespace bcgb {
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kWarps = kBlock / 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t valid_word(int nb, int j) {
+    const int lo = 32 * j;
+    if (nb >= lo + 32) return 0xffffffffu;
+    if (nb <= lo) return 0u;
+    return (1u << (nb - lo)) - 1u;
+}
+
+template <int W>
+__device__ __forceinline__ void load_row(const uint32_t *__restrict__ p, uint32_t (&w)[W]) {
+    if constexpr (W % 4 == 0) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+        for (int i = 0; i < W / 4; ++i) {
+            const uint4 t = __ldg(q + i);
+            w[4 * i] = t.x;
+            w[4 * i + 1] = t.y;
+            w[4 * i + 2] = t.z;
+            w[4 * i + 3] = t.w;
+        }
+    } else if constexpr (W % 2 == 0) {
+        const uint2 *q = reinterpret_cast<const uint2 *>(p);
+#pragma unroll
+        for (int i = 0; i < W / 2; ++i) {
+            const uint2 t = __ldg(q + i);
+            w[2 * i] = t.x;
+            w[2 * i + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; ++i) w[i] = __ldg(p + i);
+    }
+}
+
+// Write sigma and frontier words of a vertex whose level-(l+1) sums are final.
+template <int W>
+__device__ __forceinline__ bool store_next(const MsParams &p, int v, const uint64_t (&acc)[W],
+                                           const uint32_t (&nf)[W], uint32_t *Fn, uint32_t *ufn,
+                                           int lane) {
+    constexpr int B = 32 * W;
+    uint32_t any = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        any |= nf[j];
+        if (lane == j) Fn[(size_t)v * W + j] = nf[j];
+        if ((nf[j] >> lane) & 1u) p.sigma[(size_t)v * B + 32 * j + lane] = acc[j];
+    }
+    if (any != 0 && lane == 0) atomicOr(ufn + (v >> 5), 1u << (v & 31));
+    return any != 0;
+}
+
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
+    constexpr int B = 32 * W;
+    const size_t nW = (size_t)p.n * W;
+    const size_t stride = (size_t)gridDim.x * kBlock;
+    const size_t tid = (size_t)blockIdx.x * kBlock + threadIdx.x;
+    for (size_t i = tid; i < nW; i += stride) {
+        p.F[i] = 0u;  // level 0 frontier
+        p.V[i] = 0u;  // visited through level -1
+    }
+    const size_t nu = (size_t)p.Lcap * p.nw32;
+    for (size_t i = tid; i < nu; i += stride) p.ufr[i] = 0u;
+
+    __shared__ bool s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&p.ctl->blocks_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // d(s,s) = 0 and sigma_s(s) = 1 (Section 1.1)
+    for (int b = threadIdx.x; b < p.nb; b += kBlock) {
+        const int s = p.sources[b];
+        atomicOr(p.F + (size_t)s * W + (b >> 5), 1u << (b & 31));
+        atomicOr(p.ufr + (s >> 5), 1u << (s & 31));
+        p.sigma[(size_t)s * B + b] = 1ull;
+    }
+    if (threadIdx.x == 0) {
+        p.ctl->fwd_done = 0u;
+        p.ctl->nonempty = 0u;
+        p.ctl->nlevels = 0;
+        p.ctl->seq = p.seq;
+        atomicExch(&p.ctl->blocks_done, 0u);
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_forward(const MsParams p, const int l) {
+    constexpr int B = 32 * W;
+    __shared__ uint32_t s_flags;
+    __shared__ unsigned long long s_arcs;
+    if (threadIdx.x == 0) {
+        s_flags = 0u;
+        s_arcs = 0ull;
+    }
+    __syncthreads();
+    // speculative launches past the last level, and the level-capacity guard
+    if (*(volatile uint32_t *)&p.ctl->fwd_done != 0u || l + 1 >= p.Lcap) return;
+
+    const int lane = threadIdx.x & 31;
+    const int it = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const size_t nW = (size_t)p.n * W;
+    const uint32_t *Fl = p.F + (size_t)l * nW;
+    uint32_t *Fn = p.F + (size_t)(l + 1) * nW;
+    const uint32_t *ufl = p.ufr + (size_t)l * p.nw32;
+    uint32_t *ufn = p.ufr + (size_t)(l + 1) * p.nw32;
+    const uint32_t *Vin = p.V + (size_t)(l & 1) * nW;
+    uint32_t *Vout = p.V + (size_t)((l + 1) & 1) * nW;
+    bool produced = false, ovf = false;
+    uint32_t arcs = 0;  // predecessor relations found by this warp (uniform)
+
+    if (it < p.nitems) {
+        const int v = p.item_v[it];
+        const int beg = p.item_beg[it];
+        const int end = p.item_end[it];
+        const int slot = p.item_slot[it];
+        uint32_t U[W];
+        uint32_t anyU = 0;
+        {
+            uint32_t a[W], f[W];
+            load_row<W>(Vin + (size_t)v * W, a);
+            load_row<W>(Fl + (size_t)v * W, f);
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                const uint32_t vis = a[j] | f[j];
+                if (lane == j) Vout[(size_t)v * W + j] = vis;
+                U[j] = ~vis & valid_word(p.nb, j);
+                anyU |= U[j];
+            }
+        }
+        const bool first_chunk = slot < 0 || p.slot_first[slot] == slot;
+        if (anyU == 0u) {
+            if (first_chunk && lane < W) Fn[(size_t)v * W + lane] = 0u;
+        } else {
+            uint64_t acc[W];
+            uint32_t nf[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) { acc[j] = 0ull; nf[j] = 0u; }
+            for (int e0 = beg; e0 < end; e0 += 32) {
+                const int e = e0 + lane;
+                int u = 0;
+                uint32_t m[W];
+#pragma unroll
+                for (int j = 0; j < W; ++j) m[j] = 0u;
+                bool cand = false;
+                if (e < end) {
+                    u = __ldg(p.col + e);
+                    if ((__ldg(ufl + (u >> 5)) >> (u & 31)) & 1u) {
+                        uint32_t fu[W];
+                        load_row<W>(Fl + (size_t)u * W, fu);
+                        uint32_t any = 0;
+#pragma unroll
+                        for (int j = 0; j < W; ++j) { m[j] = fu[j] & U[j]; any |= m[j]; }
+                        cand = any != 0u;
+                    }
+                }
+                unsigned bal = __ballot_sync(kFull, cand);
+                while (bal) {
+                    const int k = __ffs(bal) - 1;
+                    bal &= bal - 1;
+                    const int uk = __shfl_sync(kFull, u, k);
+                    const uint64_t *su = p.sigma + (size_t)uk * B + lane;
+#pragma unroll
+                    for (int j = 0; j < W; ++j) {
+                        const uint32_t mk = __shfl_sync(kFull, m[j], k);
+                        nf[j] |= mk;
+                        arcs += __popc(mk);
+                        if ((mk >> lane) & 1u) {
+                            const uint64_t x = __ldg(su + 32 * j);
+                            const uint64_t y = acc[j] + x;
+                            ovf |= y < x;
+                            acc[j] = y;
+                        }
+                    }
+                }
+            }
+            if (slot < 0) {
+                produced = store_next<W>(p, v, acc, nf, Fn, ufn, lane);
+            } else {
+                uint64_t *pp = p.part + (size_t)slot * B + lane;
+#pragma unroll
+                for (int j = 0; j < W; ++j) pp[32 * j] = acc[j];
+#pragma unroll
+                for (int j = 0; j < W; ++j)
+                    if (lane == j) p.pmask[(size_t)slot * W + j] = nf[j];
+                __threadfence();
+                __syncwarp();
+                const int first = p.slot_first[slot];
+                const int nch = p.slot_nch[slot];
+                unsigned old = 0;
+                if (lane == 0) old = atomicAdd(p.cnt + first, 1u);
+                old = __shfl_sync(kFull, old, 0);
+                if (old == (unsigned)(nch - 1)) {
+                    __threadfence();
+#pragma unroll
+                    for (int j = 0; j < W; ++j) { acc[j] = 0ull; nf[j] = 0u; }
+                    for (int c = 0; c < nch; ++c) {
+                        const uint64_t *q = p.part + (size_t)(first + c) * B + lane;
+                        const uint32_t *qm = p.pmask + (size_t)(first + c) * W;
+#pragma unroll
+                        for (int j = 0; j < W; ++j) {
+                            const uint64_t x = __ldcg(q + 32 * j);
+                            const uint64_t y = acc[j] + x;
+                            ovf |= y < x;
+                            acc[j] = y;
+                            nf[j] |= __ldcg(qm + j);
+                        }
+                    }
+                    produced = store_next<W>(p, v, acc, nf, Fn, ufn, lane);
+                    if (lane == 0) p.cnt[first] = 0u;
+                }
+            }
+        }
+    }
+    const unsigned wovf = __ballot_sync(kFull, ovf);
+    if (lane == 0) {
+        if (produced) atomicOr(&s_flags, 1u);
+        if (wovf) atomicOr(&s_flags, 2u);
+        if (arcs) atomicAdd(&s_arcs, (unsigned long long)arcs);
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    if (s_arcs) atomicAdd(&p.ctl->dag_arcs, s_arcs);
+    if (s_flags & 1u) atomicOr(&p.ctl->nonempty, 1u);
+    if (s_flags & 2u) atomicOr(&p.ctl->status, BC_STATUS_SIGMA_OVERFLOW);
+    __threadfence();
+    if (atomicAdd(&p.ctl->blocks_done, 1u) != gridDim.x - 1) return;
+    // last block of this level: decide whether the forward pass ended
+    __threadfence();
+    const unsigned ne = atomicExch(&p.ctl->nonempty, 0u);
+    atomicExch(&p.ctl->blocks_done, 0u);
+    volatile HostCtl *h = p.hctl;
+    if (ne == 0u) {
+        p.ctl->fwd_done = 1u;
+        p.ctl->nlevels = l;
+        p.ctl->depth_sum += (unsigned long long)l;
+        h->nlevels = l;
+        __threadfence_system();
+        h->done_seq = p.seq;
+    } else if (l + 2 >= p.Lcap) {
+        p.ctl->fwd_done = 1u;
+        p.ctl->nlevels = -1;
+        h->nlevels = -1;
+        __threadfence_system();
+        h->done_seq = p.seq;
+    }
+    h->progress = l + 1;
+    __threadfence_system();
+    h->progress_seq = p.seq;
+    __threadfence_system();
+}
+
+template <int W>
+__device__ __forceinline__ void finalize_dep(const MsParams &p, int v, const uint32_t (&f)[W],
+                                             const float (&S)[W], int lane) {
+    constexpr int B = 32 * W;
+    double sum = 0.0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        if ((f[j] >> lane) & 1u) {
+            const size_t idx = (size_t)v * B + 32 * j + lane;
+            const float sg = __ull2float_rn(p.sigma[idx]);
+            const float d = sg * S[j];      // delta_s*(v) = sigma_s(v) * sum_w c_s(w)
+            p.cval[idx] = (1.0f + d) / sg;  // c_s(v) for the level above
+            sum += (double)d;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(kFull, sum, off);
+    if (lane == 0) p.bc[v] += sum;
+}
+
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_backward(const MsParams p, const int l) {
+    constexpr int B = 32 * W;
+    const int lane = threadIdx.x & 31;
+    const int it = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+    if (it >= p.nitems) return;
+    const size_t nW = (size_t)p.n * W;
+    const uint32_t *Fl = p.F + (size_t)l * nW;
+    const uint32_t *Fs = p.F + (size_t)(l + 1) * nW;
+    const uint32_t *ufs = p.ufr + (size_t)(l + 1) * p.nw32;
+    const int v = p.item_v[it];
+    const int beg = p.item_beg[it];
+    const int end = p.item_end[it];
+    const int slot = p.item_slot[it];
+    uint32_t f[W];
+    load_row<W>(Fl + (size_t)v * W, f);
+    uint32_t anyf = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) anyf |= f[j];
+    if (anyf == 0u) return;  // v is at level l for no source (same for all chunks of v)
+
+    float S[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) S[j] = 0.0f;
+    for (int e0 = beg; e0 < end; e0 += 32) {
+        const int e = e0 + lane;
+        int u = 0;
+        uint32_t m[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) m[j] = 0u;
+        bool cand = false;
+        if (e < end) {
+            u = __ldg(p.col + e);
+            if ((__ldg(ufs + (u >> 5)) >> (u & 31)) & 1u) {
+                uint32_t fu[W];
+                load_row<W>(Fs + (size_t)u * W, fu);
+                uint32_t any = 0;
+#pragma unroll
+                for (int j = 0; j < W; ++j) { m[j] = fu[j] & f[j]; any |= m[j]; }
+                cand = any != 0u;
+            }
+        }
+        unsigned bal = __ballot_sync(kFull, cand);
+        while (bal) {
+            const int k = __ffs(bal) - 1;
+            bal &= bal - 1;
+            const int uk = __shfl_sync(kFull, u, k);
+            const float *cu = p.cval + (size_t)uk * B + lane;
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                const uint32_t mk = __shfl_sync(kFull, m[j], k);
+                if ((mk >> lane) & 1u) S[j] += __ldg(cu + 32 * j);
+            }
+        }
+    }
+    if (slot < 0) {
+        finalize_dep<W>(p, v, f, S, lane);
+        return;
+    }
+    float *pp = reinterpret_cast<float *>(p.part) + (size_t)slot * B + lane;
+#pragma unroll
+    for (int j = 0; j < W; ++j) pp[32 * j] = S[j];
+    __threadfence();
+    __syncwarp();
+    const int first = p.slot_first[slot];
+    const int nch = p.slot_nch[slot];
+    unsigned old = 0;
+    if (lane == 0) old = atomicAdd(p.cnt + first, 1u);
+    old = __shfl_sync(kFull, old, 0);
+    if (old != (unsigned)(nch - 1)) return;
+    __threadfence();
+#pragma unroll
+    for (int j = 0; j < W; ++j) S[j] = 0.0f;
+    for (int c = 0; c < nch; ++c) {
+        const float *q = reinterpret_cast<const float *>(p.part) + (size_t)(first + c) * B + lane;
+#pragma unroll
+        for (int j = 0; j < W; ++j) S[j] += __ldcg(q + 32 * j);
+    }
+    finalize_dep<W>(p, v, f, S, lane);
+    if (lane == 0) p.cnt[first] = 0u;
+}
+
+// Per-source summaries: blockIdx.y = source word j, lane = source 32j+lane,
+// warps stride over vertices; the level of (v, s) is the one frontier that
+// holds its bit.
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_hash(const MsParams p, const int L) {
+    constexpr int B = 32 * W;
+    const int j = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const uint32_t bit = 1u << lane;
+    const size_t nW = (size_t)p.n * W;
+    uint64_t hs = 0, hd = 0, ds = 0, rc = 0;
+    for (int v = blockIdx.x * kWarps + wib; v < p.n; v += gridDim.x * kWarps) {
+        int lev = -1;
+        for (int l = 0; l <= L; ++l)
+            if (__ldg(p.F + (size_t)l * nW + (size_t)v * W + j) & bit) lev = l;
+        if (lev >= 0) {
+            const uint64_t sg = p.sigma[(size_t)v * B + 32 * j + lane];
+            hs += sg * (uint64_t)(v + 1);
+            hd += (uint64_t)(lev + 1) * (uint64_t)(v + 1);
+            ds += (uint64_t)lev;
+            rc += 1ull;
+        }
+    }
+    __shared__ uint64_t sh[4][kWarps][32];
+    sh[0][wib][lane] = hs;
+    sh[1][wib][lane] = hd;
+    sh[2][wib][lane] = ds;
+    sh[3][wib][lane] = rc;
+    __syncthreads();
+    if (wib != 0) return;
+    for (int w = 1; w < kWarps; ++w) {
+        hs += sh[0][w][lane];
+        hd += sh[1][w][lane];
+        ds += sh[2][w][lane];
+        rc += sh[3][w][lane];
+    }
+    const int b = 32 * j + lane;
+    if (b < p.nb) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(p.h_sigma + b), hs);
+        atomicAdd(reinterpret_cast<unsigned long long *>(p.h_dist + b), hd);
+        atomicAdd(reinterpret_cast<unsigned long long *>(p.dist_sum + b), ds);
+        atomicAdd(reinterpret_cast<unsigned long long *>(p.reach + b), rc);
+    }
+}
+
+// Rows of the forward pass for bc_forward_rows: out[b][v] for this batch.
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_rows(const MsParams p, const int L, uint64_t *sig_out,
+                                                 int32_t *dist_out) {
+    constexpr int B = 32 * W;
+    const size_t nW = (size_t)p.n * W;
+    const size_t total = (size_t)p.n * B;
+    for (size_t i = (size_t)blockIdx.x * kBlock + threadIdx.x; i < total; i += (size_t)gridDim.x * kBlock) {
+        const int v = (int)(i / B);
+        const int b = (int)(i % B);
+        if (b >= p.nb) continue;
+        int lev = -1;
+        for (int l = 0; l <= L; ++l)
+            if ((p.F[(size_t)l * nW + (size_t)v * W + (b >> 5)] >> (b & 31)) & 1u) lev = l;
+        const size_t o = (size_t)b * p.n + v;
+        if (dist_out) dist_out[o] = lev;
+        if (sig_out) sig_out[o] = lev >= 0 ? p.sigma[(size_t)v * B + b] : 0ull;
+    }
+}
+
+__global__ void k_scale(double *x, int32_t n, double f) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] *= f;
+}
+
+int sm_count() {
+    static int c = 0;
+    if (c == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+        if (c <= 0) c = 1;
+    }
+    return c;
+}
+
+int item_blocks(const MsParams &p) { return (p.nitems + kWarps - 1) / kWarps; }
+
+template <int W>
+void launch_init_t(const MsParams &p, cudaStream_t st) {
+    const size_t work = (size_t)p.n * W;
+    int g = (int)((work + kBlock - 1) / kBlock);
+    g = g < 1 ? 1 : (g > 8 * sm_count() ? 8 * sm_count() : g);
+    k_init<W><<<g, kBlock, 0, st>>>(p);
+}
+
+}  // namespace
+
+bool ms_supported_width(int W) { return W == 1 || W == 2 || W == 4 || W == 8; }
+
+#define BCGB_DISPATCH_W(W, CALL)                  \
+    switch (W) {                                  \
+        case 1: { constexpr int kW = 1; CALL; } break; \
+        case 2: { constexpr int kW = 2; CALL; } break; \
+        case 4: { constexpr int kW = 4; CALL; } break; \
+        case 8: { constexpr int kW = 8; CALL; } break; \
+        default: break;                           \
+    }
+
+void ms_launch_init(int W, const MsParams &p, cudaStream_t st) {
+    BCGB_DISPATCH_W(W, launch_init_t<kW>(p, st));
+}
+
+void ms_launch_forward(int W, const MsParams &p, int level, cudaStream_t st) {
+    const int g = item_blocks(p);
+    if (g == 0) return;
+    BCGB_DISPATCH_W(W, (k_forward<kW><<<g, kBlock, 0, st>>>(p, level)));
+}
+
+void ms_launch_backward(int W, const MsParams &p, int level, cudaStream_t st) {
+    const int g = item_blocks(p);
+    if (g == 0) return;
+    BCGB_DISPATCH_W(W, (k_backward<kW><<<g, kBlock, 0, st>>>(p, level)));
+}
+
+void ms_launch_hash(int W, const MsParams &p, int nlevels, cudaStream_t st) {
+    int gx = (p.n + kWarps - 1) / kWarps;
+    const int cap = (4 * sm_count() + W - 1) / W;
+    gx = gx > cap ? cap : gx;
+    gx = gx < 1 ? 1 : gx;
+    BCGB_DISPATCH_W(W, (k_hash<kW><<<dim3(gx, kW), kBlock, 0, st>>>(p, nlevels)));
+}
+
+void ms_launch_rows(int W, const MsParams &p, int nlevels, uint64_t *sig_out, int32_t *dist_out,
+                    cudaStream_t st) {
+    const int g = 4 * sm_count();
+    BCGB_DISPATCH_W(W, (k_rows<kW><<<g, kBlock, 0, st>>>(p, nlevels, sig_out, dist_out)));
+}
+
+void launch_scale(double *x, int32_t n, double f, cudaStream_t st) {
+    if (n <= 0) return;
+    int g = (n + kBlock - 1) / kBlock;
+    g = g > 4 * sm_count() ? 4 * sm_count() : g;
+    k_scale<<<g, kBlock, 0, st>>>(x, n, f);
+}
+
+}  // namespace bcgb
