@@ -161,6 +161,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--plain-sources", type=int, default=1024)
+    ap.add_argument("--profile", action="store_true",
+                    help="profiling driver: one bc_run over the first --sources sources, nothing else")
+    ap.add_argument("--sources", type=int, default=0)
+    ap.add_argument("--batch", type=int, default=BATCH)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -180,6 +184,15 @@ def main():
     from paper_0809_1906_gb300 import native
     native.load()
     g, desc = workload()
+    if args.profile:
+        k = args.sources or g.n
+        with native.Graph.from_csr(g, trust_input=True) as hp:
+            hp.run(np.arange(k, dtype=np.int32), batch=args.batch)
+            out, code, _ = hp.result()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": desc, "sources": k, "batch": args.batch, "status": code,
+                          "bc_sum": float(out.sum())}), flush=True)
+        return
     n, m = g.n, g.m
     # weak scaling: every rank runs the whole all-sources job, sources rotated by rank
     src = ((np.arange(n, dtype=np.int64) + rank * (n // max(world, 1))) % n).astype(np.int32)
