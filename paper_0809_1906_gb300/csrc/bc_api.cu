@@ -14,6 +14,7 @@
 #include "bc_internal.cuh"
 #include "plain.cuh"
 #include "sched.cuh"
+#include "weighted.cuh"
 
 namespace {
 
@@ -103,6 +104,13 @@ struct bc_graph {
     int64_t launches = 0;
 
     bcgb::PlainState plain;
+
+    // weighted path: per-wave state
+    int32_t maxw = 1;
+    int32_t wG = 0, wK = 0, wC = 0;
+    DevBuf<int32_t> wdist, worder, wgrp, wslots;
+    DevBuf<uint64_t> wsigma;
+    DevBuf<float> wcval, wrows;
 };
 
 namespace {
@@ -127,6 +135,10 @@ void free_graph(bc_graph *g) {
         cudaEventDestroy(e.b);
     }
     bcgb::plain_free(g->plain);
+    for (auto *b : {&g->wdist, &g->worder, &g->wgrp, &g->wslots}) b->release();
+    g->wsigma.release();
+    g->wcval.release();
+    g->wrows.release();
     delete g;
 }
 
@@ -393,6 +405,85 @@ int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStr
     return BC_OK;
 }
 
+int sm_count_host() {
+    static int c = 0;
+    if (c == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+        if (c <= 0) c = 1;
+    }
+    return c;
+}
+
+// Weighted path: waves of one CTA per source (csrc/sssp_weighted.cu).
+// opt->batch (if set) is the wave size; default 4 CTAs per SM, capped so the
+// wave state stays within 8 GiB.
+int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t st, bool backward, bool hash,
+                 uint64_t *rows_sig, int32_t *rows_dist) {
+    const int32_t n = g->n;
+    const int K = g->maxw + 1;
+    if (K > bcgb::kMaxRing)
+        return fail(BC_ERR_UNSUPPORTED, "weighted path: maximum weight must be below " +
+                                            std::to_string(bcgb::kMaxRing));
+    int C = (int)std::min<int64_t>(std::max<int64_t>(1024, (4ll << 20) / K / 4), (int64_t)n + 1);
+    C = std::max(C, 64);
+    const size_t per_src = (size_t)n * (4 + 8 + 4 + 4 + 4 + 4) + 4 + (size_t)K * C * 4;
+    int G = (opt && opt->batch > 0) ? opt->batch : 4 * sm_count_host();
+    G = (int)std::min<size_t>((size_t)G, std::max<size_t>(1, (8ull << 30) / per_src));
+    G = std::max(1, std::min(G, std::max(nsrc, 1)));
+    if (g->wG < G || g->wK != K || g->wC != C) {
+        CK(g->wdist.ensure((size_t)G * n));
+        CK(g->wsigma.ensure((size_t)G * n));
+        CK(g->wcval.ensure((size_t)G * n));
+        CK(g->worder.ensure((size_t)G * n));
+        CK(g->wgrp.ensure((size_t)G * (n + 1)));
+        CK(g->wslots.ensure((size_t)G * K * C));
+        CK(g->wrows.ensure((size_t)G * n));
+        g->wG = G;
+        g->wK = K;
+        g->wC = C;
+    }
+    for (int32_t w0 = 0; w0 < nsrc; w0 += G) {
+        const int nw = std::min<int32_t>(G, nsrc - w0);
+        bcgb::WParams p{};
+        p.n = n;
+        p.K = K;
+        p.C = C;
+        p.dmax = (int32_t)std::min<int64_t>((int64_t)n * g->maxw, INT32_MAX - 1);
+        p.row_ptr = g->row_ptr.p;
+        p.col = g->col.p;
+        p.w = g->w.p;
+        p.sources = g->sources.p + w0;
+        p.dist = g->wdist.p;
+        p.sigma = g->wsigma.p;
+        p.cval = g->wcval.p;
+        p.order = g->worder.p;
+        p.grp = g->wgrp.p;
+        p.slots = g->wslots.p;
+        p.delta_rows = backward ? g->wrows.p : nullptr;
+        if (hash) {
+            p.h_sigma = g->h_sigma.p + w0;
+            p.h_dist = g->h_dist.p + w0;
+            p.dist_sum = g->dist_sum.p + w0;
+            p.reach = g->reach.p + w0;
+        }
+        p.rows_sigma = rows_sig ? rows_sig + (size_t)w0 * n : nullptr;
+        p.rows_dist = rows_dist ? rows_dist + (size_t)w0 * n : nullptr;
+        p.ctl = g->ctl;
+        {
+            Timer t(g, st, BC_KERNEL_FORWARD);
+            bcgb::w_launch_wave(p, nw, st);
+        }
+        if (backward) {
+            Timer t(g, st, BC_KERNEL_BACKWARD);
+            bcgb::w_launch_reduce(g->wrows.p, nw, n, g->bc.p, sm_count_host(), st);
+        }
+        CK(cudaGetLastError());
+    }
+    return BC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -421,6 +512,7 @@ int bc_create_graph(int32_t n, const int32_t *row_ptr, const int32_t *col, const
     g->narcs = m2;
     g->weighted = weights != nullptr;
     g->h_row_ptr = rp;
+    for (int32_t x : ww) g->maxw = std::max(g->maxw, x);
     auto up = [&](DevBuf<int32_t> &d, const std::vector<int32_t> &h) -> int {
         CK(d.ensure(h.size()));
         if (!h.empty()) CK(cudaMemcpy(d.p, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -458,9 +550,9 @@ int bc_run(bc_graph *g, const int32_t *sources, int32_t num_sources, const bc_op
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const uint32_t flags = opt ? opt->flags : 0u;
     int W = 0;
-    int r = resolve_batch(opt, &W);
+    int r = g->weighted ? BC_OK : resolve_batch(opt, &W);
     if (r) return r;
-    if (g->weighted && !(flags & BC_PLAIN)) return fail(BC_ERR_UNSUPPORTED, "weighted graphs need the delta-stepping path");
+    if (g->weighted && (flags & BC_PLAIN)) return fail(BC_ERR_UNSUPPORTED, "the one-source path is unweighted only");
     int32_t nsrc = 0;
     r = stage_sources(g, sources, num_sources, &nsrc);
     if (r) return r;
@@ -492,6 +584,9 @@ int bc_run(bc_graph *g, const int32_t *sources, int32_t num_sources, const bc_op
                             hash ? g->h_sigma.p : nullptr, hash ? g->h_dist.p : nullptr,
                             hash ? g->dist_sum.p : nullptr, hash ? g->reach.p : nullptr, g->ctl, g->hctl,
                             g->hctl_d, &g->seq, st, hook, wait_ms, &g_err);
+        if (r) return r;
+    } else if (g->weighted) {
+        r = run_weighted(g, nsrc, opt, st, true, hash, nullptr, nullptr);
         if (r) return r;
     } else {
         r = run_batches(g, nsrc, W, opt, st, true, hash, nullptr, nullptr);
@@ -544,10 +639,9 @@ int bc_forward_rows(bc_graph *g, const int32_t *sources, int32_t k, uint64_t *si
     g_err.clear();
     if (!g) return fail(BC_ERR_ARG, "graph is NULL");
     if (k < 0 || (k > 0 && !sources)) return fail(BC_ERR_ARG, "bad source list");
-    if (g->weighted) return fail(BC_ERR_UNSUPPORTED, "weighted graphs need the delta-stepping path");
     cudaStream_t st = (cudaStream_t)cuda_stream;
     int W = 0;
-    int r = resolve_batch(opt, &W);
+    int r = g->weighted ? BC_OK : resolve_batch(opt, &W);
     if (r) return r;
     int32_t nsrc = 0;
     r = stage_sources(g, sources, k, &nsrc);
@@ -560,7 +654,10 @@ int bc_forward_rows(bc_graph *g, const int32_t *sources, int32_t k, uint64_t *si
     if (dist) CK(dd.ensure(cells));
     CK(cudaMemsetAsync(&g->ctl->status, 0, sizeof(uint32_t), st));
     g->timing = false;
-    r = run_batches(g, nsrc, W, opt, st, false, false, sigma ? ds.p : nullptr, dist ? dd.p : nullptr);
+    if (g->weighted)
+        r = run_weighted(g, nsrc, opt, st, false, false, sigma ? ds.p : nullptr, dist ? dd.p : nullptr);
+    else
+        r = run_batches(g, nsrc, W, opt, st, false, false, sigma ? ds.p : nullptr, dist ? dd.p : nullptr);
     uint32_t status = 0;
     if (!r) {
         cudaError_t e = cudaSuccess;

@@ -122,11 +122,58 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
     }
 }
 
+// Warp-wide 32x32 bit transpose: lane k holds row k; returns column `lane`
+// (bit k of the result = bit `lane` of lane k's input). Five exchange steps,
+// each swapping the off-diagonal s x s blocks of every 2s x 2s block.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const uint32_t M = s == 16 ? 0x0000FFFFu : s == 8 ? 0x00FF00FFu : s == 4 ? 0x0F0F0F0Fu
+                         : s == 2 ? 0x33333333u : 0x55555555u;
+        const uint32_t y = __shfl_xor_sync(kFull, x, s);
+        x = (lane & s) ? ((x & ~M) | ((y >> s) & M)) : ((x & M) | ((y & M) << s));
+    }
+    return x;
+}
+
+// One 32-arc chunk of a vertex's row: lanes probe one arc each; lane k ends
+// with its neighbour u_k (in s_u) and masks m_k[j] = frontier words of u_k
+// AND `want` (zero for arcs that cannot contribute). Returns the ballot of
+// contributing lanes.
 template <int W>
-__global__ void __launch_bounds__(kBlock) k_forward(const MsParams p, const int l) {
+__device__ __forceinline__ unsigned probe_chunk(const int32_t *__restrict__ col, int e, int end,
+                                                const uint32_t *__restrict__ ufr, const uint32_t *__restrict__ Fx,
+                                                const uint32_t (&want)[W], uint32_t (&m)[W], int32_t *s_u,
+                                                int lane) {
+    int u = 0;
+    bool cand = false;
+#pragma unroll
+    for (int j = 0; j < W; ++j) m[j] = 0u;
+    if (e < end) {
+        u = __ldg(col + e);
+        if ((__ldg(ufr + (u >> 5)) >> (u & 31)) & 1u) {
+            uint32_t fu[W];
+            load_row<W>(Fx + (size_t)u * W, fu);
+            uint32_t any = 0;
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                m[j] = fu[j] & want[j];
+                any |= m[j];
+            }
+            cand = any != 0u;
+        }
+    }
+    s_u[lane] = u;
+    __syncwarp();
+    return __ballot_sync(kFull, cand);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const int l) {
     constexpr int B = 32 * W;
     __shared__ uint32_t s_flags;
     __shared__ unsigned long long s_arcs;
+    __shared__ int32_t s_u[kWarps][32];
     if (threadIdx.x == 0) {
         s_flags = 0u;
         s_arcs = 0ull;
@@ -136,7 +183,7 @@ __global__ void __launch_bounds__(kBlock) k_forward(const MsParams p, const int 
     if (*(volatile uint32_t *)&p.ctl->fwd_done != 0u || l + 1 >= p.Lcap) return;
 
     const int lane = threadIdx.x & 31;
-    const int it = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const int wib = threadIdx.x >> 5;
     const size_t nW = (size_t)p.n * W;
     const uint32_t *Fl = p.F + (size_t)l * nW;
     uint32_t *Fn = p.F + (size_t)(l + 1) * nW;
@@ -145,9 +192,11 @@ __global__ void __launch_bounds__(kBlock) k_forward(const MsParams p, const int 
     const uint32_t *Vin = p.V + (size_t)(l & 1) * nW;
     uint32_t *Vout = p.V + (size_t)((l + 1) & 1) * nW;
     bool produced = false, ovf = false;
-    uint32_t arcs = 0;  // predecessor relations found by this warp (uniform)
+    uint32_t arcs = 0;  // predecessor relations counted by this lane
 
-    if (it < p.nitems) {
+    // persistent warps: items are sorted by decreasing degree, so striding
+    // gives every warp a similar mix
+    for (int it = blockIdx.x * kWarps + wib; it < p.nitems; it += gridDim.x * kWarps) {
         const int v = p.item_v[it];
         const int beg = p.item_beg[it];
         const int end = p.item_end[it];
@@ -169,88 +218,81 @@ __global__ void __launch_bounds__(kBlock) k_forward(const MsParams p, const int 
         const bool first_chunk = slot < 0 || p.slot_first[slot] == slot;
         if (anyU == 0u) {
             if (first_chunk && lane < W) Fn[(size_t)v * W + lane] = 0u;
-        } else {
-            uint64_t acc[W];
-            uint32_t nf[W];
+            continue;
+        }
+        uint64_t acc[W];  // lane owns source 32j + lane
+        uint32_t nf[W];
 #pragma unroll
-            for (int j = 0; j < W; ++j) { acc[j] = 0ull; nf[j] = 0u; }
-            for (int e0 = beg; e0 < end; e0 += 32) {
-                const int e = e0 + lane;
-                int u = 0;
-                uint32_t m[W];
+        for (int j = 0; j < W; ++j) {
+            acc[j] = 0ull;
+            nf[j] = 0u;
+        }
+        for (int e0 = beg; e0 < end; e0 += 32) {
+            uint32_t m[W];
+            const unsigned bal = probe_chunk<W>(p.col, e0 + lane, end, ufl, Fl, U, m, s_u[wib], lane);
+            if (bal) {
 #pragma unroll
-                for (int j = 0; j < W; ++j) m[j] = 0u;
-                bool cand = false;
-                if (e < end) {
-                    u = __ldg(p.col + e);
-                    if ((__ldg(ufl + (u >> 5)) >> (u & 31)) & 1u) {
-                        uint32_t fu[W];
-                        load_row<W>(Fl + (size_t)u * W, fu);
-                        uint32_t any = 0;
-#pragma unroll
-                        for (int j = 0; j < W; ++j) { m[j] = fu[j] & U[j]; any |= m[j]; }
-                        cand = any != 0u;
-                    }
-                }
-                unsigned bal = __ballot_sync(kFull, cand);
-                while (bal) {
-                    const int k = __ffs(bal) - 1;
-                    bal &= bal - 1;
-                    const int uk = __shfl_sync(kFull, u, k);
-                    const uint64_t *su = p.sigma + (size_t)uk * B + lane;
-#pragma unroll
-                    for (int j = 0; j < W; ++j) {
-                        const uint32_t mk = __shfl_sync(kFull, m[j], k);
-                        nf[j] |= mk;
-                        arcs += __popc(mk);
-                        if ((mk >> lane) & 1u) {
-                            const uint64_t x = __ldg(su + 32 * j);
-                            const uint64_t y = acc[j] + x;
-                            ovf |= y < x;
-                            acc[j] = y;
-                        }
+                for (int j = 0; j < W; ++j) {
+                    if (__ballot_sync(kFull, m[j] != 0u) == 0u) continue;
+                    // t: the chunk's neighbours that are predecessors for source 32j + lane
+                    uint32_t t = transpose32(m[j], lane);
+                    nf[j] |= __ballot_sync(kFull, t != 0u);
+                    arcs += __popc(t);
+                    const uint64_t *sj = p.sigma + 32 * j + lane;
+                    while (t) {
+                        const int k = __ffs(t) - 1;
+                        t &= t - 1;
+                        const uint64_t x = __ldg(sj + (size_t)s_u[wib][k] * B);
+                        const uint64_t y = acc[j] + x;
+                        ovf |= y < x;
+                        acc[j] = y;
                     }
                 }
             }
-            if (slot < 0) {
-                produced = store_next<W>(p, v, acc, nf, Fn, ufn, lane);
-            } else {
-                uint64_t *pp = p.part + (size_t)slot * B + lane;
+            __syncwarp();
+        }
+        if (slot < 0) {
+            produced |= store_next<W>(p, v, acc, nf, Fn, ufn, lane);
+            continue;
+        }
+        uint64_t *pp = p.part + (size_t)slot * B + lane;
 #pragma unroll
-                for (int j = 0; j < W; ++j) pp[32 * j] = acc[j];
+        for (int j = 0; j < W; ++j) pp[32 * j] = acc[j];
 #pragma unroll
-                for (int j = 0; j < W; ++j)
-                    if (lane == j) p.pmask[(size_t)slot * W + j] = nf[j];
-                __threadfence();
-                __syncwarp();
-                const int first = p.slot_first[slot];
-                const int nch = p.slot_nch[slot];
-                unsigned old = 0;
-                if (lane == 0) old = atomicAdd(p.cnt + first, 1u);
-                old = __shfl_sync(kFull, old, 0);
-                if (old == (unsigned)(nch - 1)) {
-                    __threadfence();
+        for (int j = 0; j < W; ++j)
+            if (lane == j) p.pmask[(size_t)slot * W + j] = nf[j];
+        __threadfence();
+        __syncwarp();
+        const int first = p.slot_first[slot];
+        const int nch = p.slot_nch[slot];
+        unsigned old = 0;
+        if (lane == 0) old = atomicAdd(p.cnt + first, 1u);
+        old = __shfl_sync(kFull, old, 0);
+        if (old != (unsigned)(nch - 1)) continue;
+        __threadfence();
 #pragma unroll
-                    for (int j = 0; j < W; ++j) { acc[j] = 0ull; nf[j] = 0u; }
-                    for (int c = 0; c < nch; ++c) {
-                        const uint64_t *q = p.part + (size_t)(first + c) * B + lane;
-                        const uint32_t *qm = p.pmask + (size_t)(first + c) * W;
+        for (int j = 0; j < W; ++j) {
+            acc[j] = 0ull;
+            nf[j] = 0u;
+        }
+        for (int c = 0; c < nch; ++c) {
+            const uint64_t *q = p.part + (size_t)(first + c) * B + lane;
+            const uint32_t *qm = p.pmask + (size_t)(first + c) * W;
 #pragma unroll
-                        for (int j = 0; j < W; ++j) {
-                            const uint64_t x = __ldcg(q + 32 * j);
-                            const uint64_t y = acc[j] + x;
-                            ovf |= y < x;
-                            acc[j] = y;
-                            nf[j] |= __ldcg(qm + j);
-                        }
-                    }
-                    produced = store_next<W>(p, v, acc, nf, Fn, ufn, lane);
-                    if (lane == 0) p.cnt[first] = 0u;
-                }
+            for (int j = 0; j < W; ++j) {
+                const uint64_t x = __ldcg(q + 32 * j);
+                const uint64_t y = acc[j] + x;
+                ovf |= y < x;
+                acc[j] = y;
+                nf[j] |= __ldcg(qm + j);
             }
         }
+        produced |= store_next<W>(p, v, acc, nf, Fn, ufn, lane);
+        if (lane == 0) p.cnt[first] = 0u;
     }
     const unsigned wovf = __ballot_sync(kFull, ovf);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) arcs += __shfl_xor_sync(kFull, arcs, off);
     if (lane == 0) {
         if (produced) atomicOr(&s_flags, 1u);
         if (wovf) atomicOr(&s_flags, 2u);
@@ -309,85 +351,75 @@ __device__ __forceinline__ void finalize_dep(const MsParams &p, int v, const uin
 }
 
 template <int W>
-__global__ void __launch_bounds__(kBlock) k_backward(const MsParams p, const int l) {
+__global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const int l) {
     constexpr int B = 32 * W;
+    __shared__ int32_t s_u[kWarps][32];
     const int lane = threadIdx.x & 31;
-    const int it = (blockIdx.x * kBlock + threadIdx.x) >> 5;
-    if (it >= p.nitems) return;
+    const int wib = threadIdx.x >> 5;
     const size_t nW = (size_t)p.n * W;
     const uint32_t *Fl = p.F + (size_t)l * nW;
     const uint32_t *Fs = p.F + (size_t)(l + 1) * nW;
     const uint32_t *ufs = p.ufr + (size_t)(l + 1) * p.nw32;
-    const int v = p.item_v[it];
-    const int beg = p.item_beg[it];
-    const int end = p.item_end[it];
-    const int slot = p.item_slot[it];
-    uint32_t f[W];
-    load_row<W>(Fl + (size_t)v * W, f);
-    uint32_t anyf = 0;
+    for (int it = blockIdx.x * kWarps + wib; it < p.nitems; it += gridDim.x * kWarps) {
+        const int v = p.item_v[it];
+        const int beg = p.item_beg[it];
+        const int end = p.item_end[it];
+        const int slot = p.item_slot[it];
+        uint32_t f[W];
+        load_row<W>(Fl + (size_t)v * W, f);
+        uint32_t anyf = 0;
 #pragma unroll
-    for (int j = 0; j < W; ++j) anyf |= f[j];
-    if (anyf == 0u) return;  // v is at level l for no source (same for all chunks of v)
+        for (int j = 0; j < W; ++j) anyf |= f[j];
+        if (anyf == 0u) continue;  // v is at level l for no source (same for all chunks of v)
 
-    float S[W];
+        float S[W];  // lane owns source 32j + lane
 #pragma unroll
-    for (int j = 0; j < W; ++j) S[j] = 0.0f;
-    for (int e0 = beg; e0 < end; e0 += 32) {
-        const int e = e0 + lane;
-        int u = 0;
-        uint32_t m[W];
+        for (int j = 0; j < W; ++j) S[j] = 0.0f;
+        for (int e0 = beg; e0 < end; e0 += 32) {
+            uint32_t m[W];
+            const unsigned bal = probe_chunk<W>(p.col, e0 + lane, end, ufs, Fs, f, m, s_u[wib], lane);
+            if (bal) {
 #pragma unroll
-        for (int j = 0; j < W; ++j) m[j] = 0u;
-        bool cand = false;
-        if (e < end) {
-            u = __ldg(p.col + e);
-            if ((__ldg(ufs + (u >> 5)) >> (u & 31)) & 1u) {
-                uint32_t fu[W];
-                load_row<W>(Fs + (size_t)u * W, fu);
-                uint32_t any = 0;
-#pragma unroll
-                for (int j = 0; j < W; ++j) { m[j] = fu[j] & f[j]; any |= m[j]; }
-                cand = any != 0u;
+                for (int j = 0; j < W; ++j) {
+                    if (__ballot_sync(kFull, m[j] != 0u) == 0u) continue;
+                    // t: the chunk's neighbours w with v in P_s(w), s = source 32j + lane
+                    uint32_t t = transpose32(m[j], lane);
+                    const float *cj = p.cval + 32 * j + lane;
+                    while (t) {
+                        const int k = __ffs(t) - 1;
+                        t &= t - 1;
+                        S[j] += __ldg(cj + (size_t)s_u[wib][k] * B);
+                    }
+                }
             }
+            __syncwarp();
         }
-        unsigned bal = __ballot_sync(kFull, cand);
-        while (bal) {
-            const int k = __ffs(bal) - 1;
-            bal &= bal - 1;
-            const int uk = __shfl_sync(kFull, u, k);
-            const float *cu = p.cval + (size_t)uk * B + lane;
+        if (slot < 0) {
+            finalize_dep<W>(p, v, f, S, lane);
+            continue;
+        }
+        float *pp = reinterpret_cast<float *>(p.part) + (size_t)slot * B + lane;
 #pragma unroll
-            for (int j = 0; j < W; ++j) {
-                const uint32_t mk = __shfl_sync(kFull, m[j], k);
-                if ((mk >> lane) & 1u) S[j] += __ldg(cu + 32 * j);
-            }
+        for (int j = 0; j < W; ++j) pp[32 * j] = S[j];
+        __threadfence();
+        __syncwarp();
+        const int first = p.slot_first[slot];
+        const int nch = p.slot_nch[slot];
+        unsigned old = 0;
+        if (lane == 0) old = atomicAdd(p.cnt + first, 1u);
+        old = __shfl_sync(kFull, old, 0);
+        if (old != (unsigned)(nch - 1)) continue;
+        __threadfence();
+#pragma unroll
+        for (int j = 0; j < W; ++j) S[j] = 0.0f;
+        for (int c = 0; c < nch; ++c) {
+            const float *q = reinterpret_cast<const float *>(p.part) + (size_t)(first + c) * B + lane;
+#pragma unroll
+            for (int j = 0; j < W; ++j) S[j] += __ldcg(q + 32 * j);
         }
-    }
-    if (slot < 0) {
         finalize_dep<W>(p, v, f, S, lane);
-        return;
+        if (lane == 0) p.cnt[first] = 0u;
     }
-    float *pp = reinterpret_cast<float *>(p.part) + (size_t)slot * B + lane;
-#pragma unroll
-    for (int j = 0; j < W; ++j) pp[32 * j] = S[j];
-    __threadfence();
-    __syncwarp();
-    const int first = p.slot_first[slot];
-    const int nch = p.slot_nch[slot];
-    unsigned old = 0;
-    if (lane == 0) old = atomicAdd(p.cnt + first, 1u);
-    old = __shfl_sync(kFull, old, 0);
-    if (old != (unsigned)(nch - 1)) return;
-    __threadfence();
-#pragma unroll
-    for (int j = 0; j < W; ++j) S[j] = 0.0f;
-    for (int c = 0; c < nch; ++c) {
-        const float *q = reinterpret_cast<const float *>(p.part) + (size_t)(first + c) * B + lane;
-#pragma unroll
-        for (int j = 0; j < W; ++j) S[j] += __ldcg(q + 32 * j);
-    }
-    finalize_dep<W>(p, v, f, S, lane);
-    if (lane == 0) p.cnt[first] = 0u;
 }
 
 // Per-source summaries: blockIdx.y = source word j, lane = source 32j+lane,
@@ -402,16 +434,27 @@ __global__ void __launch_bounds__(kBlock) k_hash(const MsParams p, const int L) 
     const uint32_t bit = 1u << lane;
     const size_t nW = (size_t)p.n * W;
     uint64_t hs = 0, hd = 0, ds = 0, rc = 0;
-    for (int v = blockIdx.x * kWarps + wib; v < p.n; v += gridDim.x * kWarps) {
-        int lev = -1;
-        for (int l = 0; l <= L; ++l)
-            if (__ldg(p.F + (size_t)l * nW + (size_t)v * W + j) & bit) lev = l;
-        if (lev >= 0) {
-            const uint64_t sg = p.sigma[(size_t)v * B + 32 * j + lane];
-            hs += sg * (uint64_t)(v + 1);
-            hd += (uint64_t)(lev + 1) * (uint64_t)(v + 1);
-            ds += (uint64_t)lev;
-            rc += 1ull;
+    // four vertices per warp step so their frontier-word loads overlap
+    for (int v0 = (blockIdx.x * kWarps + wib) * 4; v0 < p.n; v0 += gridDim.x * kWarps * 4) {
+        int lev[4] = {-1, -1, -1, -1};
+        for (int l = 0; l <= L; ++l) {
+            const uint32_t *Fw = p.F + (size_t)l * nW + j;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int v = v0 + q;
+                if (v < p.n && (__ldg(Fw + (size_t)v * W) & bit)) lev[q] = l;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int v = v0 + q;
+            if (lev[q] >= 0) {
+                const uint64_t sg = p.sigma[(size_t)v * B + 32 * j + lane];
+                hs += sg * (uint64_t)(v + 1);
+                hd += (uint64_t)(lev[q] + 1) * (uint64_t)(v + 1);
+                ds += (uint64_t)lev[q];
+                rc += 1ull;
+            }
         }
     }
     __shared__ uint64_t sh[4][kWarps][32];
@@ -471,7 +514,11 @@ int sm_count() {
     return c;
 }
 
-int item_blocks(const MsParams &p) { return (p.nitems + kWarps - 1) / kWarps; }
+int item_blocks(const MsParams &p, int per_sm) {
+    const int need = (p.nitems + kWarps - 1) / kWarps;
+    const int cap = per_sm * sm_count();
+    return need < cap ? need : cap;
+}
 
 template <int W>
 void launch_init_t(const MsParams &p, cudaStream_t st) {
@@ -499,20 +546,20 @@ void ms_launch_init(int W, const MsParams &p, cudaStream_t st) {
 }
 
 void ms_launch_forward(int W, const MsParams &p, int level, cudaStream_t st) {
-    const int g = item_blocks(p);
+    const int g = item_blocks(p, 3);
     if (g == 0) return;
     BCGB_DISPATCH_W(W, (k_forward<kW><<<g, kBlock, 0, st>>>(p, level)));
 }
 
 void ms_launch_backward(int W, const MsParams &p, int level, cudaStream_t st) {
-    const int g = item_blocks(p);
+    const int g = item_blocks(p, 4);
     if (g == 0) return;
     BCGB_DISPATCH_W(W, (k_backward<kW><<<g, kBlock, 0, st>>>(p, level)));
 }
 
 void ms_launch_hash(int W, const MsParams &p, int nlevels, cudaStream_t st) {
-    int gx = (p.n + kWarps - 1) / kWarps;
-    const int cap = (4 * sm_count() + W - 1) / W;
+    int gx = (p.n + 4 * kWarps - 1) / (4 * kWarps);
+    const int cap = (8 * sm_count() + W - 1) / W;
     gx = gx > cap ? cap : gx;
     gx = gx < 1 ? 1 : gx;
     BCGB_DISPATCH_W(W, (k_hash<kW><<<dim3(gx, kW), kBlock, 0, st>>>(p, nlevels)));

@@ -1,0 +1,42 @@
+// weighted.cuh -- parameters of the weighted (integer delta-stepping) path.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "bc_internal.cuh"
+
+namespace bcgb {
+
+constexpr int kMaxRing = 4096;  // bucket ring size limit: max weight < kMaxRing
+
+struct WParams {
+    int32_t n;
+    int32_t K;     // ring size (> max weight)
+    int32_t C;     // entry capacity of one bucket
+    int32_t dmax;  // bound on any distance (n * max weight), a loop guard
+    const int32_t *row_ptr;
+    const int32_t *col;
+    const int32_t *w;
+    const int32_t *sources;  // this wave's sources
+    int32_t *dist;           // [wave][n]
+    uint64_t *sigma;         // [wave][n]
+    float *cval;             // [wave][n]
+    int32_t *order;          // [wave][n] settle order
+    int32_t *grp;            // [wave][n+1] start of each distinct-distance group in order
+    int32_t *slots;          // [wave][K][C] bucket entries
+    float *delta_rows;       // [wave][n] delta_s*(v) per source (null: forward only)
+    uint64_t *h_sigma;       // per-source summaries, indexed by wave position (or null)
+    uint64_t *h_dist;
+    int64_t *dist_sum;
+    int64_t *reach;
+    uint64_t *rows_sigma;    // optional rows [wave][n]
+    int32_t *rows_dist;
+    DevCtl *ctl;
+};
+
+void w_launch_wave(const WParams &p, int nsrc, cudaStream_t st);
+void w_launch_reduce(const float *rows, int nrows, int n, double *bc, int sms, cudaStream_t st);
+
+}  // namespace bcgb

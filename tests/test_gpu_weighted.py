@@ -1,0 +1,118 @@
+"""GPU parity of the weighted path (integer buckets, tie-aware sigma) against
+the oracle's binary-heap Dijkstra Brandes."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0809_1906_gb300 import graphs as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nat():
+    from paper_0809_1906_gb300 import native
+    native.load()
+    return native
+
+
+def assert_bc_close(got, ref, n, what=""):
+    tol = np.maximum(1e-5 * np.abs(ref), 1e-6 * max(n, 1))
+    err = np.abs(got - ref)
+    bad = np.nonzero(err > tol)[0]
+    assert bad.size == 0, f"{what}: {bad.size} off, worst {err.max():.3e} (rel {np.max(err / np.maximum(np.abs(ref), 1e-30)):.2e})"
+    return float(np.max(err / np.maximum(np.abs(ref), 1.0)))
+
+
+def check(nat, g, sources=None, batch=0, rows=8):
+    ref = oracle.bc(g, sources)
+    with nat.Graph.from_csr(g) as h:
+        h.run(sources, batch=batch)
+        got, code, _ = h.result()
+        ns = g.n if sources is None else len(sources)
+        hs = h.source_hashes(ns)
+        assert np.array_equal(hs["hash_sigma"], ref["hash_sigma"]), g.name
+        assert np.array_equal(hs["hash_dist"], ref["hash_dist"]), g.name
+        assert np.array_equal(hs["reach"], ref["reach"]), g.name
+        assert code == (nat.BC_WARN_SIGMA_OVERFLOW if ref["flags"] & 1 else nat.BC_OK)
+        rel = assert_bc_close(got, ref["bc"], g.n, g.name)
+        if rows:
+            src = np.arange(g.n, dtype=np.int32) if sources is None else np.asarray(sources, np.int32)
+            pick = src[:rows]
+            sig, dist, _ = h.forward_rows(pick)
+            for i, s in enumerate(pick.tolist()):
+                o = oracle.source(g, s, with_delta=False)
+                assert np.array_equal(dist[i], o["dist"].astype(np.int32)), (g.name, s)
+                assert np.array_equal(sig[i], o["sigma"]), (g.name, s)
+    return rel
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_small_weighted_ties(nat, seed):
+    n = [9, 20, 50, 120, 333, 600, 1000, 64][seed]
+    g = G.random_small(n, min(0.5, 4.0 / n), 1200 + seed, wmax=3, connect=seed % 3 != 0)
+    check(nat, g, batch=[0, 1, 7, 64][seed % 4])
+
+
+def test_uniform_weight_equals_unweighted(nat):
+    g1 = G.grid_graph(20)
+    g5 = G.grid_graph(20, w=5)
+    with nat.Graph.from_csr(g1) as h1, nat.Graph.from_csr(g5) as h5:
+        h1.run()
+        h5.run()
+        a, _, _ = h1.result()
+        b, _, _ = h5.result()
+    assert np.allclose(a, b, rtol=2e-5)
+
+
+def test_subgrid64_all_sources(nat):
+    """Induced 64x64 block of the 512x512 long-range grid, every source."""
+    g = G.induced_subgrid(G.grid_longrange(), 512, 64)
+    rel = check(nat, g)
+    print(f"subgrid64 max rel err {rel:.2e}")
+
+
+def test_grid512_sampled_sources(nat):
+    """Full 512x512 grid + 5% long-range edges, w ~ U{1..100}: the launch
+    configuration of the full run on 4096 sampled sources, checked on
+    per-source hashes of a sample, BC over 48 sources, and the identity
+    sum_v delta = sum_t ... via reach."""
+    g = G.grid_longrange()
+    src = G.sample_sources(g.n, 4096, 33)
+    with nat.Graph.from_csr(g) as h:
+        h.run(src)
+        got, code, _ = h.result()
+        hs = h.source_hashes(src.size)
+        assert code == nat.BC_OK
+        pick = np.arange(0, 4096, 256)
+        ref = oracle.bc(g, src[pick])
+        assert np.array_equal(hs["hash_sigma"][pick], ref["hash_sigma"])
+        assert np.array_equal(hs["hash_dist"][pick], ref["hash_dist"])
+        assert np.all(hs["reach"] == g.n)
+        sub = src[:48]
+        h.run(sub)
+        got, _, _ = h.result()
+        rel = assert_bc_close(got, oracle.bc(g, sub)["bc"], g.n, "grid512 48 sources")
+        print(f"grid512 max rel err {rel:.2e}")
+
+
+def test_weighted_overflow_flag(nat):
+    g = G.grid_graph(35, w=2)
+    with nat.Graph.from_csr(g) as h:
+        sig, dist, code = h.forward_rows(np.array([0], np.int32))
+    assert code == nat.BC_WARN_SIGMA_OVERFLOW
+    assert int(sig[0, -1]) == math.comb(68, 34) % (1 << 64) and dist[0, -1] == 136
+
+
+def test_weight_limit(nat):
+    g = G.path_graph(3)
+    big = G.csr_from_edges(3, [0, 1], [1, 2], [5000, 1])
+    with nat.Graph.from_csr(big) as h:
+        with pytest.raises(nat.BcError) as e:
+            h.run()
+        assert e.value.code == nat.BC_ERR_UNSUPPORTED
+    with pytest.raises(nat.BcError) as e:
+        nat.Graph(3, g.row_ptr, g.col, np.array([1, 0, 0, 1], np.int32))
+    assert e.value.code == nat.BC_ERR_WEIGHT
