@@ -186,6 +186,36 @@ int64_t bc_launch_count(const bc_graph *g);
 /* Vertex and undirected edge counts of a graph handle. */
 int bc_graph_size(const bc_graph *g, int32_t *n, int64_t *m, int32_t *weighted);
 
+/*
+ * Many graphs in one persistent launch: exact all-sources betweenness of k
+ * independent unweighted graphs (the paper's definitions, every vertex of
+ * every graph a source).
+ *
+ * bc_many_create  builds the plan: work items (graph, range of source
+ *                 batches), ordered longest first and taken by CTAs from an
+ *                 atomic queue; per-CTA workspaces; the reset and the
+ *                 persistent kernel captured once into a CUDA graph.
+ *                 graphs: k unweighted handles from bc_create_graph, owned by
+ *                 the caller and kept alive while the plan exists.
+ *                 opt->batch: sources per batch, 32 or 64 (0 = 32).
+ * bc_many_run     replays the captured graph on cuda_stream (asynchronous).
+ *                 Each graph's BC lands in its own handle: read it with
+ *                 bc_result(graphs[i], ...) after bc_many_result.
+ * bc_many_result  synchronises; a graph deeper than the launch's level
+ *                 capacity (64 levels) is re-run with bc_run on the same
+ *                 stream; *rerun (may be NULL) receives how many were.
+ *                 Returns BC_OK or BC_WARN_SIGMA_OVERFLOW, or an error.
+ * bc_run_many     create + run + result + destroy in one call.
+ * Errors: BC_ERR_ARG, BC_ERR_UNSUPPORTED (a weighted handle), BC_ERR_OOM,
+ * BC_ERR_CUDA, BC_ERR_STATE.
+ */
+typedef struct bc_many bc_many;
+int bc_many_create(bc_graph *const *graphs, int32_t k, const bc_options *opt, bc_many **out);
+int bc_many_run(bc_many *plan, void *cuda_stream);
+int bc_many_result(bc_many *plan, uint32_t *status_flags, int32_t *rerun);
+void bc_many_destroy(bc_many *plan);
+int bc_run_many(bc_graph *const *graphs, int32_t k, const bc_options *opt, void *cuda_stream);
+
 /* Free the handle and its device memory. NULL is ignored. */
 void bc_destroy_graph(bc_graph *g);
 

@@ -15,6 +15,7 @@
 #include "plain.cuh"
 #include "sched.cuh"
 #include "weighted.cuh"
+#include "many.cuh"
 
 namespace {
 
@@ -739,5 +740,247 @@ const char *bc_status_string(int status) {
 }
 
 const char *bc_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"
+
+struct bc_many {
+    std::vector<bc_graph *> graphs;
+    int W = 1, grid = 0, Lcap = 64;
+    int32_t nitems = 0;
+    DevBuf<bcgb::ManyGraph> d_graphs;
+    DevBuf<bcgb::ManyItem> d_items;
+    DevBuf<unsigned> queue, arrive, capped;
+    DevBuf<double> partial;
+    DevBuf<uint64_t> sigma;
+    DevBuf<float> cval;
+    DevBuf<uint32_t> F, V, ufr;
+    bcgb::DevCtl *ctl = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool ran = false;
+};
+
+namespace {
+
+void free_many(bc_many *m) {
+    if (m->exec) cudaGraphExecDestroy(m->exec);
+    if (m->graph) cudaGraphDestroy(m->graph);
+    m->d_graphs.release();
+    m->d_items.release();
+    m->queue.release();
+    m->arrive.release();
+    m->capped.release();
+    m->partial.release();
+    m->sigma.release();
+    m->cval.release();
+    m->F.release();
+    m->V.release();
+    m->ufr.release();
+    if (m->ctl) cudaFree(m->ctl);
+    delete m;
+}
+
+// Work items of the many-graph launch: each graph's source batches, split
+// into several items when one graph alone is more than half a CTA's fair
+// share of the total, then sorted by decreasing cost (LPT).
+int build_many(bc_many *m, const bc_options *opt) {
+    const int B = 32 * m->W;
+    struct GInfo {
+        int nb;
+        double cost;
+    };
+    std::vector<GInfo> info(m->graphs.size());
+    double total = 0.0;
+    int nmax = 1;
+    for (size_t i = 0; i < m->graphs.size(); ++i) {
+        const bc_graph *g = m->graphs[i];
+        info[i].nb = (g->n + B - 1) / B;
+        info[i].cost = (double)info[i].nb * (double)(g->n + g->narcs + 1);
+        total += info[i].cost;
+        nmax = std::max(nmax, g->n);
+    }
+    m->grid = bcgb::many_blocks_per_sm(m->W) * sm_count_host();
+    const double share = std::max(1.0, total / (2.0 * m->grid));
+    struct Item {
+        bcgb::ManyItem it;
+        double cost;
+    };
+    std::vector<Item> items;
+    std::vector<bcgb::ManyGraph> gd(m->graphs.size());
+    int64_t part_off = 0;
+    for (size_t i = 0; i < m->graphs.size(); ++i) {
+        const bc_graph *g = m->graphs[i];
+        const int nb = info[i].nb;
+        int q = (int)std::min<double>(nb, std::max(1.0, std::ceil(info[i].cost / share)));
+        if (nb == 0) q = 0;
+        gd[i].n = g->n;
+        gd[i].nitems = std::max(q, 1);
+        gd[i].part_off = q > 1 ? part_off : 0;
+        gd[i].row_ptr = g->row_ptr.p;
+        gd[i].col = g->col.p;
+        gd[i].bc = g->bc.p;
+        if (q > 1) part_off += (int64_t)q * g->n;
+        for (int k = 0; k < q; ++k) {
+            Item x;
+            x.it.graph = (int32_t)i;
+            x.it.batch_lo = (int32_t)((int64_t)nb * k / q);
+            x.it.batch_hi = (int32_t)((int64_t)nb * (k + 1) / q);
+            x.it.part = k;
+            x.cost = info[i].cost * (x.it.batch_hi - x.it.batch_lo) / nb;
+            items.push_back(x);
+        }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) { return a.cost > b.cost; });
+    std::vector<bcgb::ManyItem> hit(items.size());
+    for (size_t i = 0; i < items.size(); ++i) hit[i] = items[i].it;
+    m->nitems = (int32_t)hit.size();
+    m->Lcap = 64;
+    const size_t nw32 = ((size_t)nmax + 31) / 32;
+    const size_t G = (size_t)m->grid;
+    CK(m->d_graphs.ensure(gd.size()));
+    CK(cudaMemcpy(m->d_graphs.p, gd.data(), gd.size() * sizeof(gd[0]), cudaMemcpyHostToDevice));
+    CK(m->d_items.ensure(hit.size()));
+    if (!hit.empty()) CK(cudaMemcpy(m->d_items.p, hit.data(), hit.size() * sizeof(hit[0]), cudaMemcpyHostToDevice));
+    CK(m->queue.ensure(1));
+    CK(m->arrive.ensure(gd.size()));
+    CK(m->capped.ensure(gd.size()));
+    CK(cudaMemset(m->arrive.p, 0, gd.size() * sizeof(unsigned)));
+    CK(m->partial.ensure((size_t)std::max<int64_t>(part_off, 1)));
+    CK(m->sigma.ensure(G * nmax * B));
+    CK(m->cval.ensure(G * nmax * B));
+    CK(m->F.ensure(G * m->Lcap * nmax * m->W));
+    CK(m->V.ensure(G * 2 * nmax * m->W));
+    CK(m->ufr.ensure(G * m->Lcap * nw32));
+    CK(cudaMalloc((void **)&m->ctl, sizeof(bcgb::DevCtl)));
+
+    bcgb::ManyParams p{};
+    p.ngraphs = (int32_t)gd.size();
+    p.nitems = m->nitems;
+    p.nmax = nmax;
+    p.nw32max = (int32_t)nw32;
+    p.Lcap = m->Lcap;
+    p.graphs = m->d_graphs.p;
+    p.items = m->d_items.p;
+    p.queue = m->queue.p;
+    p.arrive = m->arrive.p;
+    p.capped = m->capped.p;
+    p.partial = m->partial.p;
+    p.sigma = m->sigma.p;
+    p.cval = m->cval.p;
+    p.F = m->F.p;
+    p.V = m->V.p;
+    p.ufr = m->ufr.p;
+    p.ctl = m->ctl;
+    // capture the reset + persistent launch once; every run replays it
+    cudaStream_t cap = nullptr;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->queue.p, 0, sizeof(unsigned), cap);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->capped.p, 0, gd.size() * sizeof(unsigned), cap);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->ctl, 0, sizeof(bcgb::DevCtl), cap);
+    if (e == cudaSuccess && m->nitems > 0) {
+        bcgb::many_launch(m->W, p, m->grid, cap);
+        e = cudaGetLastError();
+    }
+    cudaGraph_t gr = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cap, &gr);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&m->exec, gr, 0);
+    m->graph = gr;
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return fail(BC_ERR_CUDA, std::string("many-graph capture: ") + cudaGetErrorString(e));
+    return BC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bc_many_create(bc_graph *const *graphs, int32_t k, const bc_options *opt, bc_many **out) {
+    g_err.clear();
+    if (!out || (k > 0 && !graphs) || k < 0) return fail(BC_ERR_ARG, "bad arguments");
+    *out = nullptr;
+    const int b = (opt && opt->batch) ? opt->batch : 32;
+    if (b != 32 && b != 64) return fail(BC_ERR_ARG, "many-graph batch must be 32 or 64");
+    bc_many *m = new (std::nothrow) bc_many();
+    if (!m) return fail(BC_ERR_OOM, "host allocation failed");
+    m->W = b / 32;
+    for (int32_t i = 0; i < k; ++i) {
+        if (!graphs[i] || graphs[i]->weighted) {
+            free_many(m);
+            return fail(BC_ERR_UNSUPPORTED, "bc_many takes unweighted graph handles");
+        }
+        m->graphs.push_back(graphs[i]);
+    }
+    const int r = build_many(m, opt);
+    if (r) {
+        free_many(m);
+        return r;
+    }
+    *out = m;
+    return BC_OK;
+}
+
+int bc_many_run(bc_many *m, void *cuda_stream) {
+    g_err.clear();
+    if (!m) return fail(BC_ERR_ARG, "plan is NULL");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (m->exec) CK(cudaGraphLaunch(m->exec, st));
+    for (bc_graph *g : m->graphs) {
+        g->has_run = true;
+        g->has_hash = false;
+        g->last_stream = st;
+        g->last_nsrc = g->n;
+        g->launches = 0;
+    }
+    m->last_stream = st;
+    m->ran = true;
+    return BC_OK;
+}
+
+int bc_many_result(bc_many *m, uint32_t *status_flags, int32_t *rerun) {
+    g_err.clear();
+    if (!m) return fail(BC_ERR_ARG, "plan is NULL");
+    if (!m->ran) return fail(BC_ERR_STATE, "no bc_many_run");
+    uint32_t status = 0;
+    std::vector<unsigned> capped(m->graphs.size());
+    CK(cudaMemcpyAsync(&status, &m->ctl->status, 4, cudaMemcpyDeviceToHost, m->last_stream));
+    if (!capped.empty())
+        CK(cudaMemcpyAsync(capped.data(), m->capped.p, capped.size() * 4, cudaMemcpyDeviceToHost, m->last_stream));
+    CK(cudaStreamSynchronize(m->last_stream));
+    int32_t nre = 0;
+    for (size_t i = 0; i < capped.size(); ++i) {
+        if (!capped[i]) continue;
+        bc_options o{};
+        o.batch = 32;
+        const int r = bc_run(m->graphs[i], nullptr, 0, &o, m->last_stream);
+        if (r < 0) return r;
+        uint32_t st2 = 0;
+        const int r2 = bc_result(m->graphs[i], nullptr, &st2);
+        if (r2 < 0) return r2;
+        status |= st2;
+        ++nre;
+    }
+    if (rerun) *rerun = nre;
+    if (status_flags) *status_flags = status;
+    return (status & BC_STATUS_SIGMA_OVERFLOW) ? BC_WARN_SIGMA_OVERFLOW : BC_OK;
+}
+
+void bc_many_destroy(bc_many *m) {
+    if (!m) return;
+    cudaDeviceSynchronize();
+    free_many(m);
+}
+
+int bc_run_many(bc_graph *const *graphs, int32_t k, const bc_options *opt, void *cuda_stream) {
+    bc_many *m = nullptr;
+    int r = bc_many_create(graphs, k, opt, &m);
+    if (r) return r;
+    r = bc_many_run(m, cuda_stream);
+    if (!r) r = bc_many_result(m, nullptr, nullptr);
+    bc_many_destroy(m);
+    return r;
+}
 
 }  // extern "C"

@@ -1,0 +1,196 @@
+// many.cu -- exact all-sources betweenness of many small graphs in one
+// persistent launch (bc_many_* / bc_run_many).
+//
+// Work item = (graph, range of source batches). Items are ordered by
+// decreasing cost (longest-processing-time first) and CTAs take them from an
+// atomic queue. A CTA runs its item's batches alone: the same per-vertex
+// forward and backward steps as the one-graph path (msbfs_body.cuh), with the
+// CTA's warps striding over vertices and __syncthreads between levels, so
+// no level ever waits on another CTA. Sources are the vertices in order,
+// B = 32*W per batch.
+//
+// BC of a graph handled by one item is written by that CTA alone. A large
+// graph is split into several items; each writes its own partial vector and
+// the last item to finish (atomic arrival counter) adds the partials in item
+// order into the graph's BC. Every result is deterministic.
+//
+// A graph deeper than the level capacity is flagged and left to the caller
+// (bc_many_status reports it; the host re-runs it with bc_run).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "bc_internal.cuh"
+#include "many.cuh"
+#include "msbfs_body.cuh"
+
+namespace bcgb {
+namespace {
+
+constexpr int kMBlock = 256;
+constexpr int kMWarps = kMBlock / 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int W>
+__global__ void __launch_bounds__(kMBlock, 2) k_many(const ManyParams p) {
+    constexpr int B = 32 * W;
+    __shared__ int s_item;
+    __shared__ int s_last;
+    __shared__ int32_t s_u[kMWarps][32];
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    uint64_t *sigma = p.sigma + (size_t)blockIdx.x * p.nmax * B;
+    float *cval = p.cval + (size_t)blockIdx.x * p.nmax * B;
+    uint32_t *F = p.F + (size_t)blockIdx.x * p.Lcap * p.nmax * W;
+    uint32_t *V = p.V + (size_t)blockIdx.x * 2 * p.nmax * W;
+    uint32_t *ufr = p.ufr + (size_t)blockIdx.x * p.Lcap * p.nw32max;
+    bool ovf = false;
+    uint32_t arcs = 0;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = (int)atomicAdd(p.queue, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= p.nitems) break;
+        const ManyItem item = p.items[it];
+        const ManyGraph gd = p.graphs[item.graph];
+        const int n = gd.n;
+        const size_t nW = (size_t)n * W;
+        const int nw32 = (n + 31) / 32;
+        const bool split = gd.nitems > 1;
+        double *target = split ? p.partial + gd.part_off + (size_t)item.part * n : gd.bc;
+        for (int v = tid; v < n; v += kMBlock) target[v] = 0.0;
+        bool capped = false;
+
+        for (int bt = item.batch_lo; bt < item.batch_hi && !capped; ++bt) {
+            const int s0 = bt * B;
+            const int nb = min(B, n - s0);
+            for (size_t i = tid; i < nW; i += kMBlock) {
+                F[i] = 0u;
+                V[i] = 0u;
+            }
+            for (int i = tid; i < p.Lcap * nw32; i += kMBlock) ufr[i] = 0u;
+            __syncthreads();
+            for (int b = tid; b < nb; b += kMBlock) {  // d(s,s) = 0, sigma_s(s) = 1
+                const int s = s0 + b;
+                F[(size_t)s * W + (b >> 5)] |= 1u << (b & 31);  // one source per (s, b): no race
+                atomicOr(ufr + (s >> 5), 1u << (s & 31));
+                sigma[(size_t)s * B + b] = 1ull;
+            }
+            __syncthreads();
+            // forward levels
+            int L = 0;
+            for (int l = 0;; ++l) {
+                if (l + 1 >= p.Lcap) {
+                    capped = true;
+                    break;
+                }
+                const uint32_t *Fl = F + (size_t)l * nW;
+                uint32_t *Fn = F + (size_t)(l + 1) * nW;
+                const uint32_t *ufl = ufr + (size_t)l * nw32;
+                uint32_t *ufn = ufr + (size_t)(l + 1) * nw32;
+                const uint32_t *Vin = V + (size_t)(l & 1) * nW;
+                uint32_t *Vout = V + (size_t)((l + 1) & 1) * nW;
+                bool produced = false;
+                for (int v = wib; v < n; v += kMWarps) {
+                    uint32_t U[W], a[W], f[W];
+                    body::load_row<W>(Vin + (size_t)v * W, a);
+                    body::load_row<W>(Fl + (size_t)v * W, f);
+                    uint32_t anyU = 0;
+#pragma unroll
+                    for (int j = 0; j < W; ++j) {
+                        const uint32_t vis = a[j] | f[j];
+                        if (lane == j) Vout[(size_t)v * W + j] = vis;
+                        U[j] = ~vis & body::valid_word(nb, j);
+                        anyU |= U[j];
+                    }
+                    if (anyU == 0u) {
+                        if (lane < W) Fn[(size_t)v * W + lane] = 0u;
+                        continue;
+                    }
+                    uint64_t acc[W];
+                    uint32_t nf[W];
+#pragma unroll
+                    for (int j = 0; j < W; ++j) {
+                        acc[j] = 0ull;
+                        nf[j] = 0u;
+                    }
+                    body::fwd_sum<W>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufl, Fl, sigma, U, s_u[wib], lane,
+                                     acc, nf, ovf, arcs);
+                    produced |= body::store_next<W>(sigma, Fn, ufn, v, acc, nf, lane);
+                }
+                if (!__syncthreads_or(produced)) {
+                    L = l;
+                    break;
+                }
+            }
+            if (capped) break;
+            // backward levels (Theorem 1.1), BC into this item's target
+            for (int l = L; l >= 1; --l) {
+                const uint32_t *Fl = F + (size_t)l * nW;
+                const uint32_t *Fs = F + (size_t)(l + 1) * nW;
+                const uint32_t *ufs = ufr + (size_t)(l + 1) * nw32;
+                for (int v = wib; v < n; v += kMWarps) {
+                    uint32_t f[W];
+                    body::load_row<W>(Fl + (size_t)v * W, f);
+                    uint32_t anyf = 0;
+#pragma unroll
+                    for (int j = 0; j < W; ++j) anyf |= f[j];
+                    if (anyf == 0u) continue;
+                    float S[W];
+#pragma unroll
+                    for (int j = 0; j < W; ++j) S[j] = 0.0f;
+                    body::bwd_sum<W>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufs, Fs, cval, f, s_u[wib], lane, S);
+                    body::finalize_dep<W>(sigma, cval, target, v, f, S, lane);
+                }
+                __syncthreads();
+            }
+        }
+        if (capped && tid == 0) p.capped[item.graph] = 1u;
+        if (!split) continue;
+        // last item of a split graph adds the partials in item order
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) s_last = atomicAdd(p.arrive + item.graph, 1u) == (unsigned)(gd.nitems - 1);
+        __syncthreads();
+        if (!s_last) continue;
+        __threadfence();
+        const double *part = p.partial + gd.part_off;
+        for (int v = tid; v < n; v += kMBlock) {
+            double acc = 0.0;
+            for (int q = 0; q < gd.nitems; ++q) acc += __ldcg(part + (size_t)q * n + v);
+            gd.bc[v] = acc;
+        }
+        if (tid == 0) p.arrive[item.graph] = 0u;
+    }
+    const bool wovf = __any_sync(kFull, ovf);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) arcs += __shfl_xor_sync(kFull, arcs, off);
+    if (lane == 0) {
+        if (wovf) atomicOr(&p.ctl->status, BC_STATUS_SIGMA_OVERFLOW);
+        if (arcs) atomicAdd(&p.ctl->dag_arcs, (unsigned long long)arcs);
+    }
+}
+
+}  // namespace
+
+int many_blocks_per_sm(int W) {
+    int nb = 0;
+    if (W == 1)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_many<1>, kMBlock, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_many<2>, kMBlock, 0);
+    return nb < 1 ? 1 : nb;
+}
+
+void many_launch(int W, const ManyParams &p, int grid, cudaStream_t st) {
+    if (W == 1)
+        k_many<1><<<grid, kMBlock, 0, st>>>(p);
+    else
+        k_many<2><<<grid, kMBlock, 0, st>>>(p);
+}
+
+}  // namespace bcgb

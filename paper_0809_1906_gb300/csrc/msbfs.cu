@@ -16,16 +16,16 @@
 //     into the backward step; the source itself (level 0) is never summed.
 //
 // Thread mapping: one warp per work item (a vertex, or a chunk of a
-// high-degree vertex's arcs). Lanes first probe 32 arcs at once against the
-// union-frontier bitmap (one bit per vertex, cache resident) and the
-// neighbour's frontier words; then, for each neighbour that contributes, the
-// warp switches to lanes-over-sources and reads the neighbour's sigma (or c)
-// row with coalesced 256-byte accesses. Chunks of one vertex combine through
-// partial buffers: the last chunk to arrive (atomic counter) sums them in
-// chunk order, so every result is deterministic and no wait is needed.
+// high-degree vertex's arcs); the per-vertex steps (probe, bit-transposed
+// walk, stores) are in msbfs_body.cuh. Warps are persistent and stride over
+// the items, which are sorted by decreasing degree. Chunks of one vertex
+// combine through partial buffers: the last chunk to arrive (atomic counter)
+// sums them in chunk order, so every result is deterministic and no wait is
+// needed.
 #include <cuda_runtime.h>
 
 #include "bc_internal.cuh"
+#include "msbfs_body.cuh"
 
 namespace bcgb {
 namespace {
@@ -33,56 +33,8 @@ namespace {
 constexpr int kBlock = 256;
 constexpr int kWarps = kBlock / 32;
 constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ uint32_t valid_word(int nb, int j) {
-    const int lo = 32 * j;
-    if (nb >= lo + 32) return 0xffffffffu;
-    if (nb <= lo) return 0u;
-    return (1u << (nb - lo)) - 1u;
-}
-
-template <int W>
-__device__ __forceinline__ void load_row(const uint32_t *__restrict__ p, uint32_t (&w)[W]) {
-    if constexpr (W % 4 == 0) {
-        const uint4 *q = reinterpret_cast<const uint4 *>(p);
-#pragma unroll
-        for (int i = 0; i < W / 4; ++i) {
-            const uint4 t = __ldg(q + i);
-            w[4 * i] = t.x;
-            w[4 * i + 1] = t.y;
-            w[4 * i + 2] = t.z;
-            w[4 * i + 3] = t.w;
-        }
-    } else if constexpr (W % 2 == 0) {
-        const uint2 *q = reinterpret_cast<const uint2 *>(p);
-#pragma unroll
-        for (int i = 0; i < W / 2; ++i) {
-            const uint2 t = __ldg(q + i);
-            w[2 * i] = t.x;
-            w[2 * i + 1] = t.y;
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < W; ++i) w[i] = __ldg(p + i);
-    }
-}
-
-// Write sigma and frontier words of a vertex whose level-(l+1) sums are final.
-template <int W>
-__device__ __forceinline__ bool store_next(const MsParams &p, int v, const uint64_t (&acc)[W],
-                                           const uint32_t (&nf)[W], uint32_t *Fn, uint32_t *ufn,
-                                           int lane) {
-    constexpr int B = 32 * W;
-    uint32_t any = 0;
-#pragma unroll
-    for (int j = 0; j < W; ++j) {
-        any |= nf[j];
-        if (lane == j) Fn[(size_t)v * W + j] = nf[j];
-        if ((nf[j] >> lane) & 1u) p.sigma[(size_t)v * B + 32 * j + lane] = acc[j];
-    }
-    if (any != 0 && lane == 0) atomicOr(ufn + (v >> 5), 1u << (v & 31));
-    return any != 0;
-}
+using body::load_row;
+using body::valid_word;
 
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
@@ -120,52 +72,6 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
         p.ctl->seq = p.seq;
         atomicExch(&p.ctl->blocks_done, 0u);
     }
-}
-
-// Warp-wide 32x32 bit transpose: lane k holds row k; returns column `lane`
-// (bit k of the result = bit `lane` of lane k's input). Five exchange steps,
-// each swapping the off-diagonal s x s blocks of every 2s x 2s block.
-__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
-#pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) {
-        const uint32_t M = s == 16 ? 0x0000FFFFu : s == 8 ? 0x00FF00FFu : s == 4 ? 0x0F0F0F0Fu
-                         : s == 2 ? 0x33333333u : 0x55555555u;
-        const uint32_t y = __shfl_xor_sync(kFull, x, s);
-        x = (lane & s) ? ((x & ~M) | ((y >> s) & M)) : ((x & M) | ((y & M) << s));
-    }
-    return x;
-}
-
-// One 32-arc chunk of a vertex's row: lanes probe one arc each; lane k ends
-// with its neighbour u_k (in s_u) and masks m_k[j] = frontier words of u_k
-// AND `want` (zero for arcs that cannot contribute). Returns the ballot of
-// contributing lanes.
-template <int W>
-__device__ __forceinline__ unsigned probe_chunk(const int32_t *__restrict__ col, int e, int end,
-                                                const uint32_t *__restrict__ ufr, const uint32_t *__restrict__ Fx,
-                                                const uint32_t (&want)[W], uint32_t (&m)[W], int32_t *s_u,
-                                                int lane) {
-    int u = 0;
-    bool cand = false;
-#pragma unroll
-    for (int j = 0; j < W; ++j) m[j] = 0u;
-    if (e < end) {
-        u = __ldg(col + e);
-        if ((__ldg(ufr + (u >> 5)) >> (u & 31)) & 1u) {
-            uint32_t fu[W];
-            load_row<W>(Fx + (size_t)u * W, fu);
-            uint32_t any = 0;
-#pragma unroll
-            for (int j = 0; j < W; ++j) {
-                m[j] = fu[j] & want[j];
-                any |= m[j];
-            }
-            cand = any != 0u;
-        }
-    }
-    s_u[lane] = u;
-    __syncwarp();
-    return __ballot_sync(kFull, cand);
 }
 
 template <int W>
@@ -227,32 +133,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
             acc[j] = 0ull;
             nf[j] = 0u;
         }
-        for (int e0 = beg; e0 < end; e0 += 32) {
-            uint32_t m[W];
-            const unsigned bal = probe_chunk<W>(p.col, e0 + lane, end, ufl, Fl, U, m, s_u[wib], lane);
-            if (bal) {
-#pragma unroll
-                for (int j = 0; j < W; ++j) {
-                    if (__ballot_sync(kFull, m[j] != 0u) == 0u) continue;
-                    // t: the chunk's neighbours that are predecessors for source 32j + lane
-                    uint32_t t = transpose32(m[j], lane);
-                    nf[j] |= __ballot_sync(kFull, t != 0u);
-                    arcs += __popc(t);
-                    const uint64_t *sj = p.sigma + 32 * j + lane;
-                    while (t) {
-                        const int k = __ffs(t) - 1;
-                        t &= t - 1;
-                        const uint64_t x = __ldg(sj + (size_t)s_u[wib][k] * B);
-                        const uint64_t y = acc[j] + x;
-                        ovf |= y < x;
-                        acc[j] = y;
-                    }
-                }
-            }
-            __syncwarp();
-        }
+        body::fwd_sum<W>(p.col, beg, end, ufl, Fl, p.sigma, U, s_u[wib], lane, acc, nf, ovf, arcs);
         if (slot < 0) {
-            produced |= store_next<W>(p, v, acc, nf, Fn, ufn, lane);
+            produced |= body::store_next<W>(p.sigma, Fn, ufn, v, acc, nf, lane);
             continue;
         }
         uint64_t *pp = p.part + (size_t)slot * B + lane;
@@ -287,7 +170,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
                 nf[j] |= __ldcg(qm + j);
             }
         }
-        produced |= store_next<W>(p, v, acc, nf, Fn, ufn, lane);
+        produced |= body::store_next<W>(p.sigma, Fn, ufn, v, acc, nf, lane);
         if (lane == 0) p.cnt[first] = 0u;
     }
     const unsigned wovf = __ballot_sync(kFull, ovf);
@@ -331,26 +214,6 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
 }
 
 template <int W>
-__device__ __forceinline__ void finalize_dep(const MsParams &p, int v, const uint32_t (&f)[W],
-                                             const float (&S)[W], int lane) {
-    constexpr int B = 32 * W;
-    double sum = 0.0;
-#pragma unroll
-    for (int j = 0; j < W; ++j) {
-        if ((f[j] >> lane) & 1u) {
-            const size_t idx = (size_t)v * B + 32 * j + lane;
-            const float sg = __ull2float_rn(p.sigma[idx]);
-            const float d = sg * S[j];      // delta_s*(v) = sigma_s(v) * sum_w c_s(w)
-            p.cval[idx] = (1.0f + d) / sg;  // c_s(v) for the level above
-            sum += (double)d;
-        }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(kFull, sum, off);
-    if (lane == 0) p.bc[v] += sum;
-}
-
-template <int W>
 __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const int l) {
     constexpr int B = 32 * W;
     __shared__ int32_t s_u[kWarps][32];
@@ -375,27 +238,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
         float S[W];  // lane owns source 32j + lane
 #pragma unroll
         for (int j = 0; j < W; ++j) S[j] = 0.0f;
-        for (int e0 = beg; e0 < end; e0 += 32) {
-            uint32_t m[W];
-            const unsigned bal = probe_chunk<W>(p.col, e0 + lane, end, ufs, Fs, f, m, s_u[wib], lane);
-            if (bal) {
-#pragma unroll
-                for (int j = 0; j < W; ++j) {
-                    if (__ballot_sync(kFull, m[j] != 0u) == 0u) continue;
-                    // t: the chunk's neighbours w with v in P_s(w), s = source 32j + lane
-                    uint32_t t = transpose32(m[j], lane);
-                    const float *cj = p.cval + 32 * j + lane;
-                    while (t) {
-                        const int k = __ffs(t) - 1;
-                        t &= t - 1;
-                        S[j] += __ldg(cj + (size_t)s_u[wib][k] * B);
-                    }
-                }
-            }
-            __syncwarp();
-        }
+        body::bwd_sum<W>(p.col, beg, end, ufs, Fs, p.cval, f, s_u[wib], lane, S);
         if (slot < 0) {
-            finalize_dep<W>(p, v, f, S, lane);
+            body::finalize_dep<W>(p.sigma, p.cval, p.bc, v, f, S, lane);
             continue;
         }
         float *pp = reinterpret_cast<float *>(p.part) + (size_t)slot * B + lane;
@@ -417,7 +262,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
 #pragma unroll
             for (int j = 0; j < W; ++j) S[j] += __ldcg(q + 32 * j);
         }
-        finalize_dep<W>(p, v, f, S, lane);
+        body::finalize_dep<W>(p.sigma, p.cval, p.bc, v, f, S, lane);
         if (lane == 0) p.cnt[first] = 0u;
     }
 }
@@ -514,7 +359,13 @@ int sm_count() {
     return c;
 }
 
-int item_blocks(const MsParams &p, int per_sm) {
+// Persistent grid: as many blocks as fit on the GPU at once (occupancy of
+// the kernel instance), never more than the items need.
+template <class K>
+int item_blocks(const MsParams &p, K kernel) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
     const int need = (p.nitems + kWarps - 1) / kWarps;
     const int cap = per_sm * sm_count();
     return need < cap ? need : cap;
@@ -546,15 +397,13 @@ void ms_launch_init(int W, const MsParams &p, cudaStream_t st) {
 }
 
 void ms_launch_forward(int W, const MsParams &p, int level, cudaStream_t st) {
-    const int g = item_blocks(p, 3);
-    if (g == 0) return;
-    BCGB_DISPATCH_W(W, (k_forward<kW><<<g, kBlock, 0, st>>>(p, level)));
+    if (p.nitems == 0) return;
+    BCGB_DISPATCH_W(W, (k_forward<kW><<<item_blocks(p, k_forward<kW>), kBlock, 0, st>>>(p, level)));
 }
 
 void ms_launch_backward(int W, const MsParams &p, int level, cudaStream_t st) {
-    const int g = item_blocks(p, 4);
-    if (g == 0) return;
-    BCGB_DISPATCH_W(W, (k_backward<kW><<<g, kBlock, 0, st>>>(p, level)));
+    if (p.nitems == 0) return;
+    BCGB_DISPATCH_W(W, (k_backward<kW><<<item_blocks(p, k_backward<kW>), kBlock, 0, st>>>(p, level)));
 }
 
 void ms_launch_hash(int W, const MsParams &p, int nlevels, cudaStream_t st) {

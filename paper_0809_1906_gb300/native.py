@@ -46,7 +46,8 @@ KERNEL_NAMES = {0: "init", 1: "forward", 2: "backward", 3: "hash", 4: "plain"}
 # every entry point include/bc_gb300.h declares
 EXPORTS = ["bc_create_graph", "bc_run", "bc_result", "bc_source_hashes", "bc_forward_rows",
            "bc_kernel_time", "bc_run_stats", "bc_launch_count", "bc_graph_size", "bc_destroy_graph",
-           "bc_status_string", "bc_last_error"]
+           "bc_status_string", "bc_last_error",
+           "bc_many_create", "bc_many_run", "bc_many_result", "bc_many_destroy", "bc_run_many"]
 
 
 class BcError(RuntimeError):
@@ -95,6 +96,11 @@ def load(build_if_needed: bool = True, require_gpu: bool = True):
             "bc_destroy_graph": (None, [P]),
             "bc_status_string": (ctypes.c_char_p, [i32]),
             "bc_last_error": (ctypes.c_char_p, []),
+            "bc_many_create": (i32, [P, i32, P, ctypes.POINTER(P)]),
+            "bc_many_run": (i32, [P, P]),
+            "bc_many_result": (i32, [P, P, P]),
+            "bc_many_destroy": (None, [P]),
+            "bc_run_many": (i32, [P, i32, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -240,6 +246,48 @@ class Graph:
 
     def launch_count(self) -> int:
         return int(self.lib.bc_launch_count(self.handle))
+
+
+class ManyPlan:
+    """bc_many_create / bc_many_run / bc_many_result over Graph handles: all
+    sources of every graph in one persistent launch replayed from a CUDA graph."""
+
+    def __init__(self, graphs, batch: int = 32):
+        self.lib = load()
+        self.graphs = list(graphs)
+        arr = (ctypes.c_void_p * len(self.graphs))(*[g.handle.value for g in self.graphs])
+        self._arr = arr
+        h = ctypes.c_void_p()
+        opt = make_options(batch)
+        _check(self.lib.bc_many_create(arr, len(self.graphs), ctypes.byref(opt), ctypes.byref(h)),
+               "bc_many_create", allow_warn=False)
+        self.handle = h
+
+    def run(self, stream=None):
+        _check(self.lib.bc_many_run(self.handle, _stream_ptr(stream)), "bc_many_run")
+
+    def result(self):
+        fl = ctypes.c_uint32(0)
+        rr = ctypes.c_int32(0)
+        code = _check(self.lib.bc_many_result(self.handle, ctypes.byref(fl), ctypes.byref(rr)), "bc_many_result")
+        return code, fl.value, rr.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.bc_many_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def betweenness(g, sources=None, batch=0, flags=0, stream=None):
