@@ -187,6 +187,38 @@ int64_t bc_launch_count(const bc_graph *g);
 int bc_graph_size(const bc_graph *g, int32_t *n, int64_t *m, int32_t *weighted);
 
 /*
+ * bc_run_noalloc -- betweenness for callers that cannot allocate.
+ * The paper has no counterpart: this is a deployment variant of bc_run for
+ * callers that may not call cudaMalloc (a custom allocator or memory pool owns
+ * the device, a host process forbids allocation after start-up, a fixed
+ * memory footprint is required). It allocates nothing: its scratch is one
+ * file-scope __device__ array of BC_NOALLOC_SCRATCH_BYTES that every GPU on
+ * which the library is loaded holds until the process exits.
+ *   n            vertex count, 0 <= n <= BC_NOALLOC_MAX_N.
+ *   row_ptr      int32[n+1], col int32[row_ptr[n]]: DEVICE pointers to an
+ *                undirected CSR (both arcs of each edge; symmetry is not
+ *                checked here, as with BC_GRAPH_TRUST_INPUT). Unweighted.
+ *   sources      DEVICE int32[num_sources] (ids in [0, n), at most
+ *                BC_NOALLOC_MAX_N of them), or NULL for all vertices.
+ *   bc           DEVICE double[n]: receives the ordered-pair betweenness.
+ * Runs on cuda_stream and synchronises it (it reads each batch's depth).
+ * Returns BC_OK, BC_WARN_SIGMA_OVERFLOW, BC_ERR_ARG (sizes beyond the limits,
+ * NULL pointers, ids out of range), BC_ERR_UNSUPPORTED (a BFS deeper than
+ * BC_NOALLOC_MAX_LEVELS levels), BC_ERR_CUDA. No message is recorded for
+ * bc_last_error (that would allocate); use bc_status_string.
+ * The first call on a device looks up the array's device address for that
+ * device; make that first call before any stream capture. Every call on a
+ * device shares the one array and leaves its contents behind (each call
+ * clears what must start at zero): calls that overlap on the GPU race and
+ * must not be issued concurrently.
+ */
+#define BC_NOALLOC_MAX_N 16384
+#define BC_NOALLOC_MAX_LEVELS 62
+#define BC_NOALLOC_SCRATCH_BYTES (12u << 20)
+int bc_run_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *sources,
+                   int32_t num_sources, double *bc, void *cuda_stream);
+
+/*
  * Many graphs in one persistent launch: exact all-sources betweenness of k
  * independent unweighted graphs (the paper's definitions, every vertex of
  * every graph a source).

@@ -46,7 +46,7 @@ KERNEL_NAMES = {0: "init", 1: "forward", 2: "backward", 3: "hash", 4: "plain"}
 # every entry point include/bc_gb300.h declares
 EXPORTS = ["bc_create_graph", "bc_run", "bc_result", "bc_source_hashes", "bc_forward_rows",
            "bc_kernel_time", "bc_run_stats", "bc_launch_count", "bc_graph_size", "bc_destroy_graph",
-           "bc_status_string", "bc_last_error",
+           "bc_status_string", "bc_last_error", "bc_run_noalloc",
            "bc_many_create", "bc_many_run", "bc_many_result", "bc_many_destroy", "bc_run_many"]
 
 
@@ -96,6 +96,7 @@ def load(build_if_needed: bool = True, require_gpu: bool = True):
             "bc_destroy_graph": (None, [P]),
             "bc_status_string": (ctypes.c_char_p, [i32]),
             "bc_last_error": (ctypes.c_char_p, []),
+            "bc_run_noalloc": (i32, [i32, P, P, P, i32, P, P]),
             "bc_many_create": (i32, [P, i32, P, ctypes.POINTER(P)]),
             "bc_many_run": (i32, [P, P]),
             "bc_many_result": (i32, [P, P, P]),
