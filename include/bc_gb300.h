@@ -57,6 +57,7 @@ extern "C" {
 #define BC_STATUS_SIGMA_OVERFLOW 0x1u
 #define BC_STATUS_BOUNDS 0x2u
 #define BC_STATUS_LEVEL_CAP 0x4u /* internal: a batch needed more BFS levels (re-run automatically) */
+#define BC_STATUS_DENSE_TIMEOUT 0x8u /* a tensor-core pipeline wait gave up (bc_result returns BC_ERR_TIMEOUT) */
 
 /* ---- bc_create_graph flags --------------------------------------------- */
 #define BC_GRAPH_TRUST_INPUT 0x1u /* skip the host-side symmetry/duplicate check */
@@ -67,12 +68,15 @@ extern "C" {
 #define BC_PLAIN 0x4u        /* one source per launch sequence (the unbatched GPU Brandes) */
 #define BC_TIMING 0x8u       /* record CUDA events around every kernel launch (bc_kernel_time) */
 #define BC_NO_HASH 0x10u     /* skip the per-source summary values */
+#define BC_DENSE 0x20u       /* levels >= 1 as tensor-core products with the 0/1 adjacency matrix
+                                (Section 3.1.1); unweighted graphs with n <= 65536, batch 128 */
 
 /*
  * Run options. Zero-initialise and set what you need; bc_run(..., NULL, ...)
  * uses the same defaults.
  *   batch          sources per batch for the unweighted multi-source path:
- *                  32, 64, 128 or 256 (0 = 256).
+ *                  32, 64, 128 or 256 (0 = 256; BC_DENSE uses 128). For
+ *                  weighted graphs: sources per wave (0 = 4 per SM).
  *   flags          BC_* option bits above.
  *   chunk          arcs per work item for high-degree vertices (0 = 256).
  *   wait_limit_ms  bound on every host-side wait for device progress
@@ -168,7 +172,8 @@ int bc_forward_rows(bc_graph *g, const int32_t *sources, int32_t k, uint64_t *si
 #define BC_KERNEL_BACKWARD 2
 #define BC_KERNEL_HASH 3
 #define BC_KERNEL_PLAIN 4
-#define BC_KERNEL_KINDS 5
+#define BC_KERNEL_DENSE 5
+#define BC_KERNEL_KINDS 6
 int bc_kernel_time(bc_graph *g, int32_t kind, int64_t *launches, double *total_ms);
 
 /*

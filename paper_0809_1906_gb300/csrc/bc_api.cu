@@ -16,6 +16,7 @@
 #include "sched.cuh"
 #include "weighted.cuh"
 #include "many.cuh"
+#include "dense.cuh"
 
 namespace {
 
@@ -106,6 +107,12 @@ struct bc_graph {
 
     bcgb::PlainState plain;
 
+    // dense (tensor-core) levels: bf16 adjacency, limb matrix, TMA maps
+    int32_t npad = 0;
+    DevBuf<__nv_bfloat16> dA, dX;
+    DevBuf<bcgb::DenseCtl> dctl;
+    bcgb::DenseMaps maps{};
+
     // weighted path: per-wave state
     int32_t maxw = 1;
     int32_t wG = 0, wK = 0, wC = 0;
@@ -136,6 +143,9 @@ void free_graph(bc_graph *g) {
         cudaEventDestroy(e.b);
     }
     bcgb::plain_free(g->plain);
+    g->dA.release();
+    g->dX.release();
+    g->dctl.release();
     for (auto *b : {&g->wdist, &g->worder, &g->wgrp, &g->wslots}) b->release();
     g->wsigma.release();
     g->wcval.release();
@@ -346,11 +356,94 @@ int stage_sources(bc_graph *g, const int32_t *sources, int32_t num, int32_t *cou
     return BC_OK;
 }
 
+// Tensor-core forward for one batch (BC_DENSE): level 0 by the sparse
+// kernel, every further level as limb-matrix x adjacency products. The host
+// reads each level's outcome (a few levels per batch), which fixes the limb
+// count of the next product. Returns the depth in *depth (-1: level capacity).
+int dense_forward(bc_graph *g, bcgb::MsParams &p, cudaStream_t st, int *depth) {
+    {
+        Timer t(g, st, BC_KERNEL_FORWARD);
+        bcgb::ms_launch_forward(4, p, 0, st);
+    }
+    bcgb::DevCtl c{};
+    CK(cudaMemcpyAsync(&c, g->ctl, sizeof(c), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (c.fwd_done) {
+        *depth = c.nlevels;
+        return BC_OK;
+    }
+    bcgb::DenseParams d{};
+    d.n = g->n;
+    d.npad = g->npad;
+    d.nb = p.nb;
+    d.nw32 = p.nw32;
+    d.sigma = g->sigma.p;
+    d.F = g->F.p;
+    d.V = g->V.p;
+    d.ufr = g->ufr.p;
+    d.X = g->dX.p;
+    d.ctl = g->ctl;
+    d.dctl = g->dctl.p;
+    int nl = 1;  // level-1 counts are all 1
+    for (int l = 1;; ++l) {
+        if (l + 2 >= g->Lcap) {
+            *depth = -1;
+            return BC_OK;
+        }
+        CK(cudaMemsetAsync(g->dctl.p, 0, sizeof(bcgb::DenseCtl), st));
+        {
+            Timer t(g, st, BC_KERNEL_DENSE);
+            if (bcgb::dense_launch_level(g->maps, d, l, nl, st))
+                return fail(BC_ERR_CUDA, std::string("dense level launch: ") + cudaGetErrorString(cudaGetLastError()));
+        }
+        bcgb::DenseCtl r{};
+        uint32_t status = 0;
+        CK(cudaMemcpyAsync(&r, g->dctl.p, sizeof(r), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&status, &g->ctl->status, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (status & BC_STATUS_DENSE_TIMEOUT) return fail(BC_ERR_TIMEOUT, "tensor-core pipeline wait timed out");
+        if (!r.produced) {
+            *depth = l;
+            return BC_OK;
+        }
+        if (r.remaining == 0) {  // every pair reached: the next frontier is empty
+            *depth = l + 1;
+            return BC_OK;
+        }
+        nl = 1;
+        while (nl < bcgb::kDenseMaxLimbs && (r.maxsig >> (8 * nl)) != 0ull) ++nl;
+        if (status & BC_STATUS_SIGMA_OVERFLOW) nl = bcgb::kDenseMaxLimbs;
+    }
+}
+
+int ensure_dense(bc_graph *g, cudaStream_t st) {
+    if (g->dA.p) return BC_OK;
+    if (g->weighted) return fail(BC_ERR_UNSUPPORTED, "BC_DENSE needs an unweighted graph");
+    if (g->n > bcgb::kDenseMaxN) return fail(BC_ERR_UNSUPPORTED, "BC_DENSE supports n <= 65536");
+    const int32_t npad = std::max(64, (g->n + 63) / 64 * 64);
+    CK(g->dA.ensure((size_t)npad * npad));
+    CK(g->dX.ensure((size_t)bcgb::kDenseMaxLimbs * 128 * npad));
+    CK(cudaMemsetAsync(g->dX.p, 0, g->dX.n * sizeof(__nv_bfloat16), st));
+    CK(g->dctl.ensure(1));
+    if (bcgb::dense_build_adjacency(g->row_ptr.p, g->col.p, g->n, npad, g->dA.p, st))
+        return fail(BC_ERR_CUDA, "dense adjacency build failed");
+    if (bcgb::dense_make_maps(&g->maps, g->dX.p, g->dA.p, npad))
+        return fail(BC_ERR_CUDA, "cuTensorMapEncodeTiled failed for the dense operands");
+    g->npad = npad;
+    return BC_OK;
+}
+
 // The multi-source driver shared by bc_run and bc_forward_rows.
 int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStream_t st, bool backward,
                 bool hash, uint64_t *rows_sig, int32_t *rows_dist) {
     const int64_t wait_ms = (opt && opt->wait_limit_ms > 0) ? opt->wait_limit_ms : 600000;
     const int32_t chunk = (opt && opt->chunk > 0) ? opt->chunk : 256;
+    const bool dense = opt && (opt->flags & BC_DENSE);
+    if (dense) {
+        W = 4;
+        int rd = ensure_dense(g, st);
+        if (rd) return rd;
+    }
     int r = build_items(g, chunk);
     if (r) return r;
     r = ensure_state(g, W, std::max(g->Lcap, 32));
@@ -373,11 +466,15 @@ int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStr
             bcgb::ms_launch_init(W, p, st);
         }
         int L = 0;
-        auto launch = [&](int level) {
-            Timer t(g, st, BC_KERNEL_FORWARD);
-            bcgb::ms_launch_forward(W, p, level, st);
-        };
-        r = bcgb::drive_forward(g->hctl, p.seq, g->Lcap - 2, launch, wait_ms, st, &g_err, &L);
+        if (dense) {
+            r = dense_forward(g, p, st, &L);
+        } else {
+            auto launch = [&](int level) {
+                Timer t(g, st, BC_KERNEL_FORWARD);
+                bcgb::ms_launch_forward(W, p, level, st);
+            };
+            r = bcgb::drive_forward(g->hctl, p.seq, g->Lcap - 2, launch, wait_ms, st, &g_err, &L);
+        }
         if (r) return r;
         if (L < 0) {  // deeper than the level capacity: grow it and redo this batch
             CK(cudaStreamSynchronize(st));
@@ -615,6 +712,7 @@ int bc_result(bc_graph *g, double *bc, uint32_t *status_flags) {
     CK(cudaStreamSynchronize(g->last_stream));
     if (status_flags) *status_flags = status;
     if (status & BC_STATUS_BOUNDS) return fail(BC_ERR_BOUNDS, "device bounds check fired");
+    if (status & BC_STATUS_DENSE_TIMEOUT) return fail(BC_ERR_TIMEOUT, "tensor-core pipeline wait timed out");
     if (status & BC_STATUS_SIGMA_OVERFLOW) return BC_WARN_SIGMA_OVERFLOW;
     return BC_OK;
 }

@@ -1,0 +1,389 @@
+// dense.cu -- the algebraic level expansion of Section 3.1.1 on tcgen05
+// tensor cores (flag BC_DENSE).
+//
+// ComputePathCount multiplies by the adjacency matrix A once per level. In
+// frontier form (corrected mask, see DESIGN), for a batch of B = 128 sources:
+//     C_l[s][u] = sigma_s(u) if d(s,u) = l, else 0,
+//     C_{l+1} = (C_l . A) masked to the (s, v) not reached yet,
+// and the non-zero entries of C_{l+1} are sigma_s(v) for d(s,v) = l+1.
+// sigma is an exact uint64, so C_l is split into 8-bit limbs
+//     C_l = sum_q 2^(8q) C_l^(q),   0 <= C_l^(q) <= 255,
+// and each limb matrix is multiplied on the tensor cores in bf16 with FP32
+// accumulation. Both are exact: bf16 holds every integer up to 256, A is 0/1,
+// and every partial sum is at most 255 * n < 2^24 (n <= 65536), which FP32
+// holds exactly. The epilogue converts each limb sum back to an integer and
+// carry-combines sum_q 2^(8q) acc_q in 64 bits with an overflow flag.
+// Only the limbs that can be non-zero are multiplied: the previous level
+// reports its largest sigma, which fixes the limb count (up to 8).
+//
+// GEMM tile: one CTA owns 64 target vertices (columns of A) for all 128
+// sources and all limbs: accumulator q (128 lanes x 64 columns of FP32) sits
+// in TMEM columns [64q, 64q + 64). Operand tiles arrive by TMA (128-byte
+// swizzle, one copy per CTA) through an S-stage shared-memory ring guarded by
+// mbarriers; one thread issues tcgen05.mma; four warps read TMEM back.
+// Every wait is bounded (global timer); on expiry the kernel records an error,
+// drains what it issued, frees its TMEM and returns.
+//
+// The epilogue writes the same state the sparse level kernel writes (sigma
+// [n][128], frontier and visited words, union-frontier bits), so the sparse
+// backward sweep and summaries run unchanged afterwards.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "bc_internal.cuh"
+#include "dense.cuh"
+
+namespace bcgb {
+namespace {
+
+constexpr int kDB = 128;          // sources per batch (GEMM M)
+constexpr int kDW = kDB / 32;     // frontier words per vertex
+constexpr int kNT = 64;           // target vertices per CTA (GEMM N)
+constexpr int kKT = 64;           // K per pipeline stage (128 bytes of bf16)
+constexpr int kXTile = kDB * kKT * 2;  // 16 KiB: one limb's operand tile
+constexpr int kATile = kNT * kKT * 2;  // 8 KiB: adjacency tile
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+// Bounded wait on a phase; false when the time limit passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint64_t t0 = gtimer();
+    while (!mbar_try_wait(bar, parity))
+        if (gtimer() - t0 > kWaitNs) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int32_t x, int32_t y,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+// Shared-memory matrix descriptor: K-major tile, rows of 128 bytes, 128-byte
+// swizzle (8-row atoms of 1024 bytes); start address, stride between atoms
+// (1024 B), descriptor version 1, layout SWIZZLE_128B.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)2u << 61;
+    return d;
+}
+// Instruction descriptor, kind::f16: FP32 accumulator, bf16 A and B, both
+// K-major, N = 64, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kNT >> 3) << 17) |
+                            ((uint32_t)(kDB >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__global__ void __launch_bounds__(128, 1)
+    k_dense_level(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmA, const DenseParams p,
+                  const int l, const int nl, const int stages) {
+    extern __shared__ unsigned char dsm_raw[];
+    unsigned char *dsm = reinterpret_cast<unsigned char *>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
+    const int stage_bytes = nl * kXTile + kATile;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(dsm + (size_t)stages * stage_bytes);
+    uint64_t *full = bars;
+    uint64_t *empty = bars + stages;
+    uint64_t *done = bars + 2 * stages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 1);
+    __shared__ uint32_t s_err;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int v0 = blockIdx.x * kNT;
+    const int nk = p.npad / kKT;
+    uint32_t ncols = 32;
+    while (ncols < (uint32_t)(nl * kNT)) ncols <<= 1;
+
+    if (tid == 0) {
+        s_err = 0u;
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (tid == 0) {
+        // producer: TMA the nl limb tiles and the adjacency tile of each K step
+        int issued = 0;
+        for (int it = 0; it < nk; ++it) {
+            const int s = it % stages;
+            if (it >= stages && !mbar_wait(empty + s, ((it / stages) - 1) & 1)) {
+                atomicOr(&s_err, 1u);
+                break;
+            }
+            unsigned char *st = dsm + (size_t)s * stage_bytes;
+            mbar_expect_tx(full + s, (uint32_t)stage_bytes);
+            for (int q = 0; q < nl; ++q) tma_load_2d(st + (size_t)q * kXTile, &tmX, it * kKT, q * kDB, full + s);
+            tma_load_2d(st + (size_t)nl * kXTile, &tmA, it * kKT, v0, full + s);
+            issued = it + 1;
+        }
+        // drain: every issued load must have landed before shared memory is released
+        for (int it = (issued > stages ? issued - stages : 0); it < issued; ++it)
+            if (!mbar_wait(full + (it % stages), (it / stages) & 1)) atomicOr(&s_err, 2u);
+    } else if (tid == 32) {
+        // MMA issuer: D_q += X_q . A^T over the K steps, 4 instructions (K = 16) per step
+        int it = 0;
+        for (; it < nk; ++it) {
+            const int s = it % stages;
+            if (!mbar_wait(full + s, (it / stages) & 1)) {
+                atomicOr(&s_err, 4u);
+                break;
+            }
+            tc_fence_after();
+            unsigned char *st = dsm + (size_t)s * stage_bytes;
+            const uint32_t abase = smem_u32(st + (size_t)nl * kXTile);
+            for (int q = 0; q < nl; ++q) {
+                const uint32_t xbase = smem_u32(st + (size_t)q * kXTile);
+#pragma unroll
+                for (int kk = 0; kk < kKT / 16; ++kk)
+                    umma_bf16(tmem + (uint32_t)(q * kNT), sw128_desc(xbase + kk * 32), sw128_desc(abase + kk * 32),
+                              (it > 0 || kk > 0) ? 1u : 0u);
+            }
+            umma_commit(empty + s);  // frees the stage once these MMAs have read it
+        }
+        umma_commit(done);  // arrives when every MMA issued above has completed
+    }
+    __syncwarp();
+
+    // epilogue: every thread owns one source (TMEM lane = 32 * warp + lane)
+    const bool ok = mbar_wait(done, 0);
+    tc_fence_after();
+    __syncthreads();
+    const bool good = ok && s_err == 0u;
+    if (!good && tid == 0) atomicOr(&p.ctl->status, BC_STATUS_DENSE_TIMEOUT);
+    const int b = tid;  // source index in the batch
+    const size_t nW = (size_t)p.n * kDW;
+    const uint32_t *Fl = p.F + (size_t)l * nW;
+    uint32_t *Fn = p.F + (size_t)(l + 1) * nW;
+    const uint32_t *Vin = p.V + (size_t)(l & 1) * nW;
+    uint32_t *Vout = p.V + (size_t)((l + 1) & 1) * nW;
+    uint32_t *ufn = p.ufr + (size_t)(l + 1) * p.nw32;
+    const bool valid_src = b < p.nb;
+    bool ovf = false, produced = false;
+    unsigned long long maxsig = 0, remaining = 0;
+    for (int c0 = 0; good && c0 < kNT; c0 += 16) {
+        uint64_t lo[16];
+        uint32_t hi[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            lo[i] = 0ull;
+            hi[i] = 0u;
+        }
+        for (int q = 0; q < nl; ++q) {
+            uint32_t r[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * kNT + c0), r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                // exact integer < 2^24 held in FP32; add 2^(8q) * a into (hi:lo)
+                const uint64_t a = (uint64_t)__float2uint_rn(__uint_as_float(r[i]));
+                const int sh = 8 * q;
+                const uint64_t part = a << sh;
+                const uint64_t carry_bits = sh ? (a >> (64 - sh)) : 0ull;
+                const uint64_t y = lo[i] + part;
+                hi[i] += (uint32_t)carry_bits + (y < part ? 1u : 0u);
+                lo[i] = y;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int v = v0 + c0 + i;
+            if (v >= p.n) break;  // padding columns (uniform across the block)
+            const uint32_t vis = __ldg(Vin + (size_t)v * kDW + warp) | __ldg(Fl + (size_t)v * kDW + warp);
+            const bool seen = (vis >> lane) & 1u;
+            const bool hit = valid_src && !seen && (lo[i] | hi[i]) != 0ull;
+            if (hit) {
+                p.sigma[(size_t)v * kDB + b] = lo[i];
+                ovf |= hi[i] != 0u;
+                maxsig = lo[i] > maxsig ? lo[i] : maxsig;
+            }
+            remaining += (valid_src && !seen && !hit) ? 1ull : 0ull;
+            const uint32_t word = __ballot_sync(0xffffffffu, hit);
+            if (lane == 0) {
+                Fn[(size_t)v * kDW + warp] = word;
+                Vout[(size_t)v * kDW + warp] = vis;
+                if (word) atomicOr(ufn + (v >> 5), 1u << (v & 31));
+            }
+            produced |= word != 0u;
+        }
+    }
+    if (good) {
+        if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(&p.ctl->status, BC_STATUS_SIGMA_OVERFLOW);
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, maxsig, off);
+            maxsig = o > maxsig ? o : maxsig;
+            remaining += __shfl_xor_sync(0xffffffffu, remaining, off);
+        }
+        if (lane == 0) {
+            if (produced) atomicOr(&p.dctl->produced, 1u);
+            if (maxsig) atomicMax(&p.dctl->maxsig, maxsig);
+            if (remaining) atomicAdd(&p.dctl->remaining, remaining);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// Limb matrix of level l: X[q*128 + b][u] = byte q of sigma_b(u) where
+// d(s_b, u) = l, else 0 (bf16). Tiles of 32 vertices x 128 sources through
+// shared memory so both the sigma reads and the X writes are coalesced.
+__global__ void __launch_bounds__(256) k_dense_limbs(const DenseParams p, const int l, const int nl) {
+    __shared__ uint64_t tile[32][kDB + 1];
+    const int u0 = blockIdx.x * 32;
+    const size_t nW = (size_t)p.n * kDW;
+    const uint32_t *Fl = p.F + (size_t)l * nW;
+    for (int i = threadIdx.x; i < 32 * kDB; i += 256) {
+        const int uu = i / kDB, b = i % kDB;
+        const int u = u0 + uu;
+        uint64_t s = 0;
+        if (u < p.n && ((__ldg(Fl + (size_t)u * kDW + (b >> 5)) >> (b & 31)) & 1u)) s = p.sigma[(size_t)u * kDB + b];
+        tile[uu][b] = s;
+    }
+    __syncthreads();
+    for (int q = 0; q < nl; ++q) {
+        for (int i = threadIdx.x; i < 32 * kDB; i += 256) {
+            const int b = i / 32, uu = i % 32;
+            const unsigned byte = (unsigned)((tile[uu][b] >> (8 * q)) & 0xFFu);
+            p.X[((size_t)q * kDB + b) * p.npad + u0 + uu] = __float2bfloat16_rn((float)byte);
+        }
+    }
+}
+
+// Dense 0/1 adjacency in bf16 from the CSR (rows beyond n and columns beyond
+// n stay zero).
+__global__ void k_dense_adjacency(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n,
+                                  int32_t npad, __nv_bfloat16 *A) {
+    for (int v = blockIdx.x; v < n; v += gridDim.x)
+        for (int e = row_ptr[v] + threadIdx.x; e < row_ptr[v + 1]; e += blockDim.x)
+            A[(size_t)v * npad + col[e]] = __float2bfloat16_rn(1.0f);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap *m, void *base, uint64_t inner, uint64_t rows, uint32_t box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {inner, rows};
+    const cuuint64_t strides[1] = {inner * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kKT, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int dense_stages(int nl) {
+    const int budget = 200 * 1024;
+    const int s = budget / (nl * kXTile + kATile);
+    return s < 1 ? 1 : (s > 8 ? 8 : s);
+}
+
+size_t dense_smem_bytes(int nl, int stages) {
+    return (size_t)stages * (nl * kXTile + kATile) + 1024 + (2 * stages + 2) * sizeof(uint64_t) + 64;
+}
+
+int dense_build_adjacency(const int32_t *row_ptr, const int32_t *col, int32_t n, int32_t npad, __nv_bfloat16 *A,
+                          cudaStream_t st) {
+    if (cudaMemsetAsync(A, 0, (size_t)npad * npad * sizeof(__nv_bfloat16), st) != cudaSuccess) return -1;
+    if (n > 0) k_dense_adjacency<<<n < 4096 ? n : 4096, 128, 0, st>>>(row_ptr, col, n, npad, A);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int dense_make_maps(DenseMaps *maps, __nv_bfloat16 *X, __nv_bfloat16 *A, int32_t npad) {
+    if (!make_map(&maps->x, X, (uint64_t)npad, (uint64_t)kDenseMaxLimbs * kDB, kDB)) return -1;
+    if (!make_map(&maps->a, A, (uint64_t)npad, (uint64_t)npad, kNT)) return -1;
+    return 0;
+}
+
+int dense_launch_level(const DenseMaps &maps, const DenseParams &p, int l, int nl, cudaStream_t st) {
+    const int stages = dense_stages(nl);
+    const size_t smem = dense_smem_bytes(nl, stages);
+    if (cudaFuncSetAttribute(k_dense_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return -1;
+    k_dense_limbs<<<(p.n + 31) / 32, 256, 0, st>>>(p, l, nl);
+    k_dense_level<<<p.npad / kNT, 128, smem, st>>>(maps.x, maps.a, p, l, nl, stages);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace bcgb

@@ -27,6 +27,7 @@ BC_ERR_UNSUPPORTED = -8
 BC_ERR_STATE = -9
 
 BC_STATUS_SIGMA_OVERFLOW = 0x1
+BC_STATUS_DENSE_TIMEOUT = 0x8
 
 BC_GRAPH_TRUST_INPUT = 0x1
 
@@ -35,13 +36,15 @@ BC_ACCUMULATE = 0x2
 BC_PLAIN = 0x4
 BC_TIMING = 0x8
 BC_NO_HASH = 0x10
+BC_DENSE = 0x20
 
 BC_KERNEL_INIT = 0
 BC_KERNEL_FORWARD = 1
 BC_KERNEL_BACKWARD = 2
 BC_KERNEL_HASH = 3
 BC_KERNEL_PLAIN = 4
-KERNEL_NAMES = {0: "init", 1: "forward", 2: "backward", 3: "hash", 4: "plain"}
+BC_KERNEL_DENSE = 5
+KERNEL_NAMES = {0: "init", 1: "forward", 2: "backward", 3: "hash", 4: "plain", 5: "dense"}
 
 # every entry point include/bc_gb300.h declares
 EXPORTS = ["bc_create_graph", "bc_run", "bc_result", "bc_source_hashes", "bc_forward_rows",
