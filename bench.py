@@ -153,6 +153,153 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def _timed(fn, steps, warmup, stream, flush):
+    """Median CUDA-event time (ms) of fn() on `stream`, L2 flushed before each step."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def _oracle_rate(g, sources, seconds):
+    """Oracle edges/s on a bounded prefix of `sources` (all host cores)."""
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    k = min(len(sources), 2 * threads)
+    t0 = time.perf_counter()
+    oracle.bc(g, sources[:k], threads=threads)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    k = int(min(len(sources), max(k, k * seconds / dt)))
+    t0 = time.perf_counter()
+    oracle.bc(g, sources[:k], threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": k * g.m / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{k} of the workload's sources ({dt:.1f} s)"}
+
+
+def run_extra(args):
+    """The other configurations: one JSON line each (not the default line)."""
+    import torch
+    from paper_0809_1906_gb300 import native
+    native.load()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    hbm, hbm_kind = peaks()
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "data": "synthetic", "workload": args.workload}
+    wl = args.workload
+    if wl == "er1024":
+        g = G.er_hamiltonian()
+        src = torch.arange(g.n, dtype=torch.int32, device="cuda")
+        with native.Graph.from_csr(g) as h:
+            res = {}
+            for b in (32, 64, 128, 256):
+                ms = _timed(lambda: (h.run(src, batch=b, stream=stream), h.result()), args.steps, args.warmup,
+                            stream, flush)
+                res[b] = ms
+            best = min(res, key=res.get)
+            ms_plain = _timed(lambda: (h.run(src, flags=native.BC_PLAIN, stream=stream), h.result()), 2, 1,
+                              stream, flush)
+        line.update(value=g.n * g.m / (res[best] / 1e3), ms_per_step=res[best],
+                    config={"workload": f"ER n={g.n} m={g.m} + Hamiltonian path, all sources", "batch": best,
+                            "ms_by_batch": res},
+                    vs_plain_gpu={"value": g.n * g.m / (ms_plain / 1e3), "ms": ms_plain,
+                                  "speedup": ms_plain / res[best]},
+                    cpu_baseline=_oracle_rate(g, np.arange(g.n, dtype=np.int32), args.cpu_seconds))
+    elif wl == "grid":
+        g = G.grid_longrange()
+        srcn = G.sample_sources(g.n, 4096, 33)
+        src = torch.from_numpy(srcn).cuda()
+        with native.Graph.from_csr(g) as h:
+            ms = _timed(lambda: (h.run(src, stream=stream), h.result()), args.steps, args.warmup, stream, flush)
+            arcs, _ = h.run_stats()
+            h.run(src, flags=native.BC_TIMING, stream=stream)
+            h.result()
+            fl, fms = h.kernel_time(native.BC_KERNEL_FORWARD)
+        sub = G.induced_subgrid(g, 512, 64)
+        with native.Graph.from_csr(sub) as hs:
+            ms_sub = _timed(lambda: (hs.run(stream=stream), hs.result()), args.steps, args.warmup, stream, flush)
+        n, m = g.n, g.m
+        alg = 4096 * (16 * m + 32 * n) + 12 * arcs  # per source: 2 passes x 2m x 4 B, 12 B per DAG arc, 32 B per vertex
+        achieved = alg / (fms / 1e3) / 1e9
+        line.update(value=4096 * m / (ms / 1e3), ms_per_step=ms,
+                    config={"workload": f"512x512 grid + 5% long-range, w~U[1,100] (n={n}, m={m}), 4096 sampled sources",
+                            "dag_arcs_per_source": arcs / 4096,
+                            "subgrid64_all_sources": {"n": sub.n, "m": sub.m, "ms": ms_sub,
+                                                      "value": sub.n * sub.m / (ms_sub / 1e3)}},
+                    roofline={"bound": "hbm", "kernel": "k_wsssp", "achieved": achieved, "peak": hbm,
+                              "unit": "GB/s", "frac": achieved / hbm, "peak_source": hbm_kind, "traffic": None},
+                    cpu_baseline=_oracle_rate(g, srcn, args.cpu_seconds))
+    elif wl == "gnp":
+        g = G.gnp(8192, 0.05)
+        src = torch.arange(g.n, dtype=torch.int32, device="cuda")
+        with native.Graph.from_csr(g) as h:
+            ms_d = _timed(lambda: (h.run(src, flags=native.BC_DENSE, stream=stream), h.result()), args.steps,
+                          args.warmup, stream, flush)
+            h.run(src, flags=native.BC_DENSE | native.BC_TIMING, stream=stream)
+            h.result()
+            kinds = {native.KERNEL_NAMES[k]: h.kernel_time(k) for k in native.KERNEL_NAMES}
+            flops = h.dense_flops()
+            ms_s = {b: _timed(lambda: (h.run(src, batch=b, stream=stream), h.result()), 2, 1, stream, flush)
+                    for b in (128, 256)}
+        dn, dms = kinds["dense"]
+        tf = flops / (dms / 1e3) / 1e12 if dms else 0.0
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+        line.update(value=g.n * g.m / (ms_d / 1e3), ms_per_step=ms_d,
+                    config={"workload": f"G(n=8192, p=0.05) (m={g.m}), all sources, 64 batches of 128, BC_DENSE",
+                            "kernels_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in kinds.items()}},
+                    roofline={"bound": "tensor", "kernel": "k_dense_level (+ limb build)", "achieved": tf,
+                              "peak": bf16, "unit": "TFLOP/s", "frac": tf / bf16, "peak_source": "measured bf16 burst",
+                              "flops": flops, "traffic": None},
+                    vs_sparse_same_graph={str(b): {"ms": v, "value": g.n * g.m / (v / 1e3), "speedup": v / ms_d}
+                                          for b, v in ms_s.items()},
+                    cpu_baseline=_oracle_rate(g, np.arange(g.n, dtype=np.int32), args.cpu_seconds))
+    elif wl == "many":
+        gs = G.many_graphs()
+        hs = [native.Graph.from_csr(g, trust_input=True) for g in gs]
+        work = float(sum(g.n * g.m for g in gs))
+        from paper_0809_1906_gb300 import autotune
+        best = autotune.tune_many(gs, hs)["batch"]
+        res = {}
+        with native.ManyPlan(hs, batch=best) as plan:
+            def step():
+                plan.run(stream)
+                plan.result()
+            res[best] = _timed(step, args.steps, args.warmup, stream, flush)
+        for h in hs:
+            h.close()
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        done_w = 0.0
+        k = 0
+        while time.perf_counter() - t0 < args.cpu_seconds and k < len(gs):
+            oracle.bc(gs[k], threads=os.cpu_count() or 1)
+            done_w += gs[k].n * gs[k].m
+            k += 1
+        cdt = time.perf_counter() - t0
+        line.update(value=work / (res[best] / 1e3), ms_per_step=res[best],
+                    config={"workload": f"{len(gs)} graphs, n log-uniform [50,5000], ER deg 6 / BA m=3, all sources",
+                            "graphs_per_s": len(gs) / (res[best] / 1e3), "batch": best, "ms_by_batch": res,
+                            "sum_n": int(sum(g.n for g in gs)), "sum_nm": work},
+                    cpu_baseline={"value": done_w / cdt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                  "sample": f"first {k} graphs, all sources ({cdt:.1f} s)"})
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -165,8 +312,12 @@ def main():
                     help="profiling driver: one bc_run over the first --sources sources, nothing else")
     ap.add_argument("--sources", type=int, default=0)
     ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "er1024", "grid", "gnp", "many"],
+                    help="rmat (default, the reported line) or one of the other configurations")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.workload != "rmat" and args.impl == "ours":
+        return run_extra(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -181,9 +181,11 @@ int bc_kernel_time(bc_graph *g, int32_t kind, int64_t *launches, double *total_m
  *   dag_arcs   sum over the run's sources s of the number of arcs (u,v) with
  *              u in P_s(v), i.e. the size of each shortest-path DAG (Section 1.1)
  *   depth_sum  sum over batches (one-source path: over sources) of the BFS depth
- * Either pointer may be NULL (host pointers). Errors: BC_ERR_ARG, BC_ERR_STATE.
+ *   tensor_flops  multiply-add work issued to the tensor cores by BC_DENSE
+ *              (2 * M * N * K summed over the level products), 0 otherwise
+ * Any pointer may be NULL (host pointers). Errors: BC_ERR_ARG, BC_ERR_STATE.
  */
-int bc_run_stats(bc_graph *g, int64_t *dag_arcs, int64_t *depth_sum);
+int bc_run_stats(bc_graph *g, int64_t *dag_arcs, int64_t *depth_sum, double *tensor_flops);
 
 /* Number of kernel launches the last bc_run issued (all kinds). */
 int64_t bc_launch_count(const bc_graph *g);
@@ -219,7 +221,7 @@ int bc_graph_size(const bc_graph *g, int32_t *n, int64_t *m, int32_t *weighted);
  */
 #define BC_NOALLOC_MAX_N 16384
 #define BC_NOALLOC_MAX_LEVELS 62
-#define BC_NOALLOC_SCRATCH_BYTES (12u << 20)
+#define BC_NOALLOC_SCRATCH_BYTES (24u << 20)
 int bc_run_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *sources,
                    int32_t num_sources, double *bc, void *cuda_stream);
 

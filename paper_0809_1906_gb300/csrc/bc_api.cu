@@ -77,7 +77,7 @@ struct bc_graph {
 
     // multi-source batch state for (W, Lcap)
     int32_t W = 0, Lcap = 0;
-    DevBuf<uint64_t> sigma, part;
+    DevBuf<uint64_t> sigma, Smask, part;
     DevBuf<float> cval;
     DevBuf<uint32_t> F, ufr, V, pmask, cnt;
 
@@ -112,6 +112,7 @@ struct bc_graph {
     DevBuf<__nv_bfloat16> dA, dX;
     DevBuf<bcgb::DenseCtl> dctl;
     bcgb::DenseMaps maps{};
+    double dense_flops = 0.0;
 
     // weighted path: per-wave state
     int32_t maxw = 1;
@@ -128,6 +129,7 @@ void free_graph(bc_graph *g) {
                     &g->slot_first, &g->slot_nch, &g->sources})
         b->release();
     g->sigma.release();
+    g->Smask.release();
     g->part.release();
     g->cval.release();
     for (auto *b : {&g->F, &g->ufr, &g->V, &g->pmask, &g->cnt}) b->release();
@@ -250,7 +252,8 @@ int ensure_state(bc_graph *g, int W, int Lcap) {
     const size_t B = 32 * (size_t)W;
     const size_t nw32 = (n + 31) / 32;
     CK(g->sigma.ensure(n * B));
-    CK(g->cval.ensure(n * B));
+    CK(g->Smask.ensure(2 * n * B));
+    CK(g->cval.ensure(2 * n * B));
     CK(g->F.ensure((size_t)Lcap * n * W));
     CK(g->ufr.ensure((size_t)Lcap * nw32));
     CK(g->V.ensure(2 * n * W));
@@ -318,6 +321,7 @@ bcgb::MsParams make_params(bc_graph *g) {
     p.slot_first = g->slot_first.p;
     p.slot_nch = g->slot_nch.p;
     p.sigma = g->sigma.p;
+    p.S = g->Smask.p;
     p.cval = g->cval.p;
     p.F = g->F.p;
     p.ufr = g->ufr.p;
@@ -391,6 +395,7 @@ int dense_forward(bc_graph *g, bcgb::MsParams &p, cudaStream_t st, int *depth) {
             return BC_OK;
         }
         CK(cudaMemsetAsync(g->dctl.p, 0, sizeof(bcgb::DenseCtl), st));
+        g->dense_flops += 2.0 * 128.0 * nl * (double)g->npad * (double)g->npad;
         {
             Timer t(g, st, BC_KERNEL_DENSE);
             if (bcgb::dense_launch_level(g->maps, d, l, nl, st))
@@ -657,6 +662,7 @@ int bc_run(bc_graph *g, const int32_t *sources, int32_t num_sources, const bc_op
     g->timing = (flags & BC_TIMING) != 0;
     g->evused = 0;
     g->launches = 0;
+    g->dense_flops = 0.0;
     g->has_run = false;
     const bool hash = !(flags & BC_NO_HASH);
     if (!(flags & BC_ACCUMULATE)) CK(cudaMemsetAsync(g->bc.p, 0, g->bc.n * sizeof(double), st));
@@ -794,7 +800,7 @@ int bc_kernel_time(bc_graph *g, int32_t kind, int64_t *launches, double *total_m
 
 int64_t bc_launch_count(const bc_graph *g) { return g ? g->launches : 0; }
 
-int bc_run_stats(bc_graph *g, int64_t *dag_arcs, int64_t *depth_sum) {
+int bc_run_stats(bc_graph *g, int64_t *dag_arcs, int64_t *depth_sum, double *tensor_flops) {
     g_err.clear();
     if (!g) return fail(BC_ERR_ARG, "graph is NULL");
     if (!g->has_run) return fail(BC_ERR_STATE, "no completed bc_run");
@@ -803,6 +809,7 @@ int bc_run_stats(bc_graph *g, int64_t *dag_arcs, int64_t *depth_sum) {
     CK(cudaStreamSynchronize(g->last_stream));
     if (dag_arcs) *dag_arcs = (int64_t)v[0];
     if (depth_sum) *depth_sum = (int64_t)v[1];
+    if (tensor_flops) *tensor_flops = g->dense_flops;
     return BC_OK;
 }
 
@@ -849,7 +856,7 @@ struct bc_many {
     DevBuf<bcgb::ManyItem> d_items;
     DevBuf<unsigned> queue, arrive, capped;
     DevBuf<double> partial;
-    DevBuf<uint64_t> sigma;
+    DevBuf<uint64_t> sigma, Smask;
     DevBuf<float> cval;
     DevBuf<uint32_t> F, V, ufr;
     bcgb::DevCtl *ctl = nullptr;
@@ -871,6 +878,7 @@ void free_many(bc_many *m) {
     m->capped.release();
     m->partial.release();
     m->sigma.release();
+    m->Smask.release();
     m->cval.release();
     m->F.release();
     m->V.release();
@@ -946,7 +954,8 @@ int build_many(bc_many *m, const bc_options *opt) {
     CK(cudaMemset(m->arrive.p, 0, gd.size() * sizeof(unsigned)));
     CK(m->partial.ensure((size_t)std::max<int64_t>(part_off, 1)));
     CK(m->sigma.ensure(G * nmax * B));
-    CK(m->cval.ensure(G * nmax * B));
+    CK(m->Smask.ensure(G * 2 * nmax * B));
+    CK(m->cval.ensure(G * 2 * nmax * B));
     CK(m->F.ensure(G * m->Lcap * nmax * m->W));
     CK(m->V.ensure(G * 2 * nmax * m->W));
     CK(m->ufr.ensure(G * m->Lcap * nw32));
@@ -965,6 +974,7 @@ int build_many(bc_many *m, const bc_options *opt) {
     p.capped = m->capped.p;
     p.partial = m->partial.p;
     p.sigma = m->sigma.p;
+    p.S = m->Smask.p;
     p.cval = m->cval.p;
     p.F = m->F.p;
     p.V = m->V.p;

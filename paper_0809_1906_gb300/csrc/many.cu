@@ -42,7 +42,8 @@ __global__ void __launch_bounds__(kMBlock, 2) k_many(const ManyParams p) {
     __shared__ int32_t s_u[kMWarps][32];
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     uint64_t *sigma = p.sigma + (size_t)blockIdx.x * p.nmax * B;
-    float *cval = p.cval + (size_t)blockIdx.x * p.nmax * B;
+    uint64_t *Sbuf = p.S + (size_t)blockIdx.x * 2 * p.nmax * B;
+    float *cval = p.cval + (size_t)blockIdx.x * 2 * p.nmax * B;
     uint32_t *F = p.F + (size_t)blockIdx.x * p.Lcap * p.nmax * W;
     uint32_t *V = p.V + (size_t)blockIdx.x * 2 * p.nmax * W;
     uint32_t *ufr = p.ufr + (size_t)blockIdx.x * p.Lcap * p.nw32max;
@@ -74,11 +75,13 @@ __global__ void __launch_bounds__(kMBlock, 2) k_many(const ManyParams p) {
             }
             for (int i = tid; i < p.Lcap * nw32; i += kMBlock) ufr[i] = 0u;
             __syncthreads();
+            const size_t nB = (size_t)n * B;
             for (int b = tid; b < nb; b += kMBlock) {  // d(s,s) = 0, sigma_s(s) = 1
                 const int s = s0 + b;
                 F[(size_t)s * W + (b >> 5)] |= 1u << (b & 31);  // one source per (s, b): no race
                 atomicOr(ufr + (s >> 5), 1u << (s & 31));
                 sigma[(size_t)s * B + b] = 1ull;
+                for (int k = 0; k < B; ++k) Sbuf[(size_t)s * B + k] = k == b ? 1ull : 0ull;  // masked level-0 row
             }
             __syncthreads();
             // forward levels
@@ -94,11 +97,13 @@ __global__ void __launch_bounds__(kMBlock, 2) k_many(const ManyParams p) {
                 uint32_t *ufn = ufr + (size_t)(l + 1) * nw32;
                 const uint32_t *Vin = V + (size_t)(l & 1) * nW;
                 uint32_t *Vout = V + (size_t)((l + 1) & 1) * nW;
+                const uint64_t *Sl = Sbuf + (size_t)(l & 1) * nB;
+                uint64_t *Sn = Sbuf + (size_t)((l + 1) & 1) * nB;
                 bool produced = false;
                 for (int v = wib; v < n; v += kMWarps) {
                     uint32_t U[W], a[W], f[W];
-                    body::load_row<W>(Vin + (size_t)v * W, a);
-                    body::load_row<W>(Fl + (size_t)v * W, f);
+                    body::load_row<W, false>(Vin + (size_t)v * W, a);
+                    body::load_row<W, false>(Fl + (size_t)v * W, f);
                     uint32_t anyU = 0;
 #pragma unroll
                     for (int j = 0; j < W; ++j) {
@@ -118,9 +123,9 @@ __global__ void __launch_bounds__(kMBlock, 2) k_many(const ManyParams p) {
                         acc[j] = 0ull;
                         nf[j] = 0u;
                     }
-                    body::fwd_sum<W>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufl, Fl, sigma, U, s_u[wib], lane,
-                                     acc, nf, ovf, arcs);
-                    produced |= body::store_next<W>(sigma, Fn, ufn, v, acc, nf, lane);
+                    body::fwd_sum<W, false>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufl, Fl, Sl, U, s_u[wib], lane, acc,
+                                     nf, ovf, arcs);
+                    produced |= body::store_next<W>(sigma, Sn, Fn, ufn, v, acc, nf, lane);
                 }
                 if (!__syncthreads_or(produced)) {
                     L = l;
@@ -133,9 +138,11 @@ __global__ void __launch_bounds__(kMBlock, 2) k_many(const ManyParams p) {
                 const uint32_t *Fl = F + (size_t)l * nW;
                 const uint32_t *Fs = F + (size_t)(l + 1) * nW;
                 const uint32_t *ufs = ufr + (size_t)(l + 1) * nw32;
+                float *Cl = cval + (size_t)(l & 1) * nB;
+                const float *Cs = cval + (size_t)((l + 1) & 1) * nB;
                 for (int v = wib; v < n; v += kMWarps) {
                     uint32_t f[W];
-                    body::load_row<W>(Fl + (size_t)v * W, f);
+                    body::load_row<W, false>(Fl + (size_t)v * W, f);
                     uint32_t anyf = 0;
 #pragma unroll
                     for (int j = 0; j < W; ++j) anyf |= f[j];
@@ -143,8 +150,8 @@ __global__ void __launch_bounds__(kMBlock, 2) k_many(const ManyParams p) {
                     float S[W];
 #pragma unroll
                     for (int j = 0; j < W; ++j) S[j] = 0.0f;
-                    body::bwd_sum<W>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufs, Fs, cval, f, s_u[wib], lane, S);
-                    body::finalize_dep<W>(sigma, cval, target, v, f, S, lane);
+                    body::bwd_sum<W, false>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufs, Fs, Cs, f, s_u[wib], lane, S);
+                    body::finalize_dep<W>(sigma, Cl, target, v, f, S, lane);
                 }
                 __syncthreads();
             }

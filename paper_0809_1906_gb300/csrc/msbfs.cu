@@ -58,12 +58,18 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // d(s,s) = 0 and sigma_s(s) = 1 (Section 1.1)
+    // d(s,s) = 0 and sigma_s(s) = 1 (Section 1.1); masked level-0 rows
+    for (int b = threadIdx.x; b < p.nb; b += kBlock) {
+        uint64_t *row = p.S + (size_t)p.sources[b] * B;
+        for (int k = 0; k < B; ++k) row[k] = 0ull;
+    }
+    __syncthreads();
     for (int b = threadIdx.x; b < p.nb; b += kBlock) {
         const int s = p.sources[b];
         atomicOr(p.F + (size_t)s * W + (b >> 5), 1u << (b & 31));
         atomicOr(p.ufr + (s >> 5), 1u << (s & 31));
         p.sigma[(size_t)s * B + b] = 1ull;
+        p.S[(size_t)s * B + b] = 1ull;
     }
     if (threadIdx.x == 0) {
         p.ctl->fwd_done = 0u;
@@ -97,6 +103,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     uint32_t *ufn = p.ufr + (size_t)(l + 1) * p.nw32;
     const uint32_t *Vin = p.V + (size_t)(l & 1) * nW;
     uint32_t *Vout = p.V + (size_t)((l + 1) & 1) * nW;
+    const size_t nB = (size_t)p.n * B;
+    const uint64_t *Sl = p.S + (size_t)(l & 1) * nB;
+    uint64_t *Sn = p.S + (size_t)((l + 1) & 1) * nB;
     bool produced = false, ovf = false;
     uint32_t arcs = 0;  // predecessor relations counted by this lane
 
@@ -133,9 +142,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
             acc[j] = 0ull;
             nf[j] = 0u;
         }
-        body::fwd_sum<W>(p.col, beg, end, ufl, Fl, p.sigma, U, s_u[wib], lane, acc, nf, ovf, arcs);
+        body::fwd_sum<W>(p.col, beg, end, ufl, Fl, Sl, U, s_u[wib], lane, acc, nf, ovf, arcs);
         if (slot < 0) {
-            produced |= body::store_next<W>(p.sigma, Fn, ufn, v, acc, nf, lane);
+            produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane);
             continue;
         }
         uint64_t *pp = p.part + (size_t)slot * B + lane;
@@ -170,7 +179,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
                 nf[j] |= __ldcg(qm + j);
             }
         }
-        produced |= body::store_next<W>(p.sigma, Fn, ufn, v, acc, nf, lane);
+        produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane);
         if (lane == 0) p.cnt[first] = 0u;
     }
     const unsigned wovf = __ballot_sync(kFull, ovf);
@@ -223,6 +232,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
     const uint32_t *Fl = p.F + (size_t)l * nW;
     const uint32_t *Fs = p.F + (size_t)(l + 1) * nW;
     const uint32_t *ufs = p.ufr + (size_t)(l + 1) * p.nw32;
+    const size_t nB = (size_t)p.n * B;
+    float *Cl = p.cval + (size_t)(l & 1) * nB;
+    const float *Cs = p.cval + (size_t)((l + 1) & 1) * nB;
     for (int it = blockIdx.x * kWarps + wib; it < p.nitems; it += gridDim.x * kWarps) {
         const int v = p.item_v[it];
         const int beg = p.item_beg[it];
@@ -238,9 +250,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
         float S[W];  // lane owns source 32j + lane
 #pragma unroll
         for (int j = 0; j < W; ++j) S[j] = 0.0f;
-        body::bwd_sum<W>(p.col, beg, end, ufs, Fs, p.cval, f, s_u[wib], lane, S);
+        body::bwd_sum<W>(p.col, beg, end, ufs, Fs, Cs, f, s_u[wib], lane, S);
         if (slot < 0) {
-            body::finalize_dep<W>(p.sigma, p.cval, p.bc, v, f, S, lane);
+            body::finalize_dep<W>(p.sigma, Cl, p.bc, v, f, S, lane);
             continue;
         }
         float *pp = reinterpret_cast<float *>(p.part) + (size_t)slot * B + lane;
@@ -262,7 +274,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
 #pragma unroll
             for (int j = 0; j < W; ++j) S[j] += __ldcg(q + 32 * j);
         }
-        body::finalize_dep<W>(p.sigma, p.cval, p.bc, v, f, S, lane);
+        body::finalize_dep<W>(p.sigma, Cl, p.bc, v, f, S, lane);
         if (lane == 0) p.cnt[first] = 0u;
     }
 }

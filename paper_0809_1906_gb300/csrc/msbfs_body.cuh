@@ -3,17 +3,20 @@
 // (many.cu).
 //
 // A batch holds B = 32*W sources; every per-vertex row (sigma, c, frontier
-// words) is contiguous. A warp owns a vertex v (or a chunk of its arcs) and
-// walks v's arcs 32 at a time:
-//   probe    lane k takes arc k of the chunk: neighbour u_k, one bit of the
-//            union-frontier bitmap (is u_k in any source's frontier?), then
-//            u_k's W frontier words ANDed with the sources v still wants;
-//   walk     per source word j, a 5-step shuffle transposes the 32 x 32 bit
-//            block (candidate k, source 32j+i) so that lane i holds the
-//            candidates that matter to its own source; each lane then reads
-//            only those neighbours' entries and keeps its sums in registers.
-// Every lane does useful work for its own source, whatever the density of
-// the masks, and no atomics touch the per-source sums.
+// words) is contiguous, lane i of a warp owns sources 32j + i (j < W). Beside
+// the permanent sigma array, each level keeps *masked rows*: row v of level l
+// holds sigma_s(v) (forward) or c_s(v) (backward) for the sources s with
+// d(s,v) = l and 0 for every other source, in two buffers alternating by
+// level parity. A warp owns a vertex v (or a chunk of its arcs) and walks v's
+// arcs 32 at a time:
+//   probe  lane k takes arc k of the chunk: neighbour u_k, one bit of the
+//          union-frontier bitmap (is u_k in any source's frontier?), then
+//          u_k's W frontier words ANDed with the sources v cares about; arcs
+//          whose AND is empty are dropped;
+//   add    for each remaining neighbour the warp adds its masked row to its
+//          W per-lane sums: W coalesced loads, no per-source test, because
+//          the masked row is already zero wherever u_k does not contribute.
+// The frontier words of v come from an OR-reduction of the probe masks.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,6 +28,17 @@ namespace body {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Loads of data written by an earlier kernel launch may take the read-only
+// (non-coherent) path; data written earlier in the same launch (the
+// many-graph kernel runs every level in one launch) must use coherent loads.
+template <bool NC, class T>
+__device__ __forceinline__ T ldx(const T *p) {
+    if constexpr (NC)
+        return __ldg(p);
+    else
+        return *p;
+}
+
 // Mask of valid sources in word j of a batch with nb sources.
 __device__ __forceinline__ uint32_t valid_word(int nb, int j) {
     const int lo = 32 * j;
@@ -33,13 +47,13 @@ __device__ __forceinline__ uint32_t valid_word(int nb, int j) {
     return (1u << (nb - lo)) - 1u;
 }
 
-template <int W>
+template <int W, bool NC = true>
 __device__ __forceinline__ void load_row(const uint32_t *__restrict__ p, uint32_t (&w)[W]) {
     if constexpr (W % 4 == 0) {
         const uint4 *q = reinterpret_cast<const uint4 *>(p);
 #pragma unroll
         for (int i = 0; i < W / 4; ++i) {
-            const uint4 t = __ldg(q + i);
+            const uint4 t = ldx<NC>(q + i);
             w[4 * i] = t.x;
             w[4 * i + 1] = t.y;
             w[4 * i + 2] = t.z;
@@ -49,34 +63,20 @@ __device__ __forceinline__ void load_row(const uint32_t *__restrict__ p, uint32_
         const uint2 *q = reinterpret_cast<const uint2 *>(p);
 #pragma unroll
         for (int i = 0; i < W / 2; ++i) {
-            const uint2 t = __ldg(q + i);
+            const uint2 t = ldx<NC>(q + i);
             w[2 * i] = t.x;
             w[2 * i + 1] = t.y;
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < W; ++i) w[i] = __ldg(p + i);
+        for (int i = 0; i < W; ++i) w[i] = ldx<NC>(p + i);
     }
-}
-
-// Warp-wide 32x32 bit transpose: lane k holds row k; returns column `lane`
-// (bit k of the result = bit `lane` of lane k's input). Five exchange steps,
-// each swapping the off-diagonal s x s blocks of every 2s x 2s block.
-__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
-#pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) {
-        const uint32_t M = s == 16 ? 0x0000FFFFu : s == 8 ? 0x00FF00FFu : s == 4 ? 0x0F0F0F0Fu
-                         : s == 2 ? 0x33333333u : 0x55555555u;
-        const uint32_t y = __shfl_xor_sync(kFull, x, s);
-        x = (lane & s) ? ((x & ~M) | ((y >> s) & M)) : ((x & M) | ((y & M) << s));
-    }
-    return x;
 }
 
 // One 32-arc chunk: lane k gets arc e (if e < end), its neighbour u_k (stored
 // in s_u[k]) and masks m_k[j] = frontier words of u_k AND want[j] (zero for
 // arcs that cannot contribute). Returns the ballot of contributing lanes.
-template <int W>
+template <int W, bool NC>
 __device__ __forceinline__ unsigned probe_chunk(const int32_t *__restrict__ col, int e, int end,
                                                 const uint32_t *__restrict__ ufr, const uint32_t *__restrict__ Fx,
                                                 const uint32_t (&want)[W], uint32_t (&m)[W], int32_t *s_u,
@@ -87,9 +87,9 @@ __device__ __forceinline__ unsigned probe_chunk(const int32_t *__restrict__ col,
     for (int j = 0; j < W; ++j) m[j] = 0u;
     if (e < end) {
         u = __ldg(col + e);
-        if ((__ldg(ufr + (u >> 5)) >> (u & 31)) & 1u) {
+        if ((ldx<NC>(ufr + (u >> 5)) >> (u & 31)) & 1u) {
             uint32_t fu[W];
-            load_row<W>(Fx + (size_t)u * W, fu);
+            load_row<W, NC>(Fx + (size_t)u * W, fu);
             uint32_t any = 0;
 #pragma unroll
             for (int j = 0; j < W; ++j) {
@@ -105,50 +105,40 @@ __device__ __forceinline__ unsigned probe_chunk(const int32_t *__restrict__ col,
 }
 
 // Forward sums over arcs [beg, end) of v for level l -> l+1: for source
-// s = 32j + lane, acc[j] += sigma_s(u) over neighbours u with d(s,u) = l and
-// v unvisited by s (U); nf[j] collects the sources that reach v. Exact
-// uint64 adds; ovf records a carry out of bit 63. arcs counts predecessor
-// relations (lane-local).
-template <int W>
+// s = 32j + lane, acc[j] += Sl[u][s] over the neighbours u whose level-l
+// frontier meets the sources still unvisited at v (U). Sl is the masked
+// level-l row buffer, so this adds sigma_s(u) exactly over u in P_s(v) for
+// every s in U (other entries of acc are discarded by the caller). nf[j]
+// gets the sources reaching v; exact uint64 adds, ovf flags a carry out of
+// bit 63; arcs counts predecessor relations (lane-local).
+template <int W, bool NC = true>
 __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg, int end,
                                         const uint32_t *__restrict__ ufl, const uint32_t *__restrict__ Fl,
-                                        const uint64_t *__restrict__ sigma, const uint32_t (&U)[W],
-                                        int32_t *s_u, int lane, uint64_t (&acc)[W], uint32_t (&nf)[W],
-                                        bool &ovf, uint32_t &arcs) {
+                                        const uint64_t *__restrict__ Sl, const uint32_t (&U)[W], int32_t *s_u,
+                                        int lane, uint64_t (&acc)[W], uint32_t (&nf)[W], bool &ovf, uint32_t &arcs) {
     constexpr int B = 32 * W;
     for (int e0 = beg; e0 < end; e0 += 32) {
         uint32_t m[W];
-        const unsigned bal = probe_chunk<W>(col, e0 + lane, end, ufl, Fl, U, m, s_u, lane);
-        if (bal) {
-            // t[j]: the chunk's neighbours that are predecessors for source 32j + lane
-            uint32_t t[W];
+        unsigned bal = probe_chunk<W, NC>(col, e0 + lane, end, ufl, Fl, U, m, s_u, lane);
+        if (!bal) continue;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            nf[j] |= __reduce_or_sync(kFull, m[j]);
+            arcs += __popc(m[j]);
+        }
+        const uint64_t *base = Sl + lane;
+        while (bal) {
+            const int k = __ffs(bal) - 1;
+            bal &= bal - 1;
+            const uint64_t *row = base + (size_t)s_u[k] * B;
+            uint64_t x[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) x[j] = ldx<NC>(row + 32 * j);
 #pragma unroll
             for (int j = 0; j < W; ++j) {
-                t[j] = __ballot_sync(kFull, m[j] != 0u) ? transpose32(m[j], lane) : 0u;
-                nf[j] |= __ballot_sync(kFull, t[j] != 0u);
-                arcs += __popc(t[j]);
-            }
-            // drain one candidate of every word per step: up to W independent loads in flight
-            for (;;) {
-                uint32_t left = 0;
-                uint64_t x[W];
-#pragma unroll
-                for (int j = 0; j < W; ++j) {
-                    x[j] = 0ull;
-                    if (t[j]) {
-                        const int k = __ffs(t[j]) - 1;
-                        t[j] &= t[j] - 1;
-                        x[j] = __ldg(sigma + (size_t)s_u[k] * B + 32 * j + lane);
-                    }
-                    left |= t[j];
-                }
-#pragma unroll
-                for (int j = 0; j < W; ++j) {
-                    const uint64_t y = acc[j] + x[j];
-                    ovf |= y < x[j];
-                    acc[j] = y;
-                }
-                if (!left) break;
+                const uint64_t y = acc[j] + x[j];
+                ovf |= y < x[j];
+                acc[j] = y;
             }
         }
         __syncwarp();
@@ -156,46 +146,38 @@ __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg
 }
 
 // Backward sums over arcs [beg, end) of v at level l: for source s = 32j +
-// lane with d(s,v) = l (f), S[j] += c_s(w) over neighbours w with
-// d(s,w) = l+1, i.e. over the w with v in P_s(w).
-template <int W>
+// lane with d(s,v) = l (f), S[j] += Cs[w][s] over the neighbours w whose
+// level-(l+1) frontier meets f. Cs is the masked level-(l+1) c buffer, so
+// for s in f this is the sum of c_s(w) over the w with v in P_s(w).
+template <int W, bool NC = true>
 __device__ __forceinline__ void bwd_sum(const int32_t *__restrict__ col, int beg, int end,
                                         const uint32_t *__restrict__ ufs, const uint32_t *__restrict__ Fs,
-                                        const float *__restrict__ cval, const uint32_t (&f)[W], int32_t *s_u,
-                                        int lane, float (&S)[W]) {
+                                        const float *__restrict__ Cs, const uint32_t (&f)[W], int32_t *s_u, int lane,
+                                        float (&S)[W]) {
     constexpr int B = 32 * W;
     for (int e0 = beg; e0 < end; e0 += 32) {
         uint32_t m[W];
-        const unsigned bal = probe_chunk<W>(col, e0 + lane, end, ufs, Fs, f, m, s_u, lane);
-        if (bal) {
-            uint32_t t[W];
+        unsigned bal = probe_chunk<W, NC>(col, e0 + lane, end, ufs, Fs, f, m, s_u, lane);
+        const float *base = Cs + lane;
+        while (bal) {
+            const int k = __ffs(bal) - 1;
+            bal &= bal - 1;
+            const float *row = base + (size_t)s_u[k] * B;
+            float x[W];
 #pragma unroll
-            for (int j = 0; j < W; ++j) t[j] = __ballot_sync(kFull, m[j] != 0u) ? transpose32(m[j], lane) : 0u;
-            for (;;) {
-                uint32_t left = 0;
-                float x[W];
+            for (int j = 0; j < W; ++j) x[j] = ldx<NC>(row + 32 * j);
 #pragma unroll
-                for (int j = 0; j < W; ++j) {
-                    x[j] = 0.0f;
-                    if (t[j]) {
-                        const int k = __ffs(t[j]) - 1;
-                        t[j] &= t[j] - 1;
-                        x[j] = __ldg(cval + (size_t)s_u[k] * B + 32 * j + lane);
-                    }
-                    left |= t[j];
-                }
-#pragma unroll
-                for (int j = 0; j < W; ++j) S[j] += x[j];
-                if (!left) break;
-            }
+            for (int j = 0; j < W; ++j) S[j] += x[j];
         }
         __syncwarp();
     }
 }
 
 // Store sigma and the new frontier words of v (its level-(l+1) sums are final).
+// Sn: the masked level-(l+1) row buffer, written in full (zeros for the
+// sources v is not new for) when v joins some frontier.
 template <int W>
-__device__ __forceinline__ bool store_next(uint64_t *sigma, uint32_t *Fn, uint32_t *ufn, int v,
+__device__ __forceinline__ bool store_next(uint64_t *sigma, uint64_t *Sn, uint32_t *Fn, uint32_t *ufn, int v,
                                            const uint64_t (&acc)[W], const uint32_t (&nf)[W], int lane) {
     constexpr int B = 32 * W;
     uint32_t any = 0;
@@ -205,6 +187,11 @@ __device__ __forceinline__ bool store_next(uint64_t *sigma, uint32_t *Fn, uint32
         if (lane == j) Fn[(size_t)v * W + j] = nf[j];
         if ((nf[j] >> lane) & 1u) sigma[(size_t)v * B + 32 * j + lane] = acc[j];
     }
+    if (any != 0u) {
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+            Sn[(size_t)v * B + 32 * j + lane] = ((nf[j] >> lane) & 1u) ? acc[j] : 0ull;
+    }
     if (any != 0 && lane == 0) atomicOr(ufn + (v >> 5), 1u << (v & 31));
     return any != 0;
 }
@@ -212,20 +199,24 @@ __device__ __forceinline__ bool store_next(uint64_t *sigma, uint32_t *Fn, uint32
 // Theorem 1.1 at v for the sources in f: delta = sigma * S,
 // c = (1 + delta) / sigma (FP32), and the FP64 sum of delta over the batch
 // (fixed butterfly order) added to bc[v]. v at level >= 1, so never a source.
+// Cl: the masked level-l c buffer, written in full (zeros for the sources v
+// is not at level l for).
 template <int W>
-__device__ __forceinline__ void finalize_dep(const uint64_t *sigma, float *cval, double *bc, int v,
+__device__ __forceinline__ void finalize_dep(const uint64_t *sigma, float *Cl, double *bc, int v,
                                              const uint32_t (&f)[W], const float (&S)[W], int lane) {
     constexpr int B = 32 * W;
     double sum = 0.0;
 #pragma unroll
     for (int j = 0; j < W; ++j) {
+        const size_t idx = (size_t)v * B + 32 * j + lane;
+        float c = 0.0f;
         if ((f[j] >> lane) & 1u) {
-            const size_t idx = (size_t)v * B + 32 * j + lane;
             const float sg = __ull2float_rn(sigma[idx]);
-            const float d = sg * S[j];    // delta_s*(v) = sigma_s(v) * sum_w c_s(w)
-            cval[idx] = (1.0f + d) / sg;  // c_s(v) for the level above
+            const float d = sg * S[j];  // delta_s*(v) = sigma_s(v) * sum_w c_s(w)
+            c = (1.0f + d) / sg;        // c_s(v) for the level above
             sum += (double)d;
         }
+        Cl[idx] = c;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(kFull, sum, off);

@@ -93,7 +93,7 @@ def load(build_if_needed: bool = True, require_gpu: bool = True):
             "bc_source_hashes": (i32, [P, P, P, P, P]),
             "bc_forward_rows": (i32, [P, P, i32, P, P, P, P]),
             "bc_kernel_time": (i32, [P, i32, P, P]),
-            "bc_run_stats": (i32, [P, P, P]),
+            "bc_run_stats": (i32, [P, P, P, P]),
             "bc_launch_count": (i64, [P]),
             "bc_graph_size": (i32, [P, P, P, P]),
             "bc_destroy_graph": (None, [P]),
@@ -245,8 +245,13 @@ class Graph:
     def run_stats(self):
         a = ctypes.c_int64(0)
         d = ctypes.c_int64(0)
-        _check(self.lib.bc_run_stats(self.handle, ctypes.byref(a), ctypes.byref(d)), "bc_run_stats")
+        _check(self.lib.bc_run_stats(self.handle, ctypes.byref(a), ctypes.byref(d), None), "bc_run_stats")
         return a.value, d.value
+
+    def dense_flops(self) -> float:
+        f = ctypes.c_double(0.0)
+        _check(self.lib.bc_run_stats(self.handle, None, None, ctypes.byref(f)), "bc_run_stats")
+        return f.value
 
     def launch_count(self) -> int:
         return int(self.lib.bc_launch_count(self.handle))

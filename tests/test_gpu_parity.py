@@ -211,3 +211,14 @@ def test_rmat_full_size_bench_configuration(nat):
         h.run(sub, batch=256)
         got, _, _ = h.result()
         assert_bc_close(got, oracle.bc(g, sub)["bc"], g.n, "rmat 256 sources")
+
+
+def test_autotuner_choice_runs_correctly(nat, tmp_path, monkeypatch):
+    from paper_0809_1906_gb300 import autotune
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "tune.json"))
+    g = G.er_hamiltonian(3000, 15000, 9)
+    choice = autotune.tune_graph(g, sample=256)
+    assert choice["batch"] in (64, 128, 256) and choice["chunk"] in (128, 256, 512)
+    assert (tmp_path / "tune.json").exists()
+    assert autotune.tune_graph(g)["batch"] == choice["batch"]  # served from the cache
+    check_graph(nat, g, batch=choice["batch"], chunk=choice["chunk"], rows=False)
