@@ -300,6 +300,40 @@ def run_extra(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """Profiling driver: one run of one workload's hot path on its first
+    --sources sources (a small case for ncu), nothing else."""
+    import torch
+    from paper_0809_1906_gb300 import native
+    native.load()
+    wl = args.workload
+    flags = 0
+    if wl == "rmat":
+        g, desc = workload()
+    elif wl == "er1024":
+        g, desc = G.er_hamiltonian(), "er1024"
+    elif wl == "grid":
+        g, desc = G.grid_longrange(), "grid512 weighted"
+    elif wl == "gnp":
+        g, desc, flags = G.gnp(8192, 0.05), "gnp8192 dense", native.BC_DENSE
+    else:
+        gs = G.many_graphs(args.sources or 200)
+        hs = [native.Graph.from_csr(x, trust_input=True) for x in gs]
+        with native.ManyPlan(hs, batch=64) as plan:
+            plan.run()
+            code, _, rerun = plan.result()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": "many", "graphs": len(gs), "status": code}), flush=True)
+        return
+    k = min(args.sources or g.n, g.n)
+    src = np.arange(k, dtype=np.int32) if wl != "grid" else G.sample_sources(g.n, k, 33)
+    with native.Graph.from_csr(g, trust_input=True) as hp:
+        hp.run(src, batch=args.batch if wl == "rmat" else 0, flags=flags)
+        out, code, _ = hp.result()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_run": desc, "sources": k, "status": code, "bc_sum": float(out.sum())}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -316,6 +350,8 @@ def main():
                     help="rmat (default, the reported line) or one of the other configurations")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.profile:
+        return run_profile(args)
     if args.workload != "rmat" and args.impl == "ours":
         return run_extra(args)
 
@@ -335,15 +371,6 @@ def main():
     from paper_0809_1906_gb300 import native
     native.load()
     g, desc = workload()
-    if args.profile:
-        k = args.sources or g.n
-        with native.Graph.from_csr(g, trust_input=True) as hp:
-            hp.run(np.arange(k, dtype=np.int32), batch=args.batch)
-            out, code, _ = hp.result()
-        torch.cuda.synchronize()
-        print(json.dumps({"profile_run": desc, "sources": k, "batch": args.batch, "status": code,
-                          "bc_sum": float(out.sum())}), flush=True)
-        return
     n, m = g.n, g.m
     # weak scaling: every rank runs the whole all-sources job, sources rotated by rank
     src = ((np.arange(n, dtype=np.int64) + rank * (n // max(world, 1))) % n).astype(np.int32)

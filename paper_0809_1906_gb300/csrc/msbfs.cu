@@ -48,6 +48,8 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
     }
     const size_t nu = (size_t)p.Lcap * p.nw32;
     for (size_t i = tid; i < nu; i += stride) p.ufr[i] = 0u;
+    // masked level-0 rows of the source vertices start at zero (coalesced)
+    for (size_t i = tid; i < (size_t)p.nb * B; i += stride) p.S[(size_t)p.sources[i / B] * B + i % B] = 0ull;
 
     __shared__ bool s_last;
     __syncthreads();
@@ -58,12 +60,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // d(s,s) = 0 and sigma_s(s) = 1 (Section 1.1); masked level-0 rows
-    for (int b = threadIdx.x; b < p.nb; b += kBlock) {
-        uint64_t *row = p.S + (size_t)p.sources[b] * B;
-        for (int k = 0; k < B; ++k) row[k] = 0ull;
-    }
-    __syncthreads();
+    // d(s,s) = 0 and sigma_s(s) = 1 (Section 1.1)
     for (int b = threadIdx.x; b < p.nb; b += kBlock) {
         const int s = p.sources[b];
         atomicOr(p.F + (size_t)s * W + (b >> 5), 1u << (b & 31));

@@ -128,35 +128,44 @@ __global__ void __launch_bounds__(kWBlock, 4) k_wsssp(const WParams p) {
             atomicSub(&sm.pending, cnt);
             if (k > 0) grp[sm.ngroups++] = done;
         }
-        // 2 + 3. path counts over P_s(v), then relax
+        // 2 + 3. path counts over P_s(v) and relaxation, four arcs at a time.
+        // One atomicMin per arc does both: the value it returns is u's
+        // distance before the call, which is final whenever it is below d
+        // (this step only produces distances above d), so u is in P_s(v)
+        // exactly when that value equals d - w(u,v); and the call itself
+        // relaxes the arc.
         for (int t = tid; t < k; t += kWBlock) {
             const int v = order[done + t];
-            uint64_t s = 0;
             const int e0 = p.row_ptr[v], e1 = p.row_ptr[v + 1];
-            if (v == src) {
-                s = 1ull;
-            } else {
-                for (int e = e0; e < e1; ++e) {
-                    const int u = p.col[e];
-                    const int du = __ldcg(dist + u);
-                    if (du < d && du == d - p.w[e]) {
-                        const uint64_t x = __ldcg(sigma + u);
-                        const uint64_t y = s + x;
-                        ovf64 |= y < x;
-                        s = y;
-                        ++arcs;
+            uint64_t s = v == src ? 1ull : 0ull;
+            for (int e = e0; e < e1; e += 4) {
+                int u[4], nd[4], old[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    u[i] = -1;
+                    if (e + i < e1) {
+                        u[i] = p.col[e + i];
+                        nd[i] = d + p.w[e + i];
                     }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) old[i] = u[i] >= 0 ? atomicMin(dist + u[i], nd[i]) : kInf;
+                uint64_t x[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const bool pred = u[i] >= 0 && v != src && old[i] < d && old[i] == 2 * d - nd[i];
+                    x[i] = pred ? __ldcg(sigma + u[i]) : 0ull;
+                    arcs += pred ? 1ull : 0ull;
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint64_t y = s + x[i];
+                    ovf64 |= y < x[i];
+                    s = y;
+                    if (u[i] >= 0 && nd[i] < old[i]) push_entry(p, sm, slots, u[i], nd[i]);
                 }
             }
             sigma[v] = s;
-            for (int e = e0; e < e1; ++e) {
-                const int u = p.col[e];
-                const int nd = d + p.w[e];
-                if (nd < __ldcg(dist + u)) {
-                    const int old = atomicMin(dist + u, nd);
-                    if (nd < old) push_entry(p, sm, slots, u, nd);
-                }
-            }
         }
         __syncthreads();
         done += k;
@@ -224,10 +233,25 @@ __global__ void __launch_bounds__(kWBlock, 4) k_wsssp(const WParams p) {
         for (int t = a + tid; t < z; t += kWBlock) {
             const int v = order[t];
             const int dv = dist[v];
+            const int e0 = p.row_ptr[v], e1 = p.row_ptr[v + 1];
             float S = 0.0f;
-            for (int e = p.row_ptr[v]; e < p.row_ptr[v + 1]; ++e) {
-                const int x = p.col[e];
-                if (dist[x] == dv + p.w[e]) S += __ldcg(cval + x);  // v in P_s(x)
+            for (int e = e0; e < e1; e += 4) {
+                int x[4], dx[4], want[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    x[i] = -1;
+                    if (e + i < e1) {
+                        x[i] = p.col[e + i];
+                        want[i] = dv + p.w[e + i];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) dx[i] = x[i] >= 0 ? dist[x[i]] : kInf;
+                float c[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) c[i] = (x[i] >= 0 && dx[i] == want[i]) ? __ldcg(cval + x[i]) : 0.0f;  // v in P_s(x)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) S += c[i];
             }
             const float sg = __ull2float_rn(sigma[v]);
             const float dl = sg * S;
