@@ -77,9 +77,9 @@ struct bc_graph {
 
     // multi-source batch state for (W, Lcap)
     int32_t W = 0, Lcap = 0;
-    DevBuf<uint64_t> sigma, Smask, part;
+    DevBuf<uint64_t> sigma, part;
     DevBuf<float> cval;
-    DevBuf<uint32_t> F, ufr, V, pmask, cnt;
+    DevBuf<uint32_t> Smask, wideflags, F, ufr, V, pmask, cnt;
 
     // results
     DevBuf<double> bc;
@@ -130,6 +130,7 @@ void free_graph(bc_graph *g) {
         b->release();
     g->sigma.release();
     g->Smask.release();
+    g->wideflags.release();
     g->part.release();
     g->cval.release();
     for (auto *b : {&g->F, &g->ufr, &g->V, &g->pmask, &g->cnt}) b->release();
@@ -253,6 +254,7 @@ int ensure_state(bc_graph *g, int W, int Lcap) {
     const size_t nw32 = (n + 31) / 32;
     CK(g->sigma.ensure(n * B));
     CK(g->Smask.ensure(2 * n * B));
+    CK(g->wideflags.ensure((size_t)Lcap));
     CK(g->cval.ensure(2 * n * B));
     CK(g->F.ensure((size_t)Lcap * n * W));
     CK(g->ufr.ensure((size_t)Lcap * nw32));
@@ -322,6 +324,7 @@ bcgb::MsParams make_params(bc_graph *g) {
     p.slot_nch = g->slot_nch.p;
     p.sigma = g->sigma.p;
     p.S = g->Smask.p;
+    p.wide = g->wideflags.p;
     p.cval = g->cval.p;
     p.F = g->F.p;
     p.ufr = g->ufr.p;
@@ -856,7 +859,8 @@ struct bc_many {
     DevBuf<bcgb::ManyItem> d_items;
     DevBuf<unsigned> queue, arrive, capped;
     DevBuf<double> partial;
-    DevBuf<uint64_t> sigma, Smask;
+    DevBuf<uint64_t> sigma;
+    DevBuf<uint32_t> Smask;
     DevBuf<float> cval;
     DevBuf<uint32_t> F, V, ufr;
     bcgb::DevCtl *ctl = nullptr;

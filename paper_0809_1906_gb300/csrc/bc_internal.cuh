@@ -4,8 +4,9 @@
 // vertices; every per-vertex row is contiguous so a warp reads a neighbour's
 // row in one coalesced access):
 //   sigma  uint64 [n][B]        exact path counts sigma_s(v)        (Section 1.1)
-//   S      uint64 [2][n][B]     masked rows by level parity: sigma_s(v) where
+//   S      uint32 [2][n][B]     masked rows by level parity: sigma_s(v) where
 //                               d(s,v) = l, 0 for the other sources
+//   wide   uint32 [Lcap]        level l has a count >= 2^32 (S unusable there)
 //   cval   float  [2][n][B]     masked rows by level parity of
 //                               c_s(v) = (1 + delta_s*(v)) / sigma_s(v)
 //   F      uint32 [Lcap][n][W]  frontier bit of source b at level l (d(s_b, v) = l)
@@ -63,7 +64,8 @@ struct MsParams {
     const int32_t *slot_nch;    // number of chunks of that vertex
     const int32_t *sources;     // this batch's source ids [nb]
     uint64_t *sigma;
-    uint64_t *S;   // [2][n][B]
+    uint32_t *S;   // [2][n][B]
+    uint32_t *wide;  // [Lcap]
     float *cval;   // [2][n][B]
     uint32_t *F;
     uint32_t *ufr;

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(kMBlock, 2) k_many(const ManyParams p) {
     __shared__ int32_t s_u[kMWarps][32];
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     uint64_t *sigma = p.sigma + (size_t)blockIdx.x * p.nmax * B;
-    uint64_t *Sbuf = p.S + (size_t)blockIdx.x * 2 * p.nmax * B;
+    uint32_t *Sbuf = p.S + (size_t)blockIdx.x * 2 * p.nmax * B;
     float *cval = p.cval + (size_t)blockIdx.x * 2 * p.nmax * B;
     uint32_t *F = p.F + (size_t)blockIdx.x * p.Lcap * p.nmax * W;
     uint32_t *V = p.V + (size_t)blockIdx.x * 2 * p.nmax * W;
@@ -81,11 +81,12 @@ __global__ void __launch_bounds__(kMBlock, 2) k_many(const ManyParams p) {
                 F[(size_t)s * W + (b >> 5)] |= 1u << (b & 31);  // one source per (s, b): no race
                 atomicOr(ufr + (s >> 5), 1u << (s & 31));
                 sigma[(size_t)s * B + b] = 1ull;
-                for (int k = 0; k < B; ++k) Sbuf[(size_t)s * B + k] = k == b ? 1ull : 0ull;  // masked level-0 row
+                for (int k = 0; k < B; ++k) Sbuf[(size_t)s * B + k] = k == b ? 1u : 0u;  // masked level-0 row
             }
             __syncthreads();
             // forward levels
             int L = 0;
+            bool wide = false;  // the current level has a count >= 2^32
             for (int l = 0;; ++l) {
                 if (l + 1 >= p.Lcap) {
                     capped = true;
@@ -97,9 +98,9 @@ __global__ void __launch_bounds__(kMBlock, 2) k_many(const ManyParams p) {
                 uint32_t *ufn = ufr + (size_t)(l + 1) * nw32;
                 const uint32_t *Vin = V + (size_t)(l & 1) * nW;
                 uint32_t *Vout = V + (size_t)((l + 1) & 1) * nW;
-                const uint64_t *Sl = Sbuf + (size_t)(l & 1) * nB;
-                uint64_t *Sn = Sbuf + (size_t)((l + 1) & 1) * nB;
-                bool produced = false;
+                const uint32_t *Sl = Sbuf + (size_t)(l & 1) * nB;
+                uint32_t *Sn = Sbuf + (size_t)((l + 1) & 1) * nB;
+                bool produced = false, wide_next = false;
                 for (int v = wib; v < n; v += kMWarps) {
                     uint32_t U[W], a[W], f[W];
                     body::load_row<W, false>(Vin + (size_t)v * W, a);
@@ -123,10 +124,11 @@ __global__ void __launch_bounds__(kMBlock, 2) k_many(const ManyParams p) {
                         acc[j] = 0ull;
                         nf[j] = 0u;
                     }
-                    body::fwd_sum<W, false>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufl, Fl, Sl, U, s_u[wib], lane, acc,
-                                     nf, ovf, arcs);
-                    produced |= body::store_next<W>(sigma, Sn, Fn, ufn, v, acc, nf, lane);
+                    body::fwd_sum<W, false>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufl, Fl, Sl, sigma, wide, U,
+                                            s_u[wib], lane, acc, nf, ovf, arcs);
+                    produced |= body::store_next<W>(sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
                 }
+                wide = __syncthreads_or(wide_next);
                 if (!__syncthreads_or(produced)) {
                     L = l;
                     break;

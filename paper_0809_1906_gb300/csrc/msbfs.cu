@@ -49,7 +49,8 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
     const size_t nu = (size_t)p.Lcap * p.nw32;
     for (size_t i = tid; i < nu; i += stride) p.ufr[i] = 0u;
     // masked level-0 rows of the source vertices start at zero (coalesced)
-    for (size_t i = tid; i < (size_t)p.nb * B; i += stride) p.S[(size_t)p.sources[i / B] * B + i % B] = 0ull;
+    for (size_t i = tid; i < (size_t)p.nb * B; i += stride) p.S[(size_t)p.sources[i / B] * B + i % B] = 0u;
+    for (size_t i = tid; i < (size_t)p.Lcap; i += stride) p.wide[i] = 0u;
 
     __shared__ bool s_last;
     __syncthreads();
@@ -66,7 +67,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
         atomicOr(p.F + (size_t)s * W + (b >> 5), 1u << (b & 31));
         atomicOr(p.ufr + (s >> 5), 1u << (s & 31));
         p.sigma[(size_t)s * B + b] = 1ull;
-        p.S[(size_t)s * B + b] = 1ull;
+        p.S[(size_t)s * B + b] = 1u;
     }
     if (threadIdx.x == 0) {
         p.ctl->fwd_done = 0u;
@@ -101,9 +102,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     const uint32_t *Vin = p.V + (size_t)(l & 1) * nW;
     uint32_t *Vout = p.V + (size_t)((l + 1) & 1) * nW;
     const size_t nB = (size_t)p.n * B;
-    const uint64_t *Sl = p.S + (size_t)(l & 1) * nB;
-    uint64_t *Sn = p.S + (size_t)((l + 1) & 1) * nB;
-    bool produced = false, ovf = false;
+    const uint32_t *Sl = p.S + (size_t)(l & 1) * nB;
+    uint32_t *Sn = p.S + (size_t)((l + 1) & 1) * nB;
+    const bool wide = *(volatile uint32_t *)(p.wide + l) != 0u;
+    bool produced = false, ovf = false, wide_next = false;
     uint32_t arcs = 0;  // predecessor relations counted by this lane
 
     // persistent warps: items are sorted by decreasing degree, so striding
@@ -139,9 +141,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
             acc[j] = 0ull;
             nf[j] = 0u;
         }
-        body::fwd_sum<W>(p.col, beg, end, ufl, Fl, Sl, U, s_u[wib], lane, acc, nf, ovf, arcs);
+        body::fwd_sum<W>(p.col, beg, end, ufl, Fl, Sl, p.sigma, wide, U, s_u[wib], lane, acc, nf, ovf, arcs);
         if (slot < 0) {
-            produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane);
+            produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
             continue;
         }
         uint64_t *pp = p.part + (size_t)slot * B + lane;
@@ -176,15 +178,17 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
                 nf[j] |= __ldcg(qm + j);
             }
         }
-        produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane);
+        produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
         if (lane == 0) p.cnt[first] = 0u;
     }
     const unsigned wovf = __ballot_sync(kFull, ovf);
+    const unsigned wwide = __ballot_sync(kFull, wide_next);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) arcs += __shfl_xor_sync(kFull, arcs, off);
     if (lane == 0) {
         if (produced) atomicOr(&s_flags, 1u);
         if (wovf) atomicOr(&s_flags, 2u);
+        if (wwide) atomicOr(&s_flags, 4u);
         if (arcs) atomicAdd(&s_arcs, (unsigned long long)arcs);
     }
     __syncthreads();
@@ -192,6 +196,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     if (s_arcs) atomicAdd(&p.ctl->dag_arcs, s_arcs);
     if (s_flags & 1u) atomicOr(&p.ctl->nonempty, 1u);
     if (s_flags & 2u) atomicOr(&p.ctl->status, BC_STATUS_SIGMA_OVERFLOW);
+    if (s_flags & 4u) atomicOr(p.wide + l + 1, 1u);
     __threadfence();
     if (atomicAdd(&p.ctl->blocks_done, 1u) != gridDim.x - 1) return;
     // last block of this level: decide whether the forward pass ended

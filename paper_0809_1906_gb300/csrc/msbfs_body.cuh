@@ -4,10 +4,12 @@
 //
 // A batch holds B = 32*W sources; every per-vertex row (sigma, c, frontier
 // words) is contiguous, lane i of a warp owns sources 32j + i (j < W). Beside
-// the permanent sigma array, each level keeps *masked rows*: row v of level l
-// holds sigma_s(v) (forward) or c_s(v) (backward) for the sources s with
-// d(s,v) = l and 0 for every other source, in two buffers alternating by
-// level parity. A warp owns a vertex v (or a chunk of its arcs) and walks v's
+// the permanent uint64 sigma array, each level keeps *masked rows*: row v of
+// level l holds sigma_s(v) (forward, as uint32) or c_s(v) (backward, FP32)
+// for the sources s with d(s,v) = l and 0 for every other source, in two
+// buffers alternating by level parity. A level whose counts do not all fit
+// in 32 bits is marked "wide"; the next level then reads the permanent uint64
+// sigma under per-source masks instead (exact either way). A warp owns a vertex v (or a chunk of its arcs) and walks v's
 // arcs 32 at a time:
 //   probe  lane k takes arc k of the chunk: neighbour u_k, one bit of the
 //          union-frontier bitmap (is u_k in any source's frontier?), then
@@ -105,17 +107,18 @@ __device__ __forceinline__ unsigned probe_chunk(const int32_t *__restrict__ col,
 }
 
 // Forward sums over arcs [beg, end) of v for level l -> l+1: for source
-// s = 32j + lane, acc[j] += Sl[u][s] over the neighbours u whose level-l
-// frontier meets the sources still unvisited at v (U). Sl is the masked
-// level-l row buffer, so this adds sigma_s(u) exactly over u in P_s(v) for
-// every s in U (other entries of acc are discarded by the caller). nf[j]
-// gets the sources reaching v; exact uint64 adds, ovf flags a carry out of
+// s = 32j + lane, acc[j] += sigma_s(u) over the neighbours u in P_s(v), for
+// every s still unvisited at v (U); other entries of acc are discarded by the
+// caller. Narrow levels add the masked uint32 rows Sl (zero wherever u is not
+// a predecessor); a wide level reads sigma under the per-source masks. nf[j]
+// gets the sources reaching v; exact uint64 sums, ovf flags a carry out of
 // bit 63; arcs counts predecessor relations (lane-local).
 template <int W, bool NC = true>
 __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg, int end,
                                         const uint32_t *__restrict__ ufl, const uint32_t *__restrict__ Fl,
-                                        const uint64_t *__restrict__ Sl, const uint32_t (&U)[W], int32_t *s_u,
-                                        int lane, uint64_t (&acc)[W], uint32_t (&nf)[W], bool &ovf, uint32_t &arcs) {
+                                        const uint32_t *__restrict__ Sl, const uint64_t *__restrict__ sigma,
+                                        bool wide, const uint32_t (&U)[W], int32_t *s_u, int lane,
+                                        uint64_t (&acc)[W], uint32_t (&nf)[W], bool &ovf, uint32_t &arcs) {
     constexpr int B = 32 * W;
     for (int e0 = beg; e0 < end; e0 += 32) {
         uint32_t m[W];
@@ -126,19 +129,45 @@ __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg
             nf[j] |= __reduce_or_sync(kFull, m[j]);
             arcs += __popc(m[j]);
         }
-        const uint64_t *base = Sl + lane;
-        while (bal) {
-            const int k = __ffs(bal) - 1;
-            bal &= bal - 1;
-            const uint64_t *row = base + (size_t)s_u[k] * B;
-            uint64_t x[W];
+        if (!wide) {
+            // two neighbours per step: 2W independent coalesced loads in flight
+            const uint32_t *base = Sl + lane;
+            while (bal) {
+                const int k0 = __ffs(bal) - 1;
+                bal &= bal - 1;
+                const int k1 = bal ? __ffs(bal) - 1 : -1;
+                if (k1 >= 0) bal &= bal - 1;
+                const uint32_t *r0 = base + (size_t)s_u[k0] * B;
+                const uint32_t *r1 = base + (size_t)s_u[k1 >= 0 ? k1 : k0] * B;
+                uint32_t x0[W], x1[W];
 #pragma unroll
-            for (int j = 0; j < W; ++j) x[j] = ldx<NC>(row + 32 * j);
+                for (int j = 0; j < W; ++j) {
+                    x0[j] = ldx<NC>(r0 + 32 * j);
+                    x1[j] = k1 >= 0 ? ldx<NC>(r1 + 32 * j) : 0u;
+                }
 #pragma unroll
-            for (int j = 0; j < W; ++j) {
-                const uint64_t y = acc[j] + x[j];
-                ovf |= y < x[j];
-                acc[j] = y;
+                for (int j = 0; j < W; ++j) {
+                    const uint64_t y = acc[j] + (uint64_t)x0[j] + (uint64_t)x1[j];
+                    ovf |= y < acc[j];
+                    acc[j] = y;
+                }
+            }
+        } else {
+            const uint64_t *base = sigma + lane;
+            while (bal) {
+                const int k = __ffs(bal) - 1;
+                bal &= bal - 1;
+                const uint64_t *row = base + (size_t)s_u[k] * B;
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    const uint32_t mk = __shfl_sync(kFull, m[j], k);
+                    if ((mk >> lane) & 1u) {
+                        const uint64_t x = ldx<NC>(row + 32 * j);
+                        const uint64_t y = acc[j] + x;
+                        ovf |= y < x;
+                        acc[j] = y;
+                    }
+                }
             }
         }
         __syncwarp();
@@ -159,26 +188,35 @@ __device__ __forceinline__ void bwd_sum(const int32_t *__restrict__ col, int beg
         uint32_t m[W];
         unsigned bal = probe_chunk<W, NC>(col, e0 + lane, end, ufs, Fs, f, m, s_u, lane);
         const float *base = Cs + lane;
+        // two neighbours per step: 2W independent coalesced loads in flight
         while (bal) {
-            const int k = __ffs(bal) - 1;
+            const int k0 = __ffs(bal) - 1;
             bal &= bal - 1;
-            const float *row = base + (size_t)s_u[k] * B;
-            float x[W];
+            const int k1 = bal ? __ffs(bal) - 1 : -1;
+            if (k1 >= 0) bal &= bal - 1;
+            const float *r0 = base + (size_t)s_u[k0] * B;
+            const float *r1 = base + (size_t)s_u[k1 >= 0 ? k1 : k0] * B;
+            float x0[W], x1[W];
 #pragma unroll
-            for (int j = 0; j < W; ++j) x[j] = ldx<NC>(row + 32 * j);
+            for (int j = 0; j < W; ++j) {
+                x0[j] = ldx<NC>(r0 + 32 * j);
+                x1[j] = k1 >= 0 ? ldx<NC>(r1 + 32 * j) : 0.0f;
+            }
 #pragma unroll
-            for (int j = 0; j < W; ++j) S[j] += x[j];
+            for (int j = 0; j < W; ++j) S[j] += x0[j] + x1[j];
         }
         __syncwarp();
     }
 }
 
 // Store sigma and the new frontier words of v (its level-(l+1) sums are final).
-// Sn: the masked level-(l+1) row buffer, written in full (zeros for the
-// sources v is not new for) when v joins some frontier.
+// Sn: the masked level-(l+1) uint32 row buffer, written in full (zeros for
+// the sources v is not new for) when v joins some frontier. Returns whether
+// v joined; *wide is set when one of its new counts needs more than 32 bits.
 template <int W>
-__device__ __forceinline__ bool store_next(uint64_t *sigma, uint64_t *Sn, uint32_t *Fn, uint32_t *ufn, int v,
-                                           const uint64_t (&acc)[W], const uint32_t (&nf)[W], int lane) {
+__device__ __forceinline__ bool store_next(uint64_t *sigma, uint32_t *Sn, uint32_t *Fn, uint32_t *ufn, int v,
+                                           const uint64_t (&acc)[W], const uint32_t (&nf)[W], int lane,
+                                           bool &wide) {
     constexpr int B = 32 * W;
     uint32_t any = 0;
 #pragma unroll
@@ -189,16 +227,16 @@ __device__ __forceinline__ bool store_next(uint64_t *sigma, uint64_t *Sn, uint32
     }
     if (any != 0u) {
 #pragma unroll
-        for (int j = 0; j < W; ++j)
-            Sn[(size_t)v * B + 32 * j + lane] = ((nf[j] >> lane) & 1u) ? acc[j] : 0ull;
+        for (int j = 0; j < W; ++j) {
+            const bool mine = (nf[j] >> lane) & 1u;
+            wide |= mine && (acc[j] >> 32) != 0ull;
+            Sn[(size_t)v * B + 32 * j + lane] = mine ? (uint32_t)acc[j] : 0u;
+        }
     }
     if (any != 0 && lane == 0) atomicOr(ufn + (v >> 5), 1u << (v & 31));
     return any != 0;
 }
 
-// Theorem 1.1 at v for the sources in f: delta = sigma * S,
-// c = (1 + delta) / sigma (FP32), and the FP64 sum of delta over the batch
-// (fixed butterfly order) added to bc[v]. v at level >= 1, so never a source.
 // Cl: the masked level-l c buffer, written in full (zeros for the sources v
 // is not at level l for).
 template <int W>
