@@ -35,7 +35,7 @@ constexpr int kMWarps = kMBlock / 32;
 constexpr unsigned kFull = 0xffffffffu;
 
 template <int W>
-__global__ void __launch_bounds__(kMBlock, 2) k_many(const ManyParams p) {
+__global__ void __launch_bounds__(kMBlock, 4) k_many(const ManyParams p) {
     constexpr int B = 32 * W;
     __shared__ int s_item;
     __shared__ int s_last;
