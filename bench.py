@@ -97,6 +97,34 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def csrc_digest() -> str:
+    """SHA-256 over the CUDA sources: DRAM counters taken from an older build
+    do not describe the current kernels."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_0809_1906_gb300", "csrc", "*.cu*"))):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel: str):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
+    summary profiles/traffic_rmat.json, or None when it was taken on other
+    kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic_rmat.json")
+    try:
+        with open(path) as f:
+            tr = json.load(f)
+        if tr.get("csrc_sha256") != csrc_digest():
+            return None
+        return tr["kernels"][kernel]["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
 def workload():
     g = G.rmat_lcc(16, 16)
     return g, f"rmat_s16_ef16_lcc (n={g.n}, m={g.m}), all {g.n} sources, batch {BATCH}"
@@ -430,16 +458,7 @@ def main():
     dom, dom_bytes, dom_ms, dom_cnt = ("backward", bwd_b, b_ms, ktime["backward"][0]) if b_ms >= f_ms else \
         ("forward", fwd_b, f_ms, ktime["forward"][0])
     achieved = dom_bytes / (dom_ms / 1000.0) / 1e9
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_path):
-        try:
-            with open(tr_path) as f:
-                tr = json.load(f)
-            if tr.get("kernel") == dom:
-                traffic = tr.get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = measured_traffic(dom)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     rp_h = torch.from_numpy(g.row_ptr).pin_memory()

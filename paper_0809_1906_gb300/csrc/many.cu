@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(kMBlock, 4) k_many(const ManyParams p) {
     __shared__ int s_item;
     __shared__ int s_last;
     __shared__ int32_t s_u[kMWarps][32];
+    __shared__ uint32_t s_nz[kMWarps][32];
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     uint64_t *sigma = p.sigma + (size_t)blockIdx.x * p.nmax * B;
     uint32_t *Sbuf = p.S + (size_t)blockIdx.x * 2 * p.nmax * B;
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(kMBlock, 4) k_many(const ManyParams p) {
                         nf[j] = 0u;
                     }
                     body::fwd_sum<W, false>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufl, Fl, Sl, sigma, wide, U,
-                                            s_u[wib], lane, acc, nf, ovf, arcs);
+                                            s_u[wib], s_nz[wib], lane, acc, nf, ovf, arcs);
                     produced |= body::store_next<W>(sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
                 }
                 wide = __syncthreads_or(wide_next);
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(kMBlock, 4) k_many(const ManyParams p) {
                     float S[W];
 #pragma unroll
                     for (int j = 0; j < W; ++j) S[j] = 0.0f;
-                    body::bwd_sum<W, false>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufs, Fs, Cs, f, s_u[wib], lane, S);
+                    body::bwd_sum<W, false>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufs, Fs, Cs, f, s_u[wib], s_nz[wib], lane, S);
                     body::finalize_dep<W>(sigma, Cl, target, v, f, S, lane);
                 }
                 __syncthreads();

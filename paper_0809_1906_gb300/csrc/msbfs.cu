@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     __shared__ uint32_t s_flags;
     __shared__ unsigned long long s_arcs;
     __shared__ int32_t s_u[kWarps][32];
+    __shared__ uint32_t s_nz[kWarps][32];
     if (threadIdx.x == 0) {
         s_flags = 0u;
         s_arcs = 0ull;
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
             acc[j] = 0ull;
             nf[j] = 0u;
         }
-        body::fwd_sum<W>(p.col, beg, end, ufl, Fl, Sl, p.sigma, wide, U, s_u[wib], lane, acc, nf, ovf, arcs);
+        body::fwd_sum<W>(p.col, beg, end, ufl, Fl, Sl, p.sigma, wide, U, s_u[wib], s_nz[wib], lane, acc, nf, ovf, arcs);
         if (slot < 0) {
             produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
             continue;
@@ -228,6 +229,7 @@ template <int W>
 __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const int l) {
     constexpr int B = 32 * W;
     __shared__ int32_t s_u[kWarps][32];
+    __shared__ uint32_t s_nz[kWarps][32];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const size_t nW = (size_t)p.n * W;
@@ -252,7 +254,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
         float S[W];  // lane owns source 32j + lane
 #pragma unroll
         for (int j = 0; j < W; ++j) S[j] = 0.0f;
-        body::bwd_sum<W>(p.col, beg, end, ufs, Fs, Cs, f, s_u[wib], lane, S);
+        body::bwd_sum<W>(p.col, beg, end, ufs, Fs, Cs, f, s_u[wib], s_nz[wib], lane, S);
         if (slot < 0) {
             body::finalize_dep<W>(p.sigma, Cl, p.bc, v, f, S, lane);
             continue;

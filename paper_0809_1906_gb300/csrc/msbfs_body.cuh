@@ -77,14 +77,16 @@ __device__ __forceinline__ void load_row(const uint32_t *__restrict__ p, uint32_
 
 // One 32-arc chunk: lane k gets arc e (if e < end), its neighbour u_k (stored
 // in s_u[k]) and masks m_k[j] = frontier words of u_k AND want[j] (zero for
-// arcs that cannot contribute). Returns the ballot of contributing lanes.
+// arcs that cannot contribute); s_nz[k] gets the W-bit set of non-zero words
+// of m_k, so the adders below load only the words that can contribute.
+// Returns the ballot of contributing lanes.
 template <int W, bool NC>
 __device__ __forceinline__ unsigned probe_chunk(const int32_t *__restrict__ col, int e, int end,
                                                 const uint32_t *__restrict__ ufr, const uint32_t *__restrict__ Fx,
                                                 const uint32_t (&want)[W], uint32_t (&m)[W], int32_t *s_u,
-                                                int lane) {
+                                                uint32_t *s_nz, int lane) {
     int u = 0;
-    bool cand = false;
+    uint32_t nz = 0;
 #pragma unroll
     for (int j = 0; j < W; ++j) m[j] = 0u;
     if (e < end) {
@@ -92,18 +94,17 @@ __device__ __forceinline__ unsigned probe_chunk(const int32_t *__restrict__ col,
         if ((ldx<NC>(ufr + (u >> 5)) >> (u & 31)) & 1u) {
             uint32_t fu[W];
             load_row<W, NC>(Fx + (size_t)u * W, fu);
-            uint32_t any = 0;
 #pragma unroll
             for (int j = 0; j < W; ++j) {
                 m[j] = fu[j] & want[j];
-                any |= m[j];
+                nz |= (m[j] != 0u ? 1u : 0u) << j;
             }
-            cand = any != 0u;
         }
     }
     s_u[lane] = u;
+    s_nz[lane] = nz;
     __syncwarp();
-    return __ballot_sync(kFull, cand);
+    return __ballot_sync(kFull, nz != 0u);
 }
 
 // Forward sums over arcs [beg, end) of v for level l -> l+1: for source
@@ -117,12 +118,12 @@ template <int W, bool NC = true>
 __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg, int end,
                                         const uint32_t *__restrict__ ufl, const uint32_t *__restrict__ Fl,
                                         const uint32_t *__restrict__ Sl, const uint64_t *__restrict__ sigma,
-                                        bool wide, const uint32_t (&U)[W], int32_t *s_u, int lane,
+                                        bool wide, const uint32_t (&U)[W], int32_t *s_u, uint32_t *s_nz, int lane,
                                         uint64_t (&acc)[W], uint32_t (&nf)[W], bool &ovf, uint32_t &arcs) {
     constexpr int B = 32 * W;
     for (int e0 = beg; e0 < end; e0 += 32) {
         uint32_t m[W];
-        unsigned bal = probe_chunk<W, NC>(col, e0 + lane, end, ufl, Fl, U, m, s_u, lane);
+        unsigned bal = probe_chunk<W, NC>(col, e0 + lane, end, ufl, Fl, U, m, s_u, s_nz, lane);
         if (!bal) continue;
 #pragma unroll
         for (int j = 0; j < W; ++j) {
@@ -139,11 +140,12 @@ __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg
                 if (k1 >= 0) bal &= bal - 1;
                 const uint32_t *r0 = base + (size_t)s_u[k0] * B;
                 const uint32_t *r1 = base + (size_t)s_u[k1 >= 0 ? k1 : k0] * B;
+                const uint32_t z0 = s_nz[k0], z1 = k1 >= 0 ? s_nz[k1] : 0u;
                 uint32_t x0[W], x1[W];
 #pragma unroll
                 for (int j = 0; j < W; ++j) {
-                    x0[j] = ldx<NC>(r0 + 32 * j);
-                    x1[j] = k1 >= 0 ? ldx<NC>(r1 + 32 * j) : 0u;
+                    x0[j] = ((z0 >> j) & 1u) ? ldx<NC>(r0 + 32 * j) : 0u;
+                    x1[j] = ((z1 >> j) & 1u) ? ldx<NC>(r1 + 32 * j) : 0u;
                 }
 #pragma unroll
                 for (int j = 0; j < W; ++j) {
@@ -181,12 +183,12 @@ __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg
 template <int W, bool NC = true>
 __device__ __forceinline__ void bwd_sum(const int32_t *__restrict__ col, int beg, int end,
                                         const uint32_t *__restrict__ ufs, const uint32_t *__restrict__ Fs,
-                                        const float *__restrict__ Cs, const uint32_t (&f)[W], int32_t *s_u, int lane,
-                                        float (&S)[W]) {
+                                        const float *__restrict__ Cs, const uint32_t (&f)[W], int32_t *s_u,
+                                        uint32_t *s_nz, int lane, float (&S)[W]) {
     constexpr int B = 32 * W;
     for (int e0 = beg; e0 < end; e0 += 32) {
         uint32_t m[W];
-        unsigned bal = probe_chunk<W, NC>(col, e0 + lane, end, ufs, Fs, f, m, s_u, lane);
+        unsigned bal = probe_chunk<W, NC>(col, e0 + lane, end, ufs, Fs, f, m, s_u, s_nz, lane);
         const float *base = Cs + lane;
         // two neighbours per step: 2W independent coalesced loads in flight
         while (bal) {
@@ -196,11 +198,12 @@ __device__ __forceinline__ void bwd_sum(const int32_t *__restrict__ col, int beg
             if (k1 >= 0) bal &= bal - 1;
             const float *r0 = base + (size_t)s_u[k0] * B;
             const float *r1 = base + (size_t)s_u[k1 >= 0 ? k1 : k0] * B;
+            const uint32_t z0 = s_nz[k0], z1 = k1 >= 0 ? s_nz[k1] : 0u;
             float x0[W], x1[W];
 #pragma unroll
             for (int j = 0; j < W; ++j) {
-                x0[j] = ldx<NC>(r0 + 32 * j);
-                x1[j] = k1 >= 0 ? ldx<NC>(r1 + 32 * j) : 0.0f;
+                x0[j] = ((z0 >> j) & 1u) ? ldx<NC>(r0 + 32 * j) : 0.0f;
+                x1[j] = ((z1 >> j) & 1u) ? ldx<NC>(r1 + 32 * j) : 0.0f;
             }
 #pragma unroll
             for (int j = 0; j < W; ++j) S[j] += x0[j] + x1[j];
