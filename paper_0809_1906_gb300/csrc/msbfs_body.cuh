@@ -78,7 +78,9 @@ __device__ __forceinline__ void load_row(const uint32_t *__restrict__ p, uint32_
 // One 32-arc chunk: lane k gets arc e (if e < end), its neighbour u_k (stored
 // in s_u[k]) and masks m_k[j] = frontier words of u_k AND want[j] (zero for
 // arcs that cannot contribute); s_nz[k] gets the W-bit set of non-zero words
-// of m_k, so the adders below load only the words that can contribute.
+// of m_k, so the backward adder loads only the words that can contribute
+// (measured: a gain there, a loss in the forward adder, which loads whole
+// rows).
 // Returns the ballot of contributing lanes.
 template <int W, bool NC>
 __device__ __forceinline__ unsigned probe_chunk(const int32_t *__restrict__ col, int e, int end,
@@ -140,12 +142,11 @@ __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg
                 if (k1 >= 0) bal &= bal - 1;
                 const uint32_t *r0 = base + (size_t)s_u[k0] * B;
                 const uint32_t *r1 = base + (size_t)s_u[k1 >= 0 ? k1 : k0] * B;
-                const uint32_t z0 = s_nz[k0], z1 = k1 >= 0 ? s_nz[k1] : 0u;
                 uint32_t x0[W], x1[W];
 #pragma unroll
                 for (int j = 0; j < W; ++j) {
-                    x0[j] = ((z0 >> j) & 1u) ? ldx<NC>(r0 + 32 * j) : 0u;
-                    x1[j] = ((z1 >> j) & 1u) ? ldx<NC>(r1 + 32 * j) : 0u;
+                    x0[j] = ldx<NC>(r0 + 32 * j);
+                    x1[j] = k1 >= 0 ? ldx<NC>(r1 + 32 * j) : 0u;
                 }
 #pragma unroll
                 for (int j = 0; j < W; ++j) {
