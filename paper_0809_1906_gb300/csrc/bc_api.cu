@@ -77,7 +77,8 @@ struct bc_graph {
 
     // multi-source batch state for (W, Lcap)
     int32_t W = 0, Lcap = 0;
-    DevBuf<uint64_t> sigma, part;
+    DevBuf<uint64_t> sigma, part, hpart;
+    DevBuf<uint16_t> lvl;
     DevBuf<float> cval;
     DevBuf<uint32_t> Smask, wideflags, F, ufr, V, pmask, cnt;
 
@@ -129,6 +130,8 @@ void free_graph(bc_graph *g) {
                     &g->slot_first, &g->slot_nch, &g->sources})
         b->release();
     g->sigma.release();
+    g->hpart.release();
+    g->lvl.release();
     g->Smask.release();
     g->wideflags.release();
     g->part.release();
@@ -253,6 +256,13 @@ int ensure_state(bc_graph *g, int W, int Lcap) {
     const size_t B = 32 * (size_t)W;
     const size_t nw32 = (n + 31) / 32;
     CK(g->sigma.ensure(n * B));
+    CK(g->lvl.ensure(n * B));
+    {
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        CK(g->hpart.ensure((size_t)(4 * sms + 1) * 4 * B));  // per-block summary partials
+    }
     CK(g->Smask.ensure(2 * n * B));
     CK(g->wideflags.ensure((size_t)Lcap));
     CK(g->cval.ensure(2 * n * B));
@@ -325,6 +335,8 @@ bcgb::MsParams make_params(bc_graph *g) {
     p.sigma = g->sigma.p;
     p.S = g->Smask.p;
     p.wide = g->wideflags.p;
+    p.lvl = g->lvl.p;
+    p.hpart = g->hpart.p;
     p.cval = g->cval.p;
     p.F = g->F.p;
     p.ufr = g->ufr.p;
@@ -370,7 +382,7 @@ int stage_sources(bc_graph *g, const int32_t *sources, int32_t num, int32_t *cou
 int dense_forward(bc_graph *g, bcgb::MsParams &p, cudaStream_t st, int *depth) {
     {
         Timer t(g, st, BC_KERNEL_FORWARD);
-        bcgb::ms_launch_forward(4, p, 0, st);
+        bcgb::ms_launch_first(4, p, st);
     }
     bcgb::DevCtl c{};
     CK(cudaMemcpyAsync(&c, g->ctl, sizeof(c), cudaMemcpyDeviceToHost, st));
@@ -385,6 +397,7 @@ int dense_forward(bc_graph *g, bcgb::MsParams &p, cudaStream_t st, int *depth) {
     d.nb = p.nb;
     d.nw32 = p.nw32;
     d.sigma = g->sigma.p;
+    d.lvl = g->lvl.p;
     d.F = g->F.p;
     d.V = g->V.p;
     d.ufr = g->ufr.p;
@@ -479,7 +492,10 @@ int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStr
         } else {
             auto launch = [&](int level) {
                 Timer t(g, st, BC_KERNEL_FORWARD);
-                bcgb::ms_launch_forward(W, p, level, st);
+                if (level == 0)
+                    bcgb::ms_launch_first(W, p, st);
+                else
+                    bcgb::ms_launch_forward(W, p, level, st);
             };
             r = bcgb::drive_forward(g->hctl, p.seq, g->Lcap - 2, launch, wait_ms, st, &g_err, &L);
         }

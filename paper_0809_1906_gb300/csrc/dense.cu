@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(128, 1)
             const bool hit = valid_src && !seen && (lo[i] | hi[i]) != 0ull;
             if (hit) {
                 p.sigma[(size_t)v * kDB + b] = lo[i];
+                p.lvl[(size_t)v * kDB + b] = (uint16_t)(l + 1);
                 ovf |= hi[i] != 0u;
                 maxsig = lo[i] > maxsig ? lo[i] : maxsig;
             }

@@ -24,6 +24,7 @@ struct DenseCtl {
 struct DenseParams {
     int32_t n, npad, nb, nw32;
     uint64_t *sigma;  // [n][128]
+    uint16_t *lvl;    // [n][128]
     uint32_t *F, *V, *ufr;
     __nv_bfloat16 *X;  // [8 * 128][npad] limb matrix
     DevCtl *ctl;

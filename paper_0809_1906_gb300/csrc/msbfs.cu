@@ -42,15 +42,21 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
     const size_t nW = (size_t)p.n * W;
     const size_t stride = (size_t)gridDim.x * kBlock;
     const size_t tid = (size_t)blockIdx.x * kBlock + threadIdx.x;
-    for (size_t i = tid; i < nW; i += stride) {
-        p.F[i] = 0u;  // level 0 frontier
-        p.V[i] = 0u;  // visited through level -1
+    for (size_t i = tid; i < 2 * nW; i += stride) {
+        p.F[i] = 0u;  // frontiers of levels 0 and 1
+        p.V[i] = 0u;  // visited through levels -1 and 0
     }
     const size_t nu = (size_t)p.Lcap * p.nw32;
     for (size_t i = tid; i < nu; i += stride) p.ufr[i] = 0u;
-    // masked level-0 rows of the source vertices start at zero (coalesced)
+    // masked rows start at zero: level 0 at the sources, level 1 at their neighbours
     for (size_t i = tid; i < (size_t)p.nb * B; i += stride) p.S[(size_t)p.sources[i / B] * B + i % B] = 0u;
     for (size_t i = tid; i < (size_t)p.Lcap; i += stride) p.wide[i] = 0u;
+    uint32_t *S1 = p.S + (size_t)p.n * B;
+    for (int b = blockIdx.x; b < p.nb; b += gridDim.x) {
+        const int s = p.sources[b];
+        const int e0 = p.row_ptr[s], deg = p.row_ptr[s + 1] - e0;
+        for (int i = threadIdx.x; i < deg * B; i += kBlock) S1[(size_t)p.col[e0 + i / B] * B + i % B] = 0u;
+    }
 
     __shared__ bool s_last;
     __syncthreads();
@@ -61,13 +67,16 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // d(s,s) = 0 and sigma_s(s) = 1 (Section 1.1)
+    // d(s,s) = 0 and sigma_s(s) = 1 (Section 1.1); the sources are the
+    // vertices visited through level 0
     for (int b = threadIdx.x; b < p.nb; b += kBlock) {
         const int s = p.sources[b];
         atomicOr(p.F + (size_t)s * W + (b >> 5), 1u << (b & 31));
+        atomicOr(p.V + nW + (size_t)s * W + (b >> 5), 1u << (b & 31));
         atomicOr(p.ufr + (s >> 5), 1u << (s & 31));
         p.sigma[(size_t)s * B + b] = 1ull;
         p.S[(size_t)s * B + b] = 1u;
+        if (p.lvl) p.lvl[(size_t)s * B + b] = 0;
     }
     if (threadIdx.x == 0) {
         p.ctl->fwd_done = 0u;
@@ -76,6 +85,65 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
         p.ctl->seq = p.seq;
         atomicExch(&p.ctl->blocks_done, 0u);
     }
+}
+
+// Level 0 -> 1 straight from the sources' rows: the vertices at distance 1
+// from s are its neighbours, each with exactly one shortest path (through
+// the arc from s). One warp per source; the level-1 rows were cleared by
+// k_init. Equivalent to k_forward at level 0 without scanning every arc.
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_first(const MsParams p) {
+    constexpr int B = 32 * W;
+    __shared__ uint32_t s_any;
+    __shared__ unsigned long long s_arcs;
+    if (threadIdx.x == 0) {
+        s_any = 0u;
+        s_arcs = 0ull;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int b = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+    if (b < p.nb) {
+        const size_t nW = (size_t)p.n * W;
+        uint32_t *F1 = p.F + nW;
+        uint32_t *S1 = p.S + (size_t)p.n * B;
+        uint32_t *uf1 = p.ufr + p.nw32;
+        const int s = p.sources[b];
+        const int e0 = p.row_ptr[s], e1 = p.row_ptr[s + 1];
+        for (int e = e0 + lane; e < e1; e += 32) {
+            const int v = p.col[e];
+            atomicOr(F1 + (size_t)v * W + (b >> 5), 1u << (b & 31));
+            atomicOr(uf1 + (v >> 5), 1u << (v & 31));
+            p.sigma[(size_t)v * B + b] = 1ull;
+            if (p.lvl) p.lvl[(size_t)v * B + b] = 1;
+            S1[(size_t)v * B + b] = 1u;
+        }
+        if (lane == 0 && e1 > e0) {
+            atomicOr(&s_any, 1u);
+            atomicAdd(&s_arcs, (unsigned long long)(e1 - e0));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    if (s_arcs) atomicAdd(&p.ctl->dag_arcs, s_arcs);
+    if (s_any) atomicOr(&p.ctl->nonempty, 1u);
+    __threadfence();
+    if (atomicAdd(&p.ctl->blocks_done, 1u) != gridDim.x - 1) return;
+    __threadfence();
+    const unsigned ne = atomicExch(&p.ctl->nonempty, 0u);
+    atomicExch(&p.ctl->blocks_done, 0u);
+    volatile HostCtl *h = p.hctl;
+    if (ne == 0u) {  // every source isolated: depth 0
+        p.ctl->fwd_done = 1u;
+        p.ctl->nlevels = 0;
+        h->nlevels = 0;
+        __threadfence_system();
+        h->done_seq = p.seq;
+    }
+    h->progress = 1;
+    __threadfence_system();
+    h->progress_seq = p.seq;
+    __threadfence_system();
 }
 
 template <int W>
@@ -144,7 +212,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
         }
         body::fwd_sum<W>(p.col, beg, end, ufl, Fl, Sl, p.sigma, wide, U, s_u[wib], s_nz[wib], lane, acc, nf, ovf, arcs);
         if (slot < 0) {
-            produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
+            produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next, p.lvl, l + 1);
             continue;
         }
         uint64_t *pp = p.part + (size_t)slot * B + lane;
@@ -179,7 +247,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
                 nf[j] |= __ldcg(qm + j);
             }
         }
-        produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
+        produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next, p.lvl, l + 1);
         if (lane == 0) p.cnt[first] = 0u;
     }
     const unsigned wovf = __ballot_sync(kFull, ovf);
@@ -283,61 +351,57 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
     }
 }
 
-// Per-source summaries: blockIdx.y = source word j, lane = source 32j+lane,
-// warps stride over vertices; the level of (v, s) is the one frontier that
-// holds its bit.
+// Per-source summaries. Thread t of a block owns source t % B and takes
+// every (256/B)-th vertex of the block's share; (v, s) counts when v was
+// reached (visited through level L-1, or in the last frontier), its level
+// is lvl[v][s]. Blocks write partial sums; k_hash_sum adds them in block
+// order.
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_hash(const MsParams p, const int L) {
     constexpr int B = 32 * W;
-    const int j = blockIdx.y;
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const uint32_t bit = 1u << lane;
+    constexpr int VS = kBlock / B;  // vertices per block step
+    const int s = threadIdx.x % B, vo = threadIdx.x / B;
+    const int j = s >> 5;
+    const uint32_t bit = 1u << (s & 31);
     const size_t nW = (size_t)p.n * W;
+    const uint32_t *Vl = p.V + (size_t)(L & 1) * nW;
+    const uint32_t *FL = p.F + (size_t)L * nW;
     uint64_t hs = 0, hd = 0, ds = 0, rc = 0;
-    // four vertices per warp step so their frontier-word loads overlap
-    for (int v0 = (blockIdx.x * kWarps + wib) * 4; v0 < p.n; v0 += gridDim.x * kWarps * 4) {
-        int lev[4] = {-1, -1, -1, -1};
-        for (int l = 0; l <= L; ++l) {
-            const uint32_t *Fw = p.F + (size_t)l * nW + j;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int v = v0 + q;
-                if (v < p.n && (__ldg(Fw + (size_t)v * W) & bit)) lev[q] = l;
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int v = v0 + q;
-            if (lev[q] >= 0) {
-                const uint64_t sg = p.sigma[(size_t)v * B + 32 * j + lane];
-                hs += sg * (uint64_t)(v + 1);
-                hd += (uint64_t)(lev[q] + 1) * (uint64_t)(v + 1);
-                ds += (uint64_t)lev[q];
-                rc += 1ull;
-            }
-        }
+    for (int v = blockIdx.x * VS + vo; v < p.n; v += gridDim.x * VS) {
+        if (((__ldg(Vl + (size_t)v * W + j) | __ldg(FL + (size_t)v * W + j)) & bit) == 0u) continue;
+        const uint64_t sg = __ldg(p.sigma + (size_t)v * B + s);
+        const uint64_t l = __ldg(p.lvl + (size_t)v * B + s);
+        hs += sg * (uint64_t)(v + 1);
+        hd += (l + 1) * (uint64_t)(v + 1);
+        ds += l;
+        rc += 1ull;
     }
-    __shared__ uint64_t sh[4][kWarps][32];
-    sh[0][wib][lane] = hs;
-    sh[1][wib][lane] = hd;
-    sh[2][wib][lane] = ds;
-    sh[3][wib][lane] = rc;
+    __shared__ uint64_t sh[4][kBlock];
+    sh[0][threadIdx.x] = hs;
+    sh[1][threadIdx.x] = hd;
+    sh[2][threadIdx.x] = ds;
+    sh[3][threadIdx.x] = rc;
     __syncthreads();
-    if (wib != 0) return;
-    for (int w = 1; w < kWarps; ++w) {
-        hs += sh[0][w][lane];
-        hd += sh[1][w][lane];
-        ds += sh[2][w][lane];
-        rc += sh[3][w][lane];
+    if (threadIdx.x >= B) return;
+    for (int q = 0; q < 4; ++q) {
+        uint64_t acc = 0;
+        for (int k = 0; k < VS; ++k) acc += sh[q][k * B + threadIdx.x];
+        p.hpart[((size_t)blockIdx.x * 4 + q) * B + threadIdx.x] = acc;
     }
-    const int b = 32 * j + lane;
-    if (b < p.nb) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(p.h_sigma + b), hs);
-        atomicAdd(reinterpret_cast<unsigned long long *>(p.h_dist + b), hd);
-        atomicAdd(reinterpret_cast<unsigned long long *>(p.dist_sum + b), ds);
-        atomicAdd(reinterpret_cast<unsigned long long *>(p.reach + b), rc);
-    }
+}
+
+template <int W>
+__global__ void k_hash_sum(const MsParams p, const int blocks) {
+    constexpr int B = 32 * W;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= p.nb) return;
+    uint64_t acc[4] = {0, 0, 0, 0};
+    for (int k = 0; k < blocks; ++k)
+        for (int q = 0; q < 4; ++q) acc[q] += p.hpart[((size_t)k * 4 + q) * B + s];
+    p.h_sigma[s] = acc[0];
+    p.h_dist[s] = acc[1];
+    p.dist_sum[s] = (int64_t)acc[2];
+    p.reach[s] = (int64_t)acc[3];
 }
 
 // Rows of the forward pass for bc_forward_rows: out[b][v] for this batch.
@@ -412,6 +476,12 @@ void ms_launch_init(int W, const MsParams &p, cudaStream_t st) {
     BCGB_DISPATCH_W(W, launch_init_t<kW>(p, st));
 }
 
+void ms_launch_first(int W, const MsParams &p, cudaStream_t st) {
+    const int g = (p.nb + kWarps - 1) / kWarps;
+    if (g == 0) return;
+    BCGB_DISPATCH_W(W, (k_first<kW><<<g, kBlock, 0, st>>>(p)));
+}
+
 void ms_launch_forward(int W, const MsParams &p, int level, cudaStream_t st) {
     if (p.nitems == 0) return;
     BCGB_DISPATCH_W(W, (k_forward<kW><<<item_blocks(p, k_forward<kW>), kBlock, 0, st>>>(p, level)));
@@ -422,12 +492,16 @@ void ms_launch_backward(int W, const MsParams &p, int level, cudaStream_t st) {
     BCGB_DISPATCH_W(W, (k_backward<kW><<<item_blocks(p, k_backward<kW>), kBlock, 0, st>>>(p, level)));
 }
 
+int ms_hash_blocks(const MsParams &p) {
+    int g = 4 * sm_count();
+    const int need = (p.n + 7) / 8;
+    return g < need ? g : (need < 1 ? 1 : need);
+}
+
 void ms_launch_hash(int W, const MsParams &p, int nlevels, cudaStream_t st) {
-    int gx = (p.n + 4 * kWarps - 1) / (4 * kWarps);
-    const int cap = (8 * sm_count() + W - 1) / W;
-    gx = gx > cap ? cap : gx;
-    gx = gx < 1 ? 1 : gx;
-    BCGB_DISPATCH_W(W, (k_hash<kW><<<dim3(gx, kW), kBlock, 0, st>>>(p, nlevels)));
+    const int g = ms_hash_blocks(p);
+    BCGB_DISPATCH_W(W, (k_hash<kW><<<g, kBlock, 0, st>>>(p, nlevels)));
+    BCGB_DISPATCH_W(W, (k_hash_sum<kW><<<(p.nb + 127) / 128, 128, 0, st>>>(p, g)));
 }
 
 void ms_launch_rows(int W, const MsParams &p, int nlevels, uint64_t *sig_out, int32_t *dist_out,
