@@ -80,7 +80,8 @@ struct bc_graph {
     DevBuf<uint64_t> sigma, part, hpart;
     DevBuf<uint16_t> lvl;
     DevBuf<float> cval;
-    DevBuf<uint32_t> Smask, wideflags, F, ufr, V, pmask, cnt;
+    DevBuf<uint16_t> Smask;
+    DevBuf<uint32_t> wideflags, F, ufr, V, pmask, cnt;
 
     // results
     DevBuf<double> bc;
@@ -261,7 +262,7 @@ int ensure_state(bc_graph *g, int W, int Lcap) {
         int dev = 0, sms = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        CK(g->hpart.ensure((size_t)(4 * sms + 1) * 4 * B));  // per-block summary partials
+        CK(g->hpart.ensure((size_t)(8 * sms + 1) * 4 * B));  // per-block summary partials
     }
     CK(g->Smask.ensure(2 * n * B));
     CK(g->wideflags.ensure((size_t)Lcap));
@@ -876,7 +877,7 @@ struct bc_many {
     DevBuf<unsigned> queue, arrive, capped;
     DevBuf<double> partial;
     DevBuf<uint64_t> sigma;
-    DevBuf<uint32_t> Smask;
+    DevBuf<uint16_t> Smask;
     DevBuf<float> cval;
     DevBuf<uint32_t> F, V, ufr;
     bcgb::DevCtl *ctl = nullptr;

@@ -4,9 +4,9 @@
 // vertices; every per-vertex row is contiguous so a warp reads a neighbour's
 // row in one coalesced access):
 //   sigma  uint64 [n][B]        exact path counts sigma_s(v)        (Section 1.1)
-//   S      uint32 [2][n][B]     masked rows by level parity: sigma_s(v) where
+//   S      uint16 [2][n][B]     masked rows by level parity: sigma_s(v) where
 //                               d(s,v) = l, 0 for the other sources
-//   wide   uint32 [Lcap]        level l has a count >= 2^32 (S unusable there)
+//   wide   uint32 [Lcap]        level l has a count >= 2^16 (S unusable there)
 //   lvl    uint16 [n][B]        d(s,v) for reached pairs (per-source summaries)
 //   cval   float  [2][n][B]     masked rows by level parity of
 //                               c_s(v) = (1 + delta_s*(v)) / sigma_s(v)
@@ -67,7 +67,7 @@ struct MsParams {
     uint64_t *sigma;
     uint16_t *lvl;   // [n][B] level of each reached (vertex, source)
     uint64_t *hpart; // [blocks][4][B] per-block partial summaries
-    uint32_t *S;   // [2][n][B]
+    uint16_t *S;   // [2][n][B]
     uint32_t *wide;  // [Lcap]
     float *cval;   // [2][n][B]
     uint32_t *F;

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kMBlock, 4) k_many(const ManyParams p) {
     __shared__ uint32_t s_nz[kMWarps][32];
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     uint64_t *sigma = p.sigma + (size_t)blockIdx.x * p.nmax * B;
-    uint32_t *Sbuf = p.S + (size_t)blockIdx.x * 2 * p.nmax * B;
+    uint16_t *Sbuf = p.S + (size_t)blockIdx.x * 2 * p.nmax * B;
     float *cval = p.cval + (size_t)blockIdx.x * 2 * p.nmax * B;
     uint32_t *F = p.F + (size_t)blockIdx.x * p.Lcap * p.nmax * W;
     uint32_t *V = p.V + (size_t)blockIdx.x * 2 * p.nmax * W;
@@ -82,12 +82,12 @@ __global__ void __launch_bounds__(kMBlock, 4) k_many(const ManyParams p) {
                 F[(size_t)s * W + (b >> 5)] |= 1u << (b & 31);  // one source per (s, b): no race
                 atomicOr(ufr + (s >> 5), 1u << (s & 31));
                 sigma[(size_t)s * B + b] = 1ull;
-                for (int k = 0; k < B; ++k) Sbuf[(size_t)s * B + k] = k == b ? 1u : 0u;  // masked level-0 row
+                for (int k = 0; k < B; ++k) Sbuf[(size_t)s * B + k] = k == b ? 1 : 0;  // masked level-0 row
             }
             __syncthreads();
             // forward levels
             int L = 0;
-            bool wide = false;  // the current level has a count >= 2^32
+            bool wide = false;  // the current level has a count >= 2^16
             for (int l = 0;; ++l) {
                 if (l + 1 >= p.Lcap) {
                     capped = true;
@@ -99,8 +99,8 @@ __global__ void __launch_bounds__(kMBlock, 4) k_many(const ManyParams p) {
                 uint32_t *ufn = ufr + (size_t)(l + 1) * nw32;
                 const uint32_t *Vin = V + (size_t)(l & 1) * nW;
                 uint32_t *Vout = V + (size_t)((l + 1) & 1) * nW;
-                const uint32_t *Sl = Sbuf + (size_t)(l & 1) * nB;
-                uint32_t *Sn = Sbuf + (size_t)((l + 1) & 1) * nB;
+                const uint16_t *Sl = Sbuf + (size_t)(l & 1) * nB;
+                uint16_t *Sn = Sbuf + (size_t)((l + 1) & 1) * nB;
                 bool produced = false, wide_next = false;
                 for (int v = wib; v < n; v += kMWarps) {
                     uint32_t U[W], a[W], f[W];

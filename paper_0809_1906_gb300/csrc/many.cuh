@@ -34,7 +34,7 @@ struct ManyParams {
     unsigned *capped;   // [ngraphs] set when a graph is deeper than Lcap levels
     double *partial;    // partial BC vectors of split graphs
     uint64_t *sigma;    // per-CTA workspaces
-    uint32_t *S;        // [2][nmax][B] masked forward rows
+    uint16_t *S;        // [2][nmax][B] masked forward rows
     float *cval;        // [2][nmax][B] masked backward rows
     uint32_t *F, *V, *ufr;
     DevCtl *ctl;

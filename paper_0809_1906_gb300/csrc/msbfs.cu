@@ -48,15 +48,10 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
     }
     const size_t nu = (size_t)p.Lcap * p.nw32;
     for (size_t i = tid; i < nu; i += stride) p.ufr[i] = 0u;
-    // masked rows start at zero: level 0 at the sources, level 1 at their neighbours
-    for (size_t i = tid; i < (size_t)p.nb * B; i += stride) p.S[(size_t)p.sources[i / B] * B + i % B] = 0u;
-    for (size_t i = tid; i < (size_t)p.Lcap; i += stride) p.wide[i] = 0u;
-    uint32_t *S1 = p.S + (size_t)p.n * B;
-    for (int b = blockIdx.x; b < p.nb; b += gridDim.x) {
-        const int s = p.sources[b];
-        const int e0 = p.row_ptr[s], deg = p.row_ptr[s + 1] - e0;
-        for (int i = threadIdx.x; i < deg * B; i += kBlock) S1[(size_t)p.col[e0 + i / B] * B + i % B] = 0u;
-    }
+    // masked level-0 rows of the sources start at zero
+    for (size_t i = tid; i < (size_t)p.nb * B; i += stride) p.S[(size_t)p.sources[i / B] * B + i % B] = 0;
+    // level 1 is read through the per-source masks of sigma (no masked rows)
+    for (size_t i = tid; i < (size_t)p.Lcap; i += stride) p.wide[i] = i == 1 ? 1u : 0u;
 
     __shared__ bool s_last;
     __syncthreads();
@@ -75,7 +70,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
         atomicOr(p.V + nW + (size_t)s * W + (b >> 5), 1u << (b & 31));
         atomicOr(p.ufr + (s >> 5), 1u << (s & 31));
         p.sigma[(size_t)s * B + b] = 1ull;
-        p.S[(size_t)s * B + b] = 1u;
+        p.S[(size_t)s * B + b] = 1;
         if (p.lvl) p.lvl[(size_t)s * B + b] = 0;
     }
     if (threadIdx.x == 0) {
@@ -89,8 +84,9 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
 
 // Level 0 -> 1 straight from the sources' rows: the vertices at distance 1
 // from s are its neighbours, each with exactly one shortest path (through
-// the arc from s). One warp per source; the level-1 rows were cleared by
-// k_init. Equivalent to k_forward at level 0 without scanning every arc.
+// the arc from s). One warp per source. Level 1 is marked wide by k_init, so
+// the next step reads sigma under the frontier masks and no masked rows are
+// written here. Equivalent to k_forward at level 0 without scanning every arc.
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_first(const MsParams p) {
     constexpr int B = 32 * W;
@@ -106,7 +102,6 @@ __global__ void __launch_bounds__(kBlock) k_first(const MsParams p) {
     if (b < p.nb) {
         const size_t nW = (size_t)p.n * W;
         uint32_t *F1 = p.F + nW;
-        uint32_t *S1 = p.S + (size_t)p.n * B;
         uint32_t *uf1 = p.ufr + p.nw32;
         const int s = p.sources[b];
         const int e0 = p.row_ptr[s], e1 = p.row_ptr[s + 1];
@@ -116,7 +111,6 @@ __global__ void __launch_bounds__(kBlock) k_first(const MsParams p) {
             atomicOr(uf1 + (v >> 5), 1u << (v & 31));
             p.sigma[(size_t)v * B + b] = 1ull;
             if (p.lvl) p.lvl[(size_t)v * B + b] = 1;
-            S1[(size_t)v * B + b] = 1u;
         }
         if (lane == 0 && e1 > e0) {
             atomicOr(&s_any, 1u);
@@ -171,8 +165,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     const uint32_t *Vin = p.V + (size_t)(l & 1) * nW;
     uint32_t *Vout = p.V + (size_t)((l + 1) & 1) * nW;
     const size_t nB = (size_t)p.n * B;
-    const uint32_t *Sl = p.S + (size_t)(l & 1) * nB;
-    uint32_t *Sn = p.S + (size_t)((l + 1) & 1) * nB;
+    const uint16_t *Sl = p.S + (size_t)(l & 1) * nB;
+    uint16_t *Sn = p.S + (size_t)((l + 1) & 1) * nB;
     const bool wide = *(volatile uint32_t *)(p.wide + l) != 0u;
     bool produced = false, ovf = false, wide_next = false;
     uint32_t arcs = 0;  // predecessor relations counted by this lane
@@ -367,14 +361,30 @@ __global__ void __launch_bounds__(kBlock) k_hash(const MsParams p, const int L) 
     const uint32_t *Vl = p.V + (size_t)(L & 1) * nW;
     const uint32_t *FL = p.F + (size_t)L * nW;
     uint64_t hs = 0, hd = 0, ds = 0, rc = 0;
-    for (int v = blockIdx.x * VS + vo; v < p.n; v += gridDim.x * VS) {
-        if (((__ldg(Vl + (size_t)v * W + j) | __ldg(FL + (size_t)v * W + j)) & bit) == 0u) continue;
-        const uint64_t sg = __ldg(p.sigma + (size_t)v * B + s);
-        const uint64_t l = __ldg(p.lvl + (size_t)v * B + s);
-        hs += sg * (uint64_t)(v + 1);
-        hd += (l + 1) * (uint64_t)(v + 1);
-        ds += l;
-        rc += 1ull;
+    // four vertices per step, their loads independent
+    for (int v0 = (blockIdx.x * VS + vo) * 4; v0 < p.n; v0 += gridDim.x * VS * 4) {
+        uint32_t r[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int v = v0 + q;
+            r[q] = v < p.n ? ((__ldg(Vl + (size_t)v * W + j) | __ldg(FL + (size_t)v * W + j)) & bit) : 0u;
+        }
+        uint64_t sg[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int v = v0 + q;
+            sg[q] = r[q] ? __ldg(p.sigma + (size_t)v * B + s) : 0ull;
+            l[q] = r[q] ? (uint64_t)__ldg(p.lvl + (size_t)v * B + s) : 0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!r[q]) continue;
+            const uint64_t vv = (uint64_t)(v0 + q + 1);
+            hs += sg[q] * vv;
+            hd += (l[q] + 1) * vv;
+            ds += l[q];
+            rc += 1ull;
+        }
     }
     __shared__ uint64_t sh[4][kBlock];
     sh[0][threadIdx.x] = hs;
@@ -493,8 +503,8 @@ void ms_launch_backward(int W, const MsParams &p, int level, cudaStream_t st) {
 }
 
 int ms_hash_blocks(const MsParams &p) {
-    int g = 4 * sm_count();
-    const int need = (p.n + 7) / 8;
+    int g = 8 * sm_count();
+    const int need = (p.n + 31) / 32;
     return g < need ? g : (need < 1 ? 1 : need);
 }
 

@@ -5,10 +5,10 @@
 // A batch holds B = 32*W sources; every per-vertex row (sigma, c, frontier
 // words) is contiguous, lane i of a warp owns sources 32j + i (j < W). Beside
 // the permanent uint64 sigma array, each level keeps *masked rows*: row v of
-// level l holds sigma_s(v) (forward, as uint32) or c_s(v) (backward, FP32)
+// level l holds sigma_s(v) (forward, as uint16) or c_s(v) (backward, FP32)
 // for the sources s with d(s,v) = l and 0 for every other source, in two
 // buffers alternating by level parity. A level whose counts do not all fit
-// in 32 bits is marked "wide"; the next level then reads the permanent uint64
+// in 16 bits is marked "wide"; the next level then reads the permanent uint64
 // sigma under per-source masks instead (exact either way). A warp owns a vertex v (or a chunk of its arcs) and walks v's
 // arcs 32 at a time:
 //   probe  lane k takes arc k of the chunk: neighbour u_k, one bit of the
@@ -112,14 +112,14 @@ __device__ __forceinline__ unsigned probe_chunk(const int32_t *__restrict__ col,
 // Forward sums over arcs [beg, end) of v for level l -> l+1: for source
 // s = 32j + lane, acc[j] += sigma_s(u) over the neighbours u in P_s(v), for
 // every s still unvisited at v (U); other entries of acc are discarded by the
-// caller. Narrow levels add the masked uint32 rows Sl (zero wherever u is not
+// caller. Narrow levels add the masked uint16 rows Sl (zero wherever u is not
 // a predecessor); a wide level reads sigma under the per-source masks. nf[j]
 // gets the sources reaching v; exact uint64 sums, ovf flags a carry out of
 // bit 63; arcs counts predecessor relations (lane-local).
 template <int W, bool NC = true>
 __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg, int end,
                                         const uint32_t *__restrict__ ufl, const uint32_t *__restrict__ Fl,
-                                        const uint32_t *__restrict__ Sl, const uint64_t *__restrict__ sigma,
+                                        const uint16_t *__restrict__ Sl, const uint64_t *__restrict__ sigma,
                                         bool wide, const uint32_t (&U)[W], int32_t *s_u, uint32_t *s_nz, int lane,
                                         uint64_t (&acc)[W], uint32_t (&nf)[W], bool &ovf, uint32_t &arcs) {
     constexpr int B = 32 * W;
@@ -134,19 +134,19 @@ __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg
         }
         if (!wide) {
             // two neighbours per step: 2W independent coalesced loads in flight
-            const uint32_t *base = Sl + lane;
+            const uint16_t *base = Sl + lane;
             while (bal) {
                 const int k0 = __ffs(bal) - 1;
                 bal &= bal - 1;
                 const int k1 = bal ? __ffs(bal) - 1 : -1;
                 if (k1 >= 0) bal &= bal - 1;
-                const uint32_t *r0 = base + (size_t)s_u[k0] * B;
-                const uint32_t *r1 = base + (size_t)s_u[k1 >= 0 ? k1 : k0] * B;
+                const uint16_t *r0 = base + (size_t)s_u[k0] * B;
+                const uint16_t *r1 = base + (size_t)s_u[k1 >= 0 ? k1 : k0] * B;
                 uint32_t x0[W], x1[W];
 #pragma unroll
                 for (int j = 0; j < W; ++j) {
-                    x0[j] = ldx<NC>(r0 + 32 * j);
-                    x1[j] = k1 >= 0 ? ldx<NC>(r1 + 32 * j) : 0u;
+                    x0[j] = (uint32_t)ldx<NC>(r0 + 32 * j);
+                    x1[j] = k1 >= 0 ? (uint32_t)ldx<NC>(r1 + 32 * j) : 0u;
                 }
 #pragma unroll
                 for (int j = 0; j < W; ++j) {
@@ -214,12 +214,12 @@ __device__ __forceinline__ void bwd_sum(const int32_t *__restrict__ col, int beg
 }
 
 // Store sigma and the new frontier words of v (its level-(l+1) sums are final).
-// Sn: the masked level-(l+1) uint32 row buffer, written in full (zeros for
+// Sn: the masked level-(l+1) uint16 row buffer, written in full (zeros for
 // the sources v is not new for) when v joins some frontier. Returns whether
-// v joined; *wide is set when one of its new counts needs more than 32 bits.
+// v joined; wide is set when one of its new counts needs more than 16 bits.
 // lvl (may be null): receives the new level lnext for the new pairs.
 template <int W>
-__device__ __forceinline__ bool store_next(uint64_t *sigma, uint32_t *Sn, uint32_t *Fn, uint32_t *ufn, int v,
+__device__ __forceinline__ bool store_next(uint64_t *sigma, uint16_t *Sn, uint32_t *Fn, uint32_t *ufn, int v,
                                            const uint64_t (&acc)[W], const uint32_t (&nf)[W], int lane,
                                            bool &wide, uint16_t *lvl = nullptr, int lnext = 0) {
     constexpr int B = 32 * W;
@@ -237,8 +237,8 @@ __device__ __forceinline__ bool store_next(uint64_t *sigma, uint32_t *Sn, uint32
 #pragma unroll
         for (int j = 0; j < W; ++j) {
             const bool mine = (nf[j] >> lane) & 1u;
-            wide |= mine && (acc[j] >> 32) != 0ull;
-            Sn[(size_t)v * B + 32 * j + lane] = mine ? (uint32_t)acc[j] : 0u;
+            wide |= mine && (acc[j] >> 16) != 0ull;
+            Sn[(size_t)v * B + 32 * j + lane] = mine ? (uint16_t)acc[j] : (uint16_t)0;
         }
     }
     if (any != 0 && lane == 0) atomicOr(ufn + (v >> 5), 1u << (v & 31));

@@ -24,7 +24,7 @@
 namespace {
 
 // The limits below fix the array size: with B = 32 sources per batch, a
-// batch needs per vertex 256 B of path counts, 256 B of masked count rows
+// batch needs per vertex 256 B of path counts, 128 B of masked count rows
 // (two levels), 256 B of masked dependency rows (two levels), 4 B of
 // frontier bits per level (64 levels), 8 B of visited bits and 16 B of work
 // item; plus the bitmaps and the control blocks.
@@ -37,7 +37,7 @@ constexpr int kNw32 = (kMaxN + 31) / 32;
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kOffSigma = 0;
 constexpr size_t kOffS = align256(kOffSigma + (size_t)kMaxN * kB * sizeof(uint64_t));
-constexpr size_t kOffWide = align256(kOffS + (size_t)2 * kMaxN * kB * sizeof(uint32_t));
+constexpr size_t kOffWide = align256(kOffS + (size_t)2 * kMaxN * kB * sizeof(uint16_t));
 constexpr size_t kOffCval = align256(kOffWide + (size_t)kLcap * sizeof(uint32_t));
 constexpr size_t kOffF = align256(kOffCval + (size_t)2 * kMaxN * kB * sizeof(float));
 constexpr size_t kOffUfr = align256(kOffF + (size_t)kLcap * kMaxN * kW * sizeof(uint32_t));
@@ -130,7 +130,7 @@ extern "C" int bc_run_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *
     p.slot_first = dummy;  // never read: no item has a slot
     p.slot_nch = dummy;
     p.sigma = reinterpret_cast<uint64_t *>(base + kOffSigma);
-    p.S = reinterpret_cast<uint32_t *>(base + kOffS);
+    p.S = reinterpret_cast<uint16_t *>(base + kOffS);
     p.wide = reinterpret_cast<uint32_t *>(base + kOffWide);
     p.cval = reinterpret_cast<float *>(base + kOffCval);
     p.F = reinterpret_cast<uint32_t *>(base + kOffF);
