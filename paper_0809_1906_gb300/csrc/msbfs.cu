@@ -50,8 +50,42 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
     for (size_t i = tid; i < nu; i += stride) p.ufr[i] = 0u;
     // masked level-0 rows of the sources start at zero
     for (size_t i = tid; i < (size_t)p.nb * B; i += stride) p.S[(size_t)p.sources[i / B] * B + i % B] = 0;
-    // level 1 is read through the per-source masks of sigma (no masked rows)
-    for (size_t i = tid; i < (size_t)p.Lcap; i += stride) p.wide[i] = i == 1 ? 1u : 0u;
+    for (size_t i = tid; i < (size_t)p.Lcap; i += stride) p.wide[i] = 0u;
+    // masked level-1 rows of the sources' neighbours start at zero: every
+    // block scans the batch's source degrees, then the grid strides over
+    // all (neighbour, source) entries, so a high-degree source is shared out
+    __shared__ int s_off[kBlock + 1];
+    __shared__ int s_wsum[kWarps];
+    {
+        // exclusive scan of the source degrees (nb <= kBlock): warp scan, then warp totals
+        const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+        int deg = 0;
+        if (t < p.nb) deg = p.row_ptr[p.sources[t] + 1] - p.row_ptr[p.sources[t]];
+        int x = deg;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) s_wsum[wid] = x;
+        __syncthreads();
+        int base = 0;
+        for (int k = 0; k < wid; ++k) base += s_wsum[k];
+        s_off[t] = base + x - deg;
+        if (t == kBlock - 1) s_off[kBlock] = base + x;
+        __syncthreads();
+    }
+    {
+        uint16_t *S1 = p.S + (size_t)p.n * B;
+        const size_t total = (size_t)s_off[p.nb] * B;  // entries past nb add degree 0
+        int b = 0;
+        for (size_t i = tid; i < total; i += stride) {
+            const int a = (int)(i / B);
+            while (s_off[b + 1] <= a) ++b;  // i only grows, so b only moves forward
+            const int s = p.sources[b];
+            S1[(size_t)p.col[p.row_ptr[s] + (a - s_off[b])] * B + i % B] = 0;
+        }
+    }
 
     __shared__ bool s_last;
     __syncthreads();
@@ -84,9 +118,8 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
 
 // Level 0 -> 1 straight from the sources' rows: the vertices at distance 1
 // from s are its neighbours, each with exactly one shortest path (through
-// the arc from s). One warp per source. Level 1 is marked wide by k_init, so
-// the next step reads sigma under the frontier masks and no masked rows are
-// written here. Equivalent to k_forward at level 0 without scanning every arc.
+// the arc from s). One warp per source; the level-1 masked rows were cleared
+// by k_init. Equivalent to k_forward at level 0 without scanning every arc.
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_first(const MsParams p) {
     constexpr int B = 32 * W;
@@ -103,6 +136,7 @@ __global__ void __launch_bounds__(kBlock) k_first(const MsParams p) {
         const size_t nW = (size_t)p.n * W;
         uint32_t *F1 = p.F + nW;
         uint32_t *uf1 = p.ufr + p.nw32;
+        uint16_t *S1 = p.S + (size_t)p.n * B;
         const int s = p.sources[b];
         const int e0 = p.row_ptr[s], e1 = p.row_ptr[s + 1];
         for (int e = e0 + lane; e < e1; e += 32) {
@@ -111,6 +145,7 @@ __global__ void __launch_bounds__(kBlock) k_first(const MsParams p) {
             atomicOr(uf1 + (v >> 5), 1u << (v & 31));
             p.sigma[(size_t)v * B + b] = 1ull;
             if (p.lvl) p.lvl[(size_t)v * B + b] = 1;
+            S1[(size_t)v * B + b] = 1;
         }
         if (lane == 0 && e1 > e0) {
             atomicOr(&s_any, 1u);
@@ -400,18 +435,24 @@ __global__ void __launch_bounds__(kBlock) k_hash(const MsParams p, const int L) 
     }
 }
 
+// One warp per (quantity, source): lanes add strided block partials, then a
+// fixed butterfly, so the sum order never changes.
 template <int W>
 __global__ void k_hash_sum(const MsParams p, const int blocks) {
     constexpr int B = 32 * W;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= p.nb) return;
-    uint64_t acc[4] = {0, 0, 0, 0};
-    for (int k = 0; k < blocks; ++k)
-        for (int q = 0; q < 4; ++q) acc[q] += p.hpart[((size_t)k * 4 + q) * B + s];
-    p.h_sigma[s] = acc[0];
-    p.h_dist[s] = acc[1];
-    p.dist_sum[s] = (int64_t)acc[2];
-    p.reach[s] = (int64_t)acc[3];
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int q = w / B, s = w % B;
+    if (q >= 4 || s >= p.nb) return;
+    uint64_t acc = 0;
+    for (int k = lane; k < blocks; k += 32) acc += __ldg(p.hpart + ((size_t)k * 4 + q) * B + s);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+    if (lane != 0) return;
+    if (q == 0) p.h_sigma[s] = acc;
+    if (q == 1) p.h_dist[s] = acc;
+    if (q == 2) p.dist_sum[s] = (int64_t)acc;
+    if (q == 3) p.reach[s] = (int64_t)acc;
 }
 
 // Rows of the forward pass for bc_forward_rows: out[b][v] for this batch.
@@ -511,7 +552,7 @@ int ms_hash_blocks(const MsParams &p) {
 void ms_launch_hash(int W, const MsParams &p, int nlevels, cudaStream_t st) {
     const int g = ms_hash_blocks(p);
     BCGB_DISPATCH_W(W, (k_hash<kW><<<g, kBlock, 0, st>>>(p, nlevels)));
-    BCGB_DISPATCH_W(W, (k_hash_sum<kW><<<(p.nb + 127) / 128, 128, 0, st>>>(p, g)));
+    BCGB_DISPATCH_W(W, (k_hash_sum<kW><<<(4 * 32 * kW * 32 + kBlock - 1) / kBlock, kBlock, 0, st>>>(p, g)));
 }
 
 void ms_launch_rows(int W, const MsParams &p, int nlevels, uint64_t *sig_out, int32_t *dist_out,
