@@ -475,6 +475,7 @@ int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStr
         const int32_t nb = std::min<int32_t>(B, nsrc - b0);
         bcgb::MsParams p = make_params(g);
         p.nb = nb;
+        p.first = 1;
         p.seq = ++g->seq;
         p.sources = g->sources.p + b0;
         if (hash) {

@@ -54,6 +54,7 @@ struct MsParams {
     int32_t nw32;  // words of one union-frontier bitmap
     int32_t Lcap;  // level slots in F / ufr
     int32_t nb;    // sources in this batch (<= B)
+    int32_t first; // level 1 was produced by k_first (all its counts are 1)
     uint32_t seq;
     const int32_t *row_ptr;
     const int32_t *col;

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kMBlock, 4) k_many(const ManyParams p) {
                         acc[j] = 0ull;
                         nf[j] = 0u;
                     }
-                    body::fwd_sum<W, false>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufl, Fl, Sl, sigma, wide, U,
+                    body::fwd_sum<W, false>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufl, Fl, Sl, sigma, wide, false, U,
                                             s_u[wib], s_nz[wib], lane, acc, nf, ovf, arcs);
                     produced |= body::store_next<W>(sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
                 }

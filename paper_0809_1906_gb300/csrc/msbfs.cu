@@ -51,42 +51,6 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
     // masked level-0 rows of the sources start at zero
     for (size_t i = tid; i < (size_t)p.nb * B; i += stride) p.S[(size_t)p.sources[i / B] * B + i % B] = 0;
     for (size_t i = tid; i < (size_t)p.Lcap; i += stride) p.wide[i] = 0u;
-    // masked level-1 rows of the sources' neighbours start at zero: every
-    // block scans the batch's source degrees, then the grid strides over
-    // all (neighbour, source) entries, so a high-degree source is shared out
-    __shared__ int s_off[kBlock + 1];
-    __shared__ int s_wsum[kWarps];
-    {
-        // exclusive scan of the source degrees (nb <= kBlock): warp scan, then warp totals
-        const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-        int deg = 0;
-        if (t < p.nb) deg = p.row_ptr[p.sources[t] + 1] - p.row_ptr[p.sources[t]];
-        int x = deg;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, off);
-            if (lane >= off) x += y;
-        }
-        if (lane == 31) s_wsum[wid] = x;
-        __syncthreads();
-        int base = 0;
-        for (int k = 0; k < wid; ++k) base += s_wsum[k];
-        s_off[t] = base + x - deg;
-        if (t == kBlock - 1) s_off[kBlock] = base + x;
-        __syncthreads();
-    }
-    {
-        uint16_t *S1 = p.S + (size_t)p.n * B;
-        const size_t total = (size_t)s_off[p.nb] * B;  // entries past nb add degree 0
-        int b = 0;
-        for (size_t i = tid; i < total; i += stride) {
-            const int a = (int)(i / B);
-            while (s_off[b + 1] <= a) ++b;  // i only grows, so b only moves forward
-            const int s = p.sources[b];
-            S1[(size_t)p.col[p.row_ptr[s] + (a - s_off[b])] * B + i % B] = 0;
-        }
-    }
-
     __shared__ bool s_last;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -118,51 +82,56 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
 
 // Level 0 -> 1 straight from the sources' rows: the vertices at distance 1
 // from s are its neighbours, each with exactly one shortest path (through
-// the arc from s). One warp per source; the level-1 masked rows were cleared
-// by k_init. Equivalent to k_forward at level 0 without scanning every arc.
+// the arc from s). The batch's arcs out of its sources are dealt over the
+// whole grid (block scan of the source degrees), so a high-degree source is
+// shared out. No masked rows are written: the next level sees that every
+// count is 1 and counts predecessors instead (fwd_sum, `ones`).
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_first(const MsParams p) {
     constexpr int B = 32 * W;
-    __shared__ uint32_t s_any;
-    __shared__ unsigned long long s_arcs;
-    if (threadIdx.x == 0) {
-        s_any = 0u;
-        s_arcs = 0ull;
+    __shared__ int s_off[kBlock + 1];
+    __shared__ int s_wsum[kWarps];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    {
+        int deg = 0;
+        if (t < p.nb) deg = p.row_ptr[p.sources[t] + 1] - p.row_ptr[p.sources[t]];
+        int x = deg;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(kFull, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) s_wsum[wid] = x;
+        __syncthreads();
+        int base = 0;
+        for (int k = 0; k < wid; ++k) base += s_wsum[k];
+        s_off[t] = base + x - deg;
+        if (t == kBlock - 1) s_off[kBlock] = base + x;
+        __syncthreads();
     }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int b = (blockIdx.x * kBlock + threadIdx.x) >> 5;
-    if (b < p.nb) {
-        const size_t nW = (size_t)p.n * W;
-        uint32_t *F1 = p.F + nW;
-        uint32_t *uf1 = p.ufr + p.nw32;
-        uint16_t *S1 = p.S + (size_t)p.n * B;
+    const size_t nW = (size_t)p.n * W;
+    uint32_t *F1 = p.F + nW;
+    uint32_t *uf1 = p.ufr + p.nw32;
+    const int total = s_off[p.nb];
+    int b = 0;
+    for (int a = blockIdx.x * kBlock + t; a < total; a += gridDim.x * kBlock) {
+        while (s_off[b + 1] <= a) ++b;  // a only grows, so b only moves forward
         const int s = p.sources[b];
-        const int e0 = p.row_ptr[s], e1 = p.row_ptr[s + 1];
-        for (int e = e0 + lane; e < e1; e += 32) {
-            const int v = p.col[e];
-            atomicOr(F1 + (size_t)v * W + (b >> 5), 1u << (b & 31));
-            atomicOr(uf1 + (v >> 5), 1u << (v & 31));
-            p.sigma[(size_t)v * B + b] = 1ull;
-            if (p.lvl) p.lvl[(size_t)v * B + b] = 1;
-            S1[(size_t)v * B + b] = 1;
-        }
-        if (lane == 0 && e1 > e0) {
-            atomicOr(&s_any, 1u);
-            atomicAdd(&s_arcs, (unsigned long long)(e1 - e0));
-        }
+        const int v = p.col[p.row_ptr[s] + (a - s_off[b])];
+        atomicOr(F1 + (size_t)v * W + (b >> 5), 1u << (b & 31));
+        atomicOr(uf1 + (v >> 5), 1u << (v & 31));
+        p.sigma[(size_t)v * B + b] = 1ull;
+        if (p.lvl) p.lvl[(size_t)v * B + b] = 1;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    if (s_arcs) atomicAdd(&p.ctl->dag_arcs, s_arcs);
-    if (s_any) atomicOr(&p.ctl->nonempty, 1u);
+    if (t != 0) return;
     __threadfence();
     if (atomicAdd(&p.ctl->blocks_done, 1u) != gridDim.x - 1) return;
     __threadfence();
-    const unsigned ne = atomicExch(&p.ctl->nonempty, 0u);
     atomicExch(&p.ctl->blocks_done, 0u);
+    atomicAdd(&p.ctl->dag_arcs, (unsigned long long)total);
     volatile HostCtl *h = p.hctl;
-    if (ne == 0u) {  // every source isolated: depth 0
+    if (total == 0) {  // every source isolated: depth 0
         p.ctl->fwd_done = 1u;
         p.ctl->nlevels = 0;
         h->nlevels = 0;
@@ -203,6 +172,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     const uint16_t *Sl = p.S + (size_t)(l & 1) * nB;
     uint16_t *Sn = p.S + (size_t)((l + 1) & 1) * nB;
     const bool wide = *(volatile uint32_t *)(p.wide + l) != 0u;
+    const bool ones = l == 1 && p.first;  // level 1 written by k_first: all counts 1, no masked rows
     bool produced = false, ovf = false, wide_next = false;
     uint32_t arcs = 0;  // predecessor relations counted by this lane
 
@@ -239,7 +209,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
             acc[j] = 0ull;
             nf[j] = 0u;
         }
-        body::fwd_sum<W>(p.col, beg, end, ufl, Fl, Sl, p.sigma, wide, U, s_u[wib], s_nz[wib], lane, acc, nf, ovf, arcs);
+        body::fwd_sum<W>(p.col, beg, end, ufl, Fl, Sl, p.sigma, wide, ones, U, s_u[wib], s_nz[wib], lane, acc, nf, ovf,
+                         arcs);
         if (slot < 0) {
             produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next, p.lvl, l + 1);
             continue;
@@ -528,9 +499,8 @@ void ms_launch_init(int W, const MsParams &p, cudaStream_t st) {
 }
 
 void ms_launch_first(int W, const MsParams &p, cudaStream_t st) {
-    const int g = (p.nb + kWarps - 1) / kWarps;
-    if (g == 0) return;
-    BCGB_DISPATCH_W(W, (k_first<kW><<<g, kBlock, 0, st>>>(p)));
+    if (p.nb == 0) return;
+    BCGB_DISPATCH_W(W, (k_first<kW><<<2 * sm_count(), kBlock, 0, st>>>(p)));
 }
 
 void ms_launch_forward(int W, const MsParams &p, int level, cudaStream_t st) {

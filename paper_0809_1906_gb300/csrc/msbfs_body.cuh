@@ -75,6 +75,20 @@ __device__ __forceinline__ void load_row(const uint32_t *__restrict__ p, uint32_
     }
 }
 
+// Warp-wide 32x32 bit transpose: lane k holds row k; returns column `lane`
+// (bit k of the result = bit `lane` of lane k's input). Five exchange steps,
+// each swapping the off-diagonal s x s blocks of every 2s x 2s block.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const uint32_t M = s == 16 ? 0x0000FFFFu : s == 8 ? 0x00FF00FFu : s == 4 ? 0x0F0F0F0Fu
+                         : s == 2 ? 0x33333333u : 0x55555555u;
+        const uint32_t y = __shfl_xor_sync(kFull, x, s);
+        x = (lane & s) ? ((x & ~M) | ((y >> s) & M)) : ((x & M) | ((y & M) << s));
+    }
+    return x;
+}
+
 // One 32-arc chunk: lane k gets arc e (if e < end), its neighbour u_k (stored
 // in s_u[k]) and masks m_k[j] = frontier words of u_k AND want[j] (zero for
 // arcs that cannot contribute); s_nz[k] gets the W-bit set of non-zero words
@@ -113,15 +127,16 @@ __device__ __forceinline__ unsigned probe_chunk(const int32_t *__restrict__ col,
 // s = 32j + lane, acc[j] += sigma_s(u) over the neighbours u in P_s(v), for
 // every s still unvisited at v (U); other entries of acc are discarded by the
 // caller. Narrow levels add the masked uint16 rows Sl (zero wherever u is not
-// a predecessor); a wide level reads sigma under the per-source masks. nf[j]
+// a predecessor); a wide level reads sigma under the per-source masks; a level
+// whose counts are all 1 (ones) just counts predecessors. nf[j]
 // gets the sources reaching v; exact uint64 sums, ovf flags a carry out of
 // bit 63; arcs counts predecessor relations (lane-local).
 template <int W, bool NC = true>
 __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg, int end,
                                         const uint32_t *__restrict__ ufl, const uint32_t *__restrict__ Fl,
                                         const uint16_t *__restrict__ Sl, const uint64_t *__restrict__ sigma,
-                                        bool wide, const uint32_t (&U)[W], int32_t *s_u, uint32_t *s_nz, int lane,
-                                        uint64_t (&acc)[W], uint32_t (&nf)[W], bool &ovf, uint32_t &arcs) {
+                                        bool wide, bool ones, const uint32_t (&U)[W], int32_t *s_u, uint32_t *s_nz,
+                                        int lane, uint64_t (&acc)[W], uint32_t (&nf)[W], bool &ovf, uint32_t &arcs) {
     constexpr int B = 32 * W;
     for (int e0 = beg; e0 < end; e0 += 32) {
         uint32_t m[W];
@@ -132,7 +147,14 @@ __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg
             nf[j] |= __reduce_or_sync(kFull, m[j]);
             arcs += __popc(m[j]);
         }
-        if (!wide) {
+        if (ones) {
+            // every count of this level is 1 (level 1: one shortest path from
+            // s to each neighbour of s), so the sum is the number of
+            // predecessors: per source, a column count of the chunk's masks
+#pragma unroll
+            for (int j = 0; j < W; ++j)
+                if (__any_sync(kFull, m[j] != 0u)) acc[j] += (uint64_t)__popc(transpose32(m[j], lane));
+        } else if (!wide) {
             // two neighbours per step: 2W independent coalesced loads in flight
             const uint16_t *base = Sl + lane;
             while (bal) {
