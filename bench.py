@@ -282,6 +282,8 @@ def run_extra(args):
             flops = h.dense_flops()
             ms_s = {b: _timed(lambda: (h.run(src, batch=b, stream=stream), h.result()), 2, 1, stream, flush)
                     for b in (128, 256)}
+            ms_ds = _timed(lambda: (h.run(src, flags=native.BC_DENSE | native.BC_SPARSE_BACKWARD, stream=stream),
+                                    h.result()), 2, 1, stream, flush)
         dn, dms = kinds["dense"]
         tf = flops / (dms / 1e3) / 1e12 if dms else 0.0
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -294,6 +296,7 @@ def run_extra(args):
                               "flops": flops, "traffic": None},
                     vs_sparse_same_graph={str(b): {"ms": v, "value": g.n * g.m / (v / 1e3), "speedup": v / ms_d}
                                           for b, v in ms_s.items()},
+                    dense_forward_sparse_backward={"ms": ms_ds, "value": g.n * g.m / (ms_ds / 1e3)},
                     cpu_baseline=_oracle_rate(g, np.arange(g.n, dtype=np.int32), args.cpu_seconds))
     elif wl == "many":
         gs = G.many_graphs()

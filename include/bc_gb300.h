@@ -68,8 +68,10 @@ extern "C" {
 #define BC_PLAIN 0x4u        /* one source per launch sequence (the unbatched GPU Brandes) */
 #define BC_TIMING 0x8u       /* record CUDA events around every kernel launch (bc_kernel_time) */
 #define BC_NO_HASH 0x10u     /* skip the per-source summary values */
-#define BC_DENSE 0x20u       /* levels >= 1 as tensor-core products with the 0/1 adjacency matrix
-                                (Section 3.1.1); unweighted graphs with n <= 65536, batch 128 */
+#define BC_DENSE 0x20u       /* levels >= 1 as tensor-core products with the 0/1 adjacency matrix,
+                                forward (ComputePathCount) and backward (ComputeDependency), Section 3.1;
+                                unweighted graphs with n <= 65536, batch 128 */
+#define BC_SPARSE_BACKWARD 0x40u /* with BC_DENSE: run the backward pass on the sparse kernel instead */
 
 /*
  * Run options. Zero-initialise and set what you need; bc_run(..., NULL, ...)

@@ -376,6 +376,24 @@ int stage_sources(bc_graph *g, const int32_t *sources, int32_t num, int32_t *cou
     return BC_OK;
 }
 
+bcgb::DenseParams dense_params(bc_graph *g, const bcgb::MsParams &p) {
+    bcgb::DenseParams d{};
+    d.n = g->n;
+    d.npad = g->npad;
+    d.nb = p.nb;
+    d.nw32 = p.nw32;
+    d.sigma = g->sigma.p;
+    d.lvl = g->lvl.p;
+    d.F = g->F.p;
+    d.V = g->V.p;
+    d.ufr = g->ufr.p;
+    d.X = g->dX.p;
+    d.bc = g->bc.p;
+    d.ctl = g->ctl;
+    d.dctl = g->dctl.p;
+    return d;
+}
+
 // Tensor-core forward for one batch (BC_DENSE): level 0 by the sparse
 // kernel, every further level as limb-matrix x adjacency products. The host
 // reads each level's outcome (a few levels per batch), which fixes the limb
@@ -392,19 +410,7 @@ int dense_forward(bc_graph *g, bcgb::MsParams &p, cudaStream_t st, int *depth) {
         *depth = c.nlevels;
         return BC_OK;
     }
-    bcgb::DenseParams d{};
-    d.n = g->n;
-    d.npad = g->npad;
-    d.nb = p.nb;
-    d.nw32 = p.nw32;
-    d.sigma = g->sigma.p;
-    d.lvl = g->lvl.p;
-    d.F = g->F.p;
-    d.V = g->V.p;
-    d.ufr = g->ufr.p;
-    d.X = g->dX.p;
-    d.ctl = g->ctl;
-    d.dctl = g->dctl.p;
+    bcgb::DenseParams d = dense_params(g, p);
     int nl = 1;  // level-1 counts are all 1
     for (int l = 1;; ++l) {
         if (l + 2 >= g->Lcap) {
@@ -508,7 +514,12 @@ int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStr
             if (r) return r;
             continue;
         }
-        if (backward) {
+        if (backward && dense && !(opt->flags & BC_SPARSE_BACKWARD)) {
+            Timer t(g, st, BC_KERNEL_DENSE);
+            g->dense_flops += 2.0 * 128.0 * 3.0 * (double)g->npad * (double)g->npad * (L > 1 ? L - 1 : 0);
+            if (bcgb::dense_launch_backward(g->maps, dense_params(g, p), L, st))
+                return fail(BC_ERR_CUDA, std::string("dense backward launch: ") + cudaGetErrorString(cudaGetLastError()));
+        } else if (backward) {
             for (int l = L; l >= 1; --l) {
                 Timer t(g, st, BC_KERNEL_BACKWARD);
                 bcgb::ms_launch_backward(W, p, l, st);

@@ -129,9 +129,18 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// kBwd = false: forward level l -> l+1 (limb sums -> exact counts).
+// kBwd = true:  backward level l: the three bf16 parts of the masked c rows of
+//               level l+1 (rows xrow0 .. xrow0 + 383 of X) times A give
+//               sum_w c_s(w) over the successors; the epilogue forms delta and
+//               c for level l, adds the batch's delta to BC (FP64, fixed
+//               order) and, when write_next, writes the split c rows of level l
+//               at rows xout .. xout + 383.
+template <bool kBwd>
 __global__ void __launch_bounds__(128, 1)
     k_dense_level(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmA, const DenseParams p,
-                  const int l, const int nl, const int stages) {
+                  const int l, const int nl, const int stages, const int xrow0, const int xout,
+                  const int write_next) {
     extern __shared__ unsigned char dsm_raw[];
     unsigned char *dsm = reinterpret_cast<unsigned char *>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
     const int stage_bytes = nl * kXTile + kATile;
@@ -180,7 +189,8 @@ __global__ void __launch_bounds__(128, 1)
             }
             unsigned char *st = dsm + (size_t)s * stage_bytes;
             mbar_expect_tx(full + s, (uint32_t)stage_bytes);
-            for (int q = 0; q < nl; ++q) tma_load_2d(st + (size_t)q * kXTile, &tmX, it * kKT, q * kDB, full + s);
+            for (int q = 0; q < nl; ++q)
+                tma_load_2d(st + (size_t)q * kXTile, &tmX, it * kKT, xrow0 + q * kDB, full + s);
             tma_load_2d(st + (size_t)nl * kXTile, &tmA, it * kKT, v0, full + s);
             issued = it + 1;
         }
@@ -218,74 +228,125 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     const bool good = ok && s_err == 0u;
     if (!good && tid == 0) atomicOr(&p.ctl->status, BC_STATUS_DENSE_TIMEOUT);
-    const int b = tid;  // source index in the batch
-    const size_t nW = (size_t)p.n * kDW;
-    const uint32_t *Fl = p.F + (size_t)l * nW;
-    uint32_t *Fn = p.F + (size_t)(l + 1) * nW;
-    const uint32_t *Vin = p.V + (size_t)(l & 1) * nW;
-    uint32_t *Vout = p.V + (size_t)((l + 1) & 1) * nW;
-    uint32_t *ufn = p.ufr + (size_t)(l + 1) * p.nw32;
-    const bool valid_src = b < p.nb;
-    bool ovf = false, produced = false;
-    unsigned long long maxsig = 0, remaining = 0;
-    for (int c0 = 0; good && c0 < kNT; c0 += 16) {
-        uint64_t lo[16];
-        uint32_t hi[16];
+    if constexpr (kBwd) {
+        __shared__ double s_red[4][16];
+        const int b = tid;
+        const size_t nW = (size_t)p.n * kDW;
+        const uint32_t *Fl = p.F + (size_t)l * nW;
+        const bool valid_src = b < p.nb;
+        for (int c0 = 0; good && c0 < kNT; c0 += 16) {
+            float S[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            lo[i] = 0ull;
-            hi[i] = 0u;
-        }
-        for (int q = 0; q < nl; ++q) {
-            uint32_t r[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * kNT + c0), r);
-            tmem_wait_ld();
+            for (int i = 0; i < 16; ++i) S[i] = 0.0f;
+            for (int q = 0; q < nl; ++q) {  // hi + mid + lo, in this order
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * kNT + c0), r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) S[i] += __uint_as_float(r[i]);
+            }
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                // exact integer < 2^24 held in FP32; add 2^(8q) * a into (hi:lo)
-                const uint64_t a = (uint64_t)__float2uint_rn(__uint_as_float(r[i]));
-                const int sh = 8 * q;
-                const uint64_t part = a << sh;
-                const uint64_t carry_bits = sh ? (a >> (64 - sh)) : 0ull;
-                const uint64_t y = lo[i] + part;
-                hi[i] += (uint32_t)carry_bits + (y < part ? 1u : 0u);
-                lo[i] = y;
-            }
-        }
+                const int v = v0 + c0 + i;
+                double dsum = 0.0;
+                if (v < p.n) {
+                    const bool at = valid_src && ((__ldg(Fl + (size_t)v * kDW + warp) >> lane) & 1u);
+                    float d = 0.0f, c = 0.0f;
+                    if (at) {
+                        const float sg = __ull2float_rn(p.sigma[(size_t)v * kDB + b]);
+                        d = sg * S[i];          // delta_s*(v) = sigma_s(v) * sum_w c_s(w)
+                        c = (1.0f + d) / sg;    // c_s(v) for the level above
+                    }
+                    dsum = (double)d;
+                    if (write_next) {
+                        const __nv_bfloat16 h = __float2bfloat16_rn(c);
+                        const float r1 = c - __bfloat162float(h);
+                        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+                        const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(m));
+                        p.X[((size_t)xout + b) * p.npad + v] = h;
+                        p.X[((size_t)xout + kDB + b) * p.npad + v] = m;
+                        p.X[((size_t)xout + 2 * kDB + b) * p.npad + v] = lo;
+                    }
+                }
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int v = v0 + c0 + i;
-            if (v >= p.n) break;  // padding columns (uniform across the block)
-            const uint32_t vis = __ldg(Vin + (size_t)v * kDW + warp) | __ldg(Fl + (size_t)v * kDW + warp);
-            const bool seen = (vis >> lane) & 1u;
-            const bool hit = valid_src && !seen && (lo[i] | hi[i]) != 0ull;
-            if (hit) {
-                p.sigma[(size_t)v * kDB + b] = lo[i];
-                p.lvl[(size_t)v * kDB + b] = (uint16_t)(l + 1);
-                ovf |= hi[i] != 0u;
-                maxsig = lo[i] > maxsig ? lo[i] : maxsig;
+                for (int off = 16; off > 0; off >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, off);
+                if (lane == 0) s_red[warp][i] = dsum;
             }
-            remaining += (valid_src && !seen && !hit) ? 1ull : 0ull;
-            const uint32_t word = __ballot_sync(0xffffffffu, hit);
+            __syncthreads();
+            if (tid < 16 && v0 + c0 + tid < p.n)
+                p.bc[v0 + c0 + tid] += ((s_red[0][tid] + s_red[1][tid]) + s_red[2][tid]) + s_red[3][tid];
+            __syncthreads();
+        }
+    } else {
+    const int b = tid;  // source index in the batch
+        const size_t nW = (size_t)p.n * kDW;
+        const uint32_t *Fl = p.F + (size_t)l * nW;
+        uint32_t *Fn = p.F + (size_t)(l + 1) * nW;
+        const uint32_t *Vin = p.V + (size_t)(l & 1) * nW;
+        uint32_t *Vout = p.V + (size_t)((l + 1) & 1) * nW;
+        uint32_t *ufn = p.ufr + (size_t)(l + 1) * p.nw32;
+        const bool valid_src = b < p.nb;
+        bool ovf = false, produced = false;
+        unsigned long long maxsig = 0, remaining = 0;
+        for (int c0 = 0; good && c0 < kNT; c0 += 16) {
+            uint64_t lo[16];
+            uint32_t hi[16];
+    #pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                lo[i] = 0ull;
+                hi[i] = 0u;
+            }
+            for (int q = 0; q < nl; ++q) {
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * kNT + c0), r);
+                tmem_wait_ld();
+    #pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    // exact integer < 2^24 held in FP32; add 2^(8q) * a into (hi:lo)
+                    const uint64_t a = (uint64_t)__float2uint_rn(__uint_as_float(r[i]));
+                    const int sh = 8 * q;
+                    const uint64_t part = a << sh;
+                    const uint64_t carry_bits = sh ? (a >> (64 - sh)) : 0ull;
+                    const uint64_t y = lo[i] + part;
+                    hi[i] += (uint32_t)carry_bits + (y < part ? 1u : 0u);
+                    lo[i] = y;
+                }
+            }
+    #pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int v = v0 + c0 + i;
+                if (v >= p.n) break;  // padding columns (uniform across the block)
+                const uint32_t vis = __ldg(Vin + (size_t)v * kDW + warp) | __ldg(Fl + (size_t)v * kDW + warp);
+                const bool seen = (vis >> lane) & 1u;
+                const bool hit = valid_src && !seen && (lo[i] | hi[i]) != 0ull;
+                if (hit) {
+                    p.sigma[(size_t)v * kDB + b] = lo[i];
+                    p.lvl[(size_t)v * kDB + b] = (uint16_t)(l + 1);
+                    ovf |= hi[i] != 0u;
+                    maxsig = lo[i] > maxsig ? lo[i] : maxsig;
+                }
+                remaining += (valid_src && !seen && !hit) ? 1ull : 0ull;
+                const uint32_t word = __ballot_sync(0xffffffffu, hit);
+                if (lane == 0) {
+                    Fn[(size_t)v * kDW + warp] = word;
+                    Vout[(size_t)v * kDW + warp] = vis;
+                    if (word) atomicOr(ufn + (v >> 5), 1u << (v & 31));
+                }
+                produced |= word != 0u;
+            }
+        }
+        if (good) {
+            if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(&p.ctl->status, BC_STATUS_SIGMA_OVERFLOW);
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, maxsig, off);
+                maxsig = o > maxsig ? o : maxsig;
+                remaining += __shfl_xor_sync(0xffffffffu, remaining, off);
+            }
             if (lane == 0) {
-                Fn[(size_t)v * kDW + warp] = word;
-                Vout[(size_t)v * kDW + warp] = vis;
-                if (word) atomicOr(ufn + (v >> 5), 1u << (v & 31));
+                if (produced) atomicOr(&p.dctl->produced, 1u);
+                if (maxsig) atomicMax(&p.dctl->maxsig, maxsig);
+                if (remaining) atomicAdd(&p.dctl->remaining, remaining);
             }
-            produced |= word != 0u;
-        }
-    }
-    if (good) {
-        if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(&p.ctl->status, BC_STATUS_SIGMA_OVERFLOW);
-        for (int off = 16; off > 0; off >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, maxsig, off);
-            maxsig = o > maxsig ? o : maxsig;
-            remaining += __shfl_xor_sync(0xffffffffu, remaining, off);
-        }
-        if (lane == 0) {
-            if (produced) atomicOr(&p.dctl->produced, 1u);
-            if (maxsig) atomicMax(&p.dctl->maxsig, maxsig);
-            if (remaining) atomicAdd(&p.dctl->remaining, remaining);
         }
     }
     tc_fence_before();
@@ -316,6 +377,26 @@ __global__ void __launch_bounds__(256) k_dense_limbs(const DenseParams p, const 
             p.X[((size_t)q * kDB + b) * p.npad + u0 + uu] = __float2bfloat16_rn((float)byte);
         }
     }
+}
+
+// Split masked c rows of the deepest level L (c_s(v) = 1 / sigma_s(v) there:
+// nothing depends on the farthest vertices, Lemma 3.3): rows xout + q*128 + b
+// hold part q (hi, mid, lo) of c, 0 for the pairs not at level L.
+__global__ void __launch_bounds__(256) k_dense_bwd_last(const DenseParams p, const int L, const int xout) {
+    const int v = blockIdx.x * 2 + (threadIdx.x >> 7);
+    const int b = threadIdx.x & 127;
+    if (v >= p.n) return;
+    const size_t nW = (size_t)p.n * kDW;
+    float c = 0.0f;
+    if (b < p.nb && ((p.F[(size_t)L * nW + (size_t)v * kDW + (b >> 5)] >> (b & 31)) & 1u))
+        c = 1.0f / __ull2float_rn(p.sigma[(size_t)v * kDB + b]);
+    const __nv_bfloat16 h = __float2bfloat16_rn(c);
+    const float r1 = c - __bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(m));
+    p.X[((size_t)xout + b) * p.npad + v] = h;
+    p.X[((size_t)xout + kDB + b) * p.npad + v] = m;
+    p.X[((size_t)xout + 2 * kDB + b) * p.npad + v] = lo;
 }
 
 // Dense 0/1 adjacency in bf16 from the CSR (rows beyond n and columns beyond
@@ -380,10 +461,31 @@ int dense_make_maps(DenseMaps *maps, __nv_bfloat16 *X, __nv_bfloat16 *A, int32_t
 int dense_launch_level(const DenseMaps &maps, const DenseParams &p, int l, int nl, cudaStream_t st) {
     const int stages = dense_stages(nl);
     const size_t smem = dense_smem_bytes(nl, stages);
-    if (cudaFuncSetAttribute(k_dense_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_dense_level<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
         return -1;
     k_dense_limbs<<<(p.n + 31) / 32, 256, 0, st>>>(p, l, nl);
-    k_dense_level<<<p.npad / kNT, 128, smem, st>>>(maps.x, maps.a, p, l, nl, stages);
+    k_dense_level<false><<<p.npad / kNT, 128, smem, st>>>(maps.x, maps.a, p, l, nl, stages, 0, 0, 0);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int dense_launch_backward(const DenseMaps &maps, const DenseParams &p, int L, cudaStream_t st) {
+    if (L < 1) return 0;
+    constexpr int kParts = 3;
+    const int stages = dense_stages(kParts);
+    const size_t smem = dense_smem_bytes(kParts, stages);
+    if (cudaFuncSetAttribute(k_dense_level<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return -1;
+    int cur = 0, nxt = kParts * kDB;  // two row blocks of X alternate between levels
+    k_dense_bwd_last<<<(p.n + 1) / 2, 256, 0, st>>>(p, L, cur);
+    for (int l = L - 1; l >= 1; --l) {
+        k_dense_level<true><<<p.npad / kNT, 128, smem, st>>>(maps.x, maps.a, p, l, kParts, stages, cur, nxt,
+                                                              l > 1 ? 1 : 0);
+        const int t = cur;
+        cur = nxt;
+        nxt = t;
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -26,7 +26,8 @@ struct DenseParams {
     uint64_t *sigma;  // [n][128]
     uint16_t *lvl;    // [n][128]
     uint32_t *F, *V, *ufr;
-    __nv_bfloat16 *X;  // [8 * 128][npad] limb matrix
+    __nv_bfloat16 *X;  // [8 * 128][npad] limb matrix (backward: two blocks of 3 * 128 split rows)
+    double *bc;
     DevCtl *ctl;
     DenseCtl *dctl;
 };
@@ -39,5 +40,7 @@ int dense_build_adjacency(const int32_t *row_ptr, const int32_t *col, int32_t n,
                           cudaStream_t st);
 int dense_make_maps(DenseMaps *maps, __nv_bfloat16 *X, __nv_bfloat16 *A, int32_t npad);
 int dense_launch_level(const DenseMaps &maps, const DenseParams &p, int l, int nl, cudaStream_t st);
+// Backward levels L-1 .. 1 on the tensor cores (BC accumulated into p.bc).
+int dense_launch_backward(const DenseMaps &maps, const DenseParams &p, int L, cudaStream_t st);
 
 }  // namespace bcgb

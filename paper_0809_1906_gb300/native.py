@@ -37,6 +37,7 @@ BC_PLAIN = 0x4
 BC_TIMING = 0x8
 BC_NO_HASH = 0x10
 BC_DENSE = 0x20
+BC_SPARSE_BACKWARD = 0x40
 
 BC_KERNEL_INIT = 0
 BC_KERNEL_FORWARD = 1

@@ -100,3 +100,20 @@ def test_dense_gnp8192(nat):
         got, _, _ = h.result()
         r = oracle.bc(g, sub)["bc"]
         assert np.all(np.abs(got - r) <= np.maximum(1e-5 * np.abs(r), 1e-6 * g.n))
+
+
+@pytest.mark.parametrize("n,p", [(256, 0.05), (700, 0.006), (1000, 0.01)])
+def test_dense_backward_tensor_vs_sparse(nat, n, p):
+    """The tensor-core backward (three bf16 parts of the FP32 c rows) agrees
+    with the sparse backward and with the oracle; deeper graphs exercise the
+    alternating split-row blocks over several levels."""
+    g = G.random_small(n, p, 90 + n, connect=True)
+    ref = oracle.bc(g)["bc"]
+    tol = np.maximum(1e-5 * np.abs(ref), 1e-6 * g.n)
+    with nat.Graph.from_csr(g) as h:
+        h.run(flags=nat.BC_DENSE)
+        a, _, _ = h.result()
+        h.run(flags=nat.BC_DENSE | nat.BC_SPARSE_BACKWARD)
+        b, _, _ = h.result()
+    assert np.all(np.abs(a - ref) <= tol), float(np.max(np.abs(a - ref) / np.maximum(np.abs(ref), 1)))
+    assert np.all(np.abs(b - ref) <= tol)
