@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(kMBlock, 4) k_many(const ManyParams p) {
     __shared__ int s_last;
     __shared__ int32_t s_u[kMWarps][32];
     __shared__ uint32_t s_nz[kMWarps][32];
+    __shared__ uint32_t s_w[kMWarps][32][W];  // per-lane words of a warp's 32 vertices
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     uint64_t *sigma = p.sigma + (size_t)blockIdx.x * p.nmax * B;
     uint16_t *Sbuf = p.S + (size_t)blockIdx.x * 2 * p.nmax * B;
@@ -102,32 +103,49 @@ __global__ void __launch_bounds__(kMBlock, 4) k_many(const ManyParams p) {
                 const uint16_t *Sl = Sbuf + (size_t)(l & 1) * nB;
                 uint16_t *Sn = Sbuf + (size_t)((l + 1) & 1) * nB;
                 bool produced = false, wide_next = false;
-                for (int v = wib; v < n; v += kMWarps) {
-                    uint32_t U[W], a[W], f[W];
-                    body::load_row<W, false>(Vin + (size_t)v * W, a);
-                    body::load_row<W, false>(Fl + (size_t)v * W, f);
-                    uint32_t anyU = 0;
+                // a warp checks its next 32 vertices at once (lane k: vertex
+                // v0 + k * kMWarps), then works through the active ones
+                for (int v0 = wib; v0 < n; v0 += 32 * kMWarps) {
+                    const int vk = v0 + lane * kMWarps;
+                    bool act = false;
+                    __syncwarp();  // the previous group's reads of s_w are done
+                    if (vk < n) {
+                        uint32_t a[W], f[W];
+                        body::load_row<W, false>(Vin + (size_t)vk * W, a);
+                        body::load_row<W, false>(Fl + (size_t)vk * W, f);
+                        uint32_t any = 0;
 #pragma unroll
-                    for (int j = 0; j < W; ++j) {
-                        const uint32_t vis = a[j] | f[j];
-                        if (lane == j) Vout[(size_t)v * W + j] = vis;
-                        U[j] = ~vis & body::valid_word(nb, j);
-                        anyU |= U[j];
-                    }
-                    if (anyU == 0u) {
-                        if (lane < W) Fn[(size_t)v * W + lane] = 0u;
-                        continue;
-                    }
-                    uint64_t acc[W];
-                    uint32_t nf[W];
+                        for (int j = 0; j < W; ++j) {
+                            const uint32_t vis = a[j] | f[j];
+                            Vout[(size_t)vk * W + j] = vis;
+                            const uint32_t u = ~vis & body::valid_word(nb, j);
+                            s_w[wib][lane][j] = u;
+                            any |= u;
+                        }
+                        act = any != 0u;
+                        if (!act)
 #pragma unroll
-                    for (int j = 0; j < W; ++j) {
-                        acc[j] = 0ull;
-                        nf[j] = 0u;
+                            for (int j = 0; j < W; ++j) Fn[(size_t)vk * W + j] = 0u;
                     }
-                    body::fwd_sum<W, false>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufl, Fl, Sl, sigma, wide, false, U,
-                                            s_u[wib], s_nz[wib], lane, acc, nf, ovf, arcs);
-                    produced |= body::store_next<W>(sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
+                    unsigned todo = __ballot_sync(kFull, act);
+                    __syncwarp();
+                    while (todo) {
+                        const int v = v0 + (__ffs(todo) - 1) * kMWarps;
+                        uint32_t U[W];
+#pragma unroll
+                        for (int j = 0; j < W; ++j) U[j] = s_w[wib][__ffs(todo) - 1][j];
+                        todo &= todo - 1;
+                        uint64_t acc[W];
+                        uint32_t nf[W];
+#pragma unroll
+                        for (int j = 0; j < W; ++j) {
+                            acc[j] = 0ull;
+                            nf[j] = 0u;
+                        }
+                        body::fwd_sum<W, false>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufl, Fl, Sl, sigma, wide, false, U,
+                                                s_u[wib], s_nz[wib], lane, acc, nf, ovf, arcs);
+                        produced |= body::store_next<W>(sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
+                    }
                 }
                 wide = __syncthreads_or(wide_next);
                 if (!__syncthreads_or(produced)) {
@@ -143,18 +161,35 @@ __global__ void __launch_bounds__(kMBlock, 4) k_many(const ManyParams p) {
                 const uint32_t *ufs = ufr + (size_t)(l + 1) * nw32;
                 float *Cl = cval + (size_t)(l & 1) * nB;
                 const float *Cs = cval + (size_t)((l + 1) & 1) * nB;
-                for (int v = wib; v < n; v += kMWarps) {
-                    uint32_t f[W];
-                    body::load_row<W, false>(Fl + (size_t)v * W, f);
-                    uint32_t anyf = 0;
+                for (int v0 = wib; v0 < n; v0 += 32 * kMWarps) {
+                    const int vk = v0 + lane * kMWarps;
+                    bool act = false;
+                    __syncwarp();  // the previous group's reads of s_w are done
+                    if (vk < n) {
+                        uint32_t f[W];
+                        body::load_row<W, false>(Fl + (size_t)vk * W, f);
+                        uint32_t any = 0;
 #pragma unroll
-                    for (int j = 0; j < W; ++j) anyf |= f[j];
-                    if (anyf == 0u) continue;
-                    float S[W];
+                        for (int j = 0; j < W; ++j) {
+                            s_w[wib][lane][j] = f[j];
+                            any |= f[j];
+                        }
+                        act = any != 0u;
+                    }
+                    unsigned todo = __ballot_sync(kFull, act);
+                    __syncwarp();
+                    while (todo) {
+                        const int v = v0 + (__ffs(todo) - 1) * kMWarps;
+                        uint32_t f[W];
 #pragma unroll
-                    for (int j = 0; j < W; ++j) S[j] = 0.0f;
-                    body::bwd_sum<W, false>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufs, Fs, Cs, f, s_u[wib], s_nz[wib], lane, S);
-                    body::finalize_dep<W>(sigma, Cl, target, v, f, S, lane);
+                        for (int j = 0; j < W; ++j) f[j] = s_w[wib][__ffs(todo) - 1][j];
+                        todo &= todo - 1;
+                        float S[W];
+#pragma unroll
+                        for (int j = 0; j < W; ++j) S[j] = 0.0f;
+                        body::bwd_sum<W, false>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufs, Fs, Cs, f, s_u[wib], s_nz[wib], lane, S);
+                        body::finalize_dep<W>(sigma, Cl, target, v, f, S, lane);
+                    }
                 }
                 __syncthreads();
             }

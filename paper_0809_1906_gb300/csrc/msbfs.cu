@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(kBlock) k_first(const MsParams p) {
 template <int W>
 __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const int l) {
     constexpr int B = 32 * W;
+    __shared__ uint32_t s_U[kWarps][32][W];  // unvisited words of the group's items
     __shared__ uint32_t s_flags;
     __shared__ unsigned long long s_arcs;
     __shared__ int32_t s_u[kWarps][32];
@@ -176,79 +177,97 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     bool produced = false, ovf = false, wide_next = false;
     uint32_t arcs = 0;  // predecessor relations counted by this lane
 
-    // persistent warps: items are sorted by decreasing degree, so striding
-    // gives every warp a similar mix
-    for (int it = blockIdx.x * kWarps + wib; it < p.nitems; it += gridDim.x * kWarps) {
-        const int v = p.item_v[it];
-        const int beg = p.item_beg[it];
-        const int end = p.item_end[it];
-        const int slot = p.item_slot[it];
-        uint32_t U[W];
-        uint32_t anyU = 0;
-        {
+    // Persistent warps stride over the items (sorted by decreasing degree, so
+    // every warp gets a similar mix; the chunks of one heavy vertex land on
+    // different warps). A warp takes its next 32 items at once: lane k checks
+    // item k's vertex (visited words; the new frontier row cleared when
+    // nothing is left to find), then the warp works through the active ones.
+    const int G = gridDim.x * kWarps;
+    for (int g0 = blockIdx.x * kWarps + wib; g0 < p.nitems; g0 += 32 * G) {
+        bool act = false;
+        __syncwarp();  // the previous group's reads of s_U are done
+        const int ik = g0 + lane * G;
+        if (ik < p.nitems) {
+            const int vk = p.item_v[ik];
+            const int sk = p.item_slot[ik];
             uint32_t a[W], f[W];
-            load_row<W>(Vin + (size_t)v * W, a);
-            load_row<W>(Fl + (size_t)v * W, f);
+            load_row<W>(Vin + (size_t)vk * W, a);
+            load_row<W>(Fl + (size_t)vk * W, f);
+            uint32_t any = 0;
 #pragma unroll
             for (int j = 0; j < W; ++j) {
                 const uint32_t vis = a[j] | f[j];
-                if (lane == j) Vout[(size_t)v * W + j] = vis;
-                U[j] = ~vis & valid_word(p.nb, j);
-                anyU |= U[j];
+                Vout[(size_t)vk * W + j] = vis;  // chunks of one vertex write the same words
+                const uint32_t u = ~vis & valid_word(p.nb, j);
+                s_U[wib][lane][j] = u;
+                any |= u;
             }
-        }
-        const bool first_chunk = slot < 0 || p.slot_first[slot] == slot;
-        if (anyU == 0u) {
-            if (first_chunk && lane < W) Fn[(size_t)v * W + lane] = 0u;
-            continue;
-        }
-        uint64_t acc[W];  // lane owns source 32j + lane
-        uint32_t nf[W];
+            act = any != 0u;
+            if (!act && (sk < 0 || p.slot_first[sk] == sk))
 #pragma unroll
-        for (int j = 0; j < W; ++j) {
-            acc[j] = 0ull;
-            nf[j] = 0u;
+                for (int j = 0; j < W; ++j) Fn[(size_t)vk * W + j] = 0u;
         }
-        body::fwd_sum<W>(p.col, beg, end, ufl, Fl, Sl, p.sigma, wide, ones, U, s_u[wib], s_nz[wib], lane, acc, nf, ovf,
-                         arcs);
-        if (slot < 0) {
-            produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next, p.lvl, l + 1);
-            continue;
-        }
-        uint64_t *pp = p.part + (size_t)slot * B + lane;
-#pragma unroll
-        for (int j = 0; j < W; ++j) pp[32 * j] = acc[j];
-#pragma unroll
-        for (int j = 0; j < W; ++j)
-            if (lane == j) p.pmask[(size_t)slot * W + j] = nf[j];
-        __threadfence();
+        unsigned todo = __ballot_sync(kFull, act);
         __syncwarp();
-        const int first = p.slot_first[slot];
-        const int nch = p.slot_nch[slot];
-        unsigned old = 0;
-        if (lane == 0) old = atomicAdd(p.cnt + first, 1u);
-        old = __shfl_sync(kFull, old, 0);
-        if (old != (unsigned)(nch - 1)) continue;
-        __threadfence();
+        while (todo) {
+            const int kk = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int it = g0 + kk * G;
+            const int v = p.item_v[it];
+            const int beg = p.item_beg[it];
+            const int end = p.item_end[it];
+            const int slot = p.item_slot[it];
+            uint32_t U[W];
 #pragma unroll
-        for (int j = 0; j < W; ++j) {
-            acc[j] = 0ull;
-            nf[j] = 0u;
-        }
-        for (int c = 0; c < nch; ++c) {
-            const uint64_t *q = p.part + (size_t)(first + c) * B + lane;
-            const uint32_t *qm = p.pmask + (size_t)(first + c) * W;
+            for (int j = 0; j < W; ++j) U[j] = s_U[wib][kk][j];
+            uint64_t acc[W];  // lane owns source 32j + lane
+            uint32_t nf[W];
 #pragma unroll
             for (int j = 0; j < W; ++j) {
-                const uint64_t x = __ldcg(q + 32 * j);
-                const uint64_t y = acc[j] + x;
-                ovf |= y < x;
-                acc[j] = y;
-                nf[j] |= __ldcg(qm + j);
+                acc[j] = 0ull;
+                nf[j] = 0u;
             }
+            body::fwd_sum<W>(p.col, beg, end, ufl, Fl, Sl, p.sigma, wide, ones, U, s_u[wib], s_nz[wib], lane, acc, nf, ovf,
+                             arcs);
+            if (slot < 0) {
+                produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next, p.lvl, l + 1);
+                continue;
+            }
+            uint64_t *pp = p.part + (size_t)slot * B + lane;
+#pragma unroll
+            for (int j = 0; j < W; ++j) pp[32 * j] = acc[j];
+#pragma unroll
+            for (int j = 0; j < W; ++j)
+                if (lane == j) p.pmask[(size_t)slot * W + j] = nf[j];
+            __threadfence();
+            __syncwarp();
+            const int first = p.slot_first[slot];
+            const int nch = p.slot_nch[slot];
+            unsigned old = 0;
+            if (lane == 0) old = atomicAdd(p.cnt + first, 1u);
+            old = __shfl_sync(kFull, old, 0);
+            if (old != (unsigned)(nch - 1)) continue;
+            __threadfence();
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                acc[j] = 0ull;
+                nf[j] = 0u;
+            }
+            for (int c = 0; c < nch; ++c) {
+                const uint64_t *q = p.part + (size_t)(first + c) * B + lane;
+                const uint32_t *qm = p.pmask + (size_t)(first + c) * W;
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    const uint64_t x = __ldcg(q + 32 * j);
+                    const uint64_t y = acc[j] + x;
+                    ovf |= y < x;
+                    acc[j] = y;
+                    nf[j] |= __ldcg(qm + j);
+                }
+            }
+            produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next, p.lvl, l + 1);
+            if (lane == 0) p.cnt[first] = 0u;
         }
-        produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next, p.lvl, l + 1);
-        if (lane == 0) p.cnt[first] = 0u;
     }
     const unsigned wovf = __ballot_sync(kFull, ovf);
     const unsigned wwide = __ballot_sync(kFull, wide_next);
@@ -296,6 +315,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
 template <int W>
 __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const int l) {
     constexpr int B = 32 * W;
+    __shared__ uint32_t s_f[kWarps][32][W];  // level-l words of the group's items
     __shared__ int32_t s_u[kWarps][32];
     __shared__ uint32_t s_nz[kWarps][32];
     const int lane = threadIdx.x & 31;
@@ -307,47 +327,70 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
     const size_t nB = (size_t)p.n * B;
     float *Cl = p.cval + (size_t)(l & 1) * nB;
     const float *Cs = p.cval + (size_t)((l + 1) & 1) * nB;
-    for (int it = blockIdx.x * kWarps + wib; it < p.nitems; it += gridDim.x * kWarps) {
-        const int v = p.item_v[it];
-        const int beg = p.item_beg[it];
-        const int end = p.item_end[it];
-        const int slot = p.item_slot[it];
-        uint32_t f[W];
-        load_row<W>(Fl + (size_t)v * W, f);
-        uint32_t anyf = 0;
+    // the forward pass's item striding; lane k of a warp checks whether its
+    // k-th next item's vertex is at level l for any source (the same for all
+    // chunks of v), then the warp works through the active items
+    const int G = gridDim.x * kWarps;
+    for (int g0 = blockIdx.x * kWarps + wib; g0 < p.nitems; g0 += 32 * G) {
+        bool act = false;
+        __syncwarp();  // the previous group's reads of s_f are done
+        const int ik = g0 + lane * G;
+        if (ik < p.nitems) {
+            const int vk = p.item_v[ik];
+            uint32_t f[W];
+            load_row<W>(Fl + (size_t)vk * W, f);
+            uint32_t any = 0;
 #pragma unroll
-        for (int j = 0; j < W; ++j) anyf |= f[j];
-        if (anyf == 0u) continue;  // v is at level l for no source (same for all chunks of v)
-
-        float S[W];  // lane owns source 32j + lane
-#pragma unroll
-        for (int j = 0; j < W; ++j) S[j] = 0.0f;
-        body::bwd_sum<W>(p.col, beg, end, ufs, Fs, Cs, f, s_u[wib], s_nz[wib], lane, S);
-        if (slot < 0) {
-            body::finalize_dep<W>(p.sigma, Cl, p.bc, v, f, S, lane);
-            continue;
+            for (int j = 0; j < W; ++j) {
+                s_f[wib][lane][j] = f[j];
+                any |= f[j];
+            }
+            act = any != 0u;
         }
-        float *pp = reinterpret_cast<float *>(p.part) + (size_t)slot * B + lane;
-#pragma unroll
-        for (int j = 0; j < W; ++j) pp[32 * j] = S[j];
-        __threadfence();
+        unsigned todo = __ballot_sync(kFull, act);
         __syncwarp();
-        const int first = p.slot_first[slot];
-        const int nch = p.slot_nch[slot];
-        unsigned old = 0;
-        if (lane == 0) old = atomicAdd(p.cnt + first, 1u);
-        old = __shfl_sync(kFull, old, 0);
-        if (old != (unsigned)(nch - 1)) continue;
-        __threadfence();
+        while (todo) {
+            const int kk = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int it = g0 + kk * G;
+            const int v = p.item_v[it];
+            const int beg = p.item_beg[it];
+            const int end = p.item_end[it];
+            const int slot = p.item_slot[it];
+            uint32_t f[W];
 #pragma unroll
-        for (int j = 0; j < W; ++j) S[j] = 0.0f;
-        for (int c = 0; c < nch; ++c) {
-            const float *q = reinterpret_cast<const float *>(p.part) + (size_t)(first + c) * B + lane;
+            for (int j = 0; j < W; ++j) f[j] = s_f[wib][kk][j];
+
+            float S[W];  // lane owns source 32j + lane
 #pragma unroll
-            for (int j = 0; j < W; ++j) S[j] += __ldcg(q + 32 * j);
+            for (int j = 0; j < W; ++j) S[j] = 0.0f;
+            body::bwd_sum<W>(p.col, beg, end, ufs, Fs, Cs, f, s_u[wib], s_nz[wib], lane, S);
+            if (slot < 0) {
+                body::finalize_dep<W>(p.sigma, Cl, p.bc, v, f, S, lane);
+                continue;
+            }
+            float *pp = reinterpret_cast<float *>(p.part) + (size_t)slot * B + lane;
+#pragma unroll
+            for (int j = 0; j < W; ++j) pp[32 * j] = S[j];
+            __threadfence();
+            __syncwarp();
+            const int first = p.slot_first[slot];
+            const int nch = p.slot_nch[slot];
+            unsigned old = 0;
+            if (lane == 0) old = atomicAdd(p.cnt + first, 1u);
+            old = __shfl_sync(kFull, old, 0);
+            if (old != (unsigned)(nch - 1)) continue;
+            __threadfence();
+#pragma unroll
+            for (int j = 0; j < W; ++j) S[j] = 0.0f;
+            for (int c = 0; c < nch; ++c) {
+                const float *q = reinterpret_cast<const float *>(p.part) + (size_t)(first + c) * B + lane;
+#pragma unroll
+                for (int j = 0; j < W; ++j) S[j] += __ldcg(q + 32 * j);
+            }
+            body::finalize_dep<W>(p.sigma, Cl, p.bc, v, f, S, lane);
+            if (lane == 0) p.cnt[first] = 0u;
         }
-        body::finalize_dep<W>(p.sigma, Cl, p.bc, v, f, S, lane);
-        if (lane == 0) p.cnt[first] = 0u;
     }
 }
 
