@@ -58,6 +58,7 @@ extern "C" {
 #define BC_STATUS_BOUNDS 0x2u
 #define BC_STATUS_LEVEL_CAP 0x4u /* internal: a batch needed more BFS levels (re-run automatically) */
 #define BC_STATUS_DENSE_TIMEOUT 0x8u /* a tensor-core pipeline wait gave up (bc_result returns BC_ERR_TIMEOUT) */
+#define BC_STATUS_COPY_TIMEOUT 0x10u /* a wait for staged row copies gave up (bc_result returns BC_ERR_TIMEOUT) */
 
 /* ---- bc_create_graph flags --------------------------------------------- */
 #define BC_GRAPH_TRUST_INPUT 0x1u /* skip the host-side symmetry/duplicate check */
@@ -72,6 +73,12 @@ extern "C" {
                                 forward (ComputePathCount) and backward (ComputeDependency), Section 3.1;
                                 unweighted graphs with n <= 65536, batch 128 */
 #define BC_SPARSE_BACKWARD 0x40u /* with BC_DENSE: run the backward pass on the sparse kernel instead */
+#define BC_KEEP_ORDER 0x80u  /* batch the sources in the order given. By default (unweighted, batched,
+                                more than 32 sources) batches are formed from the sources sorted by
+                                their BFS distances to 16 landmark vertices, so the sources of one
+                                32-source word have similar distance profiles and the level sweep
+                                fetches fewer rows; BC differs only by FP64 summation order, and
+                                per-source summaries keep the caller's order. */
 
 /*
  * Run options. Zero-initialise and set what you need; bc_run(..., NULL, ...)

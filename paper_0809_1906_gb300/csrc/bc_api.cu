@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cstdio>
 #include <cstring>
+#include <numeric>
 #include <string>
 #include <thread>
 #include <vector>
@@ -69,6 +70,8 @@ struct bc_graph {
     int64_t narcs = 0;
     bool weighted = false;
     std::vector<int32_t> h_row_ptr;  // host copy (work-item plan)
+    std::vector<int32_t> h_col;      // host copy (landmark order; unweighted graphs)
+    std::vector<int32_t> rank;       // landmark-order position of every vertex (built on first use)
     DevBuf<int32_t> row_ptr, col, w;
 
     // work items for the current chunk size
@@ -86,6 +89,8 @@ struct bc_graph {
     // results
     DevBuf<double> bc;
     DevBuf<int32_t> sources;
+    DevBuf<int32_t> src_index;  // caller's index of each staged source (reordered runs)
+    bool reordered = false;
     DevBuf<uint64_t> h_sigma, h_dist;
     DevBuf<int64_t> dist_sum, reach;
     int32_t last_nsrc = 0;
@@ -128,7 +133,7 @@ namespace {
 
 void free_graph(bc_graph *g) {
     for (auto *b : {&g->row_ptr, &g->col, &g->w, &g->item_v, &g->item_beg, &g->item_end, &g->item_slot,
-                    &g->slot_first, &g->slot_nch, &g->sources})
+                    &g->slot_first, &g->slot_nch, &g->sources, &g->src_index})
         b->release();
     g->sigma.release();
     g->hpart.release();
@@ -359,7 +364,61 @@ int resolve_batch(const bc_options *opt, int *W) {
 }
 
 // Upload (or copy) a source list; returns its length.
-int stage_sources(bc_graph *g, const int32_t *sources, int32_t num, int32_t *count) {
+// Landmark order of the vertices. The batches of the level sweep run best
+// when the sources of one 32-source word have nearly the same distances to
+// every vertex: their masked rows are then either useful for most of the
+// word or not needed at all. Vertices are ordered lexicographically by their
+// BFS distances to K landmarks (the K highest-degree vertices, ties by id),
+// then by id; rank[v] is v's position. K plain BFS runs over the host CSR,
+// once per graph.
+void build_rank(bc_graph *g) {
+    constexpr int kLandmarks = 16;
+    const int32_t n = g->n;
+    const auto &rp = g->h_row_ptr;
+    const auto &cl = g->h_col;
+    const int k = std::min<int32_t>(kLandmarks, n);
+    std::vector<int32_t> vs(n);
+    std::iota(vs.begin(), vs.end(), 0);
+    auto deg = [&](int32_t v) { return rp[v + 1] - rp[v]; };
+    std::partial_sort(vs.begin(), vs.begin() + k, vs.end(),
+                      [&](int32_t a, int32_t b) { return deg(a) > deg(b) || (deg(a) == deg(b) && a < b); });
+    std::vector<int32_t> dist((size_t)k * n), queue(n);
+    for (int i = 0; i < k; ++i) {
+        int32_t *d = dist.data() + (size_t)i * n;
+        std::fill(d, d + n, -1);
+        int32_t head = 0, tail = 0;
+        d[vs[i]] = 0;
+        queue[tail++] = vs[i];
+        while (head < tail) {
+            const int32_t u = queue[head++];
+            for (int32_t e = rp[u]; e < rp[u + 1]; ++e)
+                if (d[cl[e]] < 0) {
+                    d[cl[e]] = d[u] + 1;
+                    queue[tail++] = cl[e];
+                }
+        }
+        for (int32_t v = 0; v < n; ++v)  // unreachable after every reachable distance
+            if (d[v] < 0) d[v] = n;
+    }
+    // lexicographic sort: stable counting sorts, last key first
+    std::vector<int32_t> ord(n), tmp(n), cnt((size_t)n + 2);
+    std::iota(ord.begin(), ord.end(), 0);
+    for (int i = k - 1; i >= 0; --i) {
+        const int32_t *d = dist.data() + (size_t)i * n;
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (int32_t v = 0; v < n; ++v) ++cnt[d[v] + 1];
+        for (int32_t x = 1; x <= n + 1; ++x) cnt[x] += cnt[x - 1];
+        for (int32_t t = 0; t < n; ++t) tmp[cnt[d[ord[t]]]++] = ord[t];
+        ord.swap(tmp);
+    }
+    g->rank.assign(n, 0);
+    for (int32_t t = 0; t < n; ++t) g->rank[ord[t]] = t;
+}
+
+// Validate and upload the source list. With `order`, the sources are staged
+// in landmark order (stable, so duplicates keep their relative order) and
+// src_index maps each staged position back to the caller's index.
+int stage_sources(bc_graph *g, const int32_t *sources, int32_t num, int32_t *count, bool order = false) {
     std::vector<int32_t> hs;
     if (!sources) {
         hs.resize(g->n);
@@ -369,6 +428,20 @@ int stage_sources(bc_graph *g, const int32_t *sources, int32_t num, int32_t *cou
         CK(fetch(hs, sources, (size_t)num));
         for (int32_t s : hs)
             if (s < 0 || s >= g->n) return fail(BC_ERR_ARG, "source id out of range");
+    }
+    g->reordered = false;
+    if (order && hs.size() > 32 && !g->h_col.empty()) {
+        if (g->rank.empty()) build_rank(g);
+        const int32_t n = g->n;
+        std::vector<int32_t> cnt((size_t)n + 1, 0), idx(hs.size()), hs2(hs.size());
+        for (int32_t s : hs) ++cnt[g->rank[s] + 1];
+        for (int32_t x = 1; x <= n; ++x) cnt[x] += cnt[x - 1];
+        for (size_t i = 0; i < hs.size(); ++i) idx[cnt[g->rank[hs[i]]]++] = (int32_t)i;
+        for (size_t t = 0; t < hs.size(); ++t) hs2[t] = hs[idx[t]];
+        CK(g->src_index.ensure(idx.size()));
+        CK(cudaMemcpy(g->src_index.p, idx.data(), idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        hs.swap(hs2);
+        g->reordered = true;
     }
     CK(g->sources.ensure(hs.size()));
     if (!hs.empty()) CK(cudaMemcpy(g->sources.p, hs.data(), hs.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -485,10 +558,12 @@ int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStr
         p.seq = ++g->seq;
         p.sources = g->sources.p + b0;
         if (hash) {
-            p.h_sigma = g->h_sigma.p + b0;
-            p.h_dist = g->h_dist.p + b0;
-            p.dist_sum = g->dist_sum.p + b0;
-            p.reach = g->reach.p + b0;
+            const int32_t o = g->reordered ? 0 : b0;  // reordered: summaries go through src_index
+            p.h_sigma = g->h_sigma.p + o;
+            p.h_dist = g->h_dist.p + o;
+            p.dist_sum = g->dist_sum.p + o;
+            p.reach = g->reach.p + o;
+            p.out_index = g->reordered ? g->src_index.p + b0 : nullptr;
         }
         {
             Timer t(g, st, BC_KERNEL_INIT);
@@ -647,6 +722,7 @@ int bc_create_graph(int32_t n, const int32_t *row_ptr, const int32_t *col, const
     g->narcs = m2;
     g->weighted = weights != nullptr;
     g->h_row_ptr = rp;
+    if (!weights) g->h_col = cl;
     for (int32_t x : ww) g->maxw = std::max(g->maxw, x);
     auto up = [&](DevBuf<int32_t> &d, const std::vector<int32_t> &h) -> int {
         CK(d.ensure(h.size()));
@@ -689,7 +765,8 @@ int bc_run(bc_graph *g, const int32_t *sources, int32_t num_sources, const bc_op
     if (r) return r;
     if (g->weighted && (flags & BC_PLAIN)) return fail(BC_ERR_UNSUPPORTED, "the one-source path is unweighted only");
     int32_t nsrc = 0;
-    r = stage_sources(g, sources, num_sources, &nsrc);
+    r = stage_sources(g, sources, num_sources, &nsrc,
+                      !g->weighted && !(flags & (BC_PLAIN | BC_KEEP_ORDER | BC_DENSE)));
     if (r) return r;
     g->timing = (flags & BC_TIMING) != 0;
     g->evused = 0;
@@ -751,6 +828,7 @@ int bc_result(bc_graph *g, double *bc, uint32_t *status_flags) {
     if (status_flags) *status_flags = status;
     if (status & BC_STATUS_BOUNDS) return fail(BC_ERR_BOUNDS, "device bounds check fired");
     if (status & BC_STATUS_DENSE_TIMEOUT) return fail(BC_ERR_TIMEOUT, "tensor-core pipeline wait timed out");
+    if (status & BC_STATUS_COPY_TIMEOUT) return fail(BC_ERR_TIMEOUT, "staged row copy wait timed out");
     if (status & BC_STATUS_SIGMA_OVERFLOW) return BC_WARN_SIGMA_OVERFLOW;
     return BC_OK;
 }
@@ -808,6 +886,8 @@ int bc_forward_rows(bc_graph *g, const int32_t *sources, int32_t k, uint64_t *si
     ds.release();
     dd.release();
     if (r) return r;
+    if (status & (BC_STATUS_DENSE_TIMEOUT | BC_STATUS_COPY_TIMEOUT))
+        return fail(BC_ERR_TIMEOUT, "a device wait timed out");
     return (status & BC_STATUS_SIGMA_OVERFLOW) ? BC_WARN_SIGMA_OVERFLOW : BC_OK;
 }
 

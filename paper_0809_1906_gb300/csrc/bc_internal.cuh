@@ -82,6 +82,7 @@ struct MsParams {
     uint64_t *h_dist;
     int64_t *dist_sum;
     int64_t *reach;
+    const int32_t *out_index;  // may be null: summary of batch source b goes to index out_index[b]
     DevCtl *ctl;
     HostCtl *hctl;  // device pointer of the host-mapped block
 };

@@ -24,6 +24,8 @@
 // needed.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "bc_internal.cuh"
 #include "msbfs_body.cuh"
 
@@ -148,6 +150,9 @@ template <int W>
 __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const int l) {
     constexpr int B = 32 * W;
     __shared__ uint32_t s_U[kWarps][32][W];  // unvisited words of the group's items
+    __shared__ uint64_t s_bar[kWarps];
+    __shared__ uint32_t s_qz[kWarps][32];
+    extern __shared__ __align__(128) uint8_t s_stage[];
     __shared__ uint32_t s_flags;
     __shared__ unsigned long long s_arcs;
     __shared__ int32_t s_u[kWarps][32];
@@ -176,6 +181,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     const bool ones = l == 1 && p.first;  // level 1 written by k_first: all counts 1, no masked rows
     bool produced = false, ovf = false, wide_next = false;
     uint32_t arcs = 0;  // predecessor relations counted by this lane
+    body::WarpStage ws{s_stage + wib * stage::kStageBytes, s_bar + wib, s_qz[wib], 0u, false};
+    if (lane == 0) stage::bar_init(ws.bar);
+    __syncwarp();
 
     // Persistent warps stride over the items (sorted by decreasing degree, so
     // every warp gets a similar mix; the chunks of one heavy vertex land on
@@ -227,8 +235,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
                 acc[j] = 0ull;
                 nf[j] = 0u;
             }
-            body::fwd_sum<W>(p.col, beg, end, ufl, Fl, Sl, p.sigma, wide, ones, U, s_u[wib], s_nz[wib], lane, acc, nf, ovf,
-                             arcs);
+            body::fwd_sum<W, true, true>(p.col, beg, end, ufl, Fl, Sl, p.sigma, wide, ones, U, s_u[wib], s_nz[wib], lane,
+                                         acc, nf, ovf, arcs, &ws);
             if (slot < 0) {
                 produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next, p.lvl, l + 1);
                 continue;
@@ -277,6 +285,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
         if (produced) atomicOr(&s_flags, 1u);
         if (wovf) atomicOr(&s_flags, 2u);
         if (wwide) atomicOr(&s_flags, 4u);
+        if (ws.fail) atomicOr(&s_flags, 8u);
         if (arcs) atomicAdd(&s_arcs, (unsigned long long)arcs);
     }
     __syncthreads();
@@ -284,6 +293,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     if (s_arcs) atomicAdd(&p.ctl->dag_arcs, s_arcs);
     if (s_flags & 1u) atomicOr(&p.ctl->nonempty, 1u);
     if (s_flags & 2u) atomicOr(&p.ctl->status, BC_STATUS_SIGMA_OVERFLOW);
+    if (s_flags & 8u) atomicOr(&p.ctl->status, BC_STATUS_COPY_TIMEOUT);
     if (s_flags & 4u) atomicOr(p.wide + l + 1, 1u);
     __threadfence();
     if (atomicAdd(&p.ctl->blocks_done, 1u) != gridDim.x - 1) return;
@@ -313,9 +323,12 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
 }
 
 template <int W>
-__global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const int l) {
+__global__ void __launch_bounds__(kBlock, 3) k_backward(const MsParams p, const int l) {
     constexpr int B = 32 * W;
     __shared__ uint32_t s_f[kWarps][32][W];  // level-l words of the group's items
+    __shared__ uint64_t s_bar[kWarps];
+    __shared__ uint32_t s_qz[kWarps][32];
+    extern __shared__ __align__(128) uint8_t s_stage[];
     __shared__ int32_t s_u[kWarps][32];
     __shared__ uint32_t s_nz[kWarps][32];
     const int lane = threadIdx.x & 31;
@@ -327,6 +340,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
     const size_t nB = (size_t)p.n * B;
     float *Cl = p.cval + (size_t)(l & 1) * nB;
     const float *Cs = p.cval + (size_t)((l + 1) & 1) * nB;
+    body::WarpStage ws{s_stage + wib * stage::kStageBytes, s_bar + wib, s_qz[wib], 0u, false};
+    if (lane == 0) stage::bar_init(ws.bar);
+    __syncwarp();
     // the forward pass's item striding; lane k of a warp checks whether its
     // k-th next item's vertex is at level l for any source (the same for all
     // chunks of v), then the warp works through the active items
@@ -364,7 +380,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
             float S[W];  // lane owns source 32j + lane
 #pragma unroll
             for (int j = 0; j < W; ++j) S[j] = 0.0f;
-            body::bwd_sum<W>(p.col, beg, end, ufs, Fs, Cs, f, s_u[wib], s_nz[wib], lane, S);
+            body::bwd_sum<W, true, true>(p.col, beg, end, ufs, Fs, Cs, f, s_u[wib], s_nz[wib], lane, S, &ws);
             if (slot < 0) {
                 body::finalize_dep<W>(p.sigma, Cl, p.bc, v, f, S, lane);
                 continue;
@@ -392,6 +408,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
             if (lane == 0) p.cnt[first] = 0u;
         }
     }
+    if (lane == 0 && ws.fail) atomicOr(&p.ctl->status, BC_STATUS_COPY_TIMEOUT);
 }
 
 // Per-source summaries. Thread t of a block owns source t % B and takes
@@ -463,10 +480,11 @@ __global__ void k_hash_sum(const MsParams p, const int blocks) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
     if (lane != 0) return;
-    if (q == 0) p.h_sigma[s] = acc;
-    if (q == 1) p.h_dist[s] = acc;
-    if (q == 2) p.dist_sum[s] = (int64_t)acc;
-    if (q == 3) p.reach[s] = (int64_t)acc;
+    const int o = p.out_index ? p.out_index[s] : s;
+    if (q == 0) p.h_sigma[o] = acc;
+    if (q == 1) p.h_dist[o] = acc;
+    if (q == 2) p.dist_sum[o] = (int64_t)acc;
+    if (q == 3) p.reach[o] = (int64_t)acc;
 }
 
 // Rows of the forward pass for bc_forward_rows: out[b][v] for this batch.
@@ -504,12 +522,36 @@ int sm_count() {
     return c;
 }
 
+// dynamic shared memory of the level kernels: one row stage per warp
+constexpr size_t kStageSmem = (size_t)kWarps * stage::kStageBytes;
+
+// Raise the kernel's dynamic shared memory limit once per device.
+template <class K>
+void stage_attr(K kernel, std::atomic<uint32_t> &done) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint32_t bit = 1u << (dev & 31);
+    if (done.load(std::memory_order_acquire) & bit) return;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageSmem);
+    done.fetch_or(bit, std::memory_order_acq_rel);
+}
+template <int W>
+void fwd_attr() {
+    static std::atomic<uint32_t> done{0};
+    stage_attr(k_forward<W>, done);
+}
+template <int W>
+void bwd_attr() {
+    static std::atomic<uint32_t> done{0};
+    stage_attr(k_backward<W>, done);
+}
+
 // Persistent grid: as many blocks as fit on the GPU at once (occupancy of
 // the kernel instance), never more than the items need.
 template <class K>
-int item_blocks(const MsParams &p, K kernel) {
+int item_blocks(const MsParams &p, K kernel, size_t dyn_smem = 0) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, dyn_smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     const int need = (p.nitems + kWarps - 1) / kWarps;
     const int cap = per_sm * sm_count();
@@ -548,12 +590,14 @@ void ms_launch_first(int W, const MsParams &p, cudaStream_t st) {
 
 void ms_launch_forward(int W, const MsParams &p, int level, cudaStream_t st) {
     if (p.nitems == 0) return;
-    BCGB_DISPATCH_W(W, (k_forward<kW><<<item_blocks(p, k_forward<kW>), kBlock, 0, st>>>(p, level)));
+    BCGB_DISPATCH_W(W, (fwd_attr<kW>(),
+                        k_forward<kW><<<item_blocks(p, k_forward<kW>, kStageSmem), kBlock, kStageSmem, st>>>(p, level)));
 }
 
 void ms_launch_backward(int W, const MsParams &p, int level, cudaStream_t st) {
     if (p.nitems == 0) return;
-    BCGB_DISPATCH_W(W, (k_backward<kW><<<item_blocks(p, k_backward<kW>), kBlock, 0, st>>>(p, level)));
+    BCGB_DISPATCH_W(W, (bwd_attr<kW>(),
+                        k_backward<kW><<<item_blocks(p, k_backward<kW>, kStageSmem), kBlock, kStageSmem, st>>>(p, level)));
 }
 
 int ms_hash_blocks(const MsParams &p) {

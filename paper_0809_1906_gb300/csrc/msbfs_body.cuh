@@ -25,8 +25,21 @@
 
 #include <cstdint>
 
+#include "rowstage.cuh"
+
 namespace bcgb {
 namespace body {
+
+// A warp's row stage (rowstage.cuh): buffer of stage::kStageBytes, its
+// mbarrier and phase, per-slot word masks (backward), and the failure flag
+// set when a wait gave up (the warp then stops adding rows).
+struct WarpStage {
+    uint8_t *buf;
+    uint64_t *bar;
+    uint32_t *qz;
+    uint32_t phase;
+    bool fail;
+};
 
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -95,14 +108,15 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 // of m_k, so the backward adder loads only the words that can contribute
 // (measured: a gain there, a loss in the forward adder, which loads whole
 // rows).
-// Returns the ballot of contributing lanes.
+// Returns the ballot of contributing lanes; u and nz are lane k's own
+// neighbour and word set.
 template <int W, bool NC>
 __device__ __forceinline__ unsigned probe_chunk(const int32_t *__restrict__ col, int e, int end,
                                                 const uint32_t *__restrict__ ufr, const uint32_t *__restrict__ Fx,
                                                 const uint32_t (&want)[W], uint32_t (&m)[W], int32_t *s_u,
-                                                uint32_t *s_nz, int lane) {
-    int u = 0;
-    uint32_t nz = 0;
+                                                uint32_t *s_nz, int lane, int &u, uint32_t &nz) {
+    u = 0;
+    nz = 0;
 #pragma unroll
     for (int j = 0; j < W; ++j) m[j] = 0u;
     if (e < end) {
@@ -131,16 +145,19 @@ __device__ __forceinline__ unsigned probe_chunk(const int32_t *__restrict__ col,
 // whose counts are all 1 (ones) just counts predecessors. nf[j]
 // gets the sources reaching v; exact uint64 sums, ovf flags a carry out of
 // bit 63; arcs counts predecessor relations (lane-local).
-template <int W, bool NC = true>
+template <int W, bool NC = true, bool STAGED = false>
 __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg, int end,
                                         const uint32_t *__restrict__ ufl, const uint32_t *__restrict__ Fl,
                                         const uint16_t *__restrict__ Sl, const uint64_t *__restrict__ sigma,
                                         bool wide, bool ones, const uint32_t (&U)[W], int32_t *s_u, uint32_t *s_nz,
-                                        int lane, uint64_t (&acc)[W], uint32_t (&nf)[W], bool &ovf, uint32_t &arcs) {
+                                        int lane, uint64_t (&acc)[W], uint32_t (&nf)[W], bool &ovf, uint32_t &arcs,
+                                        WarpStage *ws = nullptr) {
     constexpr int B = 32 * W;
     for (int e0 = beg; e0 < end; e0 += 32) {
         uint32_t m[W];
-        unsigned bal = probe_chunk<W, NC>(col, e0 + lane, end, ufl, Fl, U, m, s_u, s_nz, lane);
+        int u;
+        uint32_t nz;
+        unsigned bal = probe_chunk<W, NC>(col, e0 + lane, end, ufl, Fl, U, m, s_u, s_nz, lane, u, nz);
         if (!bal) continue;
 #pragma unroll
         for (int j = 0; j < W; ++j) {
@@ -154,9 +171,60 @@ __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg
 #pragma unroll
             for (int j = 0; j < W; ++j)
                 if (__any_sync(kFull, m[j] != 0u)) acc[j] += (uint64_t)__popc(transpose32(m[j], lane));
+        } else if (STAGED && !wide) {
+            // rounds of up to R rows: each contributing lane copies the span of
+            // its neighbour's masked row from the first to the last word that
+            // can contribute into slot `rank` of the stage; the warp waits
+            // once and adds the contributing words of the slots (at most 32
+            // values below 2^16 per chunk: 32-bit sums are exact)
+            constexpr int RB = 2 * B;
+            constexpr int R = (int)stage::kStageBytes / RB < 32 ? (int)stage::kStageBytes / RB : 32;
+            const uint16_t *st = reinterpret_cast<const uint16_t *>(ws->buf);
+            uint32_t a32[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) a32[j] = 0u;
+            while (bal && !ws->fail) {
+                const int rank = __popc(bal & ((1u << lane) - 1u));
+                const bool go = ((bal >> lane) & 1u) && rank < R;
+                const unsigned take = __ballot_sync(kFull, go);
+                const int nq = __popc(take);
+                const int lo = __ffs(nz) - 1, hi = 31 - __clz(nz);
+                const uint32_t bytes = go ? 64u * (uint32_t)(hi - lo + 1) : 0u;
+                const uint32_t tot = __reduce_add_sync(kFull, bytes);
+                if (go) ws->qz[rank] = nz;
+                if (lane == 0) stage::expect_tx(ws->bar, tot);
+                __syncwarp();
+                if (go) stage::copy(ws->buf + rank * RB + 64 * lo, Sl + (size_t)u * B + 32 * lo, bytes, ws->bar);
+                const bool ok = stage::wait(ws->bar, ws->phase);
+                ws->phase ^= 1u;
+                if (!__all_sync(kFull, ok)) {
+                    ws->fail = true;
+                    break;
+                }
+#pragma unroll 4
+                for (int q = 0; q < nq; ++q) {
+                    const uint32_t z = ws->qz[q];
+#pragma unroll
+                    for (int j = 0; j < W; ++j)
+                        if ((z >> j) & 1u) a32[j] += st[q * B + 32 * j + lane];
+                }
+                __syncwarp();
+                bal &= ~take;
+            }
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                const uint64_t y = acc[j] + (uint64_t)a32[j];
+                ovf |= y < acc[j];
+                acc[j] = y;
+            }
         } else if (!wide) {
-            // two neighbours per step: 2W independent coalesced loads in flight
+            // two neighbours per step: 2W independent coalesced loads in flight.
+            // At most 32 values below 2^16 per chunk: 32-bit sums are exact and
+            // are folded into the 64-bit ones once per chunk.
             const uint16_t *base = Sl + lane;
+            uint32_t a32[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) a32[j] = 0u;
             while (bal) {
                 const int k0 = __ffs(bal) - 1;
                 bal &= bal - 1;
@@ -171,11 +239,13 @@ __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg
                     x1[j] = k1 >= 0 ? (uint32_t)ldx<NC>(r1 + 32 * j) : 0u;
                 }
 #pragma unroll
-                for (int j = 0; j < W; ++j) {
-                    const uint64_t y = acc[j] + (uint64_t)x0[j] + (uint64_t)x1[j];
-                    ovf |= y < acc[j];
-                    acc[j] = y;
-                }
+                for (int j = 0; j < W; ++j) a32[j] += x0[j] + x1[j];
+            }
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                const uint64_t y = acc[j] + (uint64_t)a32[j];
+                ovf |= y < acc[j];
+                acc[j] = y;
             }
         } else {
             const uint64_t *base = sigma + lane;
@@ -203,15 +273,55 @@ __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg
 // lane with d(s,v) = l (f), S[j] += Cs[w][s] over the neighbours w whose
 // level-(l+1) frontier meets f. Cs is the masked level-(l+1) c buffer, so
 // for s in f this is the sum of c_s(w) over the w with v in P_s(w).
-template <int W, bool NC = true>
+template <int W, bool NC = true, bool STAGED = false>
 __device__ __forceinline__ void bwd_sum(const int32_t *__restrict__ col, int beg, int end,
                                         const uint32_t *__restrict__ ufs, const uint32_t *__restrict__ Fs,
                                         const float *__restrict__ Cs, const uint32_t (&f)[W], int32_t *s_u,
-                                        uint32_t *s_nz, int lane, float (&S)[W]) {
+                                        uint32_t *s_nz, int lane, float (&S)[W], WarpStage *ws = nullptr) {
     constexpr int B = 32 * W;
     for (int e0 = beg; e0 < end; e0 += 32) {
         uint32_t m[W];
-        unsigned bal = probe_chunk<W, NC>(col, e0 + lane, end, ufs, Fs, f, m, s_u, s_nz, lane);
+        int u;
+        uint32_t nz;
+        unsigned bal = probe_chunk<W, NC>(col, e0 + lane, end, ufs, Fs, f, m, s_u, s_nz, lane, u, nz);
+        if constexpr (STAGED) {
+            // rounds of up to R rows; a lane copies the span of its
+            // neighbour's c row from the first to the last word that can
+            // contribute, and the adder takes only the contributing words
+            constexpr int RB = 4 * B;
+            constexpr int R = (int)stage::kStageBytes / RB < 32 ? (int)stage::kStageBytes / RB : 32;
+            const float *st = reinterpret_cast<const float *>(ws->buf);
+            while (bal && !ws->fail) {
+                const int rank = __popc(bal & ((1u << lane) - 1u));
+                const bool go = ((bal >> lane) & 1u) && rank < R;
+                const unsigned take = __ballot_sync(kFull, go);
+                const int nq = __popc(take);
+                const int lo = __ffs(nz) - 1, hi = 31 - __clz(nz);
+                const uint32_t bytes = go ? 128u * (uint32_t)(hi - lo + 1) : 0u;
+                const uint32_t tot = __reduce_add_sync(kFull, bytes);
+                if (go) ws->qz[rank] = nz;
+                if (lane == 0) stage::expect_tx(ws->bar, tot);
+                __syncwarp();
+                if (go) stage::copy(ws->buf + rank * RB + 128 * lo, Cs + (size_t)u * B + 32 * lo, bytes, ws->bar);
+                const bool ok = stage::wait(ws->bar, ws->phase);
+                ws->phase ^= 1u;
+                if (!__all_sync(kFull, ok)) {
+                    ws->fail = true;
+                    break;
+                }
+#pragma unroll 2
+                for (int q = 0; q < nq; ++q) {
+                    const uint32_t z = ws->qz[q];
+#pragma unroll
+                    for (int j = 0; j < W; ++j)
+                        if ((z >> j) & 1u) S[j] += st[q * B + 32 * j + lane];
+                }
+                __syncwarp();
+                bal &= ~take;
+            }
+            __syncwarp();
+            continue;
+        }
         const float *base = Cs + lane;
         // two neighbours per step: 2W independent coalesced loads in flight
         while (bal) {

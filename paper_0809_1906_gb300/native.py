@@ -28,6 +28,7 @@ BC_ERR_STATE = -9
 
 BC_STATUS_SIGMA_OVERFLOW = 0x1
 BC_STATUS_DENSE_TIMEOUT = 0x8
+BC_STATUS_COPY_TIMEOUT = 0x10
 
 BC_GRAPH_TRUST_INPUT = 0x1
 
@@ -38,6 +39,7 @@ BC_TIMING = 0x8
 BC_NO_HASH = 0x10
 BC_DENSE = 0x20
 BC_SPARSE_BACKWARD = 0x40
+BC_KEEP_ORDER = 0x80
 
 BC_KERNEL_INIT = 0
 BC_KERNEL_FORWARD = 1

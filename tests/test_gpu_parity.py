@@ -159,6 +159,29 @@ def test_deterministic(nat):
     assert np.array_equal(a, b)
 
 
+def test_landmark_order_matches_given_order(nat):
+    """Batches formed in landmark order (the default) and in the given order
+    give the same per-source summaries, both in the caller's order, and BC
+    within tolerance of the oracle; the source list is shuffled, holds
+    duplicates and leaves a ragged last batch."""
+    g = G.er_hamiltonian(2000, 9000, 8)
+    rng = np.random.default_rng(3)
+    src = rng.integers(0, g.n, 700).astype(np.int32)
+    ref = oracle.bc(g, src)
+    with nat.Graph.from_csr(g) as h:
+        h.run(src, batch=64)
+        a, _, _ = h.result()
+        ha = h.source_hashes(len(src))
+        h.run(src, batch=64, flags=nat.BC_KEEP_ORDER)
+        b, _, _ = h.result()
+        hb = h.source_hashes(len(src))
+    for k in ("hash_sigma", "hash_dist", "dist_sum", "reach"):
+        assert np.array_equal(ha[k], ref[k]), k
+        assert np.array_equal(hb[k], ref[k]), k
+    assert_bc_close(a, ref["bc"], g.n, "landmark order")
+    assert_bc_close(b, ref["bc"], g.n, "given order")
+
+
 def test_device_pointer_inputs(nat):
     import torch
     g = G.er_hamiltonian(500, 2000, 4)
