@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     const bool ones = l == 1 && p.first;  // level 1 written by k_first: all counts 1, no masked rows
     bool produced = false, ovf = false, wide_next = false;
     uint32_t arcs = 0;  // predecessor relations counted by this lane
-    body::WarpStage ws{s_stage + wib * stage::kStageBytes, s_bar + wib, s_qz[wib], 0u, false};
+    body::WarpStage ws{s_stage + wib * stage::kFwdStageBytes, s_bar + wib, s_qz[wib], 0u, false};
     if (lane == 0) stage::bar_init(ws.bar);
     __syncwarp();
 
@@ -323,9 +323,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
 }
 
 template <int W>
-__global__ void __launch_bounds__(kBlock, 3) k_backward(const MsParams p, const int l) {
+__global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const int l) {
     constexpr int B = 32 * W;
     __shared__ uint32_t s_f[kWarps][32][W];  // level-l words of the group's items
+    __shared__ int32_t s_v[kWarps][32];      // and their vertices
     __shared__ uint64_t s_bar[kWarps];
     __shared__ uint32_t s_qz[kWarps][32];
     extern __shared__ __align__(128) uint8_t s_stage[];
@@ -340,9 +341,26 @@ __global__ void __launch_bounds__(kBlock, 3) k_backward(const MsParams p, const 
     const size_t nB = (size_t)p.n * B;
     float *Cl = p.cval + (size_t)(l & 1) * nB;
     const float *Cs = p.cval + (size_t)((l + 1) & 1) * nB;
-    body::WarpStage ws{s_stage + wib * stage::kStageBytes, s_bar + wib, s_qz[wib], 0u, false};
+    body::WarpStage ws{s_stage + wib * stage::kBwdStageBytes, s_bar + wib, s_qz[wib], 0u, false};
     if (lane == 0) stage::bar_init(ws.bar);
     __syncwarp();
+    // sigma row span of item k of the group (its words at level l), brought
+    // into L2 two items ahead of the step that reads it
+    auto prefetch_sigma = [&](int k) {
+        uint32_t any = 0;
+        int lo = W, hi = -1;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const uint32_t x = s_f[wib][k][j];
+            any |= x;
+            if (x != 0u) {
+                lo = j < lo ? j : lo;
+                hi = j;
+            }
+        }
+        if (any != 0u)
+            stage::prefetch_l2(p.sigma + (size_t)s_v[wib][k] * B + 32 * lo, 256u * (uint32_t)(hi - lo + 1));
+    };
     // the forward pass's item striding; lane k of a warp checks whether its
     // k-th next item's vertex is at level l for any source (the same for all
     // chunks of v), then the warp works through the active items
@@ -361,13 +379,19 @@ __global__ void __launch_bounds__(kBlock, 3) k_backward(const MsParams p, const 
                 s_f[wib][lane][j] = f[j];
                 any |= f[j];
             }
+            s_v[wib][lane] = vk;
             act = any != 0u;
         }
         unsigned todo = __ballot_sync(kFull, act);
         __syncwarp();
+        if (act && __popc(todo & ((1u << lane) - 1u)) < 2) prefetch_sigma(lane);
         while (todo) {
             const int kk = __ffs(todo) - 1;
             todo &= todo - 1;
+            if (lane == 0) {
+                const unsigned k2 = __fns(todo, 0, 2);  // two active items ahead
+                if (k2 < 32u) prefetch_sigma((int)k2);
+            }
             const int it = g0 + kk * G;
             const int v = p.item_v[it];
             const int beg = p.item_beg[it];
@@ -523,27 +547,28 @@ int sm_count() {
 }
 
 // dynamic shared memory of the level kernels: one row stage per warp
-constexpr size_t kStageSmem = (size_t)kWarps * stage::kStageBytes;
+constexpr size_t kFwdSmem = (size_t)kWarps * stage::kFwdStageBytes;
+constexpr size_t kBwdSmem = (size_t)kWarps * stage::kBwdStageBytes;
 
 // Raise the kernel's dynamic shared memory limit once per device.
 template <class K>
-void stage_attr(K kernel, std::atomic<uint32_t> &done) {
+void stage_attr(K kernel, size_t bytes, std::atomic<uint32_t> &done) {
     int dev = 0;
     cudaGetDevice(&dev);
     const uint32_t bit = 1u << (dev & 31);
     if (done.load(std::memory_order_acquire) & bit) return;
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageSmem);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     done.fetch_or(bit, std::memory_order_acq_rel);
 }
 template <int W>
 void fwd_attr() {
     static std::atomic<uint32_t> done{0};
-    stage_attr(k_forward<W>, done);
+    stage_attr(k_forward<W>, kFwdSmem, done);
 }
 template <int W>
 void bwd_attr() {
     static std::atomic<uint32_t> done{0};
-    stage_attr(k_backward<W>, done);
+    stage_attr(k_backward<W>, kBwdSmem, done);
 }
 
 // Persistent grid: as many blocks as fit on the GPU at once (occupancy of
@@ -591,13 +616,13 @@ void ms_launch_first(int W, const MsParams &p, cudaStream_t st) {
 void ms_launch_forward(int W, const MsParams &p, int level, cudaStream_t st) {
     if (p.nitems == 0) return;
     BCGB_DISPATCH_W(W, (fwd_attr<kW>(),
-                        k_forward<kW><<<item_blocks(p, k_forward<kW>, kStageSmem), kBlock, kStageSmem, st>>>(p, level)));
+                        k_forward<kW><<<item_blocks(p, k_forward<kW>, kFwdSmem), kBlock, kFwdSmem, st>>>(p, level)));
 }
 
 void ms_launch_backward(int W, const MsParams &p, int level, cudaStream_t st) {
     if (p.nitems == 0) return;
     BCGB_DISPATCH_W(W, (bwd_attr<kW>(),
-                        k_backward<kW><<<item_blocks(p, k_backward<kW>, kStageSmem), kBlock, kStageSmem, st>>>(p, level)));
+                        k_backward<kW><<<item_blocks(p, k_backward<kW>, kBwdSmem), kBlock, kBwdSmem, st>>>(p, level)));
 }
 
 int ms_hash_blocks(const MsParams &p) {

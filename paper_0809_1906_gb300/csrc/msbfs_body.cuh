@@ -30,7 +30,8 @@
 namespace bcgb {
 namespace body {
 
-// A warp's row stage (rowstage.cuh): buffer of stage::kStageBytes, its
+// A warp's row stage (rowstage.cuh): buffer (stage::kFwdStageBytes forward,
+// stage::kBwdStageBytes backward), its
 // mbarrier and phase, per-slot word masks (backward), and the failure flag
 // set when a wait gave up (the warp then stops adding rows).
 struct WarpStage {
@@ -90,16 +91,94 @@ __device__ __forceinline__ void load_row(const uint32_t *__restrict__ p, uint32_
 
 // Warp-wide 32x32 bit transpose: lane k holds row k; returns column `lane`
 // (bit k of the result = bit `lane` of lane k's input). Five exchange steps,
-// each swapping the off-diagonal s x s blocks of every 2s x 2s block.
+// each swapping the off-diagonal s x s blocks of every 2s x 2s block with
+// partner lane ^ s: the partner's word rotated by s (towards the high bits
+// for lanes with bit s clear, the low bits otherwise) supplies exactly the
+// bits outside this lane's kept mask, so a step is a shuffle, a rotate and a
+// bitwise select.
 __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 #pragma unroll
     for (int s = 16; s >= 1; s >>= 1) {
         const uint32_t M = s == 16 ? 0x0000FFFFu : s == 8 ? 0x00FF00FFu : s == 4 ? 0x0F0F0F0Fu
                          : s == 2 ? 0x33333333u : 0x55555555u;
+        const bool hi = (lane & s) != 0;
+        const uint32_t keep = hi ? ~M : M;
         const uint32_t y = __shfl_xor_sync(kFull, x, s);
-        x = (lane & s) ? ((x & ~M) | ((y >> s) & M)) : ((x & M) | ((y & M) << s));
+        const uint32_t a = __funnelshift_l(y, y, hi ? 32 - s : s);
+        x = (x & keep) | (a & ~keep);
     }
     return x;
+}
+
+// Packed view of a staged row: lane l reads the W consecutive entries of
+// sources W*l .. W*l+W-1 with one vector load (its sources all lie in word
+// (W*l)/32 of the row). The adders sum in this view and hand the sums back
+// in the lane-owns-32j+lane view through shared memory.
+template <int W>
+__device__ __forceinline__ void lds_packed(const uint16_t *p, uint32_t (&x)[(W + 1) / 2]) {
+    if constexpr (W == 8) {
+        const uint4 t = *reinterpret_cast<const uint4 *>(p);
+        x[0] = t.x;
+        x[1] = t.y;
+        x[2] = t.z;
+        x[3] = t.w;
+    } else if constexpr (W == 4) {
+        const uint2 t = *reinterpret_cast<const uint2 *>(p);
+        x[0] = t.x;
+        x[1] = t.y;
+    } else if constexpr (W == 2) {
+        x[0] = *reinterpret_cast<const uint32_t *>(p);
+    } else {
+        x[0] = *p;
+    }
+}
+template <int W>
+__device__ __forceinline__ void lds_packed(const float *p, float (&x)[W]) {
+    if constexpr (W >= 4) {
+#pragma unroll
+        for (int i = 0; i < W / 4; ++i) {
+            const float4 t = reinterpret_cast<const float4 *>(p)[i];
+            x[4 * i] = t.x;
+            x[4 * i + 1] = t.y;
+            x[4 * i + 2] = t.z;
+            x[4 * i + 3] = t.w;
+        }
+    } else if constexpr (W == 2) {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        x[0] = t.x;
+        x[1] = t.y;
+    } else {
+        x[0] = *p;
+    }
+}
+__device__ __forceinline__ uint32_t as_bits(uint32_t x) { return x; }
+__device__ __forceinline__ uint32_t as_bits(float x) { return __float_as_uint(x); }
+
+// Lane l stores its W packed values at p[W*l ..]; after the warp synchronises,
+// lane l reads entries 32j + l.
+template <int W, class T>
+__device__ __forceinline__ void unpack_lanes(T *p, const T (&x)[W], T (&out)[W], int lane) {
+    T *q = p + W * lane;
+    if constexpr (W >= 4) {
+#pragma unroll
+        for (int i = 0; i < W / 4; ++i) {
+            uint4 t;
+            t.x = as_bits(x[4 * i]);
+            t.y = as_bits(x[4 * i + 1]);
+            t.z = as_bits(x[4 * i + 2]);
+            t.w = as_bits(x[4 * i + 3]);
+            reinterpret_cast<uint4 *>(q)[i] = t;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; ++i) q[i] = x[i];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < W; ++j) out[j] = p[32 * j + lane];
+    __syncwarp();
+    // the stage is written by bulk copies next: order these generic accesses first
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // One 32-arc chunk: lane k gets arc e (if e < end), its neighbour u_k (stored
@@ -178,11 +257,15 @@ __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg
             // once and adds the contributing words of the slots (at most 32
             // values below 2^16 per chunk: 32-bit sums are exact)
             constexpr int RB = 2 * B;
-            constexpr int R = (int)stage::kStageBytes / RB < 32 ? (int)stage::kStageBytes / RB : 32;
+            constexpr int R = (int)stage::kFwdStageBytes / RB < 32 ? (int)stage::kFwdStageBytes / RB : 32;
+            constexpr int P = (W + 1) / 2;  // packed 32-bit words per lane
             const uint16_t *st = reinterpret_cast<const uint16_t *>(ws->buf);
-            uint32_t a32[W];
+            const int jl = (W * lane) >> 5;  // the row word holding this lane's sources
+            // X: wrapping sums of the packed words; H: sums of their high
+            // halves. The low-half sums are X - (H << 16), exact while below 2^32.
+            uint32_t X[P], H[P];
 #pragma unroll
-            for (int j = 0; j < W; ++j) a32[j] = 0u;
+            for (int i = 0; i < P; ++i) X[i] = H[i] = 0u;
             while (bal && !ws->fail) {
                 const int rank = __popc(bal & ((1u << lane) - 1u));
                 const bool go = ((bal >> lane) & 1u) && rank < R;
@@ -203,14 +286,26 @@ __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg
                 }
 #pragma unroll 4
                 for (int q = 0; q < nq; ++q) {
-                    const uint32_t z = ws->qz[q];
+                    if ((ws->qz[q] >> jl) & 1u) {
+                        uint32_t x[P];
+                        lds_packed<W>(st + q * B + W * lane, x);
 #pragma unroll
-                    for (int j = 0; j < W; ++j)
-                        if ((z >> j) & 1u) a32[j] += st[q * B + 32 * j + lane];
+                        for (int i = 0; i < P; ++i) {
+                            X[i] += x[i];
+                            H[i] += x[i] >> 16;
+                        }
+                    }
                 }
                 __syncwarp();
                 bal &= ~take;
             }
+            uint32_t sums[W], a32[W];
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                sums[2 * i] = X[i] - (H[i] << 16);
+                if (2 * i + 1 < W) sums[2 * i + 1] = H[i];
+            }
+            unpack_lanes<W>(reinterpret_cast<uint32_t *>(ws->buf), sums, a32, lane);
 #pragma unroll
             for (int j = 0; j < W; ++j) {
                 const uint64_t y = acc[j] + (uint64_t)a32[j];
@@ -279,6 +374,10 @@ __device__ __forceinline__ void bwd_sum(const int32_t *__restrict__ col, int beg
                                         const float *__restrict__ Cs, const uint32_t (&f)[W], int32_t *s_u,
                                         uint32_t *s_nz, int lane, float (&S)[W], WarpStage *ws = nullptr) {
     constexpr int B = 32 * W;
+    float Sp[W];  // staged sums, packed view (lane owns sources W*lane + t)
+#pragma unroll
+    for (int t = 0; t < W; ++t) Sp[t] = 0.0f;
+    bool staged = false;
     for (int e0 = beg; e0 < end; e0 += 32) {
         uint32_t m[W];
         int u;
@@ -289,8 +388,9 @@ __device__ __forceinline__ void bwd_sum(const int32_t *__restrict__ col, int beg
             // neighbour's c row from the first to the last word that can
             // contribute, and the adder takes only the contributing words
             constexpr int RB = 4 * B;
-            constexpr int R = (int)stage::kStageBytes / RB < 32 ? (int)stage::kStageBytes / RB : 32;
+            constexpr int R = (int)stage::kBwdStageBytes / RB < 32 ? (int)stage::kBwdStageBytes / RB : 32;
             const float *st = reinterpret_cast<const float *>(ws->buf);
+            const int jl = (W * lane) >> 5;  // the row word holding this lane's sources
             while (bal && !ws->fail) {
                 const int rank = __popc(bal & ((1u << lane) - 1u));
                 const bool go = ((bal >> lane) & 1u) && rank < R;
@@ -311,13 +411,16 @@ __device__ __forceinline__ void bwd_sum(const int32_t *__restrict__ col, int beg
                 }
 #pragma unroll 2
                 for (int q = 0; q < nq; ++q) {
-                    const uint32_t z = ws->qz[q];
+                    if ((ws->qz[q] >> jl) & 1u) {
+                        float x[W];
+                        lds_packed<W>(st + q * B + W * lane, x);
 #pragma unroll
-                    for (int j = 0; j < W; ++j)
-                        if ((z >> j) & 1u) S[j] += st[q * B + 32 * j + lane];
+                        for (int t = 0; t < W; ++t) Sp[t] += x[t];
+                    }
                 }
                 __syncwarp();
                 bal &= ~take;
+                staged = true;
             }
             __syncwarp();
             continue;
@@ -342,6 +445,14 @@ __device__ __forceinline__ void bwd_sum(const int32_t *__restrict__ col, int beg
             for (int j = 0; j < W; ++j) S[j] += x0[j] + x1[j];
         }
         __syncwarp();
+    }
+    if constexpr (STAGED) {
+        if (staged) {
+            float Sj[W];
+            unpack_lanes<W>(reinterpret_cast<float *>(ws->buf), Sp, Sj, lane);
+#pragma unroll
+            for (int j = 0; j < W; ++j) S[j] += Sj[j];
+        }
     }
 }
 
@@ -377,28 +488,53 @@ __device__ __forceinline__ bool store_next(uint64_t *sigma, uint16_t *Sn, uint32
     return any != 0;
 }
 
+// Error-free sum of two FP32 values: s + e == a + b exactly (Knuth's
+// TwoSum; no reassociation, no contraction: additions only).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// sigma as FP32, correctly rounded; the 32-bit conversion when it fits.
+__device__ __forceinline__ float sigma_f32(uint64_t x) {
+    return (x >> 32) ? __ull2float_rn(x) : __uint2float_rn((uint32_t)x);
+}
+
 // Cl: the masked level-l c buffer, written in full (zeros for the sources v
-// is not at level l for).
+// is not at level l for). For s with d(s,v) = l: delta_s(v) = sigma_s(v) * S
+// and c_s(v) = (1 + delta_s(v)) / sigma_s(v) = 1/sigma_s(v) + S. The warp's
+// delta values are added as an unevaluated FP32 pair (hi + lo, error-free
+// transformations, about 2^-44 relative), so FP64 is used once per vertex,
+// to add hi + lo into bc[v].
 template <int W>
 __device__ __forceinline__ void finalize_dep(const uint64_t *sigma, float *Cl, double *bc, int v,
                                              const uint32_t (&f)[W], const float (&S)[W], int lane) {
     constexpr int B = 32 * W;
-    double sum = 0.0;
+    float hi = 0.0f, lo = 0.0f;
 #pragma unroll
     for (int j = 0; j < W; ++j) {
         const size_t idx = (size_t)v * B + 32 * j + lane;
         float c = 0.0f;
         if ((f[j] >> lane) & 1u) {
-            const float sg = __ull2float_rn(sigma[idx]);
-            const float d = sg * S[j];  // delta_s*(v) = sigma_s(v) * sum_w c_s(w)
-            c = (1.0f + d) / sg;        // c_s(v) for the level above
-            sum += (double)d;
+            const float sg = sigma_f32(sigma[idx]);
+            const float d = sg * S[j];  // delta_s(v) = sigma_s(v) * sum_w c_s(w)
+            c = __frcp_rn(sg) + S[j];   // c_s(v) for the level above
+            float e;
+            two_sum(hi, d, hi, e);
+            lo += e;
         }
         Cl[idx] = c;
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(kFull, sum, off);
-    if (lane == 0) bc[v] += sum;
+    for (int off = 16; off > 0; off >>= 1) {
+        const float h2 = __shfl_xor_sync(kFull, hi, off);
+        const float l2 = __shfl_xor_sync(kFull, lo, off);
+        float e;
+        two_sum(hi, h2, hi, e);
+        lo = lo + l2 + e;
+    }
+    if (lane == 0) bc[v] += (double)hi + (double)lo;
 }
 
 }  // namespace body

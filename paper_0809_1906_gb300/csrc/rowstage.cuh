@@ -20,7 +20,10 @@
 namespace bcgb {
 namespace stage {
 
-constexpr uint32_t kStageBytes = 8192;       // per warp
+// per-warp stage sizes: forward rows (uint16) and backward rows (FP32); the
+// backward kernel trades stage depth for a fourth resident block per SM
+constexpr uint32_t kFwdStageBytes = 8192;
+constexpr uint32_t kBwdStageBytes = 4096;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -74,6 +77,15 @@ __device__ __forceinline__ void copy(void *dst, const void *src, uint32_t bytes,
             smem_addr(dst)),
         "l"(static_cast<uint64_t>(__cvta_generic_to_global(src))), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
+}
+
+// Hint: bring `bytes` (a multiple of 16, 16-byte aligned) of global memory
+// into L2 without waiting for it.
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
+                     static_cast<uint64_t>(__cvta_generic_to_global(src))),
+                 "r"(bytes)
+                 : "memory");
 }
 
 }  // namespace stage
