@@ -65,6 +65,17 @@ cudaError_t fetch(std::vector<T> &dst, const T *src, size_t count) {
 
 }  // namespace
 
+// Work items of one level sweep: one per vertex, except vertices with more
+// than `chunk` arcs, which are split into chunks combining through slots.
+struct ItemPlan {
+    int32_t chunk = 0, nitems = 0, nslots = 0;
+    DevBuf<int32_t> item_v, item_beg, item_end, item_slot, slot_first, slot_nch;
+    void release() {
+        for (auto *b : {&item_v, &item_beg, &item_end, &item_slot, &slot_first, &slot_nch}) b->release();
+        chunk = nitems = nslots = 0;
+    }
+};
+
 struct bc_graph {
     int32_t n = 0;
     int64_t narcs = 0;
@@ -74,9 +85,8 @@ struct bc_graph {
     std::vector<int32_t> rank;       // landmark-order position of every vertex (built on first use)
     DevBuf<int32_t> row_ptr, col, w;
 
-    // work items for the current chunk size
-    int32_t chunk = 0, nitems = 0, nslots = 0;
-    DevBuf<int32_t> item_v, item_beg, item_end, item_slot, slot_first, slot_nch;
+    // work items of the forward and backward sweeps (each for its chunk size)
+    ItemPlan fplan, bplan;
 
     // multi-source batch state for (W, Lcap)
     int32_t W = 0, Lcap = 0;
@@ -132,9 +142,9 @@ struct bc_graph {
 namespace {
 
 void free_graph(bc_graph *g) {
-    for (auto *b : {&g->row_ptr, &g->col, &g->w, &g->item_v, &g->item_beg, &g->item_end, &g->item_slot,
-                    &g->slot_first, &g->slot_nch, &g->sources, &g->src_index})
-        b->release();
+    for (auto *b : {&g->row_ptr, &g->col, &g->w, &g->sources, &g->src_index}) b->release();
+    g->fplan.release();
+    g->bplan.release();
     g->sigma.release();
     g->hpart.release();
     g->lvl.release();
@@ -209,8 +219,8 @@ int check_graph(int32_t n, const std::vector<int32_t> &rp, const std::vector<int
 // Work items: one per vertex, except vertices with more than `chunk` arcs,
 // which are split into chunks that combine through partial slots. Heavy
 // chunks come first, then vertices by descending degree.
-int build_items(bc_graph *g, int32_t chunk) {
-    if (g->chunk == chunk && g->item_v.p) return BC_OK;
+int build_items(bc_graph *g, ItemPlan &pl, int32_t chunk) {
+    if (pl.chunk == chunk && pl.item_v.p) return BC_OK;
     const int32_t n = g->n;
     const auto &rp = g->h_row_ptr;
     std::vector<int32_t> iv, ib, ie, is, sf, sn;
@@ -240,20 +250,42 @@ int build_items(bc_graph *g, int32_t chunk) {
         ie.push_back(rp[v + 1]);
         is.push_back(-1);
     }
-    g->nitems = (int32_t)iv.size();
-    g->nslots = (int32_t)sf.size();
-    for (auto pr : {std::make_pair(&g->item_v, &iv), std::make_pair(&g->item_beg, &ib),
-                    std::make_pair(&g->item_end, &ie), std::make_pair(&g->item_slot, &is),
-                    std::make_pair(&g->slot_first, &sf), std::make_pair(&g->slot_nch, &sn)}) {
+    pl.nitems = (int32_t)iv.size();
+    pl.nslots = (int32_t)sf.size();
+    for (auto pr : {std::make_pair(&pl.item_v, &iv), std::make_pair(&pl.item_beg, &ib),
+                    std::make_pair(&pl.item_end, &ie), std::make_pair(&pl.item_slot, &is),
+                    std::make_pair(&pl.slot_first, &sf), std::make_pair(&pl.slot_nch, &sn)}) {
         CK(pr.first->ensure(pr.second->size()));
         if (!pr.second->empty())
             CK(cudaMemcpy(pr.first->p, pr.second->data(), pr.second->size() * sizeof(int32_t),
                           cudaMemcpyHostToDevice));
     }
-    g->chunk = chunk;
-    // partial slots depend on the plan: force the state to be re-sized
+    pl.chunk = chunk;
+    // partial slots depend on the plans: force the state to be re-sized
     g->W = 0;
     return BC_OK;
+}
+
+// The sweeps' plans: heavy vertices are split more finely in the backward
+// sweep, where they are active at its widest levels (measured on R-MAT:
+// 256 arcs per chunk is fastest forward, 128 backward). An explicit chunk
+// size applies to both.
+int build_plans(bc_graph *g, const bc_options *opt) {
+    const int32_t fc = (opt && opt->chunk > 0) ? opt->chunk : 256;
+    const int32_t bch = (opt && opt->chunk > 0) ? opt->chunk : 128;
+    int r = build_items(g, g->fplan, fc);
+    if (!r) r = build_items(g, g->bplan, bch);
+    return r;
+}
+
+void use_plan(bcgb::MsParams &p, const ItemPlan &pl) {
+    p.nitems = pl.nitems;
+    p.item_v = pl.item_v.p;
+    p.item_beg = pl.item_beg.p;
+    p.item_end = pl.item_end.p;
+    p.item_slot = pl.item_slot.p;
+    p.slot_first = pl.slot_first.p;
+    p.slot_nch = pl.slot_nch.p;
 }
 
 int ensure_state(bc_graph *g, int W, int Lcap) {
@@ -275,9 +307,10 @@ int ensure_state(bc_graph *g, int W, int Lcap) {
     CK(g->F.ensure((size_t)Lcap * n * W));
     CK(g->ufr.ensure((size_t)Lcap * nw32));
     CK(g->V.ensure(2 * n * W));
-    CK(g->part.ensure((size_t)std::max(g->nslots, 1) * B));
-    CK(g->pmask.ensure((size_t)std::max(g->nslots, 1) * W));
-    CK(g->cnt.ensure((size_t)std::max(g->nslots, 1)));
+    const size_t slots = (size_t)std::max({g->fplan.nslots, g->bplan.nslots, 1});
+    CK(g->part.ensure(slots * B));
+    CK(g->pmask.ensure(slots * W));
+    CK(g->cnt.ensure(slots));
     CK(cudaMemset(g->cnt.p, 0, g->cnt.n * sizeof(uint32_t)));
     g->W = W;
     g->Lcap = Lcap;
@@ -327,17 +360,11 @@ void hook_end(void *ctx, size_t idx) {
 bcgb::MsParams make_params(bc_graph *g) {
     bcgb::MsParams p{};
     p.n = g->n;
-    p.nitems = g->nitems;
     p.nw32 = (std::max(g->n, 1) + 31) / 32;
     p.Lcap = g->Lcap;
     p.row_ptr = g->row_ptr.p;
     p.col = g->col.p;
-    p.item_v = g->item_v.p;
-    p.item_beg = g->item_beg.p;
-    p.item_end = g->item_end.p;
-    p.item_slot = g->item_slot.p;
-    p.slot_first = g->slot_first.p;
-    p.slot_nch = g->slot_nch.p;
+    use_plan(p, g->fplan);
     p.sigma = g->sigma.p;
     p.S = g->Smask.p;
     p.wide = g->wideflags.p;
@@ -538,14 +565,13 @@ int ensure_dense(bc_graph *g, cudaStream_t st) {
 int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStream_t st, bool backward,
                 bool hash, uint64_t *rows_sig, int32_t *rows_dist) {
     const int64_t wait_ms = (opt && opt->wait_limit_ms > 0) ? opt->wait_limit_ms : 600000;
-    const int32_t chunk = (opt && opt->chunk > 0) ? opt->chunk : 256;
     const bool dense = opt && (opt->flags & BC_DENSE);
     if (dense) {
         W = 4;
         int rd = ensure_dense(g, st);
         if (rd) return rd;
     }
-    int r = build_items(g, chunk);
+    int r = build_plans(g, opt);
     if (r) return r;
     r = ensure_state(g, W, std::max(g->Lcap, 32));
     if (r) return r;
@@ -595,9 +621,11 @@ int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStr
             if (bcgb::dense_launch_backward(g->maps, dense_params(g, p), L, st))
                 return fail(BC_ERR_CUDA, std::string("dense backward launch: ") + cudaGetErrorString(cudaGetLastError()));
         } else if (backward) {
+            bcgb::MsParams pb = p;
+            use_plan(pb, g->bplan);
             for (int l = L; l >= 1; --l) {
                 Timer t(g, st, BC_KERNEL_BACKWARD);
-                bcgb::ms_launch_backward(W, p, l, st);
+                bcgb::ms_launch_backward(W, pb, l, st);
             }
         }
         if (hash) {

@@ -423,7 +423,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
             __threadfence();
 #pragma unroll
             for (int j = 0; j < W; ++j) S[j] = 0.0f;
-            for (int c = 0; c < nch; ++c) {
+#pragma unroll 4
+            for (int c = 0; c < nch; ++c) {  // chunk order; the unrolled loads are independent
                 const float *q = reinterpret_cast<const float *>(p.part) + (size_t)(first + c) * B + lane;
 #pragma unroll
                 for (int j = 0; j < W; ++j) S[j] += __ldcg(q + 32 * j);
