@@ -368,12 +368,97 @@ __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg
 // lane with d(s,v) = l (f), S[j] += Cs[w][s] over the neighbours w whose
 // level-(l+1) frontier meets f. Cs is the masked level-(l+1) c buffer, so
 // for s in f this is the sum of c_s(w) over the w with v in P_s(w).
+// Sources of a vertex at most which the backward takes the sparse-source
+// form (below).
+constexpr int kSparseSrc = 8;
+
+// Sparse-source form of the backward sums, for a vertex v at level l for at
+// most kSparseSrc sources (their positions in pos[], ascending): lane k adds
+// c_s(w_k) of its own arc's neighbour for each listed source s with w_k in
+// P_s's next level (one 4-byte load each), and each source's partial sums
+// are added across the warp once at the end. For such vertices this reads a
+// few values per arc instead of whole row words.
+template <int W, bool NC>
+__device__ __forceinline__ void bwd_sum_sparse(const int32_t *__restrict__ col, int beg, int end,
+                                               const uint32_t *__restrict__ ufs, const uint32_t *__restrict__ Fs,
+                                               const float *__restrict__ Cs, const uint32_t (&f)[W], int32_t *s_u,
+                                               uint32_t *s_nz, int lane, float (&S)[W], const uint32_t *pos,
+                                               int nsrc) {
+    constexpr int B = 32 * W;
+    float P[kSparseSrc];
+#pragma unroll
+    for (int i = 0; i < kSparseSrc; ++i) P[i] = 0.0f;
+    for (int e0 = beg; e0 < end; e0 += 32) {
+        uint32_t m[W];
+        int u;
+        uint32_t nz;
+        const unsigned bal = probe_chunk<W, NC>(col, e0 + lane, end, ufs, Fs, f, m, s_u, s_nz, lane, u, nz);
+        if (bal) {
+            // bit i of cm: the arc contributes to listed source i (f's set
+            // bits in order, word by word)
+            uint32_t cm = 0;
+            int i = 0;
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                uint32_t x = f[j];
+                const uint32_t mw = m[j];
+                while (x) {
+                    const int b = __ffs(x) - 1;
+                    x &= x - 1;
+                    cm |= ((mw >> b) & 1u) << i;
+                    ++i;
+                }
+            }
+            const float *row = Cs + (size_t)u * B;
+#pragma unroll
+            for (int k = 0; k < kSparseSrc; ++k)
+                if ((cm >> k) & 1u) P[k] += ldx<NC>(row + pos[k]);
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int i = 0; i < kSparseSrc; ++i) {
+        if (i < nsrc) {
+            float t = P[i];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(kFull, t, off);
+            const uint32_t p = pos[i];
+#pragma unroll
+            for (int j = 0; j < W; ++j)
+                if (p == 32u * j + (uint32_t)lane) S[j] += t;
+        }
+    }
+}
+
 template <int W, bool NC = true, bool STAGED = false>
 __device__ __forceinline__ void bwd_sum(const int32_t *__restrict__ col, int beg, int end,
                                         const uint32_t *__restrict__ ufs, const uint32_t *__restrict__ Fs,
                                         const float *__restrict__ Cs, const uint32_t (&f)[W], int32_t *s_u,
                                         uint32_t *s_nz, int lane, float (&S)[W], WarpStage *ws = nullptr) {
     constexpr int B = 32 * W;
+    if constexpr (STAGED) {
+        int nsrc = 0;
+#pragma unroll
+        for (int j = 0; j < W; ++j) nsrc += __popc(f[j]);
+        if (nsrc <= kSparseSrc) {
+            // list the sources in the stage's slot-mask array (free in this form)
+            if (lane == 0) {
+                int k = 0;
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    uint32_t x = f[j];
+                    while (x) {
+                        ws->qz[k++] = 32u * j + (uint32_t)(__ffs(x) - 1);
+                        x &= x - 1;
+                    }
+                }
+            }
+            __syncwarp();
+            bwd_sum_sparse<W, NC>(col, beg, end, ufs, Fs, Cs, f, s_u, s_nz, lane, S, ws->qz, nsrc);
+            __syncwarp();
+            return;
+        }
+    }
     float Sp[W];  // staged sums, packed view (lane owns sources W*lane + t)
 #pragma unroll
     for (int t = 0; t < W; ++t) Sp[t] = 0.0f;

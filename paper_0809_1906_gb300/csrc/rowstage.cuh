@@ -48,14 +48,18 @@ __device__ __forceinline__ void expect_tx(uint64_t *bar, uint32_t bytes) {
                  : "memory");
 }
 
+// Test the phase; while it is incomplete the thread may be suspended for up
+// to kSuspendNs (it resumes as soon as the phase completes), so a waiting
+// warp does not take issue slots from the others.
+constexpr uint32_t kSuspendNs = 20000;
 __device__ __forceinline__ bool try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0u;
 }
