@@ -81,7 +81,6 @@ struct bc_graph {
     int64_t narcs = 0;
     bool weighted = false;
     std::vector<int32_t> h_row_ptr;  // host copy (work-item plan)
-    std::vector<int32_t> h_col;      // host copy (landmark order; unweighted graphs)
     std::vector<int32_t> rank;       // landmark-order position of every vertex (built on first use)
     DevBuf<int32_t> row_ptr, col, w;
 
@@ -396,38 +395,13 @@ int resolve_batch(const bc_options *opt, int *W) {
 // every vertex: their masked rows are then either useful for most of the
 // word or not needed at all. Vertices are ordered lexicographically by their
 // BFS distances to K landmarks (the K highest-degree vertices, ties by id),
-// then by id; rank[v] is v's position. K plain BFS runs over the host CSR,
-// once per graph.
-void build_rank(bc_graph *g) {
-    constexpr int kLandmarks = 16;
+// then by id; rank[v] is v's position. The distances come from one batched
+// forward pass on the device (ensure_rank); here, stable counting sorts,
+// last key first.
+void rank_from_dist(bc_graph *g, std::vector<int32_t> &dist, int k) {
     const int32_t n = g->n;
-    const auto &rp = g->h_row_ptr;
-    const auto &cl = g->h_col;
-    const int k = std::min<int32_t>(kLandmarks, n);
-    std::vector<int32_t> vs(n);
-    std::iota(vs.begin(), vs.end(), 0);
-    auto deg = [&](int32_t v) { return rp[v + 1] - rp[v]; };
-    std::partial_sort(vs.begin(), vs.begin() + k, vs.end(),
-                      [&](int32_t a, int32_t b) { return deg(a) > deg(b) || (deg(a) == deg(b) && a < b); });
-    std::vector<int32_t> dist((size_t)k * n), queue(n);
-    for (int i = 0; i < k; ++i) {
-        int32_t *d = dist.data() + (size_t)i * n;
-        std::fill(d, d + n, -1);
-        int32_t head = 0, tail = 0;
-        d[vs[i]] = 0;
-        queue[tail++] = vs[i];
-        while (head < tail) {
-            const int32_t u = queue[head++];
-            for (int32_t e = rp[u]; e < rp[u + 1]; ++e)
-                if (d[cl[e]] < 0) {
-                    d[cl[e]] = d[u] + 1;
-                    queue[tail++] = cl[e];
-                }
-        }
-        for (int32_t v = 0; v < n; ++v)  // unreachable after every reachable distance
-            if (d[v] < 0) d[v] = n;
-    }
-    // lexicographic sort: stable counting sorts, last key first
+    for (auto &d : dist)  // unreachable after every reachable distance
+        if (d < 0) d = n;
     std::vector<int32_t> ord(n), tmp(n), cnt((size_t)n + 2);
     std::iota(ord.begin(), ord.end(), 0);
     for (int i = k - 1; i >= 0; --i) {
@@ -457,8 +431,7 @@ int stage_sources(bc_graph *g, const int32_t *sources, int32_t num, int32_t *cou
             if (s < 0 || s >= g->n) return fail(BC_ERR_ARG, "source id out of range");
     }
     g->reordered = false;
-    if (order && hs.size() > 32 && !g->h_col.empty()) {
-        if (g->rank.empty()) build_rank(g);
+    if (order && hs.size() > 32 && (int32_t)g->rank.size() == g->n) {
         const int32_t n = g->n;
         std::vector<int32_t> cnt((size_t)n + 1, 0), idx(hs.size()), hs2(hs.size());
         for (int32_t s : hs) ++cnt[g->rank[s] + 1];
@@ -643,6 +616,36 @@ int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStr
     return BC_OK;
 }
 
+// Distances from the landmarks (one W = 1 batch of the forward sweep, rows
+// copied back), then the counting sorts; once per graph.
+int ensure_rank(bc_graph *g, cudaStream_t st) {
+    constexpr int kLandmarks = 16;
+    if ((int32_t)g->rank.size() == g->n || g->n <= 32) return BC_OK;
+    const int32_t n = g->n;
+    const auto &rp = g->h_row_ptr;
+    const int k = std::min<int32_t>(kLandmarks, n);
+    std::vector<int32_t> vs(n);
+    std::iota(vs.begin(), vs.end(), 0);
+    auto deg = [&](int32_t v) { return rp[v + 1] - rp[v]; };
+    std::partial_sort(vs.begin(), vs.begin() + k, vs.end(),
+                      [&](int32_t a, int32_t b) { return deg(a) > deg(b) || (deg(a) == deg(b) && a < b); });
+    int32_t cnt = 0;
+    int r = stage_sources(g, vs.data(), k, &cnt, false);
+    if (r) return r;
+    DevBuf<int32_t> dd;
+    CK(dd.ensure((size_t)k * n));
+    bc_options o{};
+    o.batch = 32;
+    r = run_batches(g, k, 1, &o, st, false, false, nullptr, dd.p);
+    if (r) return r;
+    std::vector<int32_t> dist((size_t)k * n);
+    CK(cudaMemcpyAsync(dist.data(), dd.p, dist.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    dd.release();
+    rank_from_dist(g, dist, k);
+    return BC_OK;
+}
+
 int sm_count_host() {
     static int c = 0;
     if (c == 0) {
@@ -750,7 +753,6 @@ int bc_create_graph(int32_t n, const int32_t *row_ptr, const int32_t *col, const
     g->narcs = m2;
     g->weighted = weights != nullptr;
     g->h_row_ptr = rp;
-    if (!weights) g->h_col = cl;
     for (int32_t x : ww) g->maxw = std::max(g->maxw, x);
     auto up = [&](DevBuf<int32_t> &d, const std::vector<int32_t> &h) -> int {
         CK(d.ensure(h.size()));
@@ -793,8 +795,13 @@ int bc_run(bc_graph *g, const int32_t *sources, int32_t num_sources, const bc_op
     if (r) return r;
     if (g->weighted && (flags & BC_PLAIN)) return fail(BC_ERR_UNSUPPORTED, "the one-source path is unweighted only");
     int32_t nsrc = 0;
-    r = stage_sources(g, sources, num_sources, &nsrc,
-                      !g->weighted && !(flags & (BC_PLAIN | BC_KEEP_ORDER | BC_DENSE)));
+    const bool order = !g->weighted && !(flags & (BC_PLAIN | BC_KEEP_ORDER | BC_DENSE)) &&
+                       (sources ? num_sources : g->n) > 32;
+    if (order) {
+        r = ensure_rank(g, st);
+        if (r) return r;
+    }
+    r = stage_sources(g, sources, num_sources, &nsrc, order);
     if (r) return r;
     g->timing = (flags & BC_TIMING) != 0;
     g->evused = 0;
