@@ -110,19 +110,58 @@ def csrc_digest() -> str:
     return h.hexdigest()
 
 
-def measured_traffic(kernel: str):
-    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
-    summary profiles/traffic_rmat.json, or None when it was taken on other
-    kernel sources."""
-    path = os.path.join(ROOT, "profiles", "traffic_rmat.json")
+# Kernel kinds of bc_kernel_time and the kernels each one times.
+KIND_KERNELS = {"init": ("k_init",), "forward": ("k_first", "k_forward"), "backward": ("k_backward",),
+                "hash": ("k_hash", "k_hash_sum")}
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic_rmat.json")
+
+
+def measured_traffic(kind: str, launches: int):
+    """DRAM bytes (read + write) per launch of kernel kind `kind`: the bytes of
+    one full pass from the committed ncu capture profiles/traffic_rmat.json,
+    divided by this run's launch count of that kind; None when the capture
+    was taken on other kernel sources."""
     try:
-        with open(path) as f:
+        with open(TRAFFIC_JSON) as f:
             tr = json.load(f)
         if tr.get("csrc_sha256") != csrc_digest():
             return None
-        return tr["kernels"][kernel]["dram_bytes_per_launch"]
+        return tr["kinds"][kind]["dram_bytes_per_pass"] / max(launches, 1)
     except Exception:
         return None
+
+
+def write_traffic(csv_path: str, command: str):
+    """Turn an ncu capture of one full pass (metrics dram__bytes_read.sum,
+    dram__bytes_write.sum, gpu__time_duration.sum; --csv) into
+    profiles/traffic_rmat.json."""
+    import collections
+    import csv
+    with open(csv_path) as f:
+        rows = list(csv.reader(line for line in f if line.startswith('"')))
+    h = rows[0]
+    per = collections.defaultdict(dict)
+    for r in rows[1:]:
+        i = int(r[h.index("ID")])
+        per[i]["kernel"] = r[h.index("Kernel Name")].split("(")[0].split("::")[-1].split("<")[0]
+        per[i][r[h.index("Metric Name")]] = float(r[h.index("Metric Value")])
+    kinds = {}
+    for kind, names in KIND_KERNELS.items():
+        sel = [x for x in per.values() if x["kernel"] in names]
+        if not sel:
+            continue
+        rd = sum(x.get("dram__bytes_read.sum", 0.0) for x in sel)
+        wr = sum(x.get("dram__bytes_write.sum", 0.0) for x in sel)
+        kinds[kind] = {"launches": len(sel), "dram_bytes_per_pass": rd + wr, "dram_read_bytes": rd,
+                       "dram_write_bytes": wr,
+                       "ncu_time_ms": sum(x.get("gpu__time_duration.sum", 0.0) for x in sel) / 1e6}
+    out = {"csrc_sha256": csrc_digest(), "command": command,
+           "note": "one bc_run over every source of the R-MAT workload (batch 256); ncu replays each launch "
+                   "with cold caches, so bytes are an upper bound of a warm run",
+           "kinds": kinds}
+    with open(TRAFFIC_JSON, "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out, indent=1))
 
 
 def workload():
@@ -379,7 +418,12 @@ def main():
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--workload", default="rmat", choices=["rmat", "er1024", "grid", "gnp", "many"],
                     help="rmat (default, the reported line) or one of the other configurations")
+    ap.add_argument("--write-traffic", metavar="CSV", default=None,
+                    help="write profiles/traffic_rmat.json from an ncu CSV capture of --profile, then exit")
+    ap.add_argument("--traffic-command", default="", help="the ncu command line recorded with --write-traffic")
     args = ap.parse_args()
+    if args.write_traffic:
+        return write_traffic(args.write_traffic, args.traffic_command)
     args.warmup = max(args.warmup, 3)
     if args.profile:
         return run_profile(args)
@@ -461,7 +505,7 @@ def main():
     dom, dom_bytes, dom_ms, dom_cnt = ("backward", bwd_b, b_ms, ktime["backward"][0]) if b_ms >= f_ms else \
         ("forward", fwd_b, f_ms, ktime["forward"][0])
     achieved = dom_bytes / (dom_ms / 1000.0) / 1e9
-    traffic = measured_traffic(dom)
+    traffic = measured_traffic(dom, dom_cnt)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     rp_h = torch.from_numpy(g.row_ptr).pin_memory()
