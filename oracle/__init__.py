@@ -56,9 +56,9 @@ def _load():
             P = ctypes.c_void_p
             i32 = ctypes.c_int32
             lib.oracle_source.restype = i32
-            lib.oracle_source.argtypes = [i32, P, P, P, i32, P, P, P, P, P, P, P]
+            lib.oracle_source.argtypes = [i32, P, P, P, P, P, P, i32, P, P, P, P, P, P, P]
             lib.oracle_bc.restype = i32
-            lib.oracle_bc.argtypes = [i32, P, P, P, P, i32, i32, P, P, P, P, P, P, P]
+            lib.oracle_bc.argtypes = [i32, P, P, P, P, P, P, P, i32, i32, P, P, P, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -72,6 +72,15 @@ def _csr(g):
     col = np.ascontiguousarray(g.col, dtype=np.int32)
     w = None if g.w is None else np.ascontiguousarray(g.w, dtype=np.int32)
     return rp, col, w
+
+
+def _in_csr(g):
+    """In-arc CSR of a directed graph (its transpose), or Nones: an undirected
+    graph's out-arcs serve as in-arcs."""
+    if not getattr(g, "directed", False):
+        return None, None, None
+    from paper_0809_1906_gb300.graphs import transpose
+    return _csr(transpose(g))
 
 
 def source(g, s: int, with_delta: bool = True) -> dict:
@@ -92,7 +101,9 @@ def source(g, s: int, with_delta: bool = True) -> dict:
     order = np.empty(max(n, 1), np.int32)
     flags = ctypes.c_int32(0)
     arcs = ctypes.c_int64(0)
-    cnt = lib.oracle_source(n, _ptr(rp), _ptr(col), _ptr(w), int(s), _ptr(dist), _ptr(lo), _ptr(hi),
+    irp, icol, iw = _in_csr(g)
+    cnt = lib.oracle_source(n, _ptr(rp), _ptr(col), _ptr(w), _ptr(irp), _ptr(icol), _ptr(iw), int(s),
+                            _ptr(dist), _ptr(lo), _ptr(hi),
                             _ptr(delta), _ptr(order), ctypes.byref(flags), ctypes.byref(arcs))
     if cnt < 0:
         raise ValueError(f"oracle_source rejected input (flags={flags.value})")
@@ -118,7 +129,9 @@ def bc(g, sources=None, threads: int = 0) -> dict:
     rc = np.zeros(ns, np.int64)
     ar = np.zeros(ns, np.int64)
     flags = ctypes.c_int32(0)
-    r = lib.oracle_bc(n, _ptr(rp), _ptr(col), _ptr(w), _ptr(src), ns, int(threads), _ptr(out),
+    irp, icol, iw = _in_csr(g)
+    r = lib.oracle_bc(n, _ptr(rp), _ptr(col), _ptr(w), _ptr(irp), _ptr(icol), _ptr(iw), _ptr(src), ns,
+                      int(threads), _ptr(out),
                       _ptr(hs), _ptr(hd), _ptr(ds), _ptr(rc), _ptr(ar), ctypes.byref(flags))
     if r != 0:
         raise ValueError(f"oracle_bc rejected input (flags={flags.value})")

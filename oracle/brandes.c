@@ -18,6 +18,11 @@
  * unweighted, Dijkstra with a binary heap when weighted), then the dependencies
  * in reverse settle order, summed into a running score.
  *
+ * Directed graphs: the CSR lists out-arcs; P_s(v) takes v's in-arcs, which
+ * the caller passes as a second CSR (the transpose, with its weights). When
+ * no transpose is given the graph is taken as undirected (symmetric CSR) and
+ * the out-arcs serve as in-arcs too.
+ *
  * Precision: distances int64; path counts unsigned 128-bit with a flag when a
  * count exceeds 2^64 (the GPU's uint64 wraps there) and another when it would
  * exceed 2^128 (never on the test graphs); dependencies FP64, the ratio
@@ -118,6 +123,7 @@ static inline int64_t arc_w(const int32_t *w, int64_t e) { return w ? (int64_t)w
  * *arcs the number of predecessor relations.
  */
 static int32_t forward(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                       const int32_t *irp, const int32_t *icol, const int32_t *iw,
                        int32_t s, work_t *ws, int32_t *flags, int64_t *arcs) {
     for (int32_t v = 0; v < n; v++) { ws->dist[v] = -1; ws->sigma[v] = 0; }
     int32_t cnt = 0;
@@ -155,15 +161,15 @@ static int32_t forward(int32_t n, const int32_t *rp, const int32_t *col, const i
         }
         free(done);
     }
-    /* path counts over P_s(v) */
+    /* path counts over P_s(v): v's in-arcs (u, v) */
     ws->sigma[s] = 1;
     int64_t a = 0;
     for (int32_t i = 1; i < cnt; i++) {
         int32_t v = ws->order[i];
         u128 acc = 0;
-        for (int64_t e = rp[v]; e < rp[v + 1]; e++) {
-            int32_t u = col[e];
-            if (ws->dist[u] >= 0 && ws->dist[u] + arc_w(w, e) == ws->dist[v]) {
+        for (int64_t e = irp[v]; e < irp[v + 1]; e++) {
+            int32_t u = icol[e];
+            if (ws->dist[u] >= 0 && ws->dist[u] + arc_w(iw, e) == ws->dist[v]) {
                 u128 nxt = acc + ws->sigma[u];
                 if (nxt < acc) *flags |= ORC_OVERFLOW128;
                 acc = nxt;
@@ -179,18 +185,19 @@ static int32_t forward(int32_t n, const int32_t *rp, const int32_t *col, const i
 
 /*
  * Backward pass (Theorem 1.1): vertices w in reverse settle order push
- * lambda_sv/lambda_sw * (1 + delta_s*(w)) to each predecessor v in P_s(w).
+ * lambda_sv/lambda_sw * (1 + delta_s*(w)) to each predecessor v in P_s(w)
+ * (over w's in-arcs (v, w)).
  */
-static void backward(const int32_t *rp, const int32_t *col, const int32_t *w,
+static void backward(const int32_t *irp, const int32_t *icol, const int32_t *iw,
                      int32_t cnt, work_t *ws) {
     for (int32_t i = 0; i < cnt; i++) ws->delta[ws->order[i]] = 0.0;
     for (int32_t i = cnt - 1; i > 0; i--) {
         int32_t x = ws->order[i];
         double sx = (double)ws->sigma[x];
         double f = 1.0 + ws->delta[x];
-        for (int64_t e = rp[x]; e < rp[x + 1]; e++) {
-            int32_t v = col[e];
-            if (ws->dist[v] >= 0 && ws->dist[v] + arc_w(w, e) == ws->dist[x])
+        for (int64_t e = irp[x]; e < irp[x + 1]; e++) {
+            int32_t v = icol[e];
+            if (ws->dist[v] >= 0 && ws->dist[v] + arc_w(iw, e) == ws->dist[x])
                 ws->delta[v] += ((double)ws->sigma[v] / sx) * f;
         }
     }
@@ -210,22 +217,26 @@ static int check_csr(int32_t n, const int32_t *rp, const int32_t *col, const int
 }
 
 /*
- * One source, full rows. dist: int64[n] (-1 unreachable); sigma_lo/hi: the
+ * One source, full rows. irp/icol/iw: the in-arc CSR of a directed graph
+ * (NULL: undirected, the out-arcs serve). dist: int64[n] (-1 unreachable); sigma_lo/hi: the
  * 128-bit count split in two uint64 (may be NULL); delta: double[n] (may be
  * NULL; delta[s] = reach-1 by the recurrence, which BC excludes); order:
  * int32[n] settle order (may be NULL). Returns the reachable count, or -1 on
  * bad input / allocation failure.
  */
-int oracle_source(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w, int32_t s,
+int oracle_source(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                  const int32_t *irp, const int32_t *icol, const int32_t *iw, int32_t s,
                   int64_t *dist, uint64_t *sigma_lo, uint64_t *sigma_hi, double *delta,
                   int32_t *order, int32_t *flags, int64_t *arcs) {
     *flags = 0;
-    if (!check_csr(n, rp, col, w) || s < 0 || s >= n) { *flags = ORC_BAD_INPUT; return -1; }
+    if (!irp) { irp = rp; icol = col; iw = w; }
+    if (!check_csr(n, rp, col, w) || !check_csr(n, irp, icol, iw) || (w == NULL) != (iw == NULL) ||
+        s < 0 || s >= n) { *flags = ORC_BAD_INPUT; return -1; }
     work_t ws;
     if (!work_init(&ws, n, (int64_t)rp[n])) { work_free(&ws); *flags = ORC_OOM; return -1; }
     int64_t a = 0;
-    int32_t cnt = forward(n, rp, col, w, s, &ws, flags, &a);
-    if (delta) backward(rp, col, w, cnt, &ws);
+    int32_t cnt = forward(n, rp, col, w, irp, icol, iw, s, &ws, flags, &a);
+    if (delta) backward(irp, icol, iw, cnt, &ws);
     for (int32_t v = 0; v < n; v++) {
         if (dist) dist[v] = ws.dist[v];
         if (sigma_lo) sigma_lo[v] = (uint64_t)ws.sigma[v];
@@ -239,7 +250,8 @@ int oracle_source(int32_t n, const int32_t *rp, const int32_t *col, const int32_
 }
 
 /*
- * Betweenness over a source list (sources == NULL: all n vertices).
+ * Betweenness over a source list (sources == NULL: all n vertices);
+ * irp/icol/iw as for oracle_source.
  * bc: double[n], the ordered-pair sum over the listed sources. Per-source
  * outputs (each may be NULL, else length nsrc): hash_sigma, hash_dist,
  * dist_sum, reach, arcs. Sources are split statically over nthreads OpenMP
@@ -249,11 +261,16 @@ int oracle_source(int32_t n, const int32_t *rp, const int32_t *col, const int32_
  * input or allocation failure.
  */
 int oracle_bc(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+              const int32_t *irp, const int32_t *icol, const int32_t *iw,
               const int32_t *sources, int32_t nsrc, int32_t nthreads, double *bc,
               uint64_t *hash_sigma, uint64_t *hash_dist, int64_t *dist_sum, int64_t *reach,
               int64_t *arcs, int32_t *flags) {
     *flags = 0;
-    if (!check_csr(n, rp, col, w)) { *flags = ORC_BAD_INPUT; return -1; }
+    if (!irp) { irp = rp; icol = col; iw = w; }
+    if (!check_csr(n, rp, col, w) || !check_csr(n, irp, icol, iw) || (w == NULL) != (iw == NULL)) {
+        *flags = ORC_BAD_INPUT;
+        return -1;
+    }
     int32_t ns = sources ? nsrc : n;
     if (ns < 0) { *flags = ORC_BAD_INPUT; return -1; }
     if (sources)
@@ -285,8 +302,8 @@ int oracle_bc(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w
             int32_t s = sources ? sources[i] : (int32_t)i;
             int32_t f = 0;
             int64_t a = 0;
-            int32_t cnt = forward(n, rp, col, w, s, &ws, &f, &a);
-            backward(rp, col, w, cnt, &ws);
+            int32_t cnt = forward(n, rp, col, w, irp, icol, iw, s, &ws, &f, &a);
+            backward(irp, icol, iw, cnt, &ws);
             gflags |= f;
             uint64_t hs = 0, hd = 0;
             int64_t ds = 0;

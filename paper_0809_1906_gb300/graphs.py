@@ -67,17 +67,20 @@ class Stream:
 
 @dataclasses.dataclass
 class Graph:
-    """Undirected graph in CSR form (both arcs of each edge stored)."""
+    """Graph in CSR form. Undirected (the default): both arcs of each edge
+    stored. Directed: each arc once, in the row of its tail."""
 
     n: int
     row_ptr: np.ndarray  # int32 [n+1]
-    col: np.ndarray  # int32 [2m], neighbours of each row sorted ascending
-    w: np.ndarray | None  # int32 [2m] arc weights (None = unweighted)
+    col: np.ndarray  # int32 [arcs], heads of each row sorted ascending
+    w: np.ndarray | None  # int32 [arcs] arc weights (None = unweighted)
     name: str = ""
+    directed: bool = False
 
     @property
     def m(self) -> int:
-        return int(self.col.shape[0]) // 2
+        """Undirected edges, or arcs of a directed graph."""
+        return int(self.col.shape[0]) if self.directed else int(self.col.shape[0]) // 2
 
     @property
     def weighted(self) -> bool:
@@ -130,6 +133,86 @@ def csr_from_edges(n: int, u, v, w=None, name: str = "") -> Graph:
             raise ValueError("weights must be positive int32")
         ww = np.concatenate([w, w])[order].astype(np.int32)
     return Graph(n, row_ptr.astype(np.int32), dst.astype(np.int32), ww, name)
+
+
+def csr_from_arcs(n: int, u, v, w=None, name: str = "") -> Graph:
+    """Build a directed CSR from an arc list (u -> v).
+
+    Raises ValueError on out-of-range ids, self-loops, duplicate arcs or
+    non-positive weights.
+    """
+    u = np.asarray(u, dtype=np.int64)
+    v = np.asarray(v, dtype=np.int64)
+    if u.shape != v.shape:
+        raise ValueError("u and v differ in length")
+    if n < 0 or n >= (1 << 31):
+        raise ValueError("n out of range")
+    if u.size and (u.min() < 0 or v.min() < 0 or u.max() >= n or v.max() >= n):
+        raise ValueError("vertex id out of range")
+    if np.any(u == v):
+        raise ValueError("self-loop")
+    key = u * n + v
+    if np.unique(key).size != key.size:
+        raise ValueError("duplicate arc")
+    if u.size >= (1 << 31):
+        raise ValueError("too many arcs for int32 CSR")
+    order = np.lexsort((v, u))
+    src, dst = u[order], v[order]
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(src, minlength=n), out=row_ptr[1:])
+    ww = None
+    if w is not None:
+        w = np.asarray(w, dtype=np.int64)
+        if w.shape != u.shape:
+            raise ValueError("weights differ in length")
+        if w.size and (w.min() <= 0 or w.max() >= (1 << 31)):
+            raise ValueError("weights must be positive int32")
+        ww = w[order].astype(np.int32)
+    return Graph(n, row_ptr.astype(np.int32), dst.astype(np.int32), ww, name, directed=True)
+
+
+def transpose(g: Graph) -> Graph:
+    """The in-arc CSR of a directed graph: row v lists the tails u of the arcs
+    (u, v), with their weights."""
+    src = np.repeat(np.arange(g.n, dtype=np.int64), g.degrees())
+    t = csr_from_arcs(g.n, g.col.astype(np.int64), src, None if g.w is None else g.w, g.name + "^T")
+    return t
+
+
+def directed_path(n: int) -> Graph:
+    """0 -> 1 -> ... -> n-1."""
+    return csr_from_arcs(n, np.arange(n - 1), np.arange(1, n), name=f"dpath{n}")
+
+
+def directed_cycle(n: int) -> Graph:
+    """0 -> 1 -> ... -> n-1 -> 0."""
+    a = np.arange(n)
+    return csr_from_arcs(n, a, (a + 1) % n, name=f"dcycle{n}")
+
+
+def directed_random(n: int, p: float, seed: int, wmax: int = 0) -> Graph:
+    """Each ordered pair (u, v), u != v, an arc with probability p (seeded);
+    weights U{1..wmax} when wmax > 0."""
+    st = Stream(seed)
+    r = st.uniform(n * n).reshape(n, n)
+    np.fill_diagonal(r, 1.0)
+    u, v = np.nonzero(r < p)
+    w = None if wmax <= 0 else 1 + st.below(u.size, wmax)
+    return csr_from_arcs(n, u, v, w, name=f"dG({n},{p})")
+
+
+def kkp_tripartite(n: int) -> Graph:
+    """Section 2's directed tripartite graph on u_i, v_j, w_k (0 <= i,j,k < n):
+    arcs u_i -> v_j and v_j -> w_k, weighted so that every shortest u_i - w_k
+    path goes through v_0 alone: weight 1 on arcs into and out of v_0, 2 on
+    the others (paths through v_0 have length 2, all others 4). Vertex ids:
+    u_i = i, v_j = n + j, w_k = 2n + k."""
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    i, j = i.ravel(), j.ravel()
+    uv_u, uv_v, uv_w = i, n + j, np.where(j == 0, 1, 2)
+    vw_u, vw_v, vw_w = n + i, 2 * n + j, np.where(i == 0, 1, 2)
+    return csr_from_arcs(3 * n, np.concatenate([uv_u, vw_u]), np.concatenate([uv_v, vw_v]),
+                         np.concatenate([uv_w, vw_w]), name=f"kkp{n}")
 
 
 def _dedupe_pairs(a: np.ndarray, b: np.ndarray, n: int):

@@ -232,6 +232,65 @@ def test_algorithm2_weighted_matches_oracle(oracle_lib):
         assert _close(algebraic.algorithm2(dist, lam), oracle_lib.bc(g)["bc"])
 
 
+# ------------------------------------------------ directed graphs (Section 2)
+
+@pytest.mark.parametrize("seed", range(8))
+def test_directed_random_against_enumeration(oracle_lib, seed):
+    """Directed graphs take P_s(v) over v's in-arcs (Section 1.1's definition
+    with (u, v) an arc): the oracle against enumeration of the shortest
+    directed paths, unweighted and with weights in {1, 2, 3}."""
+    g = G.directed_random(8, 0.3, 700 + seed, wmax=0 if seed % 2 == 0 else 3)
+    _check_against_brute(oracle_lib, g)
+
+
+def test_directed_raw_enumeration(oracle_lib):
+    g = G.directed_random(6, 0.4, 77, wmax=2)
+    _check_against_brute(oracle_lib, g, brute.all_simple_paths_min(g))
+
+
+@pytest.mark.parametrize("n", [2, 5, 12])
+def test_directed_path_and_cycle(oracle_lib, n):
+    """One-way path: vertex i is inside the unique path of the pairs
+    s < i < t, so BC(i) = i(n-1-i). One-way cycle: at forward distance k
+    (k = 2..n-1) each of the n pairs has k-1 inside vertices, so every vertex
+    gets (n-1)(n-2)/2."""
+    i = np.arange(n)
+    assert _close(oracle_lib.bc(G.directed_path(n))["bc"], i * (n - 1 - i))
+    assert _close(oracle_lib.bc(G.directed_cycle(n))["bc"], np.full(n, (n - 1) * (n - 2) / 2))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 6, 10])
+def test_kkp_tripartite(oracle_lib, n):
+    """Section 2's directed tripartite graph, weighted so that every shortest
+    u_i - w_k path goes through v_0: the betweenness of v_0 is n^2 and every
+    other vertex's is 0."""
+    g = G.kkp_tripartite(n)
+    want = np.zeros(3 * n)
+    want[n] = n * n
+    assert _close(oracle_lib.bc(g)["bc"], want)
+    if n <= 3:
+        _check_against_brute(oracle_lib, g)
+
+
+def test_directed_algorithm2_matches_oracle(oracle_lib):
+    for seed in range(3):
+        g = G.directed_random(9, 0.3, 800 + seed, wmax=3)
+        ref = brute.betweenness(g)
+        dist = np.array([[-1 if x is None else x for x in row] for row in ref["dist"]])
+        lam = np.array(ref["lam"], dtype=object)
+        assert _close(algebraic.algorithm2(dist, lam), oracle_lib.bc(g)["bc"])
+
+
+def test_undirected_given_as_directed(oracle_lib):
+    """An undirected graph given as a directed one with both arcs of every
+    edge has the same betweenness (its transpose is itself)."""
+    g = G.random_small(30, 0.15, 901, connect=True, wmax=4)
+    src = np.repeat(np.arange(g.n), g.degrees())
+    d = G.csr_from_arcs(g.n, src, g.col, g.w)
+    assert d.directed and np.array_equal(d.col, g.col)
+    assert _close(oracle_lib.bc(d)["bc"], oracle_lib.bc(g)["bc"])
+
+
 # ------------------------------------------------------------- invariants
 
 @pytest.mark.parametrize("seed", range(4))
