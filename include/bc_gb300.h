@@ -62,6 +62,13 @@ extern "C" {
 
 /* ---- bc_create_graph flags --------------------------------------------- */
 #define BC_GRAPH_TRUST_INPUT 0x1u /* skip the host-side symmetry/duplicate check */
+#define BC_GRAPH_DIRECTED 0x2u    /* row_ptr/col list out-arcs of a directed graph (Section 2's model):
+                                     P_s(v) takes v's in-arcs, built here as the transpose. No symmetry
+                                     check (self-loops, duplicates and weights are still checked).
+                                     bc_run supports it on the batched unweighted path, BC_PLAIN and
+                                     the weighted path; BC_DENSE and bc_many_create return
+                                     BC_ERR_UNSUPPORTED. BC is the ordered-pair sum (BC_HALVE is not
+                                     meaningful for directed graphs). */
 
 /* ---- bc_options.flags ---------------------------------------------------- */
 #define BC_HALVE 0x1u        /* divide BC by 2 (unordered pairs, Section 1.1) */

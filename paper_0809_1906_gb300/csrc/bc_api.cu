@@ -80,9 +80,12 @@ struct bc_graph {
     int32_t n = 0;
     int64_t narcs = 0;
     bool weighted = false;
-    std::vector<int32_t> h_row_ptr;  // host copy (work-item plan)
+    bool directed = false;
+    std::vector<int32_t> h_row_ptr;     // host copy (work-item plans)
+    std::vector<int32_t> h_row_ptr_in;  // directed: in-arc CSR rows (forward plan)
     std::vector<int32_t> rank;       // landmark-order position of every vertex (built on first use)
     DevBuf<int32_t> row_ptr, col, w;
+    DevBuf<int32_t> row_ptr_in, col_in, w_in;  // directed: the transpose
 
     // work items of the forward and backward sweeps (each for its chunk size)
     ItemPlan fplan, bplan;
@@ -141,7 +144,8 @@ struct bc_graph {
 namespace {
 
 void free_graph(bc_graph *g) {
-    for (auto *b : {&g->row_ptr, &g->col, &g->w, &g->sources, &g->src_index}) b->release();
+    for (auto *b : {&g->row_ptr, &g->col, &g->w, &g->row_ptr_in, &g->col_in, &g->w_in, &g->sources, &g->src_index})
+        b->release();
     g->fplan.release();
     g->bplan.release();
     g->sigma.release();
@@ -177,7 +181,7 @@ void free_graph(bc_graph *g) {
 // Host check of the paper's graph model: every arc has its reverse with the
 // same weight, no self-loops, no duplicate arcs, positive weights.
 int check_graph(int32_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &col,
-                const std::vector<int32_t> *w) {
+                const std::vector<int32_t> *w, bool directed) {
     if (rp[0] != 0) return fail(BC_ERR_ARG, "row_ptr[0] != 0");
     for (int32_t v = 0; v < n; ++v)
         if (rp[v + 1] < rp[v]) return fail(BC_ERR_ARG, "row_ptr not non-decreasing");
@@ -203,6 +207,7 @@ int check_graph(int32_t n, const std::vector<int32_t> &rp, const std::vector<int
                 return fail(BC_ERR_NOT_SYMMETRIC, "duplicate arc at vertex " + std::to_string(v));
         }
     }
+    if (directed) return BC_OK;
     for (int32_t v = 0; v < n; ++v) {
         for (int64_t e = rp[v]; e < rp[v + 1]; ++e) {
             const int32_t u = arcs[e].first;
@@ -218,10 +223,9 @@ int check_graph(int32_t n, const std::vector<int32_t> &rp, const std::vector<int
 // Work items: one per vertex, except vertices with more than `chunk` arcs,
 // which are split into chunks that combine through partial slots. Heavy
 // chunks come first, then vertices by descending degree.
-int build_items(bc_graph *g, ItemPlan &pl, int32_t chunk) {
+int build_items(bc_graph *g, ItemPlan &pl, int32_t chunk, const std::vector<int32_t> &rp) {
     if (pl.chunk == chunk && pl.item_v.p) return BC_OK;
     const int32_t n = g->n;
-    const auto &rp = g->h_row_ptr;
     std::vector<int32_t> iv, ib, ie, is, sf, sn;
     std::vector<int32_t> light;
     for (int32_t v = 0; v < n; ++v) {
@@ -272,8 +276,9 @@ int build_items(bc_graph *g, ItemPlan &pl, int32_t chunk) {
 int build_plans(bc_graph *g, const bc_options *opt) {
     const int32_t fc = (opt && opt->chunk > 0) ? opt->chunk : 256;
     const int32_t bch = (opt && opt->chunk > 0) ? opt->chunk : 128;
-    int r = build_items(g, g->fplan, fc);
-    if (!r) r = build_items(g, g->bplan, bch);
+    // the forward sweep pulls over in-arcs, the backward over out-arcs
+    int r = build_items(g, g->fplan, fc, g->directed ? g->h_row_ptr_in : g->h_row_ptr);
+    if (!r) r = build_items(g, g->bplan, bch, g->h_row_ptr);
     return r;
 }
 
@@ -363,6 +368,7 @@ bcgb::MsParams make_params(bc_graph *g) {
     p.Lcap = g->Lcap;
     p.row_ptr = g->row_ptr.p;
     p.col = g->col.p;
+    p.col_f = g->directed ? g->col_in.p : g->col.p;
     use_plan(p, g->fplan);
     p.sigma = g->sigma.p;
     p.S = g->Smask.p;
@@ -520,6 +526,7 @@ int dense_forward(bc_graph *g, bcgb::MsParams &p, cudaStream_t st, int *depth) {
 int ensure_dense(bc_graph *g, cudaStream_t st) {
     if (g->dA.p) return BC_OK;
     if (g->weighted) return fail(BC_ERR_UNSUPPORTED, "BC_DENSE needs an unweighted graph");
+    if (g->directed) return fail(BC_ERR_UNSUPPORTED, "BC_DENSE needs an undirected graph");
     if (g->n > bcgb::kDenseMaxN) return fail(BC_ERR_UNSUPPORTED, "BC_DENSE supports n <= 65536");
     const int32_t npad = std::max(64, (g->n + 63) / 64 * 64);
     CK(g->dA.ensure((size_t)npad * npad));
@@ -695,6 +702,11 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
         p.row_ptr = g->row_ptr.p;
         p.col = g->col.p;
         p.w = g->w.p;
+        if (g->directed) {
+            p.row_ptr_in = g->row_ptr_in.p;
+            p.col_in = g->col_in.p;
+            p.w_in = g->w_in.p;
+        }
         p.sources = g->sources.p + w0;
         p.dist = g->wdist.p;
         p.sigma = g->wsigma.p;
@@ -743,9 +755,26 @@ int bc_create_graph(int32_t n, const int32_t *row_ptr, const int32_t *col, const
     if (m2 > 0 && !col) return fail(BC_ERR_ARG, "col is NULL");
     CK(fetch(cl, col, (size_t)m2));
     if (weights) CK(fetch(ww, weights, (size_t)m2));
+    const bool directed = (flags & BC_GRAPH_DIRECTED) != 0;
     if (!(flags & BC_GRAPH_TRUST_INPUT)) {
-        int r = check_graph(n, rp, cl, weights ? &ww : nullptr);
+        int r = check_graph(n, rp, cl, weights ? &ww : nullptr, directed);
         if (r) return r;
+    }
+    // directed: the in-arc CSR (transpose), rows by head, tails in arc order
+    std::vector<int32_t> rpi, cli, wwi;
+    if (directed) {
+        rpi.assign((size_t)n + 1, 0);
+        for (int64_t e = 0; e < m2; ++e) ++rpi[(size_t)cl[e] + 1];
+        for (int32_t v = 0; v < n; ++v) rpi[v + 1] += rpi[v];
+        std::vector<int32_t> pos(rpi.begin(), rpi.end() - 1);
+        cli.resize(m2);
+        if (weights) wwi.resize(m2);
+        for (int32_t u = 0; u < n; ++u)
+            for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+                const int32_t at = pos[cl[e]]++;
+                cli[at] = u;
+                if (weights) wwi[at] = ww[e];
+            }
     }
     bc_graph *g = new (std::nothrow) bc_graph();
     if (!g) return fail(BC_ERR_OOM, "host allocation failed");
@@ -753,6 +782,8 @@ int bc_create_graph(int32_t n, const int32_t *row_ptr, const int32_t *col, const
     g->narcs = m2;
     g->weighted = weights != nullptr;
     g->h_row_ptr = rp;
+    g->directed = directed;
+    if (directed) g->h_row_ptr_in = rpi;
     for (int32_t x : ww) g->maxw = std::max(g->maxw, x);
     auto up = [&](DevBuf<int32_t> &d, const std::vector<int32_t> &h) -> int {
         CK(d.ensure(h.size()));
@@ -762,6 +793,9 @@ int bc_create_graph(int32_t n, const int32_t *row_ptr, const int32_t *col, const
     int r = up(g->row_ptr, rp);
     if (!r) r = up(g->col, cl);
     if (!r && weights) r = up(g->w, ww);
+    if (!r && directed) r = up(g->row_ptr_in, rpi);
+    if (!r && directed) r = up(g->col_in, cli);
+    if (!r && directed && weights) r = up(g->w_in, wwi);
     if (!r) {
         cudaError_t e = g->bc.ensure((size_t)std::max(n, 1));
         if (e == cudaSuccess) e = cudaMalloc((void **)&g->ctl, sizeof(bcgb::DevCtl));
@@ -1163,9 +1197,9 @@ int bc_many_create(bc_graph *const *graphs, int32_t k, const bc_options *opt, bc
     if (!m) return fail(BC_ERR_OOM, "host allocation failed");
     m->W = b / 32;
     for (int32_t i = 0; i < k; ++i) {
-        if (!graphs[i] || graphs[i]->weighted) {
+        if (!graphs[i] || graphs[i]->weighted || graphs[i]->directed) {
             free_many(m);
-            return fail(BC_ERR_UNSUPPORTED, "bc_many takes unweighted graph handles");
+            return fail(BC_ERR_UNSUPPORTED, "bc_many takes unweighted undirected graph handles");
         }
         m->graphs.push_back(graphs[i]);
     }

@@ -56,8 +56,9 @@ struct MsParams {
     int32_t nb;    // sources in this batch (<= B)
     int32_t first; // level 1 was produced by k_first (all its counts are 1)
     uint32_t seq;
-    const int32_t *row_ptr;
+    const int32_t *row_ptr;  // out-arcs: level 0->1 and the backward sweep
     const int32_t *col;
+    const int32_t *col_f;    // arcs the forward sweep pulls over: in-arcs (= col when undirected)
     const int32_t *item_v;
     const int32_t *item_beg;
     const int32_t *item_end;

@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
                 acc[j] = 0ull;
                 nf[j] = 0u;
             }
-            body::fwd_sum<W, true, true>(p.col, beg, end, ufl, Fl, Sl, p.sigma, wide, ones, U, s_u[wib], s_nz[wib], lane,
+            body::fwd_sum<W, true, true>(p.col_f, beg, end, ufl, Fl, Sl, p.sigma, wide, ones, U, s_u[wib], s_nz[wib], lane,
                                          acc, nf, ovf, arcs, &ws);
             if (slot < 0) {
                 produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next, p.lvl, l + 1);

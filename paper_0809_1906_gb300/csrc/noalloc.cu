@@ -121,6 +121,7 @@ extern "C" int bc_run_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *
     p.Lcap = kLcap;
     p.row_ptr = row_ptr;
     p.col = col;
+    p.col_f = col;  // undirected: the forward pulls over the same arcs
     int32_t *items = reinterpret_cast<int32_t *>(base + kOffItems);
     p.item_v = items;
     p.item_beg = items + kMaxN;

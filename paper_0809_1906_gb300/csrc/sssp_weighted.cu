@@ -134,7 +134,33 @@ __global__ void __launch_bounds__(kWBlock, 4) k_wsssp(const WParams p) {
         // (this step only produces distances above d), so u is in P_s(v)
         // exactly when that value equals d - w(u,v); and the call itself
         // relaxes the arc.
-        for (int t = tid; t < k; t += kWBlock) {
+        for (int t = tid; p.col_in && t < k; t += kWBlock) {
+            // directed graphs: P_s(v) over v's in-arcs, whose tails below d are
+            // final; the out-arcs are relaxed below
+            const int v = order[done + t];
+            uint64_t s = v == src ? 1ull : 0ull;
+            if (v != src) {
+                for (int e = p.row_ptr_in[v]; e < p.row_ptr_in[v + 1]; ++e) {
+                    const int u = p.col_in[e];
+                    const int du = __ldcg(dist + u);
+                    if (du < d && du + p.w_in[e] == d) {
+                        const uint64_t x = __ldcg(sigma + u);
+                        const uint64_t y = s + x;
+                        ovf64 |= y < x;
+                        s = y;
+                        ++arcs;
+                    }
+                }
+            }
+            sigma[v] = s;
+            for (int e = p.row_ptr[v]; e < p.row_ptr[v + 1]; ++e) {
+                const int u = p.col[e];
+                const int nd = d + p.w[e];
+                const int old = atomicMin(dist + u, nd);
+                if (nd < old) push_entry(p, sm, slots, u, nd);
+            }
+        }
+        for (int t = tid; t < k && !p.col_in; t += kWBlock) {
             const int v = order[done + t];
             const int e0 = p.row_ptr[v], e1 = p.row_ptr[v + 1];
             uint64_t s = v == src ? 1ull : 0ull;

@@ -18,6 +18,9 @@ struct WParams {
     int32_t dmax;  // bound on any distance (n * max weight), a loop guard
     const int32_t *row_ptr;
     const int32_t *col;
+    const int32_t *row_ptr_in;  // directed graphs: in-arc CSR for P_s(v) (null when undirected)
+    const int32_t *col_in;
+    const int32_t *w_in;
     const int32_t *w;
     const int32_t *sources;  // this wave's sources
     int32_t *dist;           // [wave][n]

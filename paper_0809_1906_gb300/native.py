@@ -31,6 +31,7 @@ BC_STATUS_DENSE_TIMEOUT = 0x8
 BC_STATUS_COPY_TIMEOUT = 0x10
 
 BC_GRAPH_TRUST_INPUT = 0x1
+BC_GRAPH_DIRECTED = 0x2
 
 BC_HALVE = 0x1
 BC_ACCUMULATE = 0x2
@@ -169,10 +170,10 @@ class Graph:
     (host or CUDA), int32, C-contiguous.
     """
 
-    def __init__(self, n: int, row_ptr, col, weights=None, trust_input: bool = False):
+    def __init__(self, n: int, row_ptr, col, weights=None, trust_input: bool = False, directed: bool = False):
         self.lib = load()
         h = ctypes.c_void_p()
-        flags = BC_GRAPH_TRUST_INPUT if trust_input else 0
+        flags = (BC_GRAPH_TRUST_INPUT if trust_input else 0) | (BC_GRAPH_DIRECTED if directed else 0)
         for a in (row_ptr, col, weights):
             if a is not None and getattr(a, "dtype", None) not in (np.int32, None) and str(a.dtype) != "torch.int32":
                 raise TypeError("CSR arrays must be int32")
@@ -183,6 +184,7 @@ class Graph:
 
     @classmethod
     def from_csr(cls, g, **kw):
+        kw.setdefault("directed", bool(getattr(g, "directed", False)))
         return cls(g.n, np.ascontiguousarray(g.row_ptr, np.int32), np.ascontiguousarray(g.col, np.int32),
                    None if g.w is None else np.ascontiguousarray(g.w, np.int32), **kw)
 
