@@ -80,6 +80,11 @@ extern "C" {
                                 forward (ComputePathCount) and backward (ComputeDependency), Section 3.1;
                                 unweighted graphs with n <= 65536, batch 128 */
 #define BC_SPARSE_BACKWARD 0x40u /* with BC_DENSE: run the backward pass on the sparse kernel instead */
+#define BC_PAIRS 0x100u      /* BC from all-pairs distances and path counts with Algorithm 2's pair formula
+                                (Section 4.2.1): BC(v) = sum over ordered (s,t), d(s,v)+d(v,t)=d(s,t),
+                                of lambda_sv lambda_vt / lambda_st. Needs sources = NULL, n <= 16384
+                                (12 n^2 bytes of rows plus 8 n^2 of scratch); unweighted or weighted,
+                                directed or not; not with BC_PLAIN / BC_DENSE. */
 #define BC_KEEP_ORDER 0x80u  /* batch the sources in the order given. By default (unweighted, batched,
                                 more than 32 sources) batches are formed from the sources sorted by
                                 their BFS distances to 16 landmark vertices, so the sources of one

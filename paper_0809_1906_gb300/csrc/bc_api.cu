@@ -18,6 +18,7 @@
 #include "weighted.cuh"
 #include "many.cuh"
 #include "dense.cuh"
+#include "pairs.cuh"
 
 namespace {
 
@@ -53,6 +54,15 @@ struct DevBuf {
         if (e == cudaSuccess) n = c;
         return e;
     }
+};
+
+// A DevBuf owned by one scope (cudaFree waits for the device's work first).
+template <class T>
+struct ScopedBuf : DevBuf<T> {
+    ScopedBuf() = default;
+    ScopedBuf(const ScopedBuf &) = delete;
+    ScopedBuf &operator=(const ScopedBuf &) = delete;
+    ~ScopedBuf() { this->release(); }
 };
 
 // Copy `count` elements from a host-or-device pointer into a host vector.
@@ -639,7 +649,7 @@ int ensure_rank(bc_graph *g, cudaStream_t st) {
     int32_t cnt = 0;
     int r = stage_sources(g, vs.data(), k, &cnt, false);
     if (r) return r;
-    DevBuf<int32_t> dd;
+    ScopedBuf<int32_t> dd;
     CK(dd.ensure((size_t)k * n));
     bc_options o{};
     o.batch = 32;
@@ -648,7 +658,6 @@ int ensure_rank(bc_graph *g, cudaStream_t st) {
     std::vector<int32_t> dist((size_t)k * n);
     CK(cudaMemcpyAsync(dist.data(), dd.p, dist.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    dd.release();
     rank_from_dist(g, dist, k);
     return BC_OK;
 }
@@ -734,6 +743,33 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
         }
         CK(cudaGetLastError());
     }
+    return BC_OK;
+}
+
+// Algorithm 2 (Section 4.2.1): forward rows of every source (distances and
+// path counts, n x n), then BC from the pair formula (pairs.cu).
+constexpr int32_t kPairsMaxN = 16384;
+
+int run_pairs(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStream_t st, bool hash) {
+    const int32_t n = g->n;
+    if (nsrc != n) return fail(BC_ERR_ARG, "BC_PAIRS needs every vertex as a source");
+    if (n == 0) return BC_OK;
+    const size_t cells = (size_t)n * n;
+    ScopedBuf<int32_t> D;
+    ScopedBuf<uint64_t> L;
+    ScopedBuf<unsigned char> scratch;
+    CK(D.ensure(cells));
+    CK(L.ensure(cells));
+    CK(scratch.ensure(bcgb::pair_scratch_bytes(n)));
+    int r = g->weighted ? run_weighted(g, n, opt, st, false, hash, L.p, D.p)
+                        : run_batches(g, n, W, opt, st, false, hash, L.p, D.p);
+    if (r) return r;
+    {
+        Timer t(g, st, BC_KERNEL_BACKWARD);
+        if (bcgb::pair_launch(D.p, L.p, n, scratch.p, g->bc.p, sm_count_host(), st))
+            return fail(BC_ERR_CUDA, std::string("pair formula launch: ") + cudaGetErrorString(cudaGetLastError()));
+    }
+    CK(cudaStreamSynchronize(st));
     return BC_OK;
 }
 
@@ -829,7 +865,11 @@ int bc_run(bc_graph *g, const int32_t *sources, int32_t num_sources, const bc_op
     if (r) return r;
     if (g->weighted && (flags & BC_PLAIN)) return fail(BC_ERR_UNSUPPORTED, "the one-source path is unweighted only");
     int32_t nsrc = 0;
-    const bool order = !g->weighted && !(flags & (BC_PLAIN | BC_KEEP_ORDER | BC_DENSE)) &&
+    if ((flags & BC_PAIRS) && (sources || (flags & (BC_PLAIN | BC_DENSE))))
+        return fail(BC_ERR_ARG, "BC_PAIRS takes every vertex as a source (sources = NULL), without BC_PLAIN / BC_DENSE");
+    if ((flags & BC_PAIRS) && g->n > kPairsMaxN)
+        return fail(BC_ERR_UNSUPPORTED, "BC_PAIRS supports n <= " + std::to_string(kPairsMaxN));
+    const bool order = !g->weighted && !(flags & (BC_PLAIN | BC_KEEP_ORDER | BC_DENSE | BC_PAIRS)) &&
                        (sources ? num_sources : g->n) > 32;
     if (order) {
         r = ensure_rank(g, st);
@@ -858,7 +898,10 @@ int bc_run(bc_graph *g, const int32_t *sources, int32_t num_sources, const bc_op
             CK(cudaMemsetAsync(g->reach.p, 0, nsrc * sizeof(int64_t), st));
         }
     }
-    if (flags & BC_PLAIN) {
+    if (flags & BC_PAIRS) {
+        r = run_pairs(g, nsrc, W, opt, st, hash);
+        if (r) return r;
+    } else if (flags & BC_PLAIN) {
         std::pair<bc_graph *, cudaStream_t> ctx{g, st};
         bcgb::LaunchHook hook{&ctx, hook_begin, hook_end};
         const int64_t wait_ms = (opt && opt->wait_limit_ms > 0) ? opt->wait_limit_ms : 600000;

@@ -41,6 +41,7 @@ BC_NO_HASH = 0x10
 BC_DENSE = 0x20
 BC_SPARSE_BACKWARD = 0x40
 BC_KEEP_ORDER = 0x80
+BC_PAIRS = 0x100
 
 BC_KERNEL_INIT = 0
 BC_KERNEL_FORWARD = 1
