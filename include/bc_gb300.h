@@ -65,8 +65,9 @@ extern "C" {
 #define BC_GRAPH_DIRECTED 0x2u    /* row_ptr/col list out-arcs of a directed graph (Section 2's model):
                                      P_s(v) takes v's in-arcs, built here as the transpose. No symmetry
                                      check (self-loops, duplicates and weights are still checked).
-                                     bc_run supports it on the batched unweighted path, BC_PLAIN and
-                                     the weighted path; BC_DENSE and bc_many_create return
+                                     bc_run supports it on the batched unweighted path, BC_PLAIN,
+                                     the weighted path, BC_PAIRS and BC_DENSE on weighted graphs;
+                                     BC_DENSE on unweighted graphs and bc_many_create return
                                      BC_ERR_UNSUPPORTED. BC is the ordered-pair sum (BC_HALVE is not
                                      meaningful for directed graphs). */
 
@@ -76,9 +77,14 @@ extern "C" {
 #define BC_PLAIN 0x4u        /* one source per launch sequence (the unbatched GPU Brandes) */
 #define BC_TIMING 0x8u       /* record CUDA events around every kernel launch (bc_kernel_time) */
 #define BC_NO_HASH 0x10u     /* skip the per-source summary values */
-#define BC_DENSE 0x20u       /* levels >= 1 as tensor-core products with the 0/1 adjacency matrix,
-                                forward (ComputePathCount) and backward (ComputeDependency), Section 3.1;
-                                unweighted graphs with n <= 65536, batch 128 */
+#define BC_DENSE 0x20u       /* the algebraic forms of Section 3. Unweighted graphs: levels >= 1 as
+                                tensor-core products with the 0/1 adjacency matrix, forward
+                                (ComputePathCount) and backward (ComputeDependency), Section 3.1;
+                                n <= 65536, batch 128. Weighted graphs: distance products with path
+                                counts on the dense weight matrix until a step changes nothing
+                                (Section 3.2), then BC by Algorithm 2's pair formula; every vertex a
+                                source, n <= 16384 (bc_forward_rows: n <= 32768), n * max weight < 2^30 - 1;
+                                directed or not (the unweighted tensor-core form is undirected only). */
 #define BC_SPARSE_BACKWARD 0x40u /* with BC_DENSE: run the backward pass on the sparse kernel instead */
 #define BC_PAIRS 0x100u      /* BC from all-pairs distances and path counts with Algorithm 2's pair formula
                                 (Section 4.2.1): BC(v) = sum over ordered (s,t), d(s,v)+d(v,t)=d(s,t),
@@ -99,7 +105,8 @@ extern "C" {
  *                  32, 64, 128 or 256 (0 = 256; BC_DENSE uses 128). For
  *                  weighted graphs: sources per wave (0 = 4 per SM).
  *   flags          BC_* option bits above.
- *   chunk          arcs per work item for high-degree vertices (0 = 256).
+ *   chunk          arcs per work item for high-degree vertices (0 = 256 in the
+ *                  forward sweep, 128 in the backward sweep).
  *   wait_limit_ms  bound on every host-side wait for device progress
  *                  (0 = 600000). Expiry returns BC_ERR_TIMEOUT.
  */

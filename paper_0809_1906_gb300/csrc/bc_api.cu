@@ -18,6 +18,7 @@
 #include "weighted.cuh"
 #include "many.cuh"
 #include "dense.cuh"
+#include "minplus.cuh"
 #include "pairs.cuh"
 
 namespace {
@@ -143,6 +144,9 @@ struct bc_graph {
     bcgb::DenseMaps maps{};
     double dense_flops = 0.0;
 
+    // weighted algebraic forward (BC_DENSE on a weighted graph): dense weights
+    DevBuf<int32_t> mpW;
+
     // weighted path: per-wave state
     int32_t maxw = 1;
     int32_t wG = 0, wK = 0, wC = 0;
@@ -159,13 +163,13 @@ void free_graph(bc_graph *g) {
     g->fplan.release();
     g->bplan.release();
     g->sigma.release();
-    g->hpart.release();
     g->lvl.release();
     g->Smask.release();
     g->wideflags.release();
     g->part.release();
     g->cval.release();
     for (auto *b : {&g->F, &g->ufr, &g->V, &g->pmask, &g->cnt}) b->release();
+    g->mpW.release();
     g->bc.release();
     g->h_sigma.release();
     g->h_dist.release();
@@ -773,6 +777,89 @@ int run_pairs(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStrea
     return BC_OK;
 }
 
+// Weighted algebraic forward (Section 3.2; BC_DENSE on a weighted graph):
+// per batch of sources, distance products with path counts on the dense
+// weight matrix until a step changes nothing (minplus.cu). Rows of the
+// staged sources [b0, b0 + nsrc) go to rows_sig / rows_dist in that order.
+constexpr int32_t kMpMaxN = 32768;
+constexpr int kMpBatch = 512;
+
+int run_minplus(bc_graph *g, int32_t nsrc, cudaStream_t st, bool hash, uint64_t *rows_sig, int32_t *rows_dist) {
+    const int32_t n = g->n;
+    if (n > kMpMaxN) return fail(BC_ERR_UNSUPPORTED, "BC_DENSE on a weighted graph supports n <= 32768");
+    if ((int64_t)n * g->maxw >= (int64_t)bcgb::kMpInf)
+        return fail(BC_ERR_UNSUPPORTED, "BC_DENSE on a weighted graph needs n * max weight < 2^30 - 1");
+    if (!rows_sig || !rows_dist) return fail(BC_ERR_ARG, "weighted dense forward writes full rows");
+    const int sms = sm_count_host();
+    if (!g->mpW.p) {
+        CK(g->mpW.ensure((size_t)n * n));
+        if (bcgb::mp_build_weights(g->row_ptr.p, g->col.p, g->w.p, n, g->mpW.p, sms, st))
+            return fail(BC_ERR_CUDA, "weight matrix build");
+    }
+    const int B = std::min<int32_t>(kMpBatch, std::max<int32_t>(nsrc, 1));
+    ScopedBuf<int32_t> xd;
+    ScopedBuf<uint64_t> xc;
+    ScopedBuf<uint32_t> flag;
+    CK(xd.ensure(2 * (size_t)B * n));
+    CK(xc.ensure(2 * (size_t)B * n));
+    CK(flag.ensure(1));
+    for (int32_t b0 = 0; b0 < nsrc; b0 += B) {
+        const int nb = std::min<int32_t>(B, nsrc - b0);
+        const size_t half = (size_t)B * n;
+        int cur = 0;
+        if (bcgb::mp_init(xd.p, xc.p, g->sources.p + b0, nb, n, sms, st)) return fail(BC_ERR_CUDA, "min-plus init");
+        for (int step = 0;; ++step) {
+            if (step > n) return fail(BC_ERR_BOUNDS, "distance products did not settle within n steps");
+            CK(cudaMemsetAsync(flag.p, 0, sizeof(uint32_t), st));
+            {
+                Timer t(g, st, BC_KERNEL_DENSE);
+                if (bcgb::mp_step(xd.p + cur * half, xc.p + cur * half, xd.p + (1 - cur) * half, xc.p + (1 - cur) * half,
+                                  g->mpW.p, g->sources.p + b0, nb, n, flag.p, &g->ctl->status, st))
+                    return fail(BC_ERR_CUDA, "min-plus step launch");
+            }
+            uint32_t f = 0;
+            CK(cudaMemcpyAsync(&f, flag.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            cur ^= 1;
+            if (!(f & 1u)) break;
+        }
+        int32_t *dr = rows_dist + (size_t)b0 * n;
+        uint64_t *sr = rows_sig + (size_t)b0 * n;
+        if (bcgb::mp_rows(xd.p + cur * half, xc.p + cur * half, nb, n, dr, sr, sms, st))
+            return fail(BC_ERR_CUDA, "min-plus rows");
+        if (hash && bcgb::mp_row_hashes(dr, sr, nb, n, g->h_sigma.p + b0, g->h_dist.p + b0, g->dist_sum.p + b0,
+                                        g->reach.p + b0, sms, st))
+            return fail(BC_ERR_CUDA, "row summaries");
+    }
+    CK(cudaStreamSynchronize(st));
+    return BC_OK;
+}
+
+// BC_DENSE on a weighted graph: every source's rows by distance products,
+// then Algorithm 2's pair formula.
+int run_dense_weighted(bc_graph *g, int32_t nsrc, cudaStream_t st, bool hash) {
+    const int32_t n = g->n;
+    if (nsrc != n) return fail(BC_ERR_ARG, "BC_DENSE on a weighted graph takes every vertex as a source");
+    if (n > kPairsMaxN) return fail(BC_ERR_UNSUPPORTED, "BC_DENSE on a weighted graph computes BC for n <= 16384");
+    if (n == 0) return BC_OK;
+    const size_t cells = (size_t)n * n;
+    ScopedBuf<int32_t> D;
+    ScopedBuf<uint64_t> L;
+    ScopedBuf<unsigned char> scratch;
+    CK(D.ensure(cells));
+    CK(L.ensure(cells));
+    CK(scratch.ensure(bcgb::pair_scratch_bytes(n)));
+    int r = run_minplus(g, n, st, hash, L.p, D.p);
+    if (r) return r;
+    {
+        Timer t(g, st, BC_KERNEL_BACKWARD);
+        if (bcgb::pair_launch(D.p, L.p, n, scratch.p, g->bc.p, sm_count_host(), st))
+            return fail(BC_ERR_CUDA, std::string("pair formula launch: ") + cudaGetErrorString(cudaGetLastError()));
+    }
+    CK(cudaStreamSynchronize(st));
+    return BC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -865,6 +952,8 @@ int bc_run(bc_graph *g, const int32_t *sources, int32_t num_sources, const bc_op
     if (r) return r;
     if (g->weighted && (flags & BC_PLAIN)) return fail(BC_ERR_UNSUPPORTED, "the one-source path is unweighted only");
     int32_t nsrc = 0;
+    if (g->weighted && (flags & BC_DENSE) && sources)
+        return fail(BC_ERR_ARG, "BC_DENSE on a weighted graph takes every vertex as a source (sources = NULL)");
     if ((flags & BC_PAIRS) && (sources || (flags & (BC_PLAIN | BC_DENSE))))
         return fail(BC_ERR_ARG, "BC_PAIRS takes every vertex as a source (sources = NULL), without BC_PLAIN / BC_DENSE");
     if ((flags & BC_PAIRS) && g->n > kPairsMaxN)
@@ -909,6 +998,9 @@ int bc_run(bc_graph *g, const int32_t *sources, int32_t num_sources, const bc_op
                             hash ? g->h_sigma.p : nullptr, hash ? g->h_dist.p : nullptr,
                             hash ? g->dist_sum.p : nullptr, hash ? g->reach.p : nullptr, g->ctl, g->hctl,
                             g->hctl_d, &g->seq, st, hook, wait_ms, &g_err);
+        if (r) return r;
+    } else if (g->weighted && (flags & BC_DENSE)) {
+        r = run_dense_weighted(g, nsrc, st, hash);
         if (r) return r;
     } else if (g->weighted) {
         r = run_weighted(g, nsrc, opt, st, true, hash, nullptr, nullptr);
@@ -981,7 +1073,10 @@ int bc_forward_rows(bc_graph *g, const int32_t *sources, int32_t k, uint64_t *si
     if (dist) CK(dd.ensure(cells));
     CK(cudaMemsetAsync(&g->ctl->status, 0, sizeof(uint32_t), st));
     g->timing = false;
-    if (g->weighted)
+    if (g->weighted && opt && (opt->flags & BC_DENSE)) {
+        if (!sigma || !dist) return fail(BC_ERR_ARG, "BC_DENSE rows of a weighted graph need both outputs");
+        r = run_minplus(g, nsrc, st, false, ds.p, dd.p);
+    } else if (g->weighted)
         r = run_weighted(g, nsrc, opt, st, false, false, sigma ? ds.p : nullptr, dist ? dd.p : nullptr);
     else
         r = run_batches(g, nsrc, W, opt, st, false, false, sigma ? ds.p : nullptr, dist ? dd.p : nullptr);
