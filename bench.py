@@ -337,6 +337,64 @@ def run_extra(args):
                                           for b, v in ms_s.items()},
                     dense_forward_sparse_backward={"ms": ms_ds, "value": g.n * g.m / (ms_ds / 1e3)},
                     cpu_baseline=_oracle_rate(g, np.arange(g.n, dtype=np.int32), args.cpu_seconds))
+    elif wl == "directed":
+        g = G.rmat_directed()
+        src = torch.arange(g.n, dtype=torch.int32, device="cuda")
+        with native.Graph.from_csr(g, trust_input=True) as h:
+            ms = _timed(lambda: (h.run(src, batch=BATCH, stream=stream), h.result()), args.steps, args.warmup,
+                        stream, flush)
+        line.update(value=g.n * g.m / (ms / 1e3), ms_per_step=ms,
+                    config={"workload": f"R-MAT s16 ef16 kept directed, weakly connected LCC (n={g.n}, "
+                                        f"arcs={g.m}), all sources, batch {BATCH}", "metric_m": "arcs"},
+                    cpu_baseline=_oracle_rate(g, np.arange(g.n, dtype=np.int32), args.cpu_seconds))
+    elif wl == "wdense":
+        g = G.gnp_weighted(4096, 0.05, 10)
+        with native.Graph.from_csr(g, trust_input=True) as h:
+            ms_d = _timed(lambda: (h.run(flags=native.BC_DENSE, stream=stream), h.result()), args.steps,
+                          args.warmup, stream, flush)
+            h.run(flags=native.BC_DENSE | native.BC_TIMING, stream=stream)
+            h.result()
+            kinds = {native.KERNEL_NAMES[k]: h.kernel_time(k) for k in native.KERNEL_NAMES}
+            ms_s = _timed(lambda: (h.run(stream=stream), h.result()), 2, 1, stream, flush)
+        steps, mp_ms = kinds["dense"]
+        # one product step: 512 sources x n x n (add + min) pairs; lanes x clock = 1 issue per lane
+        elem = steps * 512.0 * g.n * g.n
+        lane_peak = 152 * 128 * 2.07e9
+        ach = elem / (mp_ms / 1e3)
+        line.update(value=g.n * g.m / (ms_d / 1e3), ms_per_step=ms_d,
+                    config={"workload": f"G(n=4096, p=0.05) weighted U{{1..10}} (m={g.m}), all sources, "
+                                        "BC_DENSE: distance products with counts + pair formula",
+                            "kernels_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in kinds.items()},
+                            "product_steps": steps},
+                    roofline={"bound": "alu", "kernel": "k_mp_step", "achieved": ach / 1e12, "peak": lane_peak / 1e12,
+                              "unit": "T (min,+) elements/s", "frac": ach / lane_peak,
+                              "peak_source": "152 SMs x 128 int32 lanes x 2.07 GHz, one element per lane-instruction",
+                              "traffic": None},
+                    vs_bucket_kernel_same_graph={"ms": ms_s, "value": g.n * g.m / (ms_s / 1e3)},
+                    cpu_baseline=_oracle_rate(g, np.arange(g.n, dtype=np.int32), args.cpu_seconds))
+    elif wl == "pairs":
+        g = G.gnp(4096, 0.01)
+        with native.Graph.from_csr(g, trust_input=True) as h:
+            ms_p = _timed(lambda: (h.run(flags=native.BC_PAIRS, stream=stream), h.result()), args.steps,
+                          args.warmup, stream, flush)
+            h.run(flags=native.BC_PAIRS | native.BC_TIMING, stream=stream)
+            h.result()
+            kinds = {native.KERNEL_NAMES[k]: h.kernel_time(k) for k in native.KERNEL_NAMES}
+            ms_s = _timed(lambda: (h.run(stream=stream), h.result()), 2, 1, stream, flush)
+        _, pair_ms = kinds["backward"]
+        triples = float(g.n) ** 3
+        lane_peak = 152 * 128 * 2.07e9
+        ach = triples / (pair_ms / 1e3)
+        line.update(value=g.n * g.m / (ms_p / 1e3), ms_per_step=ms_p,
+                    config={"workload": f"G(n=4096, p=0.01) (m={g.m}), all pairs, BC_PAIRS: forward rows + "
+                                        "Algorithm 2 pair formula",
+                            "kernels_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in kinds.items()}},
+                    roofline={"bound": "alu", "kernel": "k_pair_bc (+ prep, reduce)", "achieved": ach / 1e12,
+                              "peak": lane_peak / 1e12, "unit": "T (s,v,t) triples/s", "frac": ach / lane_peak,
+                              "peak_source": "152 SMs x 128 lanes x 2.07 GHz, one triple per lane-instruction",
+                              "traffic": None},
+                    vs_level_sweep_same_graph={"ms": ms_s, "value": g.n * g.m / (ms_s / 1e3)},
+                    cpu_baseline=_oracle_rate(g, np.arange(g.n, dtype=np.int32), args.cpu_seconds))
     elif wl == "many":
         gs = G.many_graphs()
         hs = [native.Graph.from_csr(g, trust_input=True) for g in gs]
@@ -416,7 +474,8 @@ def main():
                     help="profiling driver: one bc_run over the first --sources sources, nothing else")
     ap.add_argument("--sources", type=int, default=0)
     ap.add_argument("--batch", type=int, default=BATCH)
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "er1024", "grid", "gnp", "many"],
+    ap.add_argument("--workload", default="rmat",
+                    choices=["rmat", "er1024", "grid", "gnp", "many", "directed", "wdense", "pairs"],
                     help="rmat (default, the reported line) or one of the other configurations")
     ap.add_argument("--write-traffic", metavar="CSV", default=None,
                     help="write profiles/traffic_rmat.json from an ncu CSV capture of --profile, then exit")

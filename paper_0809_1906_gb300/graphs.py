@@ -281,6 +281,46 @@ def rmat_lcc(scale: int = 16, edge_factor: int = 16, abcd=(0.57, 0.19, 0.19, 0.0
                           name=f"rmat_s{scale}_ef{edge_factor}_lcc")
 
 
+def rmat_directed(scale: int = 16, edge_factor: int = 16, abcd=(0.57, 0.19, 0.19, 0.05),
+                  seed: int = BASE_SEED + 2) -> Graph:
+    """The same R-MAT draw as rmat_lcc, kept directed: each generated pair is
+    the arc u -> v (self-loops and repeated arcs dropped), restricted to the
+    vertices of the largest weakly connected component and relabelled."""
+    a, b, c, _ = abcd
+    n = 1 << scale
+    ne = edge_factor * n
+    rs = Stream(seed, 3)
+    src = np.zeros(ne, dtype=np.int64)
+    dst = np.zeros(ne, dtype=np.int64)
+    for bit in range(scale):
+        r = rs.uniform(ne)
+        sbit = r >= a + b
+        dbit = ((r >= a) & (r < a + b)) | (r >= a + b + c)
+        src |= sbit.astype(np.int64) << bit
+        dst |= dbit.astype(np.int64) << bit
+    perm = Stream(seed, 4).permutation(n)
+    src, dst = perm[src], perm[dst]
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    _, first = np.unique(src * n + dst, return_index=True)
+    first.sort()
+    src, dst = src[first], dst[first]
+    comp = largest_component(n, *_dedupe_pairs(src, dst, n))
+    newid = np.full(n, -1, dtype=np.int64)
+    newid[comp] = np.arange(comp.size)
+    keep = newid[src] >= 0
+    return csr_from_arcs(comp.size, newid[src[keep]], newid[dst[keep]],
+                         name=f"rmat_s{scale}_ef{edge_factor}_directed")
+
+
+def gnp_weighted(n: int = 4096, p: float = 0.05, wmax: int = 10, seed: int = BASE_SEED + 6) -> Graph:
+    """G(n, p) as gnp(), every undirected edge with an integer weight uniform in [1, wmax]."""
+    g = gnp(n, p, seed)
+    u, v, _ = g.edges()
+    w = 1 + Stream(seed, 8).below(u.size, wmax)
+    return csr_from_edges(n, u, v, w, name=f"gnp_n{n}_p{p}_w{wmax}")
+
+
 def grid_longrange(side: int = 512, frac: float = 0.05, wmax: int = 100,
                    seed: int = BASE_SEED + 3) -> Graph:
     """side x side 4-neighbour grid plus round(frac * grid_edges) uniform random
