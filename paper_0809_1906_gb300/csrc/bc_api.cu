@@ -150,7 +150,10 @@ struct bc_graph {
     // weighted path: per-wave state
     int32_t maxw = 1;
     int32_t wG = 0, wK = 0, wC = 0;
-    DevBuf<int32_t> wdist, worder, wgrp, wslots;
+    DevBuf<int32_t> wdist, worder, wgrp, wslots, wpos, wsrc;
+    DevBuf<uint64_t> wds;     // packed per-vertex state of the packed kernel
+    DevBuf<uint8_t> wredo;    // sources whose counts need 64 bits
+    std::vector<int32_t> h_sources;  // host copy of the staged source list
     DevBuf<uint64_t> wsigma;
     DevBuf<float> wcval, wrows;
 };
@@ -170,6 +173,9 @@ void free_graph(bc_graph *g) {
     g->cval.release();
     for (auto *b : {&g->F, &g->ufr, &g->V, &g->pmask, &g->cnt}) b->release();
     g->mpW.release();
+    for (auto *b : {&g->wpos, &g->wsrc}) b->release();
+    g->wds.release();
+    g->wredo.release();
     g->bc.release();
     g->h_sigma.release();
     g->h_dist.release();
@@ -466,6 +472,7 @@ int stage_sources(bc_graph *g, const int32_t *sources, int32_t num, int32_t *cou
     CK(g->sources.ensure(hs.size()));
     if (!hs.empty()) CK(cudaMemcpy(g->sources.p, hs.data(), hs.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     *count = (int32_t)hs.size();
+    g->h_sources.swap(hs);
     return BC_OK;
 }
 
@@ -689,7 +696,7 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
                                             std::to_string(bcgb::kMaxRing));
     int C = (int)std::min<int64_t>(std::max<int64_t>(1024, (4ll << 20) / K / 4), (int64_t)n + 1);
     C = std::max(C, 64);
-    const size_t per_src = (size_t)n * (4 + 8 + 4 + 4 + 4 + 4) + 4 + (size_t)K * C * 4;
+    const size_t per_src = (size_t)n * (4 + 8 + 4 + 4 + 4 + 4 + 8) + 4 + (size_t)K * C * 4;
     int G = (opt && opt->batch > 0) ? opt->batch : 4 * sm_count_host();
     G = (int)std::min<size_t>((size_t)G, std::max<size_t>(1, (8ull << 30) / per_src));
     G = std::max(1, std::min(G, std::max(nsrc, 1)));
@@ -701,6 +708,10 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
         CK(g->wgrp.ensure((size_t)G * (n + 1)));
         CK(g->wslots.ensure((size_t)G * K * C));
         CK(g->wrows.ensure((size_t)G * n));
+        CK(g->wds.ensure((size_t)G * n));
+        CK(g->wredo.ensure((size_t)G));
+        CK(g->wpos.ensure((size_t)G));
+        CK(g->wsrc.ensure((size_t)G));
         g->wG = G;
         g->wK = K;
         g->wC = C;
@@ -737,9 +748,31 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
         p.rows_sigma = rows_sig ? rows_sig + (size_t)w0 * n : nullptr;
         p.rows_dist = rows_dist ? rows_dist + (size_t)w0 * n : nullptr;
         p.ctl = g->ctl;
+        p.ds = g->wds.p;
+        p.redo = g->wredo.p;
+        CK(cudaMemsetAsync(g->wredo.p, 0, (size_t)nw, st));
         {
             Timer t(g, st, BC_KERNEL_FORWARD);
-            bcgb::w_launch_wave(p, nw, st);
+            bcgb::w_launch_wave_packed(p, nw, st);
+        }
+        // sources whose path counts need 64 bits: again with the 64-bit kernel
+        std::vector<uint8_t> redo(nw);
+        CK(cudaMemcpyAsync(redo.data(), g->wredo.p, (size_t)nw, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        std::vector<int32_t> rpos, rsrc;
+        for (int i = 0; i < nw; ++i)
+            if (redo[i]) {
+                rpos.push_back(i);
+                rsrc.push_back(g->h_sources[(size_t)w0 + i]);
+            }
+        if (!rpos.empty()) {
+            CK(cudaMemcpyAsync(g->wpos.p, rpos.data(), rpos.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(g->wsrc.p, rsrc.data(), rsrc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            bcgb::WParams p64 = p;
+            p64.sources = g->wsrc.p;
+            p64.pos = g->wpos.p;
+            Timer t(g, st, BC_KERNEL_FORWARD);
+            bcgb::w_launch_wave(p64, (int)rpos.size(), st);
         }
         if (backward) {
             Timer t(g, st, BC_KERNEL_BACKWARD);

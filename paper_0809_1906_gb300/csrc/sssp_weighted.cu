@@ -60,6 +60,7 @@ __device__ __forceinline__ void push_entry(const WParams &p, WSmem &sm, int32_t 
 __global__ void __launch_bounds__(kWBlock, 4) k_wsssp(const WParams p) {
     __shared__ WSmem sm;
     const int i = blockIdx.x;  // source index within the wave
+    const int o = p.pos ? p.pos[i] : i;  // output position
     const int tid = threadIdx.x;
     const int lane = tid & 31, wid = tid >> 5;
     const int32_t src = p.sources[i];
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(kWBlock, 4) k_wsssp(const WParams p) {
     int32_t *order = p.order + (size_t)i * n;
     int32_t *grp = p.grp + (size_t)i * (n + 1);
     int32_t *slots = p.slots + (size_t)i * p.K * p.C;
-    float *drow = p.delta_rows ? p.delta_rows + (size_t)i * n : nullptr;
+    float *drow = p.delta_rows ? p.delta_rows + (size_t)o * n : nullptr;
 
     for (int v = tid; v < n; v += kWBlock) {
         dist[v] = kInf;
@@ -179,7 +180,8 @@ __global__ void __launch_bounds__(kWBlock, 4) k_wsssp(const WParams p) {
                 uint64_t x[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const bool pred = u[i] >= 0 && v != src && old[i] < d && old[i] == 2 * d - nd[i];
+                    // u before v (old < d, final) with old + w(u,v) = d; nd - d = w
+                    const bool pred = u[i] >= 0 && v != src && old[i] < d && old[i] + (nd[i] - d) == d;
                     x[i] = pred ? __ldcg(sigma + u[i]) : 0ull;
                     arcs += pred ? 1ull : 0ull;
                 }
@@ -217,8 +219,8 @@ __global__ void __launch_bounds__(kWBlock, 4) k_wsssp(const WParams p) {
     if (p.rows_dist || p.rows_sigma) {
         for (int v = tid; v < n; v += kWBlock) {
             const int dv = dist[v];
-            if (p.rows_dist) p.rows_dist[(size_t)i * n + v] = dv == kInf ? -1 : dv;
-            if (p.rows_sigma) p.rows_sigma[(size_t)i * n + v] = dv == kInf ? 0ull : sigma[v];
+            if (p.rows_dist) p.rows_dist[(size_t)o * n + v] = dv == kInf ? -1 : dv;
+            if (p.rows_sigma) p.rows_sigma[(size_t)o * n + v] = dv == kInf ? 0ull : sigma[v];
         }
     }
 #pragma unroll
@@ -243,10 +245,10 @@ __global__ void __launch_bounds__(kWBlock, 4) k_wsssp(const WParams p) {
         for (int w = 1; w < kWBlock / 32; ++w)
             for (int q = 0; q < 4; ++q) sm.red[q][0] += sm.red[q][w];
         if (p.h_sigma) {
-            p.h_sigma[i] = sm.red[0][0];
-            p.h_dist[i] = sm.red[1][0];
-            p.dist_sum[i] = (int64_t)sm.red[2][0];
-            p.reach[i] = (int64_t)sm.red[3][0];
+            p.h_sigma[o] = sm.red[0][0];
+            p.h_dist[o] = sm.red[1][0];
+            p.dist_sum[o] = (int64_t)sm.red[2][0];
+            p.reach[o] = (int64_t)sm.red[3][0];
         }
         if (sm.flags & 1u) atomicOr(&p.ctl->status, BC_STATUS_SIGMA_OVERFLOW);
         atomicAdd(&p.ctl->depth_sum, (unsigned long long)(ng > 0 ? ng - 1 : 0));

@@ -23,6 +23,9 @@ struct WParams {
     const int32_t *w_in;
     const int32_t *w;
     const int32_t *sources;  // this wave's sources
+    const int32_t *pos;      // output position of each CTA's source (null: its index)
+    uint64_t *ds;            // [wave][n] packed state (distance << 32 | sigma or c bits)
+    uint8_t *redo;           // [wave] set where a count reached 2^32 (packed kernel)
     int32_t *dist;           // [wave][n]
     uint64_t *sigma;         // [wave][n]
     float *cval;             // [wave][n]
@@ -39,7 +42,8 @@ struct WParams {
     DevCtl *ctl;
 };
 
-void w_launch_wave(const WParams &p, int nsrc, cudaStream_t st);
+void w_launch_wave(const WParams &p, int nsrc, cudaStream_t st);         // 64-bit counts
+void w_launch_wave_packed(const WParams &p, int nsrc, cudaStream_t st);  // packed state, 32-bit counts
 void w_launch_reduce(const float *rows, int nrows, int n, double *bc, int sms, cudaStream_t st);
 
 }  // namespace bcgb

@@ -116,3 +116,29 @@ def test_weight_limit(nat):
     with pytest.raises(nat.BcError) as e:
         nat.Graph(3, g.row_ptr, g.col, np.array([1, 0, 0, 1], np.int32))
     assert e.value.code == nat.BC_ERR_WEIGHT
+
+
+def test_counts_beyond_32_bits_fall_back_exactly(nat):
+    """Unit weights on a 20 x 20 grid given as a weighted graph: counts up to
+    C(38,19) > 2^32 exceed the packed kernel's 32-bit sigma, so those sources
+    are recomputed with 64-bit counts; sources whose counts stay small (a
+    ragged wave mixing both kinds) keep the packed result. Rows, summaries and
+    BC match the oracle."""
+    g0 = G.grid_graph(20)
+    g = G.Graph(g0.n, g0.row_ptr, g0.col, np.ones_like(g0.col), "grid20w")
+    src = np.array([0, 210, 399, 19, 55, 380, 7, 200], np.int32)
+    check(nat, g, sources=src, batch=5)
+
+
+def test_packed_and_64bit_overflow_flag(nat):
+    """35 x 35 unit-weight grid: sigma(corner, far corner) = C(68,34) >= 2^64;
+    the fallback keeps the low 64 bits and raises the overflow warning."""
+    g0 = G.grid_graph(35)
+    g = G.Graph(g0.n, g0.row_ptr, g0.col, np.ones_like(g0.col), "grid35w")
+    with nat.Graph.from_csr(g) as h:
+        sig, dist, code = h.forward_rows(np.array([0, 17], np.int32))
+    assert code == nat.BC_WARN_SIGMA_OVERFLOW
+    assert int(sig[0, -1]) == math.comb(68, 34) % (1 << 64) and dist[0, -1] == 68
+    o = oracle.source(g, 17, with_delta=False)
+    assert np.array_equal(sig[1], o["sigma"]) and np.array_equal(dist[1], o["dist"].astype(np.int32))
+
