@@ -137,12 +137,19 @@ struct bc_graph {
 
     bcgb::PlainState plain;
 
-    // dense (tensor-core) levels: bf16 adjacency, limb matrix, TMA maps
+    // dense (tensor-core) levels: bf16 adjacency, per-batch limb rows, TMA
+    // maps, and the state of a group of batches run in lockstep
     int32_t npad = 0;
     DevBuf<__nv_bfloat16> dA, dX;
     DevBuf<bcgb::DenseCtl> dctl;
     bcgb::DenseMaps maps{};
     double dense_flops = 0.0;
+    int32_t gNB = 0, gLcap = 0;  // group capacity (batches) and its level capacity
+    DevBuf<uint64_t> gsigma;
+    DevBuf<uint16_t> glvl;
+    DevBuf<uint32_t> gF, gV, gufr;
+    DevBuf<double> gbcpart;
+    DevBuf<int32_t> gmeta;  // [3][gNB]: active list, valid sources, depth
 
     // weighted algebraic forward (BC_DENSE on a weighted graph): dense weights
     DevBuf<int32_t> mpW;
@@ -173,6 +180,11 @@ void free_graph(bc_graph *g) {
     g->cval.release();
     for (auto *b : {&g->F, &g->ufr, &g->V, &g->pmask, &g->cnt}) b->release();
     g->mpW.release();
+    g->gsigma.release();
+    g->glvl.release();
+    for (auto *b : {&g->gF, &g->gV, &g->gufr}) b->release();
+    g->gbcpart.release();
+    g->gmeta.release();
     for (auto *b : {&g->wpos, &g->wsrc}) b->release();
     g->wds.release();
     g->wredo.release();
@@ -476,74 +488,6 @@ int stage_sources(bc_graph *g, const int32_t *sources, int32_t num, int32_t *cou
     return BC_OK;
 }
 
-bcgb::DenseParams dense_params(bc_graph *g, const bcgb::MsParams &p) {
-    bcgb::DenseParams d{};
-    d.n = g->n;
-    d.npad = g->npad;
-    d.nb = p.nb;
-    d.nw32 = p.nw32;
-    d.sigma = g->sigma.p;
-    d.lvl = g->lvl.p;
-    d.F = g->F.p;
-    d.V = g->V.p;
-    d.ufr = g->ufr.p;
-    d.X = g->dX.p;
-    d.bc = g->bc.p;
-    d.ctl = g->ctl;
-    d.dctl = g->dctl.p;
-    return d;
-}
-
-// Tensor-core forward for one batch (BC_DENSE): level 0 by the sparse
-// kernel, every further level as limb-matrix x adjacency products. The host
-// reads each level's outcome (a few levels per batch), which fixes the limb
-// count of the next product. Returns the depth in *depth (-1: level capacity).
-int dense_forward(bc_graph *g, bcgb::MsParams &p, cudaStream_t st, int *depth) {
-    {
-        Timer t(g, st, BC_KERNEL_FORWARD);
-        bcgb::ms_launch_first(4, p, st);
-    }
-    bcgb::DevCtl c{};
-    CK(cudaMemcpyAsync(&c, g->ctl, sizeof(c), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (c.fwd_done) {
-        *depth = c.nlevels;
-        return BC_OK;
-    }
-    bcgb::DenseParams d = dense_params(g, p);
-    int nl = 1;  // level-1 counts are all 1
-    for (int l = 1;; ++l) {
-        if (l + 2 >= g->Lcap) {
-            *depth = -1;
-            return BC_OK;
-        }
-        CK(cudaMemsetAsync(g->dctl.p, 0, sizeof(bcgb::DenseCtl), st));
-        g->dense_flops += 2.0 * 128.0 * nl * (double)g->npad * (double)g->npad;
-        {
-            Timer t(g, st, BC_KERNEL_DENSE);
-            if (bcgb::dense_launch_level(g->maps, d, l, nl, st))
-                return fail(BC_ERR_CUDA, std::string("dense level launch: ") + cudaGetErrorString(cudaGetLastError()));
-        }
-        bcgb::DenseCtl r{};
-        uint32_t status = 0;
-        CK(cudaMemcpyAsync(&r, g->dctl.p, sizeof(r), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(&status, &g->ctl->status, 4, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (status & BC_STATUS_DENSE_TIMEOUT) return fail(BC_ERR_TIMEOUT, "tensor-core pipeline wait timed out");
-        if (!r.produced) {
-            *depth = l;
-            return BC_OK;
-        }
-        if (r.remaining == 0) {  // every pair reached: the next frontier is empty
-            *depth = l + 1;
-            return BC_OK;
-        }
-        nl = 1;
-        while (nl < bcgb::kDenseMaxLimbs && (r.maxsig >> (8 * nl)) != 0ull) ++nl;
-        if (status & BC_STATUS_SIGMA_OVERFLOW) nl = bcgb::kDenseMaxLimbs;
-    }
-}
-
 int ensure_dense(bc_graph *g, cudaStream_t st) {
     if (g->dA.p) return BC_OK;
     if (g->weighted) return fail(BC_ERR_UNSUPPORTED, "BC_DENSE needs an unweighted graph");
@@ -551,14 +495,214 @@ int ensure_dense(bc_graph *g, cudaStream_t st) {
     if (g->n > bcgb::kDenseMaxN) return fail(BC_ERR_UNSUPPORTED, "BC_DENSE supports n <= 65536");
     const int32_t npad = std::max(64, (g->n + 63) / 64 * 64);
     CK(g->dA.ensure((size_t)npad * npad));
-    CK(g->dX.ensure((size_t)bcgb::kDenseMaxLimbs * 128 * npad));
-    CK(cudaMemsetAsync(g->dX.p, 0, g->dX.n * sizeof(__nv_bfloat16), st));
-    CK(g->dctl.ensure(1));
     if (bcgb::dense_build_adjacency(g->row_ptr.p, g->col.p, g->n, npad, g->dA.p, st))
         return fail(BC_ERR_CUDA, "dense adjacency build failed");
-    if (bcgb::dense_make_maps(&g->maps, g->dX.p, g->dA.p, npad))
-        return fail(BC_ERR_CUDA, "cuTensorMapEncodeTiled failed for the dense operands");
     g->npad = npad;
+    return BC_OK;
+}
+
+// State of a group of nb batches (B = 128) with level capacity Lcap; the X
+// map covers the group's limb rows.
+int ensure_dense_group(bc_graph *g, int nb, int Lcap, cudaStream_t st) {
+    if (g->gNB >= nb && g->gLcap == Lcap && g->gsigma.p) return BC_OK;
+    const size_t n = (size_t)std::max(g->n, 1), nw32 = (n + 31) / 32;
+    CK(g->gsigma.ensure((size_t)nb * n * 128));
+    CK(g->glvl.ensure((size_t)nb * n * 128));
+    CK(g->gF.ensure((size_t)nb * Lcap * n * 4));
+    CK(g->gV.ensure((size_t)nb * 2 * n * 4));
+    CK(g->gufr.ensure((size_t)nb * Lcap * nw32));
+    CK(g->gbcpart.ensure((size_t)nb * n));
+    CK(g->gmeta.ensure((size_t)3 * nb));
+    CK(g->dctl.ensure((size_t)nb));
+    CK(g->dX.ensure((size_t)nb * bcgb::kDenseXRows * g->npad));
+    CK(cudaMemsetAsync(g->dX.p, 0, g->dX.n * sizeof(__nv_bfloat16), st));
+    if (bcgb::dense_make_maps(&g->maps, g->dX.p, (uint64_t)nb * bcgb::kDenseXRows, g->dA.p, g->npad))
+        return fail(BC_ERR_CUDA, "cuTensorMapEncodeTiled failed for the dense operands");
+    g->gNB = nb;
+    g->gLcap = Lcap;
+    return BC_OK;
+}
+
+// BC_DENSE on an unweighted graph: batches of 128 sources in groups run level
+// by level in lockstep, one tensor-core launch per level for the whole group
+// (every batch's state stays resident). Forward: level 0 -> 1 by the sparse
+// first-level kernel per batch, then limb products until every batch's
+// frontier is empty; each level's outcome fixes the next limb count.
+// Backward: from the deepest level of the group down, the split c rows times
+// A per level (or, with BC_SPARSE_BACKWARD, the sparse backward per batch);
+// BC partials of the group are added in batch order.
+constexpr size_t kDenseGroupBudget = 24ull << 30;
+constexpr int kDenseL2Group = 8;  // batches that share each adjacency tile in turn
+
+int run_dense_group(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t st, bool backward, bool hash,
+                    uint64_t *rows_sig, int32_t *rows_dist) {
+    constexpr int W = 4, B = 128;
+    const int32_t n = g->n;
+    const size_t nn = (size_t)std::max(n, 1), nw32 = (nn + 31) / 32;
+    const bool sparse_bwd = opt && (opt->flags & BC_SPARSE_BACKWARD);
+    int r = build_plans(g, opt);
+    if (r) return r;
+    r = ensure_state(g, W, std::max(g->Lcap, 32));
+    if (r) return r;
+    const int nbat = (nsrc + B - 1) / B;
+    for (int gb0 = 0; gb0 < nbat;) {
+        const int Lcap = g->Lcap;
+        const size_t per = nn * B * 10 + (size_t)Lcap * nn * 16 + 2 * nn * 16 + (size_t)Lcap * nw32 * 4 +
+                           (size_t)bcgb::kDenseXRows * g->npad * 2 + nn * 8;
+        const int NB = (int)std::max<size_t>(1, std::min<size_t>((size_t)(nbat - gb0), kDenseGroupBudget / per));
+        r = ensure_dense_group(g, NB, Lcap, st);
+        if (r) return r;
+        const size_t sstr = nn * B, fstr = (size_t)Lcap * nn * W, vstr = 2 * nn * W, ustr = (size_t)Lcap * nw32;
+        std::vector<int32_t> nbs(NB), depth(NB, 0);
+        std::vector<bcgb::MsParams> ps(NB);
+        for (int b = 0; b < NB; ++b) {
+            const int32_t b0 = (gb0 + b) * B;
+            nbs[b] = std::min<int32_t>(B, nsrc - b0);
+            bcgb::MsParams p = make_params(g);
+            p.nb = nbs[b];
+            p.first = 1;
+            p.seq = ++g->seq;
+            p.sources = g->sources.p + b0;
+            p.sigma = g->gsigma.p + b * sstr;
+            p.lvl = g->glvl.p + b * sstr;
+            p.F = g->gF.p + b * fstr;
+            p.V = g->gV.p + b * vstr;
+            p.ufr = g->gufr.p + b * ustr;
+            p.Lcap = Lcap;
+            if (hash) {
+                p.h_sigma = g->h_sigma.p + b0;
+                p.h_dist = g->h_dist.p + b0;
+                p.dist_sum = g->dist_sum.p + b0;
+                p.reach = g->reach.p + b0;
+            }
+            ps[b] = p;
+            {
+                Timer t(g, st, BC_KERNEL_INIT);
+                bcgb::ms_launch_init(W, p, st);
+            }
+            {
+                Timer t(g, st, BC_KERNEL_FORWARD);
+                bcgb::ms_launch_first(W, p, st);
+            }
+        }
+        int32_t *d_blist = g->gmeta.p, *d_nbs = g->gmeta.p + NB, *d_depth = g->gmeta.p + 2 * NB;
+        CK(cudaMemcpyAsync(d_nbs, nbs.data(), NB * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        bcgb::DenseParams d{};
+        d.n = n;
+        d.npad = g->npad;
+        d.nw32 = (int32_t)nw32;
+        d.Lcap = Lcap;
+        d.group = kDenseL2Group;
+        d.blist = d_blist;
+        d.nbs = d_nbs;
+        d.depth = d_depth;
+        d.sig_stride = sstr;
+        d.f_stride = fstr;
+        d.v_stride = vstr;
+        d.u_stride = ustr;
+        d.xrows = bcgb::kDenseXRows;
+        d.sigma = g->gsigma.p;
+        d.lvl = g->glvl.p;
+        d.F = g->gF.p;
+        d.V = g->gV.p;
+        d.ufr = g->gufr.p;
+        d.X = g->dX.p;
+        d.bcpart = g->gbcpart.p;
+        d.ctl = g->ctl;
+        d.dctl = g->dctl.p;
+        // ---- forward, all batches in lockstep
+        std::vector<int32_t> active(NB);
+        std::iota(active.begin(), active.end(), 0);
+        std::vector<bcgb::DenseCtl> res(NB);
+        int nl = 1;  // level-1 counts are all 1
+        bool capped = false;
+        for (int l = 1; !active.empty(); ++l) {
+            if (l + 2 >= Lcap) {
+                capped = true;
+                break;
+            }
+            CK(cudaMemcpyAsync(d_blist, active.data(), active.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            CK(cudaMemsetAsync(g->dctl.p, 0, NB * sizeof(bcgb::DenseCtl), st));
+            d.nactive = (int32_t)active.size();
+            g->dense_flops += 2.0 * B * nl * (double)g->npad * (double)g->npad * (double)active.size();
+            {
+                Timer t(g, st, BC_KERNEL_DENSE);
+                if (bcgb::dense_launch_level(g->maps, d, l, nl, st))
+                    return fail(BC_ERR_CUDA, std::string("dense level launch: ") + cudaGetErrorString(cudaGetLastError()));
+            }
+            uint32_t status = 0;
+            CK(cudaMemcpyAsync(res.data(), g->dctl.p, NB * sizeof(bcgb::DenseCtl), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(&status, &g->ctl->status, 4, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (status & BC_STATUS_DENSE_TIMEOUT) return fail(BC_ERR_TIMEOUT, "tensor-core pipeline wait timed out");
+            std::vector<int32_t> still;
+            unsigned long long maxsig = 0;
+            for (int b : active) {
+                if (!res[b].produced) {
+                    depth[b] = l;
+                } else if (res[b].remaining == 0) {  // every pair reached: the next frontier is empty
+                    depth[b] = l + 1;
+                } else {
+                    still.push_back(b);
+                    maxsig = std::max(maxsig, res[b].maxsig);
+                }
+            }
+            active.swap(still);
+            nl = 1;
+            while (nl < bcgb::kDenseMaxLimbs && (maxsig >> (8 * nl)) != 0ull) ++nl;
+            if (status & BC_STATUS_SIGMA_OVERFLOW) nl = bcgb::kDenseMaxLimbs;
+        }
+        if (capped) {  // deeper than the level capacity: grow it and redo this group
+            CK(cudaStreamSynchronize(st));
+            r = ensure_state(g, W, g->Lcap * 2);
+            if (r) return r;
+            continue;
+        }
+        CK(cudaMemcpyAsync(d_depth, depth.data(), NB * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        // ---- backward
+        if (backward && sparse_bwd) {
+            for (int b = 0; b < NB; ++b) {
+                bcgb::MsParams pb = ps[b];
+                use_plan(pb, g->bplan);
+                for (int l = depth[b]; l >= 1; --l) {
+                    Timer t(g, st, BC_KERNEL_BACKWARD);
+                    bcgb::ms_launch_backward(W, pb, l, st);
+                }
+            }
+        } else if (backward) {
+            CK(cudaMemsetAsync(g->gbcpart.p, 0, (size_t)NB * nn * sizeof(double), st));
+            Timer t(g, st, BC_KERNEL_DENSE);
+            if (bcgb::dense_launch_bwd_last(d, NB, st)) return fail(BC_ERR_CUDA, "dense backward launch");
+            const int Lmax = *std::max_element(depth.begin(), depth.end());
+            for (int l = Lmax - 1; l >= 1; --l) {
+                active.clear();
+                for (int b = 0; b < NB; ++b)
+                    if (depth[b] - 1 >= l) active.push_back(b);
+                CK(cudaMemcpyAsync(d_blist, active.data(), active.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                   st));
+                d.nactive = (int32_t)active.size();
+                g->dense_flops += 2.0 * B * 3.0 * (double)g->npad * (double)g->npad * (double)active.size();
+                if (bcgb::dense_launch_bwd_level(g->maps, d, l, st))
+                    return fail(BC_ERR_CUDA, std::string("dense backward launch: ") +
+                                                 cudaGetErrorString(cudaGetLastError()));
+            }
+            if (bcgb::dense_reduce_bc(g->gbcpart.p, NB, n, g->bc.p, st)) return fail(BC_ERR_CUDA, "BC reduction");
+        }
+        for (int b = 0; b < NB; ++b) {
+            const int32_t b0 = (gb0 + b) * B;
+            if (hash) {
+                Timer t(g, st, BC_KERNEL_HASH);
+                bcgb::ms_launch_hash(W, ps[b], depth[b], st);
+            }
+            if (rows_sig || rows_dist) {
+                Timer t(g, st, BC_KERNEL_HASH);
+                bcgb::ms_launch_rows(W, ps[b], depth[b], rows_sig ? rows_sig + (size_t)b0 * n : nullptr,
+                                     rows_dist ? rows_dist + (size_t)b0 * n : nullptr, st);
+            }
+        }
+        CK(cudaGetLastError());
+        gb0 += NB;
+    }
     return BC_OK;
 }
 
@@ -566,11 +710,10 @@ int ensure_dense(bc_graph *g, cudaStream_t st) {
 int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStream_t st, bool backward,
                 bool hash, uint64_t *rows_sig, int32_t *rows_dist) {
     const int64_t wait_ms = (opt && opt->wait_limit_ms > 0) ? opt->wait_limit_ms : 600000;
-    const bool dense = opt && (opt->flags & BC_DENSE);
-    if (dense) {
-        W = 4;
+    if (opt && (opt->flags & BC_DENSE)) {
         int rd = ensure_dense(g, st);
         if (rd) return rd;
+        return run_dense_group(g, nsrc, opt, st, backward, hash, rows_sig, rows_dist);
     }
     int r = build_plans(g, opt);
     if (r) return r;
@@ -597,9 +740,7 @@ int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStr
             bcgb::ms_launch_init(W, p, st);
         }
         int L = 0;
-        if (dense) {
-            r = dense_forward(g, p, st, &L);
-        } else {
+        {
             auto launch = [&](int level) {
                 Timer t(g, st, BC_KERNEL_FORWARD);
                 if (level == 0)
@@ -616,12 +757,7 @@ int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStr
             if (r) return r;
             continue;
         }
-        if (backward && dense && !(opt->flags & BC_SPARSE_BACKWARD)) {
-            Timer t(g, st, BC_KERNEL_DENSE);
-            g->dense_flops += 2.0 * 128.0 * 3.0 * (double)g->npad * (double)g->npad * (L > 1 ? L - 1 : 0);
-            if (bcgb::dense_launch_backward(g->maps, dense_params(g, p), L, st))
-                return fail(BC_ERR_CUDA, std::string("dense backward launch: ") + cudaGetErrorString(cudaGetLastError()));
-        } else if (backward) {
+        if (backward) {
             bcgb::MsParams pb = p;
             use_plan(pb, g->bplan);
             for (int l = L; l >= 1; --l) {

@@ -139,8 +139,7 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 template <bool kBwd>
 __global__ void __launch_bounds__(128, 1)
     k_dense_level(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmA, const DenseParams p,
-                  const int l, const int nl, const int stages, const int xrow0, const int xout,
-                  const int write_next) {
+                  const int l, const int nl, const int stages, const int write_next) {
     extern __shared__ unsigned char dsm_raw[];
     unsigned char *dsm = reinterpret_cast<unsigned char *>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
     const int stage_bytes = nl * kXTile + kATile;
@@ -152,7 +151,31 @@ __global__ void __launch_bounds__(128, 1)
     __shared__ uint32_t s_err;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int v0 = blockIdx.x * kNT;
+    // CTA -> (batch, 64-vertex tile): groups of p.group batches walk the
+    // vertex tiles together, so each adjacency tile is read by p.group
+    // batches in turn while it is in L2, and each batch's limb rows stay hot
+    const int NV = p.npad / kNT;
+    const int per = p.group * NV;
+    const int bg = blockIdx.x / per;
+    const int gbase = bg * p.group;
+    const int gsz = min(p.group, p.nactive - gbase);
+    const int within = blockIdx.x - bg * per;
+    const int vt = within / gsz;
+    const int bb = p.blist[gbase + (within - vt * gsz)];
+    const int v0 = vt * kNT;
+    uint64_t *const sigma = p.sigma + (size_t)bb * p.sig_stride;
+    uint16_t *const lvl = p.lvl + (size_t)bb * p.sig_stride;
+    uint32_t *const Fb = p.F + (size_t)bb * p.f_stride;
+    uint32_t *const Vb = p.V + (size_t)bb * p.v_stride;
+    uint32_t *const ufb = p.ufr + (size_t)bb * p.u_stride;
+    const int nbv = p.nbs[bb];
+    int xin = 0, xout = 0;
+    if constexpr (kBwd) {  // the two split-row blocks of this batch alternate from its deepest level down
+        const int L = p.depth[bb];
+        xin = ((L - 1 - l) & 1) ? 3 * kDB : 0;
+        xout = 3 * kDB - xin;
+    }
+    const int xrow0 = bb * p.xrows + xin;
     const int nk = p.npad / kKT;
     uint32_t ncols = 32;
     while (ncols < (uint32_t)(nl * kNT)) ncols <<= 1;
@@ -232,8 +255,8 @@ __global__ void __launch_bounds__(128, 1)
         __shared__ double s_red[4][16];
         const int b = tid;
         const size_t nW = (size_t)p.n * kDW;
-        const uint32_t *Fl = p.F + (size_t)l * nW;
-        const bool valid_src = b < p.nb;
+        const uint32_t *Fl = Fb + (size_t)l * nW;
+        const bool valid_src = b < nbv;
         for (int c0 = 0; good && c0 < kNT; c0 += 16) {
             float S[16];
 #pragma unroll
@@ -253,7 +276,7 @@ __global__ void __launch_bounds__(128, 1)
                     const bool at = valid_src && ((__ldg(Fl + (size_t)v * kDW + warp) >> lane) & 1u);
                     float d = 0.0f, c = 0.0f;
                     if (at) {
-                        const float sg = __ull2float_rn(p.sigma[(size_t)v * kDB + b]);
+                        const float sg = __ull2float_rn(sigma[(size_t)v * kDB + b]);
                         d = sg * S[i];          // delta_s*(v) = sigma_s(v) * sum_w c_s(w)
                         c = (1.0f + d) / sg;    // c_s(v) for the level above
                     }
@@ -263,9 +286,10 @@ __global__ void __launch_bounds__(128, 1)
                         const float r1 = c - __bfloat162float(h);
                         const __nv_bfloat16 m = __float2bfloat16_rn(r1);
                         const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(m));
-                        p.X[((size_t)xout + b) * p.npad + v] = h;
-                        p.X[((size_t)xout + kDB + b) * p.npad + v] = m;
-                        p.X[((size_t)xout + 2 * kDB + b) * p.npad + v] = lo;
+                        const size_t xr = (size_t)bb * p.xrows + xout + b;
+                        p.X[xr * p.npad + v] = h;
+                        p.X[(xr + kDB) * p.npad + v] = m;
+                        p.X[(xr + 2 * kDB) * p.npad + v] = lo;
                     }
                 }
 #pragma unroll
@@ -274,18 +298,19 @@ __global__ void __launch_bounds__(128, 1)
             }
             __syncthreads();
             if (tid < 16 && v0 + c0 + tid < p.n)
-                p.bc[v0 + c0 + tid] += ((s_red[0][tid] + s_red[1][tid]) + s_red[2][tid]) + s_red[3][tid];
+                p.bcpart[(size_t)bb * p.n + v0 + c0 + tid] +=
+                    ((s_red[0][tid] + s_red[1][tid]) + s_red[2][tid]) + s_red[3][tid];
             __syncthreads();
         }
     } else {
-    const int b = tid;  // source index in the batch
+        const int b = tid;  // source index in the batch
         const size_t nW = (size_t)p.n * kDW;
-        const uint32_t *Fl = p.F + (size_t)l * nW;
-        uint32_t *Fn = p.F + (size_t)(l + 1) * nW;
-        const uint32_t *Vin = p.V + (size_t)(l & 1) * nW;
-        uint32_t *Vout = p.V + (size_t)((l + 1) & 1) * nW;
-        uint32_t *ufn = p.ufr + (size_t)(l + 1) * p.nw32;
-        const bool valid_src = b < p.nb;
+        const uint32_t *Fl = Fb + (size_t)l * nW;
+        uint32_t *Fn = Fb + (size_t)(l + 1) * nW;
+        const uint32_t *Vin = Vb + (size_t)(l & 1) * nW;
+        uint32_t *Vout = Vb + (size_t)((l + 1) & 1) * nW;
+        uint32_t *ufn = ufb + (size_t)(l + 1) * p.nw32;
+        const bool valid_src = b < nbv;
         bool ovf = false, produced = false;
         unsigned long long maxsig = 0, remaining = 0;
         for (int c0 = 0; good && c0 < kNT; c0 += 16) {
@@ -320,8 +345,8 @@ __global__ void __launch_bounds__(128, 1)
                 const bool seen = (vis >> lane) & 1u;
                 const bool hit = valid_src && !seen && (lo[i] | hi[i]) != 0ull;
                 if (hit) {
-                    p.sigma[(size_t)v * kDB + b] = lo[i];
-                    p.lvl[(size_t)v * kDB + b] = (uint16_t)(l + 1);
+                    sigma[(size_t)v * kDB + b] = lo[i];
+                    lvl[(size_t)v * kDB + b] = (uint16_t)(l + 1);
                     ovf |= hi[i] != 0u;
                     maxsig = lo[i] > maxsig ? lo[i] : maxsig;
                 }
@@ -343,9 +368,10 @@ __global__ void __launch_bounds__(128, 1)
                 remaining += __shfl_xor_sync(0xffffffffu, remaining, off);
             }
             if (lane == 0) {
-                if (produced) atomicOr(&p.dctl->produced, 1u);
-                if (maxsig) atomicMax(&p.dctl->maxsig, maxsig);
-                if (remaining) atomicAdd(&p.dctl->remaining, remaining);
+                DenseCtl *dc = p.dctl + bb;
+                if (produced) atomicOr(&dc->produced, 1u);
+                if (maxsig) atomicMax(&dc->maxsig, maxsig);
+                if (remaining) atomicAdd(&dc->remaining, remaining);
             }
         }
     }
@@ -360,13 +386,16 @@ __global__ void __launch_bounds__(128, 1)
 __global__ void __launch_bounds__(256) k_dense_limbs(const DenseParams p, const int l, const int nl) {
     __shared__ uint64_t tile[32][kDB + 1];
     const int u0 = blockIdx.x * 32;
+    const int bb = p.blist[blockIdx.y];
+    const uint64_t *sigma = p.sigma + (size_t)bb * p.sig_stride;
+    __nv_bfloat16 *X = p.X + (size_t)bb * p.xrows * p.npad;
     const size_t nW = (size_t)p.n * kDW;
-    const uint32_t *Fl = p.F + (size_t)l * nW;
+    const uint32_t *Fl = p.F + (size_t)bb * p.f_stride + (size_t)l * nW;
     for (int i = threadIdx.x; i < 32 * kDB; i += 256) {
         const int uu = i / kDB, b = i % kDB;
         const int u = u0 + uu;
         uint64_t s = 0;
-        if (u < p.n && ((__ldg(Fl + (size_t)u * kDW + (b >> 5)) >> (b & 31)) & 1u)) s = p.sigma[(size_t)u * kDB + b];
+        if (u < p.n && ((__ldg(Fl + (size_t)u * kDW + (b >> 5)) >> (b & 31)) & 1u)) s = sigma[(size_t)u * kDB + b];
         tile[uu][b] = s;
     }
     __syncthreads();
@@ -374,7 +403,7 @@ __global__ void __launch_bounds__(256) k_dense_limbs(const DenseParams p, const 
         for (int i = threadIdx.x; i < 32 * kDB; i += 256) {
             const int b = i / 32, uu = i % 32;
             const unsigned byte = (unsigned)((tile[uu][b] >> (8 * q)) & 0xFFu);
-            p.X[((size_t)q * kDB + b) * p.npad + u0 + uu] = __float2bfloat16_rn((float)byte);
+            X[((size_t)q * kDB + b) * p.npad + u0 + uu] = __float2bfloat16_rn((float)byte);
         }
     }
 }
@@ -382,21 +411,35 @@ __global__ void __launch_bounds__(256) k_dense_limbs(const DenseParams p, const 
 // Split masked c rows of the deepest level L (c_s(v) = 1 / sigma_s(v) there:
 // nothing depends on the farthest vertices, Lemma 3.3): rows xout + q*128 + b
 // hold part q (hi, mid, lo) of c, 0 for the pairs not at level L.
-__global__ void __launch_bounds__(256) k_dense_bwd_last(const DenseParams p, const int L, const int xout) {
+__global__ void __launch_bounds__(256) k_dense_bwd_last(const DenseParams p) {
     const int v = blockIdx.x * 2 + (threadIdx.x >> 7);
     const int b = threadIdx.x & 127;
-    if (v >= p.n) return;
+    const int bb = blockIdx.y;
+    const int L = p.depth[bb];
+    if (v >= p.n || L < 1) return;
     const size_t nW = (size_t)p.n * kDW;
+    const uint32_t *FL = p.F + (size_t)bb * p.f_stride + (size_t)L * nW;
     float c = 0.0f;
-    if (b < p.nb && ((p.F[(size_t)L * nW + (size_t)v * kDW + (b >> 5)] >> (b & 31)) & 1u))
-        c = 1.0f / __ull2float_rn(p.sigma[(size_t)v * kDB + b]);
+    if (b < p.nbs[bb] && ((FL[(size_t)v * kDW + (b >> 5)] >> (b & 31)) & 1u))
+        c = 1.0f / __ull2float_rn(p.sigma[(size_t)bb * p.sig_stride + (size_t)v * kDB + b]);
     const __nv_bfloat16 h = __float2bfloat16_rn(c);
     const float r1 = c - __bfloat162float(h);
     const __nv_bfloat16 m = __float2bfloat16_rn(r1);
     const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(m));
-    p.X[((size_t)xout + b) * p.npad + v] = h;
-    p.X[((size_t)xout + kDB + b) * p.npad + v] = m;
-    p.X[((size_t)xout + 2 * kDB + b) * p.npad + v] = lo;
+    const size_t xr = (size_t)bb * p.xrows + b;  // block 0 holds level L
+    p.X[xr * p.npad + v] = h;
+    p.X[(xr + kDB) * p.npad + v] = m;
+    p.X[(xr + 2 * kDB) * p.npad + v] = lo;
+}
+
+// BC of a group: bc[v] += sum_b bcpart[b][v], batches in order.
+__global__ void __launch_bounds__(256) k_dense_bc_reduce(const double *__restrict__ part, int nbatch, int n,
+                                                         double *__restrict__ bc) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int b = 0; b < nbatch; ++b) acc += part[(size_t)b * n + v];
+        bc[v] += acc;
+    }
 }
 
 // Dense 0/1 adjacency in bf16 from the CSR (rows beyond n and columns beyond
@@ -452,40 +495,47 @@ int dense_build_adjacency(const int32_t *row_ptr, const int32_t *col, int32_t n,
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int dense_make_maps(DenseMaps *maps, __nv_bfloat16 *X, __nv_bfloat16 *A, int32_t npad) {
-    if (!make_map(&maps->x, X, (uint64_t)npad, (uint64_t)kDenseMaxLimbs * kDB, kDB)) return -1;
+int dense_make_maps(DenseMaps *maps, __nv_bfloat16 *X, uint64_t xrows_total, __nv_bfloat16 *A, int32_t npad) {
+    if (!make_map(&maps->x, X, (uint64_t)npad, xrows_total, kDB)) return -1;
     if (!make_map(&maps->a, A, (uint64_t)npad, (uint64_t)npad, kNT)) return -1;
     return 0;
 }
 
 int dense_launch_level(const DenseMaps &maps, const DenseParams &p, int l, int nl, cudaStream_t st) {
+    if (p.nactive <= 0) return 0;
     const int stages = dense_stages(nl);
     const size_t smem = dense_smem_bytes(nl, stages);
     if (cudaFuncSetAttribute(k_dense_level<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return -1;
-    k_dense_limbs<<<(p.n + 31) / 32, 256, 0, st>>>(p, l, nl);
-    k_dense_level<false><<<p.npad / kNT, 128, smem, st>>>(maps.x, maps.a, p, l, nl, stages, 0, 0, 0);
+    k_dense_limbs<<<dim3((p.n + 31) / 32, p.nactive), 256, 0, st>>>(p, l, nl);
+    k_dense_level<false><<<p.nactive * (p.npad / kNT), 128, smem, st>>>(maps.x, maps.a, p, l, nl, stages, 0);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int dense_launch_backward(const DenseMaps &maps, const DenseParams &p, int L, cudaStream_t st) {
-    if (L < 1) return 0;
+int dense_launch_bwd_last(const DenseParams &p, int nbatch, cudaStream_t st) {
+    if (nbatch <= 0 || p.n <= 0) return 0;
+    k_dense_bwd_last<<<dim3((p.n + 1) / 2, nbatch), 256, 0, st>>>(p);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int dense_launch_bwd_level(const DenseMaps &maps, const DenseParams &p, int l, cudaStream_t st) {
+    if (p.nactive <= 0) return 0;
     constexpr int kParts = 3;
     const int stages = dense_stages(kParts);
     const size_t smem = dense_smem_bytes(kParts, stages);
     if (cudaFuncSetAttribute(k_dense_level<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return -1;
-    int cur = 0, nxt = kParts * kDB;  // two row blocks of X alternate between levels
-    k_dense_bwd_last<<<(p.n + 1) / 2, 256, 0, st>>>(p, L, cur);
-    for (int l = L - 1; l >= 1; --l) {
-        k_dense_level<true><<<p.npad / kNT, 128, smem, st>>>(maps.x, maps.a, p, l, kParts, stages, cur, nxt,
-                                                              l > 1 ? 1 : 0);
-        const int t = cur;
-        cur = nxt;
-        nxt = t;
-    }
+    k_dense_level<true><<<p.nactive * (p.npad / kNT), 128, smem, st>>>(maps.x, maps.a, p, l, kParts, stages,
+                                                                        l > 1 ? 1 : 0);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int dense_reduce_bc(const double *bcpart, int nbatch, int n, double *bc, cudaStream_t st) {
+    if (n <= 0 || nbatch <= 0) return 0;
+    const int g = (n + 255) / 256;
+    k_dense_bc_reduce<<<g < 1024 ? g : 1024, 256, 0, st>>>(bcpart, nbatch, n, bc);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -21,26 +21,47 @@ struct DenseCtl {
     unsigned long long remaining;  // (source, vertex) pairs still unreached
 };
 
+// A group of batches processed level by level in lockstep: every batch keeps
+// its own state slice (batch b at offset b * stride), one launch per level
+// covers (active batch, 64-vertex tile) pairs.
 struct DenseParams {
-    int32_t n, npad, nb, nw32;
-    uint64_t *sigma;  // [n][128]
-    uint16_t *lvl;    // [n][128]
+    int32_t n, npad, nw32, Lcap;
+    int32_t nactive;        // batches in this launch (blist[0 .. nactive))
+    int32_t group;          // batches that share each adjacency tile in turn (L2 reuse)
+    const int32_t *blist;   // active batch ids
+    const int32_t *nbs;     // valid sources of each batch (<= 128)
+    const int32_t *depth;   // backward: depth L of each batch
+    size_t sig_stride;      // sigma / lvl: n * 128
+    size_t f_stride;        // F: Lcap * n * 4
+    size_t v_stride;        // V: 2 * n * 4
+    size_t u_stride;        // ufr: Lcap * nw32
+    int32_t xrows;          // X rows per batch
+    uint64_t *sigma;        // [batch][n][128]
+    uint16_t *lvl;          // [batch][n][128]
     uint32_t *F, *V, *ufr;
-    __nv_bfloat16 *X;  // [8 * 128][npad] limb matrix (backward: two blocks of 3 * 128 split rows)
-    double *bc;
+    __nv_bfloat16 *X;       // [batch][xrows][npad]: limb rows (forward) or two blocks of 3 x 128 split rows
+    double *bcpart;         // [batch][n] BC contributions of each batch (added in batch order later)
     DevCtl *ctl;
-    DenseCtl *dctl;
+    DenseCtl *dctl;         // [batch]
 };
 
 struct DenseMaps {
     CUtensorMap x, a;
 };
 
+constexpr int kDenseXRows = kDenseMaxLimbs * 128;  // X rows per batch (>= 2 x 3 x 128 for the backward)
+
 int dense_build_adjacency(const int32_t *row_ptr, const int32_t *col, int32_t n, int32_t npad, __nv_bfloat16 *A,
                           cudaStream_t st);
-int dense_make_maps(DenseMaps *maps, __nv_bfloat16 *X, __nv_bfloat16 *A, int32_t npad);
+// Maps for X ([xrows_total][npad]) and A ([npad][npad]).
+int dense_make_maps(DenseMaps *maps, __nv_bfloat16 *X, uint64_t xrows_total, __nv_bfloat16 *A, int32_t npad);
+// Forward level l -> l+1 for the p.nactive batches of p.blist (limbs, then the product).
 int dense_launch_level(const DenseMaps &maps, const DenseParams &p, int l, int nl, cudaStream_t st);
-// Backward levels L-1 .. 1 on the tensor cores (BC accumulated into p.bc).
-int dense_launch_backward(const DenseMaps &maps, const DenseParams &p, int L, cudaStream_t st);
+// Split c rows of each batch's deepest level (batches 0 .. nbatch).
+int dense_launch_bwd_last(const DenseParams &p, int nbatch, cudaStream_t st);
+// Backward level l for the p.nactive batches with depth > l (BC into p.bcpart).
+int dense_launch_bwd_level(const DenseMaps &maps, const DenseParams &p, int l, cudaStream_t st);
+// bc[v] += sum over batches 0 .. nbatch of bcpart[b][v], in batch order.
+int dense_reduce_bc(const double *bcpart, int nbatch, int n, double *bc, cudaStream_t st);
 
 }  // namespace bcgb
