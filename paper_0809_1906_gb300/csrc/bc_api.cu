@@ -493,7 +493,7 @@ int ensure_dense(bc_graph *g, cudaStream_t st) {
     if (g->weighted) return fail(BC_ERR_UNSUPPORTED, "BC_DENSE needs an unweighted graph");
     if (g->directed) return fail(BC_ERR_UNSUPPORTED, "BC_DENSE needs an undirected graph");
     if (g->n > bcgb::kDenseMaxN) return fail(BC_ERR_UNSUPPORTED, "BC_DENSE supports n <= 65536");
-    const int32_t npad = std::max(64, (g->n + 63) / 64 * 64);
+    const int32_t npad = std::max(128, (g->n + 127) / 128 * 128);  // whole 128-vertex tiles
     CK(g->dA.ensure((size_t)npad * npad));
     if (bcgb::dense_build_adjacency(g->row_ptr.p, g->col.p, g->n, npad, g->dA.p, st))
         return fail(BC_ERR_CUDA, "dense adjacency build failed");

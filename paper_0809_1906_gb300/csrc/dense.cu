@@ -42,10 +42,13 @@ namespace {
 
 constexpr int kDB = 128;          // sources per batch (GEMM M)
 constexpr int kDW = kDB / 32;     // frontier words per vertex
-constexpr int kNT = 64;           // target vertices per CTA (GEMM N)
+constexpr int kNT = 64;           // target vertices per CTA (GEMM N) of the narrow tile
+constexpr int kNW = 128;          // of the wide tile
 constexpr int kKT = 64;           // K per pipeline stage (128 bytes of bf16)
 constexpr int kXTile = kDB * kKT * 2;  // 16 KiB: one limb's operand tile
-constexpr int kATile = kNT * kKT * 2;  // 8 KiB: adjacency tile
+// adjacency tile of an N-vertex CTA: N rows of 128 bytes
+template <int kN>
+constexpr int a_tile() { return kN * kKT * 2; }
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -102,16 +105,19 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 // Instruction descriptor, kind::f16: FP32 accumulator, bf16 A and B, both
-// K-major, N = 64, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kNT >> 3) << 17) |
-                            ((uint32_t)(kDB >> 4) << 24);
+// K-major, M = 128, N = kN.
+template <int kN>
+constexpr uint32_t idesc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(kDB >> 4) << 24);
+}
 
+template <int kN>
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc)
+        "l"(adesc), "l"(bdesc), "r"(idesc<kN>()), "r"(acc)
         : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
@@ -136,13 +142,13 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 //               c for level l, adds the batch's delta to BC (FP64, fixed
 //               order) and, when write_next, writes the split c rows of level l
 //               at rows xout .. xout + 383.
-template <bool kBwd>
+template <bool kBwd, int kN>
 __global__ void __launch_bounds__(128, 1)
     k_dense_level(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmA, const DenseParams p,
                   const int l, const int nl, const int stages, const int write_next) {
     extern __shared__ unsigned char dsm_raw[];
     unsigned char *dsm = reinterpret_cast<unsigned char *>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
-    const int stage_bytes = nl * kXTile + kATile;
+    const int stage_bytes = nl * kXTile + a_tile<kN>();
     uint64_t *bars = reinterpret_cast<uint64_t *>(dsm + (size_t)stages * stage_bytes);
     uint64_t *full = bars;
     uint64_t *empty = bars + stages;
@@ -154,7 +160,7 @@ __global__ void __launch_bounds__(128, 1)
     // CTA -> (batch, 64-vertex tile): groups of p.group batches walk the
     // vertex tiles together, so each adjacency tile is read by p.group
     // batches in turn while it is in L2, and each batch's limb rows stay hot
-    const int NV = p.npad / kNT;
+    const int NV = p.npad / kN;
     const int per = p.group * NV;
     const int bg = blockIdx.x / per;
     const int gbase = bg * p.group;
@@ -162,7 +168,7 @@ __global__ void __launch_bounds__(128, 1)
     const int within = blockIdx.x - bg * per;
     const int vt = within / gsz;
     const int bb = p.blist[gbase + (within - vt * gsz)];
-    const int v0 = vt * kNT;
+    const int v0 = vt * kN;
     uint64_t *const sigma = p.sigma + (size_t)bb * p.sig_stride;
     uint16_t *const lvl = p.lvl + (size_t)bb * p.sig_stride;
     uint32_t *const Fb = p.F + (size_t)bb * p.f_stride;
@@ -178,7 +184,7 @@ __global__ void __launch_bounds__(128, 1)
     const int xrow0 = bb * p.xrows + xin;
     const int nk = p.npad / kKT;
     uint32_t ncols = 32;
-    while (ncols < (uint32_t)(nl * kNT)) ncols <<= 1;
+    while (ncols < (uint32_t)(nl * kN)) ncols <<= 1;
 
     if (tid == 0) {
         s_err = 0u;
@@ -236,7 +242,7 @@ __global__ void __launch_bounds__(128, 1)
                 const uint32_t xbase = smem_u32(st + (size_t)q * kXTile);
 #pragma unroll
                 for (int kk = 0; kk < kKT / 16; ++kk)
-                    umma_bf16(tmem + (uint32_t)(q * kNT), sw128_desc(xbase + kk * 32), sw128_desc(abase + kk * 32),
+                    umma_bf16<kN>(tmem + (uint32_t)(q * kN), sw128_desc(xbase + kk * 32), sw128_desc(abase + kk * 32),
                               (it > 0 || kk > 0) ? 1u : 0u);
             }
             umma_commit(empty + s);  // frees the stage once these MMAs have read it
@@ -257,13 +263,13 @@ __global__ void __launch_bounds__(128, 1)
         const size_t nW = (size_t)p.n * kDW;
         const uint32_t *Fl = Fb + (size_t)l * nW;
         const bool valid_src = b < nbv;
-        for (int c0 = 0; good && c0 < kNT; c0 += 16) {
+        for (int c0 = 0; good && c0 < kN; c0 += 16) {
             float S[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) S[i] = 0.0f;
             for (int q = 0; q < nl; ++q) {  // hi + mid + lo, in this order
                 uint32_t r[16];
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * kNT + c0), r);
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * kN + c0), r);
                 tmem_wait_ld();
 #pragma unroll
                 for (int i = 0; i < 16; ++i) S[i] += __uint_as_float(r[i]);
@@ -313,7 +319,7 @@ __global__ void __launch_bounds__(128, 1)
         const bool valid_src = b < nbv;
         bool ovf = false, produced = false;
         unsigned long long maxsig = 0, remaining = 0;
-        for (int c0 = 0; good && c0 < kNT; c0 += 16) {
+        for (int c0 = 0; good && c0 < kN; c0 += 16) {
             uint64_t lo[16];
             uint32_t hi[16];
     #pragma unroll
@@ -323,7 +329,7 @@ __global__ void __launch_bounds__(128, 1)
             }
             for (int q = 0; q < nl; ++q) {
                 uint32_t r[16];
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * kNT + c0), r);
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * kN + c0), r);
                 tmem_wait_ld();
     #pragma unroll
                 for (int i = 0; i < 16; ++i) {
@@ -478,14 +484,16 @@ bool make_map(CUtensorMap *m, void *base, uint64_t inner, uint64_t rows, uint32_
 
 }  // namespace
 
+template <int kN>
 int dense_stages(int nl) {
     const int budget = 200 * 1024;
-    const int s = budget / (nl * kXTile + kATile);
+    const int s = budget / (nl * kXTile + a_tile<kN>());
     return s < 1 ? 1 : (s > 8 ? 8 : s);
 }
 
+template <int kN>
 size_t dense_smem_bytes(int nl, int stages) {
-    return (size_t)stages * (nl * kXTile + kATile) + 1024 + (2 * stages + 2) * sizeof(uint64_t) + 64;
+    return (size_t)stages * (nl * kXTile + a_tile<kN>()) + 1024 + (2 * stages + 2) * sizeof(uint64_t) + 64;
 }
 
 int dense_build_adjacency(const int32_t *row_ptr, const int32_t *col, int32_t n, int32_t npad, __nv_bfloat16 *A,
@@ -498,19 +506,29 @@ int dense_build_adjacency(const int32_t *row_ptr, const int32_t *col, int32_t n,
 int dense_make_maps(DenseMaps *maps, __nv_bfloat16 *X, uint64_t xrows_total, __nv_bfloat16 *A, int32_t npad) {
     if (!make_map(&maps->x, X, (uint64_t)npad, xrows_total, kDB)) return -1;
     if (!make_map(&maps->a, A, (uint64_t)npad, (uint64_t)npad, kNT)) return -1;
+    if (!make_map(&maps->a_wide, A, (uint64_t)npad, (uint64_t)npad, kNW)) return -1;
     return 0;
+}
+
+// A CTA covers kNW = 128 vertices when the limb accumulators fit TMEM
+// (nl * 128 <= 512 columns), else kNT = 64.
+template <bool kBwd, int kN>
+int launch_level_t(const DenseMaps &maps, const DenseParams &p, int l, int nl, int write_next, cudaStream_t st) {
+    const int stages = dense_stages<kN>(nl);
+    const size_t smem = dense_smem_bytes<kN>(nl, stages);
+    if (cudaFuncSetAttribute(k_dense_level<kBwd, kN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return -1;
+    k_dense_level<kBwd, kN><<<p.nactive * (p.npad / kN), 128, smem, st>>>(maps.x, kN == kNW ? maps.a_wide : maps.a,
+                                                                          p, l, nl, stages, write_next);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int dense_launch_level(const DenseMaps &maps, const DenseParams &p, int l, int nl, cudaStream_t st) {
     if (p.nactive <= 0) return 0;
-    const int stages = dense_stages(nl);
-    const size_t smem = dense_smem_bytes(nl, stages);
-    if (cudaFuncSetAttribute(k_dense_level<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return -1;
     k_dense_limbs<<<dim3((p.n + 31) / 32, p.nactive), 256, 0, st>>>(p, l, nl);
-    k_dense_level<false><<<p.nactive * (p.npad / kNT), 128, smem, st>>>(maps.x, maps.a, p, l, nl, stages, 0);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    if (nl * kNW <= 512) return launch_level_t<false, kNW>(maps, p, l, nl, 0, st);
+    return launch_level_t<false, kNT>(maps, p, l, nl, 0, st);
 }
 
 int dense_launch_bwd_last(const DenseParams &p, int nbatch, cudaStream_t st) {
@@ -521,15 +539,7 @@ int dense_launch_bwd_last(const DenseParams &p, int nbatch, cudaStream_t st) {
 
 int dense_launch_bwd_level(const DenseMaps &maps, const DenseParams &p, int l, cudaStream_t st) {
     if (p.nactive <= 0) return 0;
-    constexpr int kParts = 3;
-    const int stages = dense_stages(kParts);
-    const size_t smem = dense_smem_bytes(kParts, stages);
-    if (cudaFuncSetAttribute(k_dense_level<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return -1;
-    k_dense_level<true><<<p.nactive * (p.npad / kNT), 128, smem, st>>>(maps.x, maps.a, p, l, kParts, stages,
-                                                                        l > 1 ? 1 : 0);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return launch_level_t<true, kNW>(maps, p, l, 3, l > 1 ? 1 : 0, st);  // hi, mid, lo parts
 }
 
 int dense_reduce_bc(const double *bcpart, int nbatch, int n, double *bc, cudaStream_t st) {

@@ -46,7 +46,7 @@ struct DenseParams {
 };
 
 struct DenseMaps {
-    CUtensorMap x, a;
+    CUtensorMap x, a, a_wide;  // adjacency boxes of 64 and 128 rows
 };
 
 constexpr int kDenseXRows = kDenseMaxLimbs * 128;  // X rows per batch (>= 2 x 3 x 128 for the backward)
