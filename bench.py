@@ -306,7 +306,7 @@ def run_extra(args):
                             "dag_arcs_per_source": arcs / 4096,
                             "subgrid64_all_sources": {"n": sub.n, "m": sub.m, "ms": ms_sub,
                                                       "value": sub.n * sub.m / (ms_sub / 1e3)}},
-                    roofline={"bound": "hbm", "kernel": "k_wsssp", "achieved": achieved, "peak": hbm,
+                    roofline={"bound": "hbm", "kernel": "k_wsssp_packed", "achieved": achieved, "peak": hbm,
                               "unit": "GB/s", "frac": achieved / hbm, "peak_source": hbm_kind, "traffic": None},
                     cpu_baseline=_oracle_rate(g, srcn, args.cpu_seconds))
     elif wl == "gnp":
