@@ -93,7 +93,7 @@ extern "C" {
                                 directed or not; not with BC_PLAIN / BC_DENSE. */
 #define BC_KEEP_ORDER 0x80u  /* batch the sources in the order given. By default (unweighted, batched,
                                 more than 32 sources) batches are formed from the sources sorted by
-                                their BFS distances to 16 landmark vertices, so the sources of one
+                                their BFS distances to 32 landmark vertices, so the sources of one
                                 32-source word have similar distance profiles and the level sweep
                                 fetches fewer rows; BC differs only by FP64 summation order, and
                                 per-source summaries keep the caller's order. */

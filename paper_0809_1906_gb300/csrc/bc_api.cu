@@ -783,7 +783,7 @@ int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStr
 // Distances from the landmarks (one W = 1 batch of the forward sweep, rows
 // copied back), then the counting sorts; once per graph.
 int ensure_rank(bc_graph *g, cudaStream_t st) {
-    constexpr int kLandmarks = 16;
+    constexpr int kLandmarks = 32;  // one full 32-source batch of the forward sweep
     if ((int32_t)g->rank.size() == g->n || g->n <= 32) return BC_OK;
     const int32_t n = g->n;
     const auto &rp = g->h_row_ptr;
