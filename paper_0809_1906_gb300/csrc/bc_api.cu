@@ -103,8 +103,7 @@ struct bc_graph {
 
     // multi-source batch state for (W, Lcap)
     int32_t W = 0, Lcap = 0;
-    DevBuf<uint64_t> sigma, part, hpart;
-    DevBuf<uint16_t> lvl;
+    DevBuf<uint64_t> sigma, part;
     DevBuf<float> cval;
     DevBuf<uint16_t> Smask;
     DevBuf<uint32_t> wideflags, F, ufr, V, pmask, cnt;
@@ -146,7 +145,6 @@ struct bc_graph {
     double dense_flops = 0.0;
     int32_t gNB = 0, gLcap = 0;  // group capacity (batches) and its level capacity
     DevBuf<uint64_t> gsigma;
-    DevBuf<uint16_t> glvl;
     DevBuf<uint32_t> gF, gV, gufr;
     DevBuf<double> gbcpart;
     DevBuf<int32_t> gmeta;  // [3][gNB]: active list, valid sources, depth
@@ -173,7 +171,6 @@ void free_graph(bc_graph *g) {
     g->fplan.release();
     g->bplan.release();
     g->sigma.release();
-    g->lvl.release();
     g->Smask.release();
     g->wideflags.release();
     g->part.release();
@@ -181,7 +178,6 @@ void free_graph(bc_graph *g) {
     for (auto *b : {&g->F, &g->ufr, &g->V, &g->pmask, &g->cnt}) b->release();
     g->mpW.release();
     g->gsigma.release();
-    g->glvl.release();
     for (auto *b : {&g->gF, &g->gV, &g->gufr}) b->release();
     g->gbcpart.release();
     g->gmeta.release();
@@ -330,13 +326,6 @@ int ensure_state(bc_graph *g, int W, int Lcap) {
     const size_t B = 32 * (size_t)W;
     const size_t nw32 = (n + 31) / 32;
     CK(g->sigma.ensure(n * B));
-    CK(g->lvl.ensure(n * B));
-    {
-        int dev = 0, sms = 1;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        CK(g->hpart.ensure((size_t)(8 * sms + 1) * 4 * B));  // per-block summary partials
-    }
     CK(g->Smask.ensure(2 * n * B));
     CK(g->wideflags.ensure((size_t)Lcap));
     CK(g->cval.ensure(2 * n * B));
@@ -405,8 +394,6 @@ bcgb::MsParams make_params(bc_graph *g) {
     p.sigma = g->sigma.p;
     p.S = g->Smask.p;
     p.wide = g->wideflags.p;
-    p.lvl = g->lvl.p;
-    p.hpart = g->hpart.p;
     p.cval = g->cval.p;
     p.F = g->F.p;
     p.ufr = g->ufr.p;
@@ -507,7 +494,6 @@ int ensure_dense_group(bc_graph *g, int nb, int Lcap, cudaStream_t st) {
     if (g->gNB >= nb && g->gLcap == Lcap && g->gsigma.p) return BC_OK;
     const size_t n = (size_t)std::max(g->n, 1), nw32 = (n + 31) / 32;
     CK(g->gsigma.ensure((size_t)nb * n * 128));
-    CK(g->glvl.ensure((size_t)nb * n * 128));
     CK(g->gF.ensure((size_t)nb * Lcap * n * 4));
     CK(g->gV.ensure((size_t)nb * 2 * n * 4));
     CK(g->gufr.ensure((size_t)nb * Lcap * nw32));
@@ -564,7 +550,6 @@ int run_dense_group(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream
             p.seq = ++g->seq;
             p.sources = g->sources.p + b0;
             p.sigma = g->gsigma.p + b * sstr;
-            p.lvl = g->glvl.p + b * sstr;
             p.F = g->gF.p + b * fstr;
             p.V = g->gV.p + b * vstr;
             p.ufr = g->gufr.p + b * ustr;
@@ -602,7 +587,6 @@ int run_dense_group(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream
         d.u_stride = ustr;
         d.xrows = bcgb::kDenseXRows;
         d.sigma = g->gsigma.p;
-        d.lvl = g->glvl.p;
         d.F = g->gF.p;
         d.V = g->gV.p;
         d.ufr = g->gufr.p;

@@ -7,7 +7,6 @@
 //   S      uint16 [2][n][B]     masked rows by level parity: sigma_s(v) where
 //                               d(s,v) = l, 0 for the other sources
 //   wide   uint32 [Lcap]        level l has a count >= 2^16 (S unusable there)
-//   lvl    uint16 [n][B]        d(s,v) for reached pairs (per-source summaries)
 //   cval   float  [2][n][B]     masked rows by level parity of
 //                               c_s(v) = (1 + delta_s*(v)) / sigma_s(v)
 //   F      uint32 [Lcap][n][W]  frontier bit of source b at level l (d(s_b, v) = l)
@@ -67,8 +66,6 @@ struct MsParams {
     const int32_t *slot_nch;    // number of chunks of that vertex
     const int32_t *sources;     // this batch's source ids [nb]
     uint64_t *sigma;
-    uint16_t *lvl;   // [n][B] level of each reached (vertex, source)
-    uint64_t *hpart; // [blocks][4][B] per-block partial summaries
     uint16_t *S;   // [2][n][B]
     uint32_t *wide;  // [Lcap]
     float *cval;   // [2][n][B]
@@ -95,7 +92,6 @@ void ms_launch_first(int W, const MsParams &p, cudaStream_t st);  // level 0 -> 
 void ms_launch_forward(int W, const MsParams &p, int level, cudaStream_t st);
 void ms_launch_backward(int W, const MsParams &p, int level, cudaStream_t st);
 void ms_launch_hash(int W, const MsParams &p, int nlevels, cudaStream_t st);
-int ms_hash_blocks(const MsParams &p);  // size of MsParams::hpart = blocks * 4 * B
 void ms_launch_rows(int W, const MsParams &p, int nlevels, uint64_t *sig_out, int32_t *dist_out,
                     cudaStream_t st);
 void launch_scale(double *x, int32_t n, double f, cudaStream_t st);

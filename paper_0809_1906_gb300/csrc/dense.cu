@@ -170,7 +170,6 @@ __global__ void __launch_bounds__(128, 1)
     const int bb = p.blist[gbase + (within - vt * gsz)];
     const int v0 = vt * kN;
     uint64_t *const sigma = p.sigma + (size_t)bb * p.sig_stride;
-    uint16_t *const lvl = p.lvl + (size_t)bb * p.sig_stride;
     uint32_t *const Fb = p.F + (size_t)bb * p.f_stride;
     uint32_t *const Vb = p.V + (size_t)bb * p.v_stride;
     uint32_t *const ufb = p.ufr + (size_t)bb * p.u_stride;
@@ -352,7 +351,6 @@ __global__ void __launch_bounds__(128, 1)
                 const bool hit = valid_src && !seen && (lo[i] | hi[i]) != 0ull;
                 if (hit) {
                     sigma[(size_t)v * kDB + b] = lo[i];
-                    lvl[(size_t)v * kDB + b] = (uint16_t)(l + 1);
                     ovf |= hi[i] != 0u;
                     maxsig = lo[i] > maxsig ? lo[i] : maxsig;
                 }

@@ -31,13 +31,12 @@ struct DenseParams {
     const int32_t *blist;   // active batch ids
     const int32_t *nbs;     // valid sources of each batch (<= 128)
     const int32_t *depth;   // backward: depth L of each batch
-    size_t sig_stride;      // sigma / lvl: n * 128
+    size_t sig_stride;      // sigma: n * 128
     size_t f_stride;        // F: Lcap * n * 4
     size_t v_stride;        // V: 2 * n * 4
     size_t u_stride;        // ufr: Lcap * nw32
     int32_t xrows;          // X rows per batch
     uint64_t *sigma;        // [batch][n][128]
-    uint16_t *lvl;          // [batch][n][128]
     uint32_t *F, *V, *ufr;
     __nv_bfloat16 *X;       // [batch][xrows][npad]: limb rows (forward) or two blocks of 3 x 128 split rows
     double *bcpart;         // [batch][n] BC contributions of each batch (added in batch order later)

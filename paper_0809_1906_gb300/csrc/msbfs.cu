@@ -28,6 +28,7 @@
 
 #include "bc_internal.cuh"
 #include "msbfs_body.cuh"
+#include "pdl.cuh"
 
 namespace bcgb {
 namespace {
@@ -37,10 +38,12 @@ constexpr int kWarps = kBlock / 32;
 constexpr unsigned kFull = 0xffffffffu;
 using body::load_row;
 using body::valid_word;
+using body::transpose32;
 
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
     constexpr int B = 32 * W;
+    pdl::enter();
     const size_t nW = (size_t)p.n * W;
     const size_t stride = (size_t)gridDim.x * kBlock;
     const size_t tid = (size_t)blockIdx.x * kBlock + threadIdx.x;
@@ -71,7 +74,6 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
         atomicOr(p.ufr + (s >> 5), 1u << (s & 31));
         p.sigma[(size_t)s * B + b] = 1ull;
         p.S[(size_t)s * B + b] = 1;
-        if (p.lvl) p.lvl[(size_t)s * B + b] = 0;
     }
     if (threadIdx.x == 0) {
         p.ctl->fwd_done = 0u;
@@ -91,6 +93,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_first(const MsParams p) {
     constexpr int B = 32 * W;
+    pdl::enter();
     __shared__ int s_off[kBlock + 1];
     __shared__ int s_wsum[kWarps];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -123,7 +126,6 @@ __global__ void __launch_bounds__(kBlock) k_first(const MsParams p) {
         atomicOr(F1 + (size_t)v * W + (b >> 5), 1u << (b & 31));
         atomicOr(uf1 + (v >> 5), 1u << (v & 31));
         p.sigma[(size_t)v * B + b] = 1ull;
-        if (p.lvl) p.lvl[(size_t)v * B + b] = 1;
     }
     __syncthreads();
     if (t != 0) return;
@@ -149,6 +151,7 @@ __global__ void __launch_bounds__(kBlock) k_first(const MsParams p) {
 template <int W>
 __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const int l) {
     constexpr int B = 32 * W;
+    pdl::enter();
     __shared__ uint32_t s_U[kWarps][32][W];  // unvisited words of the group's items
     __shared__ uint64_t s_bar[kWarps];
     __shared__ uint32_t s_qz[kWarps][32];
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
             body::fwd_sum<W, true, true>(p.col_f, beg, end, ufl, Fl, Sl, p.sigma, wide, ones, U, s_u[wib], s_nz[wib], lane,
                                          acc, nf, ovf, arcs, &ws);
             if (slot < 0) {
-                produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next, p.lvl, l + 1);
+                produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
                 continue;
             }
             uint64_t *pp = p.part + (size_t)slot * B + lane;
@@ -273,7 +276,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
                     nf[j] |= __ldcg(qm + j);
                 }
             }
-            produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next, p.lvl, l + 1);
+            produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
             if (lane == 0) p.cnt[first] = 0u;
         }
     }
@@ -325,6 +328,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
 template <int W>
 __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const int l) {
     constexpr int B = 32 * W;
+    pdl::enter();
     __shared__ uint32_t s_f[kWarps][32][W];  // level-l words of the group's items
     __shared__ int32_t s_v[kWarps][32];      // and their vertices
     __shared__ uint64_t s_bar[kWarps];
@@ -436,86 +440,94 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
     if (lane == 0 && ws.fail) atomicOr(&p.ctl->status, BC_STATUS_COPY_TIMEOUT);
 }
 
-// Per-source summaries. Thread t of a block owns source t % B and takes
-// every (256/B)-th vertex of the block's share; (v, s) counts when v was
-// reached (visited through level L-1, or in the last frontier), its level
-// is lvl[v][s]. Blocks write partial sums; k_hash_sum adds them in block
-// order.
+// Per-source summaries over tiles of 32 vertices x 32 sources: a warp keeps
+// one frontier word j (sources 32j .. 32j+31) and strides over the vertex
+// tiles. Lane k loads word j of vertex v0+k for the reached set (visited
+// through level L-1 or in frontier L) and for every frontier F[l], l <= L;
+// a 32x32 bit transpose gives lane s the 32-vertex mask of its own source.
+// Per level, the count of set bits and the sum of (v+1) over them (a popcount
+// of the mask and five popcounts weighted by the bits of the in-tile index)
+// give the distance terms; the path-count term adds sigma_s(v) (v+1) over the
+// reached vertices, one coalesced 8-byte load per vertex. All loads of a
+// tile are issued before any is used. Every sum is an integer mod 2^64, so
+// the block totals go straight into the outputs with atomic adds (the run
+// zeroes them first) and the result does not depend on the order of adds.
 template <int W>
-__global__ void __launch_bounds__(kBlock) k_hash(const MsParams p, const int L) {
+__global__ void __launch_bounds__(kBlock, 2) k_hash(const MsParams p, const int L) {
     constexpr int B = 32 * W;
-    constexpr int VS = kBlock / B;  // vertices per block step
-    const int s = threadIdx.x % B, vo = threadIdx.x / B;
-    const int j = s >> 5;
-    const uint32_t bit = 1u << (s & 31);
+    constexpr int kHL = 12;  // frontier levels loaded up front; deeper ones in a loop
+    pdl::enter();
+    __shared__ unsigned long long sh[4][B];
+    for (int i = threadIdx.x; i < 4 * B; i += kBlock) (&sh[0][0])[i] = 0ull;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int j = gw % W;                        // this warp's frontier word
+    const int tstride = gridDim.x * kWarps / W;  // warps per word
+    const int ntiles = (p.n + 31) / 32;
     const size_t nW = (size_t)p.n * W;
     const uint32_t *Vl = p.V + (size_t)(L & 1) * nW;
     const uint32_t *FL = p.F + (size_t)L * nW;
     uint64_t hs = 0, hd = 0, ds = 0, rc = 0;
-    // four vertices per step, their loads independent
-    for (int v0 = (blockIdx.x * VS + vo) * 4; v0 < p.n; v0 += gridDim.x * VS * 4) {
-        uint32_t r[4];
+    auto level_terms = [&](uint32_t word, int l, int v0) {
+        const uint32_t T = transpose32(word, lane);
+        const uint32_t c = (uint32_t)__popc(T);
+        // the sum of the in-tile indices k of the set bits, bit by bit of k
+        const uint32_t ks = (uint32_t)__popc(T & 0xAAAAAAAAu) + 2u * (uint32_t)__popc(T & 0xCCCCCCCCu) +
+                            4u * (uint32_t)__popc(T & 0xF0F0F0F0u) + 8u * (uint32_t)__popc(T & 0xFF00FF00u) +
+                            16u * (uint32_t)__popc(T & 0xFFFF0000u);
+        const uint64_t vsum = (uint64_t)c * (uint64_t)(v0 + 1) + (uint64_t)ks;  // sum of (v+1)
+        hd += (uint64_t)(l + 1) * vsum;
+        ds += (uint64_t)l * (uint64_t)c;
+    };
+    for (int t = gw / W; t < ntiles; t += tstride) {
+        const int v0 = 32 * t;
+        const int vk = v0 + lane;
+        const bool in = vk < p.n;
+        const size_t wk = (size_t)(in ? vk : 0) * W + j;
+        uint32_t fw[kHL];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int v = v0 + q;
-            r[q] = v < p.n ? ((__ldg(Vl + (size_t)v * W + j) | __ldg(FL + (size_t)v * W + j)) & bit) : 0u;
-        }
-        uint64_t sg[4], l[4];
+        for (int l = 0; l < kHL; ++l) fw[l] = (in && l <= L) ? __ldg(p.F + (size_t)l * nW + wk) : 0u;
+        const uint32_t rv = in ? (__ldg(Vl + wk) | __ldg(FL + wk)) : 0u;
+        const int nk = p.n - v0 < 32 ? p.n - v0 : 32;  // vertices in this tile
+        const uint64_t *sg = p.sigma + (size_t)v0 * B + 32 * j + lane;
+        uint64_t x[16];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int v = v0 + q;
-            sg[q] = r[q] ? __ldg(p.sigma + (size_t)v * B + s) : 0ull;
-            l[q] = r[q] ? (uint64_t)__ldg(p.lvl + (size_t)v * B + s) : 0ull;
-        }
+        for (int k = 0; k < 16; ++k) x[k] = k < nk ? __ldg(sg + (size_t)k * B) : 0ull;
+        const uint32_t R = transpose32(rv, lane);
+        rc += (uint64_t)__popc(R);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (!r[q]) continue;
-            const uint64_t vv = (uint64_t)(v0 + q + 1);
-            hs += sg[q] * vv;
-            hd += (l[q] + 1) * vv;
-            ds += l[q];
-            rc += 1ull;
-        }
+        for (int l = 0; l < kHL; ++l)
+            if (l <= L) level_terms(fw[l], l, v0);
+        for (int l = kHL; l <= L; ++l) level_terms(in ? __ldg(p.F + (size_t)l * nW + wk) : 0u, l, v0);
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if ((R >> k) & 1u) hs += x[k] * (uint64_t)(v0 + k + 1);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) x[k] = 16 + k < nk ? __ldg(sg + (size_t)(16 + k) * B) : 0ull;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if ((R >> (16 + k)) & 1u) hs += x[k] * (uint64_t)(v0 + 16 + k + 1);
     }
-    __shared__ uint64_t sh[4][kBlock];
-    sh[0][threadIdx.x] = hs;
-    sh[1][threadIdx.x] = hd;
-    sh[2][threadIdx.x] = ds;
-    sh[3][threadIdx.x] = rc;
+    atomicAdd(&sh[0][32 * j + lane], (unsigned long long)hs);
+    atomicAdd(&sh[1][32 * j + lane], (unsigned long long)hd);
+    atomicAdd(&sh[2][32 * j + lane], (unsigned long long)ds);
+    atomicAdd(&sh[3][32 * j + lane], (unsigned long long)rc);
     __syncthreads();
-    if (threadIdx.x >= B) return;
-    for (int q = 0; q < 4; ++q) {
-        uint64_t acc = 0;
-        for (int k = 0; k < VS; ++k) acc += sh[q][k * B + threadIdx.x];
-        p.hpart[((size_t)blockIdx.x * 4 + q) * B + threadIdx.x] = acc;
+    for (int b = threadIdx.x; b < p.nb; b += kBlock) {
+        const int o = p.out_index ? p.out_index[b] : b;
+        atomicAdd(reinterpret_cast<unsigned long long *>(p.h_sigma + o), sh[0][b]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(p.h_dist + o), sh[1][b]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(p.dist_sum + o), sh[2][b]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(p.reach + o), sh[3][b]);
     }
-}
-
-// One warp per (quantity, source): lanes add strided block partials, then a
-// fixed butterfly, so the sum order never changes.
-template <int W>
-__global__ void k_hash_sum(const MsParams p, const int blocks) {
-    constexpr int B = 32 * W;
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    const int q = w / B, s = w % B;
-    if (q >= 4 || s >= p.nb) return;
-    uint64_t acc = 0;
-    for (int k = lane; k < blocks; k += 32) acc += __ldg(p.hpart + ((size_t)k * 4 + q) * B + s);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
-    if (lane != 0) return;
-    const int o = p.out_index ? p.out_index[s] : s;
-    if (q == 0) p.h_sigma[o] = acc;
-    if (q == 1) p.h_dist[o] = acc;
-    if (q == 2) p.dist_sum[o] = (int64_t)acc;
-    if (q == 3) p.reach[o] = (int64_t)acc;
 }
 
 // Rows of the forward pass for bc_forward_rows: out[b][v] for this batch.
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_rows(const MsParams p, const int L, uint64_t *sig_out,
                                                  int32_t *dist_out) {
+    pdl::enter();
     constexpr int B = 32 * W;
     const size_t nW = (size_t)p.n * W;
     const size_t total = (size_t)p.n * B;
@@ -589,7 +601,7 @@ void launch_init_t(const MsParams &p, cudaStream_t st) {
     const size_t work = (size_t)p.n * W;
     int g = (int)((work + kBlock - 1) / kBlock);
     g = g < 1 ? 1 : (g > 8 * sm_count() ? 8 * sm_count() : g);
-    k_init<W><<<g, kBlock, 0, st>>>(p);
+    pdl::launch(k_init<W>, g, kBlock, 0, st, p);
 }
 
 }  // namespace
@@ -611,37 +623,35 @@ void ms_launch_init(int W, const MsParams &p, cudaStream_t st) {
 
 void ms_launch_first(int W, const MsParams &p, cudaStream_t st) {
     if (p.nb == 0) return;
-    BCGB_DISPATCH_W(W, (k_first<kW><<<2 * sm_count(), kBlock, 0, st>>>(p)));
+    BCGB_DISPATCH_W(W, pdl::launch(k_first<kW>, 2 * sm_count(), kBlock, 0, st, p));
 }
 
 void ms_launch_forward(int W, const MsParams &p, int level, cudaStream_t st) {
     if (p.nitems == 0) return;
     BCGB_DISPATCH_W(W, (fwd_attr<kW>(),
-                        k_forward<kW><<<item_blocks(p, k_forward<kW>, kFwdSmem), kBlock, kFwdSmem, st>>>(p, level)));
+                        pdl::launch(k_forward<kW>, item_blocks(p, k_forward<kW>, kFwdSmem), kBlock, kFwdSmem, st, p,
+                                    level)));
 }
 
 void ms_launch_backward(int W, const MsParams &p, int level, cudaStream_t st) {
     if (p.nitems == 0) return;
     BCGB_DISPATCH_W(W, (bwd_attr<kW>(),
-                        k_backward<kW><<<item_blocks(p, k_backward<kW>, kBwdSmem), kBlock, kBwdSmem, st>>>(p, level)));
-}
-
-int ms_hash_blocks(const MsParams &p) {
-    int g = 8 * sm_count();
-    const int need = (p.n + 31) / 32;
-    return g < need ? g : (need < 1 ? 1 : need);
+                        pdl::launch(k_backward<kW>, item_blocks(p, k_backward<kW>, kBwdSmem), kBlock, kBwdSmem, st, p,
+                                    level)));
 }
 
 void ms_launch_hash(int W, const MsParams &p, int nlevels, cudaStream_t st) {
-    const int g = ms_hash_blocks(p);
-    BCGB_DISPATCH_W(W, (k_hash<kW><<<g, kBlock, 0, st>>>(p, nlevels)));
-    BCGB_DISPATCH_W(W, (k_hash_sum<kW><<<(4 * 32 * kW * 32 + kBlock - 1) / kBlock, kBlock, 0, st>>>(p, g)));
+    const int units = ((p.n + 31) / 32) * W;  // (tile, word) pairs
+    const int need = (units + kWarps - 1) / kWarps;
+    const int cap = 2 * sm_count();            // one wave at the kernel's occupancy
+    const int g = need < 1 ? 1 : (need < cap ? need : cap);
+    BCGB_DISPATCH_W(W, pdl::launch(k_hash<kW>, g, kBlock, 0, st, p, nlevels));
 }
 
 void ms_launch_rows(int W, const MsParams &p, int nlevels, uint64_t *sig_out, int32_t *dist_out,
                     cudaStream_t st) {
     const int g = 4 * sm_count();
-    BCGB_DISPATCH_W(W, (k_rows<kW><<<g, kBlock, 0, st>>>(p, nlevels, sig_out, dist_out)));
+    BCGB_DISPATCH_W(W, pdl::launch(k_rows<kW>, g, kBlock, 0, st, p, nlevels, sig_out, dist_out));
 }
 
 void launch_scale(double *x, int32_t n, double f, cudaStream_t st) {

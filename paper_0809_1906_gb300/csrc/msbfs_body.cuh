@@ -545,21 +545,17 @@ __device__ __forceinline__ void bwd_sum(const int32_t *__restrict__ col, int beg
 // Sn: the masked level-(l+1) uint16 row buffer, written in full (zeros for
 // the sources v is not new for) when v joins some frontier. Returns whether
 // v joined; wide is set when one of its new counts needs more than 16 bits.
-// lvl (may be null): receives the new level lnext for the new pairs.
 template <int W>
 __device__ __forceinline__ bool store_next(uint64_t *sigma, uint16_t *Sn, uint32_t *Fn, uint32_t *ufn, int v,
                                            const uint64_t (&acc)[W], const uint32_t (&nf)[W], int lane,
-                                           bool &wide, uint16_t *lvl = nullptr, int lnext = 0) {
+                                           bool &wide) {
     constexpr int B = 32 * W;
     uint32_t any = 0;
 #pragma unroll
     for (int j = 0; j < W; ++j) {
         any |= nf[j];
         if (lane == j) Fn[(size_t)v * W + j] = nf[j];
-        if ((nf[j] >> lane) & 1u) {
-            sigma[(size_t)v * B + 32 * j + lane] = acc[j];
-            if (lvl) lvl[(size_t)v * B + 32 * j + lane] = (uint16_t)lnext;
-        }
+        if ((nf[j] >> lane) & 1u) sigma[(size_t)v * B + 32 * j + lane] = acc[j];
     }
     if (any != 0u) {
 #pragma unroll
