@@ -80,9 +80,12 @@ cudaError_t fetch(std::vector<T> &dst, const T *src, size_t count) {
 // than `chunk` arcs, which are split into chunks combining through slots.
 struct ItemPlan {
     int32_t chunk = 0, nitems = 0, nslots = 0;
-    DevBuf<int32_t> item_v, item_beg, item_end, item_slot, slot_first, slot_nch;
+    DevBuf<int32_t> blob;  // item_v, item_beg, item_end, item_slot [nitems], slot_first, slot_nch [nslots]
+    const int32_t *item_v = nullptr, *item_beg = nullptr, *item_end = nullptr, *item_slot = nullptr;
+    const int32_t *slot_first = nullptr, *slot_nch = nullptr;
     void release() {
-        for (auto *b : {&item_v, &item_beg, &item_end, &item_slot, &slot_first, &slot_nch}) b->release();
+        blob.release();
+        item_v = item_beg = item_end = item_slot = slot_first = slot_nch = nullptr;
         chunk = nitems = nslots = 0;
     }
 };
@@ -252,45 +255,62 @@ int check_graph(int32_t n, const std::vector<int32_t> &rp, const std::vector<int
 // which are split into chunks that combine through partial slots. Heavy
 // chunks come first, then vertices by descending degree.
 int build_items(bc_graph *g, ItemPlan &pl, int32_t chunk, const std::vector<int32_t> &rp) {
-    if (pl.chunk == chunk && pl.item_v.p) return BC_OK;
+    if (pl.chunk == chunk && pl.item_v) return BC_OK;
     const int32_t n = g->n;
-    std::vector<int32_t> iv, ib, ie, is, sf, sn;
-    std::vector<int32_t> light;
+    // items: the chunks of the split vertices (in vertex order), then the
+    // other vertices by decreasing degree (a stable counting sort: degree <= chunk)
+    int64_t nitems = 0, nslots = 0;
+    std::vector<int32_t> cnt((size_t)chunk + 2, 0);
     for (int32_t v = 0; v < n; ++v) {
         const int64_t deg = rp[v + 1] - rp[v];
-        const int64_t nch = std::max<int64_t>(1, (deg + chunk - 1) / chunk);
-        if (nch == 1) {
-            light.push_back(v);
-            continue;
-        }
-        const int32_t first = (int32_t)sf.size();
-        for (int64_t c = 0; c < nch; ++c) {
-            iv.push_back(v);
-            ib.push_back((int32_t)(rp[v] + c * chunk));
-            ie.push_back((int32_t)std::min<int64_t>(rp[v + 1], rp[v] + (c + 1) * chunk));
-            is.push_back((int32_t)sf.size());
-            sf.push_back(first);
-            sn.push_back((int32_t)nch);
+        if (deg > chunk) {
+            const int64_t nch = (deg + chunk - 1) / chunk;
+            nitems += nch;
+            nslots += nch;
+        } else {
+            ++cnt[(size_t)(chunk - deg) + 1];
+            ++nitems;
         }
     }
-    std::stable_sort(light.begin(), light.end(),
-                     [&](int32_t a, int32_t b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
-    for (int32_t v : light) {
-        iv.push_back(v);
-        ib.push_back(rp[v]);
-        ie.push_back(rp[v + 1]);
-        is.push_back(-1);
+    for (size_t x = 1; x < cnt.size(); ++x) cnt[x] += cnt[x - 1];
+    // one host block, one device allocation and one copy for the six arrays
+    std::vector<int32_t> h((size_t)(4 * nitems + 2 * nslots));
+    int32_t *iv = h.data(), *ib = iv + nitems, *ie = ib + nitems, *is = ie + nitems;
+    int32_t *sf = is + nitems, *sn = sf + nslots;
+    int64_t k = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        const int64_t deg = rp[v + 1] - rp[v];
+        if (deg <= chunk) continue;
+        const int64_t nch = (deg + chunk - 1) / chunk;
+        const int32_t first = (int32_t)k;
+        for (int64_t c = 0; c < nch; ++c, ++k) {
+            iv[k] = v;
+            ib[k] = (int32_t)(rp[v] + c * chunk);
+            ie[k] = (int32_t)std::min<int64_t>(rp[v + 1], rp[v] + (c + 1) * chunk);
+            is[k] = (int32_t)k;
+            sf[k] = first;
+            sn[k] = (int32_t)nch;
+        }
     }
-    pl.nitems = (int32_t)iv.size();
-    pl.nslots = (int32_t)sf.size();
-    for (auto pr : {std::make_pair(&pl.item_v, &iv), std::make_pair(&pl.item_beg, &ib),
-                    std::make_pair(&pl.item_end, &ie), std::make_pair(&pl.item_slot, &is),
-                    std::make_pair(&pl.slot_first, &sf), std::make_pair(&pl.slot_nch, &sn)}) {
-        CK(pr.first->ensure(pr.second->size()));
-        if (!pr.second->empty())
-            CK(cudaMemcpy(pr.first->p, pr.second->data(), pr.second->size() * sizeof(int32_t),
-                          cudaMemcpyHostToDevice));
+    for (int32_t v = 0; v < n; ++v) {
+        const int64_t deg = rp[v + 1] - rp[v];
+        if (deg > chunk) continue;
+        const int64_t t = nslots + cnt[(size_t)(chunk - deg)]++;
+        iv[t] = v;
+        ib[t] = rp[v];
+        ie[t] = rp[v + 1];
+        is[t] = -1;
     }
+    pl.nitems = (int32_t)nitems;
+    pl.nslots = (int32_t)nslots;
+    CK(pl.blob.ensure(h.size()));
+    if (!h.empty()) CK(cudaMemcpy(pl.blob.p, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    pl.item_v = pl.blob.p;
+    pl.item_beg = pl.item_v + nitems;
+    pl.item_end = pl.item_beg + nitems;
+    pl.item_slot = pl.item_end + nitems;
+    pl.slot_first = pl.item_slot + nitems;
+    pl.slot_nch = pl.slot_first + nslots;
     pl.chunk = chunk;
     // partial slots depend on the plans: force the state to be re-sized
     g->W = 0;
@@ -312,12 +332,12 @@ int build_plans(bc_graph *g, const bc_options *opt) {
 
 void use_plan(bcgb::MsParams &p, const ItemPlan &pl) {
     p.nitems = pl.nitems;
-    p.item_v = pl.item_v.p;
-    p.item_beg = pl.item_beg.p;
-    p.item_end = pl.item_end.p;
-    p.item_slot = pl.item_slot.p;
-    p.slot_first = pl.slot_first.p;
-    p.slot_nch = pl.slot_nch.p;
+    p.item_v = pl.item_v;
+    p.item_beg = pl.item_beg;
+    p.item_end = pl.item_end;
+    p.item_slot = pl.item_slot;
+    p.slot_first = pl.slot_first;
+    p.slot_nch = pl.slot_nch;
 }
 
 int ensure_state(bc_graph *g, int W, int Lcap) {
@@ -425,17 +445,50 @@ int resolve_batch(const bc_options *opt, int *W) {
 // last key first.
 void rank_from_dist(bc_graph *g, std::vector<int32_t> &dist, int k) {
     const int32_t n = g->n;
-    for (auto &d : dist)  // unreachable after every reachable distance
-        if (d < 0) d = n;
-    std::vector<int32_t> ord(n), tmp(n), cnt((size_t)n + 2);
+    // Each vertex's key: its distances to landmarks 0, 1, ... (unreachable
+    // after every reachable distance) packed most significant first into 128
+    // bits, each field just wide enough for its landmark's largest value;
+    // landmarks that no longer fit are left out. A stable LSD radix sort on
+    // the key (8-bit digits, digits every key shares skipped) orders the
+    // vertices lexicographically by their distance profiles, ties by id.
+    std::vector<uint64_t> hi((size_t)n, 0), lo((size_t)n, 0);
+    int used = 0;
+    for (int i = 0; i < k; ++i) {
+        int32_t *d = dist.data() + (size_t)i * n;
+        int32_t dmax = 0;
+        for (int32_t v = 0; v < n; ++v) dmax = std::max(dmax, d[v]);
+        const uint64_t unreached = (uint64_t)dmax + 1;
+        int b = 1;
+        while ((uint64_t{1} << b) <= unreached) ++b;
+        if (used + b > 128) break;
+        used += b;
+        for (int32_t v = 0; v < n; ++v) {
+            const uint64_t x = d[v] < 0 ? unreached : (uint64_t)d[v];
+            hi[v] = (hi[v] << b) | (lo[v] >> (64 - b));
+            lo[v] = (lo[v] << b) | x;
+        }
+    }
+    std::vector<int32_t> ord(n), tmp(n);
+    std::vector<uint64_t> hi2((size_t)n), lo2((size_t)n);
     std::iota(ord.begin(), ord.end(), 0);
-    for (int i = k - 1; i >= 0; --i) {
-        const int32_t *d = dist.data() + (size_t)i * n;
-        std::fill(cnt.begin(), cnt.end(), 0);
-        for (int32_t v = 0; v < n; ++v) ++cnt[d[v] + 1];
-        for (int32_t x = 1; x <= n + 1; ++x) cnt[x] += cnt[x - 1];
-        for (int32_t t = 0; t < n; ++t) tmp[cnt[d[ord[t]]]++] = ord[t];
+    for (int digit = 0; digit < 16; ++digit) {
+        const int sh = 8 * (digit & 7);
+        std::vector<uint64_t> &key = digit < 8 ? lo : hi;
+        size_t cnt[257] = {0};
+        for (int32_t t = 0; t < n; ++t) ++cnt[((key[t] >> sh) & 0xFF) + 1];
+        bool shared = false;
+        for (int x = 1; x <= 256; ++x) shared |= cnt[x] == (size_t)n;
+        if (shared) continue;
+        for (int x = 1; x <= 256; ++x) cnt[x] += cnt[x - 1];
+        for (int32_t t = 0; t < n; ++t) {
+            const size_t at = cnt[(key[t] >> sh) & 0xFF]++;
+            tmp[at] = ord[t];
+            hi2[at] = hi[t];
+            lo2[at] = lo[t];
+        }
         ord.swap(tmp);
+        hi.swap(hi2);
+        lo.swap(lo2);
     }
     g->rank.assign(n, 0);
     for (int32_t t = 0; t < n; ++t) g->rank[ord[t]] = t;
@@ -1114,7 +1167,11 @@ int bc_run(bc_graph *g, const int32_t *sources, int32_t num_sources, const bc_op
     const bool order = !g->weighted && !(flags & (BC_PLAIN | BC_KEEP_ORDER | BC_DENSE | BC_PAIRS)) &&
                        (sources ? num_sources : g->n) > 32;
     if (order) {
-        r = ensure_rank(g, st);
+        // size the sweep state for this run's width first, so the landmark
+        // pass (32 sources) runs in it instead of allocating its own
+        r = build_plans(g, opt);
+        if (!r) r = ensure_state(g, W, std::max(g->Lcap, 32));
+        if (!r) r = ensure_rank(g, st);
         if (r) return r;
     }
     r = stage_sources(g, sources, num_sources, &nsrc, order);
