@@ -264,7 +264,7 @@ int bc_run_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col, const 
  *                 persistent kernel captured once into a CUDA graph.
  *                 graphs: k unweighted handles from bc_create_graph, owned by
  *                 the caller and kept alive while the plan exists.
- *                 opt->batch: sources per batch, 32 or 64 (0 = 32).
+ *                 opt->batch: sources per batch, 32, 64, 128 or 256 (0 = 32).
  * bc_many_run     replays the captured graph on cuda_stream (asynchronous).
  *                 Each graph's BC lands in its own handle: read it with
  *                 bc_result(graphs[i], ...) after bc_many_result.

@@ -95,7 +95,7 @@ def tune_graph(g, handle=None, batches=(64, 128, 256), chunks=(128, 256, 512), s
     return out
 
 
-def tune_many(gs, handles, batches=(32, 64), use_cache=True):
+def tune_many(gs, handles, batches=(32, 64, 128, 256), use_cache=True):
     """Best batch width for a many-graph plan over handles."""
     big = max(gs, key=lambda g: g.n * g.m)
     key = _key(big, f"many{len(gs)}")

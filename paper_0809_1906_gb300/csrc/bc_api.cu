@@ -1540,7 +1540,7 @@ int bc_many_create(bc_graph *const *graphs, int32_t k, const bc_options *opt, bc
     if (!out || (k > 0 && !graphs) || k < 0) return fail(BC_ERR_ARG, "bad arguments");
     *out = nullptr;
     const int b = (opt && opt->batch) ? opt->batch : 32;
-    if (b != 32 && b != 64) return fail(BC_ERR_ARG, "many-graph batch must be 32 or 64");
+    if (b != 32 && b != 64 && b != 128 && b != 256) return fail(BC_ERR_ARG, "many-graph batch must be 32, 64, 128 or 256");
     bc_many *m = new (std::nothrow) bc_many();
     if (!m) return fail(BC_ERR_OOM, "host allocation failed");
     m->W = b / 32;

@@ -35,7 +35,7 @@ constexpr int kMWarps = kMBlock / 32;
 constexpr unsigned kFull = 0xffffffffu;
 
 template <int W>
-__global__ void __launch_bounds__(kMBlock, 4) k_many(const ManyParams p) {
+__global__ void __launch_bounds__(kMBlock, W >= 4 ? 3 : 4) k_many(const ManyParams p) {
     constexpr int B = 32 * W;
     __shared__ int s_item;
     __shared__ int s_last;
@@ -224,18 +224,22 @@ __global__ void __launch_bounds__(kMBlock, 4) k_many(const ManyParams p) {
 
 int many_blocks_per_sm(int W) {
     int nb = 0;
-    if (W == 1)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_many<1>, kMBlock, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_many<2>, kMBlock, 0);
+    switch (W) {
+        case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_many<1>, kMBlock, 0); break;
+        case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_many<2>, kMBlock, 0); break;
+        case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_many<4>, kMBlock, 0); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_many<8>, kMBlock, 0); break;
+    }
     return nb < 1 ? 1 : nb;
 }
 
 void many_launch(int W, const ManyParams &p, int grid, cudaStream_t st) {
-    if (W == 1)
-        k_many<1><<<grid, kMBlock, 0, st>>>(p);
-    else
-        k_many<2><<<grid, kMBlock, 0, st>>>(p);
+    switch (W) {
+        case 1: k_many<1><<<grid, kMBlock, 0, st>>>(p); break;
+        case 2: k_many<2><<<grid, kMBlock, 0, st>>>(p); break;
+        case 4: k_many<4><<<grid, kMBlock, 0, st>>>(p); break;
+        default: k_many<8><<<grid, kMBlock, 0, st>>>(p); break;
+    }
 }
 
 }  // namespace bcgb

@@ -20,7 +20,7 @@ def close(got, ref, n):
     return np.all(np.abs(got - ref) <= tol)
 
 
-@pytest.mark.parametrize("batch", [32, 64])
+@pytest.mark.parametrize("batch", [32, 64, 128, 256])
 def test_many_small_graphs(nat, batch):
     gs = G.many_graphs(40, 20, 600, seed=77)
     gs.append(G.path_graph(100))  # deeper than the 64-level capacity: re-run path
