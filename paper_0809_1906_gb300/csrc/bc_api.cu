@@ -90,6 +90,42 @@ struct ItemPlan {
     }
 };
 
+constexpr int kSweepLanes = 4;                    // concurrent batches of the unweighted sweep
+constexpr double kLaneBudgetBytes = 8.0 * (1 << 30);  // batch state of the extra lanes
+
+// An extra lane of the batched sweep: its own stream, batch state, control
+// blocks and BC accumulator, so that batches run concurrently (one lane's
+// latency-bound levels overlap another lane's wide ones).
+struct SweepLane {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    int32_t W = 0, Lcap = 0;
+    DevBuf<uint64_t> sigma, part;
+    DevBuf<float> cval;
+    DevBuf<uint16_t> Smask;
+    DevBuf<uint32_t> wideflags, F, ufr, V, pmask, cnt;
+    DevBuf<double> bc;
+    bcgb::DevCtl *ctl = nullptr;
+    bcgb::HostCtl *hctl = nullptr, *hctl_d = nullptr;
+    void release() {
+        sigma.release();
+        part.release();
+        cval.release();
+        Smask.release();
+        for (auto *b : {&wideflags, &F, &ufr, &V, &pmask, &cnt}) b->release();
+        bc.release();
+        if (ctl) cudaFree(ctl);
+        if (hctl) cudaFreeHost(hctl);
+        if (ev) cudaEventDestroy(ev);
+        if (st) cudaStreamDestroy(st);
+        ctl = nullptr;
+        hctl = hctl_d = nullptr;
+        ev = nullptr;
+        st = nullptr;
+        W = Lcap = 0;
+    }
+};
+
 struct bc_graph {
     int32_t n = 0;
     int64_t narcs = 0;
@@ -126,6 +162,8 @@ struct bc_graph {
     bcgb::HostCtl *hctl = nullptr;    // host view
     bcgb::HostCtl *hctl_d = nullptr;  // device view
     uint32_t seq = 0;
+    SweepLane lanes[kSweepLanes - 1];  // lanes 1.. of the concurrent sweep (lane 0 is the state above)
+    cudaEvent_t ev0 = nullptr;        // lane 0's join / fork event
 
     // timing
     struct Ev {
@@ -194,6 +232,8 @@ void free_graph(bc_graph *g) {
     g->reach.release();
     if (g->ctl) cudaFree(g->ctl);
     if (g->hctl) cudaFreeHost(g->hctl);
+    for (auto &ln : g->lanes) ln.release();
+    if (g->ev0) cudaEventDestroy(g->ev0);
     for (auto &e : g->evpool) {
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);
@@ -424,6 +464,62 @@ bcgb::MsParams make_params(bc_graph *g) {
     p.bc = g->bc.p;
     p.ctl = g->ctl;
     p.hctl = g->hctl_d;
+    return p;
+}
+
+// Batch state of sweep lane k >= 1 (same shapes as ensure_state's), plus its
+// stream, control blocks and BC accumulator, created on first use.
+int ensure_lane(bc_graph *g, SweepLane &ln, int W, int Lcap) {
+    if (!ln.st) {
+        CK(cudaStreamCreateWithFlags(&ln.st, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ln.ev, cudaEventDisableTiming));
+        CK(cudaMalloc((void **)&ln.ctl, sizeof(bcgb::DevCtl)));
+        CK(cudaMemset(ln.ctl, 0, sizeof(bcgb::DevCtl)));
+        CK(cudaHostAlloc((void **)&ln.hctl, sizeof(bcgb::HostCtl), cudaHostAllocMapped | cudaHostAllocPortable));
+        std::memset(ln.hctl, 0, sizeof(bcgb::HostCtl));
+        CK(cudaHostGetDevicePointer((void **)&ln.hctl_d, ln.hctl, 0));
+    }
+    if (ln.W == W && ln.Lcap >= Lcap && ln.sigma.p) return BC_OK;
+    const size_t n = (size_t)std::max(g->n, 1);
+    const size_t B = 32 * (size_t)W;
+    const size_t nw32 = (n + 31) / 32;
+    CK(ln.sigma.ensure(n * B));
+    CK(ln.Smask.ensure(2 * n * B));
+    CK(ln.wideflags.ensure((size_t)Lcap));
+    CK(ln.cval.ensure(2 * n * B));
+    CK(ln.F.ensure((size_t)Lcap * n * W));
+    CK(ln.ufr.ensure((size_t)Lcap * nw32));
+    CK(ln.V.ensure(2 * n * W));
+    const size_t slots = (size_t)std::max({g->fplan.nslots, g->bplan.nslots, 1});
+    CK(ln.part.ensure(slots * B));
+    CK(ln.pmask.ensure(slots * W));
+    CK(ln.cnt.ensure(slots));
+    CK(cudaMemset(ln.cnt.p, 0, ln.cnt.n * sizeof(uint32_t)));
+    CK(ln.bc.ensure(n));
+    ln.W = W;
+    ln.Lcap = Lcap;
+    return BC_OK;
+}
+
+// Kernel parameters of sweep lane k (0: the graph's own state).
+bcgb::MsParams lane_params(bc_graph *g, int k) {
+    bcgb::MsParams p = make_params(g);
+    if (k == 0) return p;
+    SweepLane &ln = g->lanes[k - 1];
+    p.Lcap = ln.Lcap;
+    p.sigma = ln.sigma.p;
+    p.S = ln.Smask.p;
+    p.wide = ln.wideflags.p;
+    p.cval = ln.cval.p;
+    p.F = ln.F.p;
+    p.ufr = ln.ufr.p;
+    p.V = ln.V.p;
+    p.part = ln.part.p;
+    p.pmask = ln.pmask.p;
+    p.cnt = ln.cnt.p;
+    p.bc = ln.bc.p;
+    p.ctl = ln.ctl;
+    p.hctl = ln.hctl_d;
     return p;
 }
 
@@ -744,6 +840,166 @@ int run_dense_group(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream
 }
 
 // The multi-source driver shared by bc_run and bc_forward_rows.
+// Concurrent sweep over K lanes (K >= 2). Batch i runs on lane i % K, each
+// lane on its own stream with its own batch state and BC accumulator, so the
+// narrow, latency-bound levels of one batch overlap the wide levels of
+// another. The host drives every lane's level loop without blocking on any
+// of them (the same look-ahead as drive_forward). The lanes start after the
+// work already queued on st; at the end st waits for them and adds lanes
+// 1..K-1 into the graph's BC in lane order, so the result is the same on
+// every run. A batch deeper than the level capacity stops every lane: the
+// capacity is doubled and each lane's unfinished batch starts over.
+int run_lanes(bc_graph *g, int32_t nsrc, int W, int K, cudaStream_t st, bool backward, bool hash,
+              uint64_t *rows_sig, int32_t *rows_dist, int64_t wait_ms) {
+    const int B = 32 * W;
+    const int32_t nbat = (nsrc + B - 1) / B;
+    int Lcap = g->Lcap;
+    for (int k = 1; k < K; ++k) {
+        const int r = ensure_lane(g, g->lanes[k - 1], W, Lcap);
+        if (r) return r;
+    }
+    if (!g->ev0) CK(cudaEventCreateWithFlags(&g->ev0, cudaEventDisableTiming));
+    CK(cudaEventRecord(g->ev0, st));
+    for (int k = 1; k < K; ++k) {
+        SweepLane &ln = g->lanes[k - 1];
+        CK(cudaStreamWaitEvent(ln.st, g->ev0, 0));
+        CK(cudaMemsetAsync(ln.bc.p, 0, (size_t)g->n * sizeof(double), ln.st));
+        CK(cudaMemsetAsync(ln.ctl, 0, sizeof(bcgb::DevCtl), ln.st));
+    }
+    auto lane_stream = [&](int k) { return k == 0 ? st : g->lanes[k - 1].st; };
+    auto lane_hctl = [&](int k) -> const bcgb::HostCtl * { return k == 0 ? g->hctl : g->lanes[k - 1].hctl; };
+    struct Job {
+        int32_t bi = -1;
+        int phase = 0;  // 0: no batch in flight, 1: forward levels in flight
+        int launched = 0;
+        bcgb::MsParams p{};
+        std::chrono::steady_clock::time_point t0;
+    };
+    Job jobs[kSweepLanes];
+    int32_t next[kSweepLanes];
+    for (int k = 0; k < K; ++k) next[k] = k;
+    using clock = std::chrono::steady_clock;
+    for (long spins = 0;; ++spins) {
+        bool moved = false, busy = false;
+        for (int k = 0; k < K; ++k) {
+            Job &j = jobs[k];
+            const cudaStream_t ls = lane_stream(k);
+            if (j.phase == 0 && next[k] < nbat) {
+                j.bi = next[k];
+                next[k] += K;
+                const int32_t b0 = j.bi * B;
+                j.p = lane_params(g, k);
+                j.p.nb = std::min<int32_t>(B, nsrc - b0);
+                j.p.first = 1;
+                j.p.seq = ++g->seq;
+                j.p.sources = g->sources.p + b0;
+                if (hash) {
+                    const int32_t o = g->reordered ? 0 : b0;
+                    j.p.h_sigma = g->h_sigma.p + o;
+                    j.p.h_dist = g->h_dist.p + o;
+                    j.p.dist_sum = g->dist_sum.p + o;
+                    j.p.reach = g->reach.p + o;
+                    j.p.out_index = g->reordered ? g->src_index.p + b0 : nullptr;
+                }
+                {
+                    Timer t(g, ls, BC_KERNEL_INIT);
+                    bcgb::ms_launch_init(W, j.p, ls);
+                }
+                j.phase = 1;
+                j.launched = 0;
+                j.t0 = clock::now();
+                moved = true;
+            }
+            if (j.phase != 1) continue;
+            busy = true;
+            const bcgb::HostCtl *h = lane_hctl(k);
+            int done_lv = 0;
+            if (bcgb::load_acquire_u(&h->progress_seq) == j.p.seq) done_lv = bcgb::load_acquire_i(&h->progress);
+            while (j.launched <= j.p.Lcap - 2 && j.launched < done_lv + bcgb::kLookahead) {
+                Timer t(g, ls, BC_KERNEL_FORWARD);
+                if (j.launched == 0)
+                    bcgb::ms_launch_first(W, j.p, ls);
+                else
+                    bcgb::ms_launch_forward(W, j.p, j.launched, ls);
+                ++j.launched;
+                moved = true;
+            }
+            if (bcgb::load_acquire_u(&h->done_seq) != j.p.seq) continue;
+            const int L = bcgb::load_acquire_i(&h->nlevels);
+            moved = true;
+            if (L < 0) {
+                // deeper than the level capacity: grow it on every lane and
+                // start each lane's unfinished batch again
+                for (int q = 0; q < K; ++q) CK(cudaStreamSynchronize(lane_stream(q)));
+                Lcap *= 2;
+                int r = ensure_state(g, W, Lcap);
+                for (int q = 1; q < K && !r; ++q) r = ensure_lane(g, g->lanes[q - 1], W, Lcap);
+                if (r) return r;
+                for (int q = 0; q < K; ++q)
+                    if (jobs[q].phase == 1) {
+                        jobs[q].phase = 0;
+                        next[q] = jobs[q].bi;
+                    }
+                break;
+            }
+            if (backward) {
+                bcgb::MsParams pb = j.p;
+                use_plan(pb, g->bplan);
+                for (int l = L; l >= 1; --l) {
+                    Timer t(g, ls, BC_KERNEL_BACKWARD);
+                    bcgb::ms_launch_backward(W, pb, l, ls);
+                }
+            }
+            if (hash) {
+                Timer t(g, ls, BC_KERNEL_HASH);
+                bcgb::ms_launch_hash(W, j.p, L, ls);
+            }
+            if (rows_sig || rows_dist) {
+                Timer t(g, ls, BC_KERNEL_HASH);
+                const size_t off = (size_t)j.bi * B * g->n;
+                bcgb::ms_launch_rows(W, j.p, L, rows_sig ? rows_sig + off : nullptr, rows_dist ? rows_dist + off : nullptr,
+                                     ls);
+            }
+            CK(cudaGetLastError());
+            j.phase = 0;
+        }
+        if (!busy && !moved) {
+            bool left = false;
+            for (int k = 0; k < K; ++k) left |= next[k] < nbat;
+            if (!left) break;
+        }
+        if (moved) continue;
+        if (spins % 64 == 63) {
+            CK(cudaGetLastError());
+            for (int k = 0; k < K; ++k) {
+                if (jobs[k].phase != 1) continue;
+                const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(clock::now() - jobs[k].t0).count();
+                if (ms > wait_ms)
+                    return fail(BC_ERR_TIMEOUT, "the device did not report the end of a forward pass within the wait limit");
+                const cudaError_t e = cudaStreamQuery(lane_stream(k));
+                if (e != cudaSuccess && e != cudaErrorNotReady)
+                    return fail(BC_ERR_CUDA, std::string("device error during a forward pass: ") + cudaGetErrorString(e));
+                if (e == cudaSuccess && bcgb::load_acquire_u(&lane_hctl(k)->done_seq) != jobs[k].p.seq &&
+                    jobs[k].launched > jobs[k].p.Lcap - 2)
+                    return fail(BC_ERR_STATE, "forward pass ended without reporting its depth");
+            }
+            if (spins % 4096 == 4095) std::this_thread::yield();
+        }
+    }
+    // join: st waits for every lane, then adds their BC and counters in lane order
+    for (int k = 1; k < K; ++k) {
+        SweepLane &ln = g->lanes[k - 1];
+        CK(cudaEventRecord(ln.ev, ln.st));
+        CK(cudaStreamWaitEvent(st, ln.ev, 0));
+    }
+    for (int k = 1; k < K; ++k) {
+        SweepLane &ln = g->lanes[k - 1];
+        bcgb::ms_launch_merge(ln.bc.p, g->bc.p, g->n, ln.ctl, g->ctl, st);
+    }
+    CK(cudaGetLastError());
+    return BC_OK;
+}
+
 int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStream_t st, bool backward,
                 bool hash, uint64_t *rows_sig, int32_t *rows_dist) {
     const int64_t wait_ms = (opt && opt->wait_limit_ms > 0) ? opt->wait_limit_ms : 600000;
@@ -757,6 +1013,16 @@ int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStr
     r = ensure_state(g, W, std::max(g->Lcap, 32));
     if (r) return r;
     const int B = 32 * W;
+    {
+        // lanes: as many as there are batches, up to kSweepLanes, within a
+        // memory budget for the extra lanes' batch state. With BC_TIMING one
+        // lane, so that every launch's event time is its own.
+        const int32_t nbat = (nsrc + B - 1) / B;
+        const double lane_bytes = (double)std::max(g->n, 1) * ((double)B * 28.0 + (double)g->Lcap * W * 4.0 + 16.0);
+        int K = g->timing ? 1 : std::min<int32_t>(kSweepLanes, nbat);
+        while (K > 1 && (K - 1) * lane_bytes > kLaneBudgetBytes) --K;
+        if (K > 1) return run_lanes(g, nsrc, W, K, st, backward, hash, rows_sig, rows_dist, wait_ms);
+    }
     for (int32_t b0 = 0; b0 < nsrc;) {
         const int32_t nb = std::min<int32_t>(B, nsrc - b0);
         bcgb::MsParams p = make_params(g);

@@ -544,6 +544,16 @@ __global__ void __launch_bounds__(kBlock) k_rows(const MsParams p, const int L, 
     }
 }
 
+__global__ void k_merge(const double *__restrict__ src, double *__restrict__ dst, int32_t n, const DevCtl *from,
+                        DevCtl *to) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] += src[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicOr(&to->status, from->status);
+        atomicAdd(&to->dag_arcs, from->dag_arcs);
+        atomicAdd(&to->depth_sum, from->depth_sum);
+    }
+}
+
 __global__ void k_scale(double *x, int32_t n, double f) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] *= f;
 }
@@ -652,6 +662,12 @@ void ms_launch_rows(int W, const MsParams &p, int nlevels, uint64_t *sig_out, in
                     cudaStream_t st) {
     const int g = 4 * sm_count();
     BCGB_DISPATCH_W(W, pdl::launch(k_rows<kW>, g, kBlock, 0, st, p, nlevels, sig_out, dist_out));
+}
+
+void ms_launch_merge(const double *src, double *dst, int32_t n, const DevCtl *from, DevCtl *to, cudaStream_t st) {
+    int g = (n + kBlock - 1) / kBlock;
+    g = g < 1 ? 1 : (g > 4 * sm_count() ? 4 * sm_count() : g);
+    k_merge<<<g, kBlock, 0, st>>>(src, dst, n, from, to);
 }
 
 void launch_scale(double *x, int32_t n, double f, cudaStream_t st) {

@@ -245,3 +245,23 @@ def test_autotuner_choice_runs_correctly(nat, tmp_path, monkeypatch):
     assert (tmp_path / "tune.json").exists()
     assert autotune.tune_graph(g)["batch"] == choice["batch"]  # served from the cache
     check_graph(nat, g, batch=choice["batch"], chunk=choice["chunk"], rows=False)
+
+
+@pytest.mark.parametrize("batch", [32, 64])
+def test_concurrent_lanes_deep_batches(nat, batch):
+    """Many batches run on concurrent lanes; a path of 300 vertices is deeper
+    than the starting level capacity, so the capacity grows (every lane's
+    unfinished batch starts over) several times within one run."""
+    for g in (G.path_graph(300), G.random_small(700, 0.004, 4242, connect=True)):
+        ref = oracle.bc(g)
+        with nat.Graph.from_csr(g) as h:
+            h.run(batch=batch)
+            got, code, _ = h.result()
+            hs = h.source_hashes(g.n)
+            h.run(batch=batch)
+            again, _, _ = h.result()
+        assert code == nat.BC_OK
+        tol = np.maximum(1e-5 * np.abs(ref["bc"]), 1e-6 * g.n)
+        assert np.all(np.abs(got - ref["bc"]) <= tol), g.name
+        assert np.array_equal(hs["hash_sigma"], ref["hash_sigma"]) and np.array_equal(hs["hash_dist"], ref["hash_dist"])
+        assert np.array_equal(got, again), g.name
