@@ -90,7 +90,7 @@ struct ItemPlan {
     }
 };
 
-constexpr int kSweepLanes = 4;                    // concurrent batches of the unweighted sweep
+constexpr int kSweepLanes = 8;                    // concurrent batches of the unweighted sweep
 constexpr double kLaneBudgetBytes = 8.0 * (1 << 30);  // batch state of the extra lanes
 
 // An extra lane of the batched sweep: its own stream, batch state, control
