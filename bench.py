@@ -97,15 +97,18 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# Sources of the sweep kernels whose DRAM bytes profiles/traffic_rmat.json holds.
+SWEEP_SOURCES = ("msbfs.cu", "msbfs_body.cuh", "rowstage.cuh", "pdl.cuh", "bc_internal.cuh")
+
+
 def csrc_digest() -> str:
-    """SHA-256 over the CUDA sources: DRAM counters taken from an older build
-    do not describe the current kernels."""
-    import glob
+    """SHA-256 over the sweep kernels' sources: DRAM counters taken from an
+    older build do not describe the current kernels."""
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_0809_1906_gb300", "csrc", "*.cu*"))):
-        with open(f, "rb") as fh:
-            h.update(os.path.basename(f).encode())
+    for name in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_0809_1906_gb300", "csrc", name), "rb") as fh:
+            h.update(name.encode())
             h.update(fh.read())
     return h.hexdigest()
 
@@ -616,7 +619,11 @@ def main():
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
                          "traffic": traffic, "algorithmic_bytes_per_launch": dom_bytes / max(dom_cnt, 1),
-                         "avg_launch_ms": dom_ms / max(dom_cnt, 1), "launches": dom_cnt},
+                         "avg_launch_ms": dom_ms / max(dom_cnt, 1), "launches": dom_cnt,
+                         "kernel_timing": "BC_TIMING pass: one lane, CUDA events around every launch",
+                         "step_achieved": (fwd_b + bwd_b) / (ms_per_step / 1000.0) / 1e9,
+                         "step_frac": (fwd_b + bwd_b) / (ms_per_step / 1000.0) / 1e9 / peak,
+                         "step_note": "forward + backward algorithmic bytes / ms_per_step (concurrent lanes)"},
             "kernels_ms": {k2: {"launches": v[0], "total_ms": v[1]} for k2, v in ktime.items()},
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{k} seeded sources of the same graph ({dt:.1f} s, OpenMP over sources)"},

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -97,9 +98,11 @@ constexpr double kLaneBudgetBytes = 8.0 * (1 << 30);  // batch state of the extr
 // blocks and BC accumulator, so that batches run concurrently (one lane's
 // latency-bound levels overlap another lane's wide ones).
 struct SweepLane {
+    int dev = -1;  // device of the stream and buffers
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
-    int32_t W = 0, Lcap = 0;
+    int32_t W = 0, Lcap = 0, n = 0;
+    size_t slots = 0;
     DevBuf<uint64_t> sigma, part;
     DevBuf<float> cval;
     DevBuf<uint16_t> Smask;
@@ -122,9 +125,49 @@ struct SweepLane {
         hctl = hctl_d = nullptr;
         ev = nullptr;
         st = nullptr;
-        W = Lcap = 0;
+        W = Lcap = n = 0;
+        slots = 0;
+        dev = -1;
     }
 };
+
+// Lanes of destroyed graphs are kept for the next graph on the same device
+// (stream, control blocks and buffers, which grow when a graph needs more):
+// a program that builds many graphs in turn allocates them once.
+namespace lane_pool {
+std::mutex mu;
+std::vector<SweepLane> idle;
+constexpr size_t kMax = 16;
+
+// Move lane `from` into `to` (the fields are plain handles and pointers).
+void move_lane(SweepLane &to, SweepLane &from) {
+    to = from;
+    from = SweepLane{};
+}
+bool take(SweepLane &ln, int dev) {
+    std::lock_guard<std::mutex> lk(mu);
+    for (size_t i = 0; i < idle.size(); ++i)
+        if (idle[i].dev == dev) {
+            move_lane(ln, idle[i]);
+            idle.erase(idle.begin() + (long)i);
+            // the progress block carries the previous owner's batch numbers
+            std::memset(ln.hctl, 0, sizeof(bcgb::HostCtl));
+            return true;
+        }
+    return false;
+}
+void give(SweepLane &ln) {
+    if (!ln.st) return;
+    cudaStreamSynchronize(ln.st);  // nothing of the previous owner may still run on it
+    std::lock_guard<std::mutex> lk(mu);
+    if (idle.size() < kMax) {
+        idle.emplace_back();
+        move_lane(idle.back(), ln);
+    } else {
+        ln.release();
+    }
+}
+}  // namespace lane_pool
 
 struct bc_graph {
     int32_t n = 0;
@@ -232,7 +275,7 @@ void free_graph(bc_graph *g) {
     g->reach.release();
     if (g->ctl) cudaFree(g->ctl);
     if (g->hctl) cudaFreeHost(g->hctl);
-    for (auto &ln : g->lanes) ln.release();
+    for (auto &ln : g->lanes) lane_pool::give(ln);
     if (g->ev0) cudaEventDestroy(g->ev0);
     for (auto &e : g->evpool) {
         cudaEventDestroy(e.a);
@@ -470,7 +513,13 @@ bcgb::MsParams make_params(bc_graph *g) {
 // Batch state of sweep lane k >= 1 (same shapes as ensure_state's), plus its
 // stream, control blocks and BC accumulator, created on first use.
 int ensure_lane(bc_graph *g, SweepLane &ln, int W, int Lcap) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    bool fresh = false;
+    if (!ln.st) fresh = lane_pool::take(ln, dev);
     if (!ln.st) {
+        fresh = true;
+        ln.dev = dev;
         CK(cudaStreamCreateWithFlags(&ln.st, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&ln.ev, cudaEventDisableTiming));
         CK(cudaMalloc((void **)&ln.ctl, sizeof(bcgb::DevCtl)));
@@ -479,7 +528,8 @@ int ensure_lane(bc_graph *g, SweepLane &ln, int W, int Lcap) {
         std::memset(ln.hctl, 0, sizeof(bcgb::HostCtl));
         CK(cudaHostGetDevicePointer((void **)&ln.hctl_d, ln.hctl, 0));
     }
-    if (ln.W == W && ln.Lcap >= Lcap && ln.sigma.p) return BC_OK;
+    const size_t slots = (size_t)std::max({g->fplan.nslots, g->bplan.nslots, 1});
+    if (!fresh && ln.W == W && ln.Lcap >= Lcap && ln.n >= g->n && ln.slots >= slots && ln.sigma.p) return BC_OK;
     const size_t n = (size_t)std::max(g->n, 1);
     const size_t B = 32 * (size_t)W;
     const size_t nw32 = (n + 31) / 32;
@@ -490,7 +540,6 @@ int ensure_lane(bc_graph *g, SweepLane &ln, int W, int Lcap) {
     CK(ln.F.ensure((size_t)Lcap * n * W));
     CK(ln.ufr.ensure((size_t)Lcap * nw32));
     CK(ln.V.ensure(2 * n * W));
-    const size_t slots = (size_t)std::max({g->fplan.nslots, g->bplan.nslots, 1});
     CK(ln.part.ensure(slots * B));
     CK(ln.pmask.ensure(slots * W));
     CK(ln.cnt.ensure(slots));
@@ -498,6 +547,8 @@ int ensure_lane(bc_graph *g, SweepLane &ln, int W, int Lcap) {
     CK(ln.bc.ensure(n));
     ln.W = W;
     ln.Lcap = Lcap;
+    ln.n = (int32_t)n;
+    ln.slots = slots;
     return BC_OK;
 }
 

@@ -265,3 +265,19 @@ def test_concurrent_lanes_deep_batches(nat, batch):
         assert np.all(np.abs(got - ref["bc"]) <= tol), g.name
         assert np.array_equal(hs["hash_sigma"], ref["hash_sigma"]) and np.array_equal(hs["hash_dist"], ref["hash_dist"])
         assert np.array_equal(got, again), g.name
+
+
+def test_lanes_reused_across_graphs(nat):
+    """Lanes of a destroyed graph serve the next graph (grown when it is
+    larger, with fresh progress blocks): each result still matches."""
+    for g in (G.random_small(300, 0.02, 51, connect=True), G.er_hamiltonian(1500, 6000, 52),
+              G.random_small(400, 0.01, 53, connect=True), G.path_graph(200)):
+        ref = oracle.bc(g)
+        with nat.Graph.from_csr(g) as h:
+            h.run(batch=32)
+            got, code, _ = h.result()
+            hs = h.source_hashes(g.n)
+        assert code == nat.BC_OK
+        tol = np.maximum(1e-5 * np.abs(ref["bc"]), 1e-6 * g.n)
+        assert np.all(np.abs(got - ref["bc"]) <= tol), g.name
+        assert np.array_equal(hs["hash_sigma"], ref["hash_sigma"]), g.name
