@@ -245,6 +245,13 @@ struct bc_graph {
     std::vector<int32_t> h_sources;  // host copy of the staged source list
     DevBuf<uint64_t> wsigma;
     DevBuf<float> wcval, wrows;
+    // second lane of waves: its own stream, packed state, rows and BC accumulator
+    cudaStream_t wst = nullptr;
+    cudaEvent_t wev = nullptr;
+    DevBuf<int32_t> worder2, wgrp2, wslots2;
+    DevBuf<uint64_t> wds2;
+    DevBuf<float> wrows2;
+    DevBuf<double> wbc2;
 };
 
 namespace {
@@ -266,6 +273,12 @@ void free_graph(bc_graph *g) {
     g->gbcpart.release();
     g->gmeta.release();
     for (auto *b : {&g->wpos, &g->wsrc}) b->release();
+    for (auto *b : {&g->worder2, &g->wgrp2, &g->wslots2}) b->release();
+    g->wds2.release();
+    g->wrows2.release();
+    g->wbc2.release();
+    if (g->wev) cudaEventDestroy(g->wev);
+    if (g->wst) cudaStreamDestroy(g->wst);
     g->wds.release();
     g->wredo.release();
     g->bc.release();
@@ -1177,6 +1190,15 @@ int sm_count_host() {
 // Weighted path: waves of one CTA per source (csrc/sssp_weighted.cu).
 // opt->batch (if set) is the wave size; default 4 CTAs per SM, capped so the
 // wave state stays within 8 GiB.
+// Weighted sweep: waves of G sources (one CTA each, packed state) on two
+// lanes: wave k runs on lane k % 2, each lane with its own stream, state,
+// delta rows and BC accumulator, so one wave's slowest sources overlap the
+// next wave. The delta rows of a wave are added to its lane's BC in source
+// order right after the wave; lane 1's BC is added into the graph's at the
+// end, so the result does not change from run to run. Sources whose path
+// counts reach 2^32 write nothing in the packed kernel; they are flagged and
+// computed again at the end by the 64-bit kernel, whose delta rows are added
+// in the order of the flagged sources.
 int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t st, bool backward, bool hash,
                  uint64_t *rows_sig, int32_t *rows_dist) {
     const int32_t n = g->n;
@@ -1190,6 +1212,8 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
     int G = (opt && opt->batch > 0) ? opt->batch : 4 * sm_count_host();
     G = (int)std::min<size_t>((size_t)G, std::max<size_t>(1, (8ull << 30) / per_src));
     G = std::max(1, std::min(G, std::max(nsrc, 1)));
+    const int32_t nwaves = (nsrc + G - 1) / G;
+    const int lanes = (nwaves >= 2 && !g->timing) ? 2 : 1;  // BC_TIMING: one lane, launch times of their own
     if (g->wG < G || g->wK != K || g->wC != C) {
         CK(g->wdist.ensure((size_t)G * n));
         CK(g->wsigma.ensure((size_t)G * n));
@@ -1199,36 +1223,60 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
         CK(g->wslots.ensure((size_t)G * K * C));
         CK(g->wrows.ensure((size_t)G * n));
         CK(g->wds.ensure((size_t)G * n));
-        CK(g->wredo.ensure((size_t)G));
         CK(g->wpos.ensure((size_t)G));
         CK(g->wsrc.ensure((size_t)G));
         g->wG = G;
         g->wK = K;
         g->wC = C;
     }
-    for (int32_t w0 = 0; w0 < nsrc; w0 += G) {
-        const int nw = std::min<int32_t>(G, nsrc - w0);
-        bcgb::WParams p{};
-        p.n = n;
-        p.K = K;
-        p.C = C;
-        p.dmax = (int32_t)std::min<int64_t>((int64_t)n * g->maxw, INT32_MAX - 1);
-        p.row_ptr = g->row_ptr.p;
-        p.col = g->col.p;
-        p.w = g->w.p;
-        if (g->directed) {
-            p.row_ptr_in = g->row_ptr_in.p;
-            p.col_in = g->col_in.p;
-            p.w_in = g->w_in.p;
+    if (lanes == 2) {
+        if (!g->wst) {
+            CK(cudaStreamCreateWithFlags(&g->wst, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&g->wev, cudaEventDisableTiming));
         }
+        CK(g->worder2.ensure((size_t)G * n));
+        CK(g->wgrp2.ensure((size_t)G * (n + 1)));
+        CK(g->wslots2.ensure((size_t)G * K * C));
+        CK(g->wrows2.ensure((size_t)G * n));
+        CK(g->wds2.ensure((size_t)G * n));
+        CK(g->wbc2.ensure((size_t)std::max(n, 1)));
+        CK(cudaEventRecord(g->wev, st));
+        CK(cudaStreamWaitEvent(g->wst, g->wev, 0));
+        CK(cudaMemsetAsync(g->wbc2.p, 0, (size_t)std::max(n, 1) * sizeof(double), g->wst));
+    }
+    CK(g->wredo.ensure((size_t)std::max(nsrc, 1)));
+    CK(cudaMemsetAsync(g->wredo.p, 0, (size_t)std::max(nsrc, 1), st));
+    if (lanes == 2) {
+        CK(cudaEventRecord(g->wev, st));
+        CK(cudaStreamWaitEvent(g->wst, g->wev, 0));
+    }
+    bcgb::WParams base{};
+    base.n = n;
+    base.K = K;
+    base.C = C;
+    base.dmax = (int32_t)std::min<int64_t>((int64_t)n * g->maxw, INT32_MAX - 1);
+    base.row_ptr = g->row_ptr.p;
+    base.col = g->col.p;
+    base.w = g->w.p;
+    if (g->directed) {
+        base.row_ptr_in = g->row_ptr_in.p;
+        base.col_in = g->col_in.p;
+        base.w_in = g->w_in.p;
+    }
+    base.ctl = g->ctl;
+    for (int32_t k = 0; k < nwaves; ++k) {
+        const int32_t w0 = k * G;
+        const int nw = std::min<int32_t>(G, nsrc - w0);
+        const int ln = k % lanes;
+        const cudaStream_t ls = ln == 0 ? st : g->wst;
+        bcgb::WParams p = base;
         p.sources = g->sources.p + w0;
-        p.dist = g->wdist.p;
-        p.sigma = g->wsigma.p;
-        p.cval = g->wcval.p;
-        p.order = g->worder.p;
-        p.grp = g->wgrp.p;
-        p.slots = g->wslots.p;
-        p.delta_rows = backward ? g->wrows.p : nullptr;
+        p.order = ln == 0 ? g->worder.p : g->worder2.p;
+        p.grp = ln == 0 ? g->wgrp.p : g->wgrp2.p;
+        p.slots = ln == 0 ? g->wslots.p : g->wslots2.p;
+        p.ds = ln == 0 ? g->wds.p : g->wds2.p;
+        float *rows = ln == 0 ? g->wrows.p : g->wrows2.p;
+        p.delta_rows = backward ? rows : nullptr;
         if (hash) {
             p.h_sigma = g->h_sigma.p + w0;
             p.h_dist = g->h_dist.p + w0;
@@ -1237,36 +1285,61 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
         }
         p.rows_sigma = rows_sig ? rows_sig + (size_t)w0 * n : nullptr;
         p.rows_dist = rows_dist ? rows_dist + (size_t)w0 * n : nullptr;
-        p.ctl = g->ctl;
-        p.ds = g->wds.p;
-        p.redo = g->wredo.p;
-        CK(cudaMemsetAsync(g->wredo.p, 0, (size_t)nw, st));
+        p.redo = g->wredo.p + w0;
+        {
+            Timer t(g, ls, BC_KERNEL_FORWARD);
+            bcgb::w_launch_wave_packed(p, nw, ls);
+        }
+        if (backward) {
+            Timer t(g, ls, BC_KERNEL_BACKWARD);
+            bcgb::w_launch_reduce(rows, nw, n, ln == 0 ? g->bc.p : g->wbc2.p, sm_count_host(), ls);
+        }
+        CK(cudaGetLastError());
+    }
+    if (lanes == 2) {
+        CK(cudaEventRecord(g->wev, g->wst));
+        CK(cudaStreamWaitEvent(st, g->wev, 0));
+        if (backward) bcgb::ms_launch_merge(g->wbc2.p, g->bc.p, n, nullptr, nullptr, st);
+    }
+    // sources whose path counts need 64 bits: again with the 64-bit kernel
+    std::vector<uint8_t> redo((size_t)std::max(nsrc, 1));
+    CK(cudaMemcpyAsync(redo.data(), g->wredo.p, redo.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<int32_t> rpos, rsrc;
+    for (int32_t i = 0; i < nsrc; ++i)
+        if (redo[i]) {
+            rpos.push_back(i);
+            rsrc.push_back(g->h_sources[(size_t)i]);
+        }
+    for (size_t r0 = 0; r0 < rpos.size(); r0 += (size_t)G) {
+        const int nr = (int)std::min<size_t>((size_t)G, rpos.size() - r0);
+        CK(cudaMemcpyAsync(g->wpos.p, rpos.data() + r0, (size_t)nr * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(g->wsrc.p, rsrc.data() + r0, (size_t)nr * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        bcgb::WParams p = base;
+        p.sources = g->wsrc.p;
+        p.pos = g->wpos.p;
+        p.dist = g->wdist.p;
+        p.sigma = g->wsigma.p;
+        p.cval = g->wcval.p;
+        p.order = g->worder.p;
+        p.grp = g->wgrp.p;
+        p.slots = g->wslots.p;
+        p.delta_rows = backward ? g->wrows.p : nullptr;
+        if (hash) {
+            p.h_sigma = g->h_sigma.p;
+            p.h_dist = g->h_dist.p;
+            p.dist_sum = g->dist_sum.p;
+            p.reach = g->reach.p;
+        }
+        p.rows_sigma = rows_sig;
+        p.rows_dist = rows_dist;
         {
             Timer t(g, st, BC_KERNEL_FORWARD);
-            bcgb::w_launch_wave_packed(p, nw, st);
-        }
-        // sources whose path counts need 64 bits: again with the 64-bit kernel
-        std::vector<uint8_t> redo(nw);
-        CK(cudaMemcpyAsync(redo.data(), g->wredo.p, (size_t)nw, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        std::vector<int32_t> rpos, rsrc;
-        for (int i = 0; i < nw; ++i)
-            if (redo[i]) {
-                rpos.push_back(i);
-                rsrc.push_back(g->h_sources[(size_t)w0 + i]);
-            }
-        if (!rpos.empty()) {
-            CK(cudaMemcpyAsync(g->wpos.p, rpos.data(), rpos.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-            CK(cudaMemcpyAsync(g->wsrc.p, rsrc.data(), rsrc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-            bcgb::WParams p64 = p;
-            p64.sources = g->wsrc.p;
-            p64.pos = g->wpos.p;
-            Timer t(g, st, BC_KERNEL_FORWARD);
-            bcgb::w_launch_wave(p64, (int)rpos.size(), st);
+            bcgb::w_launch_wave(p, nr, st);
         }
         if (backward) {
             Timer t(g, st, BC_KERNEL_BACKWARD);
-            bcgb::w_launch_reduce(g->wrows.p, nw, n, g->bc.p, sm_count_host(), st);
+            bcgb::w_launch_reduce(g->wrows.p, nr, n, g->bc.p, sm_count_host(), st);
         }
         CK(cudaGetLastError());
     }

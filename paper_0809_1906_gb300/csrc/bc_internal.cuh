@@ -95,7 +95,8 @@ void ms_launch_hash(int W, const MsParams &p, int nlevels, cudaStream_t st);
 void ms_launch_rows(int W, const MsParams &p, int nlevels, uint64_t *sig_out, int32_t *dist_out,
                     cudaStream_t st);
 void launch_scale(double *x, int32_t n, double f, cudaStream_t st);
-// dst[i] += src[i] for i < n; to's status |= from's, its arc and depth sums += from's
+// dst[i] += src[i] for i < n; unless from is null, to's status |= from's and
+// its arc and depth sums += from's
 void ms_launch_merge(const double *src, double *dst, int32_t n, const DevCtl *from, DevCtl *to, cudaStream_t st);
 
 }  // namespace bcgb

@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(kBlock) k_rows(const MsParams p, const int L, 
 __global__ void k_merge(const double *__restrict__ src, double *__restrict__ dst, int32_t n, const DevCtl *from,
                         DevCtl *to) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] += src[i];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (from && blockIdx.x == 0 && threadIdx.x == 0) {
         atomicOr(&to->status, from->status);
         atomicAdd(&to->dag_arcs, from->dag_arcs);
         atomicAdd(&to->depth_sum, from->depth_sum);

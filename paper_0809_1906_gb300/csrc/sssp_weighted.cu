@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kWBlock, 4) k_wsssp(const WParams p) {
     int32_t *order = p.order + (size_t)i * n;
     int32_t *grp = p.grp + (size_t)i * (n + 1);
     int32_t *slots = p.slots + (size_t)i * p.K * p.C;
-    float *drow = p.delta_rows ? p.delta_rows + (size_t)o * n : nullptr;
+    float *drow = p.delta_rows ? p.delta_rows + (size_t)i * n : nullptr;  // reduced after the wave
 
     for (int v = tid; v < n; v += kWBlock) {
         dist[v] = kInf;

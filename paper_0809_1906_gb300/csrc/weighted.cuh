@@ -23,9 +23,10 @@ struct WParams {
     const int32_t *w_in;
     const int32_t *w;
     const int32_t *sources;  // this wave's sources
-    const int32_t *pos;      // output position of each CTA's source (null: its index)
+    const int32_t *pos;      // position of each CTA's source in the summaries and rows (null: its index);
+                             // delta rows are always at the CTA's index
     uint64_t *ds;            // [wave][n] packed state (distance << 32 | sigma or c bits)
-    uint8_t *redo;           // [wave] set where a count reached 2^32 (packed kernel)
+    uint8_t *redo;           // [wave] set where a count reached 2^32 (packed kernel; that source writes nothing)
     int32_t *dist;           // [wave][n]
     uint64_t *sigma;         // [wave][n]
     float *cval;             // [wave][n]
