@@ -245,13 +245,17 @@ struct bc_graph {
     std::vector<int32_t> h_sources;  // host copy of the staged source list
     DevBuf<uint64_t> wsigma;
     DevBuf<float> wcval, wrows;
-    // second lane of waves: its own stream, packed state, rows and BC accumulator
-    cudaStream_t wst = nullptr;
+    // lanes 1..3 of the weighted waves: stream, packed state, rows, BC accumulator
+    struct WLane {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        DevBuf<int32_t> order, grp, slots;
+        DevBuf<uint64_t> ds;
+        DevBuf<float> rows;
+        DevBuf<double> bc;
+    };
+    WLane wl[3];
     cudaEvent_t wev = nullptr;
-    DevBuf<int32_t> worder2, wgrp2, wslots2;
-    DevBuf<uint64_t> wds2;
-    DevBuf<float> wrows2;
-    DevBuf<double> wbc2;
 };
 
 namespace {
@@ -273,12 +277,15 @@ void free_graph(bc_graph *g) {
     g->gbcpart.release();
     g->gmeta.release();
     for (auto *b : {&g->wpos, &g->wsrc}) b->release();
-    for (auto *b : {&g->worder2, &g->wgrp2, &g->wslots2}) b->release();
-    g->wds2.release();
-    g->wrows2.release();
-    g->wbc2.release();
+    for (auto &l : g->wl) {
+        for (auto *b : {&l.order, &l.grp, &l.slots}) b->release();
+        l.ds.release();
+        l.rows.release();
+        l.bc.release();
+        if (l.ev) cudaEventDestroy(l.ev);
+        if (l.st) cudaStreamDestroy(l.st);
+    }
     if (g->wev) cudaEventDestroy(g->wev);
-    if (g->wst) cudaStreamDestroy(g->wst);
     g->wds.release();
     g->wredo.release();
     g->bc.release();
@@ -1190,15 +1197,18 @@ int sm_count_host() {
 // Weighted path: waves of one CTA per source (csrc/sssp_weighted.cu).
 // opt->batch (if set) is the wave size; default 4 CTAs per SM, capped so the
 // wave state stays within 8 GiB.
-// Weighted sweep: waves of G sources (one CTA each, packed state) on two
-// lanes: wave k runs on lane k % 2, each lane with its own stream, state,
-// delta rows and BC accumulator, so one wave's slowest sources overlap the
-// next wave. The delta rows of a wave are added to its lane's BC in source
-// order right after the wave; lane 1's BC is added into the graph's at the
-// end, so the result does not change from run to run. Sources whose path
-// counts reach 2^32 write nothing in the packed kernel; they are flagged and
-// computed again at the end by the 64-bit kernel, whose delta rows are added
-// in the order of the flagged sources.
+// Weighted sweep: waves of G sources (one CTA each, packed state) on
+// kWeightedLanes lanes: wave k runs on lane k % lanes, each with its own stream,
+// state, delta rows and BC accumulator, so one wave's slowest sources overlap
+// the next waves. The delta rows of a wave are added to its lane's BC in
+// source order right after the wave; lanes 1.. are added into the graph's BC
+// in lane order at the end, so the result does not change from run to run.
+// Sources whose path counts reach 2^32 write nothing in the packed kernel;
+// they are flagged and computed again at the end by the 64-bit kernel, whose
+// delta rows are added in the order of the flagged sources.
+constexpr int kWeightedLanes = 2;  // measured: 3 or 4 lanes no faster on the 512x512 grid
+constexpr double kWeightedLaneBudget = 24.0 * (1 << 30);  // packed wave state of all lanes
+
 int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t st, bool backward, bool hash,
                  uint64_t *rows_sig, int32_t *rows_dist) {
     const int32_t n = g->n;
@@ -1213,7 +1223,11 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
     G = (int)std::min<size_t>((size_t)G, std::max<size_t>(1, (8ull << 30) / per_src));
     G = std::max(1, std::min(G, std::max(nsrc, 1)));
     const int32_t nwaves = (nsrc + G - 1) / G;
-    const int lanes = (nwaves >= 2 && !g->timing) ? 2 : 1;  // BC_TIMING: one lane, launch times of their own
+    // lanes: up to kWeightedLanes within the memory budget; BC_TIMING: one
+    // lane, so that every launch's event time is its own
+    const double lane_bytes = (double)G * ((double)n * 20.0 + (double)K * C * 4.0);
+    int lanes = g->timing ? 1 : std::min<int32_t>(kWeightedLanes, nwaves);
+    while (lanes > 1 && lanes * lane_bytes > kWeightedLaneBudget) --lanes;
     if (g->wG < G || g->wK != K || g->wC != C) {
         CK(g->wdist.ensure((size_t)G * n));
         CK(g->wsigma.ensure((size_t)G * n));
@@ -1229,26 +1243,24 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
         g->wK = K;
         g->wC = C;
     }
-    if (lanes == 2) {
-        if (!g->wst) {
-            CK(cudaStreamCreateWithFlags(&g->wst, cudaStreamNonBlocking));
-            CK(cudaEventCreateWithFlags(&g->wev, cudaEventDisableTiming));
-        }
-        CK(g->worder2.ensure((size_t)G * n));
-        CK(g->wgrp2.ensure((size_t)G * (n + 1)));
-        CK(g->wslots2.ensure((size_t)G * K * C));
-        CK(g->wrows2.ensure((size_t)G * n));
-        CK(g->wds2.ensure((size_t)G * n));
-        CK(g->wbc2.ensure((size_t)std::max(n, 1)));
-        CK(cudaEventRecord(g->wev, st));
-        CK(cudaStreamWaitEvent(g->wst, g->wev, 0));
-        CK(cudaMemsetAsync(g->wbc2.p, 0, (size_t)std::max(n, 1) * sizeof(double), g->wst));
-    }
     CK(g->wredo.ensure((size_t)std::max(nsrc, 1)));
     CK(cudaMemsetAsync(g->wredo.p, 0, (size_t)std::max(nsrc, 1), st));
-    if (lanes == 2) {
-        CK(cudaEventRecord(g->wev, st));
-        CK(cudaStreamWaitEvent(g->wst, g->wev, 0));
+    if (lanes > 1 && !g->wev) CK(cudaEventCreateWithFlags(&g->wev, cudaEventDisableTiming));
+    if (lanes > 1) CK(cudaEventRecord(g->wev, st));
+    for (int k = 1; k < lanes; ++k) {
+        auto &l = g->wl[k - 1];
+        if (!l.st) {
+            CK(cudaStreamCreateWithFlags(&l.st, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&l.ev, cudaEventDisableTiming));
+        }
+        CK(l.order.ensure((size_t)G * n));
+        CK(l.grp.ensure((size_t)G * (n + 1)));
+        CK(l.slots.ensure((size_t)G * K * C));
+        CK(l.rows.ensure((size_t)G * n));
+        CK(l.ds.ensure((size_t)G * n));
+        CK(l.bc.ensure((size_t)std::max(n, 1)));
+        CK(cudaStreamWaitEvent(l.st, g->wev, 0));
+        CK(cudaMemsetAsync(l.bc.p, 0, (size_t)std::max(n, 1) * sizeof(double), l.st));
     }
     bcgb::WParams base{};
     base.n = n;
@@ -1268,14 +1280,15 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
         const int32_t w0 = k * G;
         const int nw = std::min<int32_t>(G, nsrc - w0);
         const int ln = k % lanes;
-        const cudaStream_t ls = ln == 0 ? st : g->wst;
+        bc_graph::WLane *l = ln == 0 ? nullptr : &g->wl[ln - 1];
+        const cudaStream_t ls = l ? l->st : st;
         bcgb::WParams p = base;
         p.sources = g->sources.p + w0;
-        p.order = ln == 0 ? g->worder.p : g->worder2.p;
-        p.grp = ln == 0 ? g->wgrp.p : g->wgrp2.p;
-        p.slots = ln == 0 ? g->wslots.p : g->wslots2.p;
-        p.ds = ln == 0 ? g->wds.p : g->wds2.p;
-        float *rows = ln == 0 ? g->wrows.p : g->wrows2.p;
+        p.order = l ? l->order.p : g->worder.p;
+        p.grp = l ? l->grp.p : g->wgrp.p;
+        p.slots = l ? l->slots.p : g->wslots.p;
+        p.ds = l ? l->ds.p : g->wds.p;
+        float *rows = l ? l->rows.p : g->wrows.p;
         p.delta_rows = backward ? rows : nullptr;
         if (hash) {
             p.h_sigma = g->h_sigma.p + w0;
@@ -1292,15 +1305,16 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
         }
         if (backward) {
             Timer t(g, ls, BC_KERNEL_BACKWARD);
-            bcgb::w_launch_reduce(rows, nw, n, ln == 0 ? g->bc.p : g->wbc2.p, sm_count_host(), ls);
+            bcgb::w_launch_reduce(rows, nw, n, l ? l->bc.p : g->bc.p, sm_count_host(), ls);
         }
         CK(cudaGetLastError());
     }
-    if (lanes == 2) {
-        CK(cudaEventRecord(g->wev, g->wst));
-        CK(cudaStreamWaitEvent(st, g->wev, 0));
-        if (backward) bcgb::ms_launch_merge(g->wbc2.p, g->bc.p, n, nullptr, nullptr, st);
+    for (int k = 1; k < lanes; ++k) {
+        auto &l = g->wl[k - 1];
+        CK(cudaEventRecord(l.ev, l.st));
+        CK(cudaStreamWaitEvent(st, l.ev, 0));
     }
+    for (int k = 1; k < lanes && backward; ++k) bcgb::ms_launch_merge(g->wl[k - 1].bc.p, g->bc.p, n, nullptr, nullptr, st);
     // sources whose path counts need 64 bits: again with the 64-bit kernel
     std::vector<uint8_t> redo((size_t)std::max(nsrc, 1));
     CK(cudaMemcpyAsync(redo.data(), g->wredo.p, redo.size(), cudaMemcpyDeviceToHost, st));
