@@ -450,7 +450,7 @@ def run_profile(args):
     else:
         gs = G.many_graphs(args.sources or 200)
         hs = [native.Graph.from_csr(x, trust_input=True) for x in gs]
-        with native.ManyPlan(hs, batch=64) as plan:
+        with native.ManyPlan(hs, batch=256) as plan:
             plan.run()
             code, _, rerun = plan.result()
         torch.cuda.synchronize()

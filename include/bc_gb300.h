@@ -26,9 +26,14 @@
  *   - Pointer arguments marked "host or device" may be either: copies use
  *     unified addressing (cudaMemcpyDefault).
  *   - cuda_stream: a cudaStream_t passed as void* (NULL = legacy default
- *     stream). All device work of a call is ordered on it.
+ *     stream). A call's work starts after the work already on it and ends
+ *     before anything enqueued on it later: bc_run spreads the batches over
+ *     internal streams (lanes) that fork from cuda_stream when it starts and
+ *     join it before it returns.
  *   - The library allocates the device memory it needs (cudaMalloc) and frees
- *     it in bc_destroy_graph. Caller buffers stay owned by the caller.
+ *     it in bc_destroy_graph, except the lanes' streams and buffers, which are
+ *     kept for the next graph created on the same device. Caller buffers stay
+ *     owned by the caller.
  *   - A graph handle may be used by one thread at a time.
  */
 #ifndef BC_GB300_H
@@ -75,7 +80,8 @@ extern "C" {
 #define BC_HALVE 0x1u        /* divide BC by 2 (unordered pairs, Section 1.1) */
 #define BC_ACCUMULATE 0x2u   /* add to the previous run's BC instead of starting from 0 */
 #define BC_PLAIN 0x4u        /* one source per launch sequence (the unbatched GPU Brandes) */
-#define BC_TIMING 0x8u       /* record CUDA events around every kernel launch (bc_kernel_time) */
+#define BC_TIMING 0x8u       /* record CUDA events around every kernel launch (bc_kernel_time); the run
+                                uses one lane so that each launch's event time is its own */
 #define BC_NO_HASH 0x10u     /* skip the per-source summary values */
 #define BC_DENSE 0x20u       /* the algebraic forms of Section 3. Unweighted graphs: levels >= 1 as
                                 tensor-core products with the 0/1 adjacency matrix, forward
@@ -148,8 +154,11 @@ int bc_create_graph(int32_t n, const int32_t *row_ptr, const int32_t *col, const
  *   opt          NULL = defaults.
  * Without BC_ACCUMULATE the result starts from zero. Returns when all work is
  * enqueued on cuda_stream, except for the bounded host waits the level loop
- * needs to learn each batch's depth. Errors: BC_ERR_ARG, BC_ERR_OOM,
- * BC_ERR_CUDA, BC_ERR_TIMEOUT, BC_ERR_UNSUPPORTED.
+ * needs to learn each batch's depth. Unweighted batches run on up to eight
+ * concurrent lanes (batch i on lane i mod lanes, each lane with its own state
+ * and BC accumulator, added in lane order at the end); weighted waves on two.
+ * The assignment is fixed, so repeated runs give identical results. Errors:
+ * BC_ERR_ARG, BC_ERR_OOM, BC_ERR_CUDA, BC_ERR_TIMEOUT, BC_ERR_UNSUPPORTED.
  */
 int bc_run(bc_graph *g, const int32_t *sources, int32_t num_sources, const bc_options *opt,
            void *cuda_stream);
