@@ -14,7 +14,8 @@
 // k_mp_step is a GEMM-shaped kernel on CUDA cores (there is no tensor-core
 // min-plus): a block owns 64 sources x 64 targets, stages 32 intermediate
 // vertices u at a time (distances, counts, weight rows) in shared memory, and
-// each thread keeps a 4 x 4 tile of (d, c) in registers. Counts are uint64
+// each thread keeps a 4 x 4 tile of (d, c) in registers, in two passes over u
+// (least weights, then the counts that reach them). Counts are uint64
 // (mod 2^64, a carry sets the overflow status bit); distances int32 with
 // kMpInf for "no walk yet" (the caller guarantees every distance < 2^30).
 #include <cuda_runtime.h>
@@ -44,64 +45,109 @@ __global__ void __launch_bounds__(256) k_mp_init(int32_t *__restrict__ xd, uint6
 }
 
 // wm: [n][n] weight of arc (u, v), kMpInf when there is none.
+// Two passes over the intermediate vertices u: the first finds the least
+// walk weight of every (s, v) of the tile (an add and a min per element), the
+// second adds the counts of the walks that reach it (a compare and a
+// predicated 64-bit add whose carry is kept, per element). That is about
+// half the instructions of one pass that tracks both together.
+__device__ __forceinline__ void add_if_equal(int32_t t, int32_t b, uint32_t alo, uint32_t ahi, uint32_t &lo,
+                                             uint32_t &hi, uint32_t &ov) {
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.eq.s32 p, %3, %4;\n\t"
+        "@p add.cc.u32 %0, %0, %5;\n\t"
+        "@p addc.cc.u32 %1, %1, %6;\n\t"
+        "@p addc.u32 %2, %2, 0;\n\t}"
+        : "+r"(lo), "+r"(hi), "+r"(ov)
+        : "r"(t), "r"(b), "r"(alo), "r"(ahi));
+}
+
 __global__ void __launch_bounds__(kMBlk) k_mp_step(const int32_t *__restrict__ xd, const uint64_t *__restrict__ xc,
                                                    int32_t *__restrict__ yd, uint64_t *__restrict__ yc,
                                                    const int32_t *__restrict__ wm, const int32_t *__restrict__ src,
                                                    int nb, int n, uint32_t *__restrict__ flags,
                                                    uint32_t *__restrict__ status) {
-    __shared__ int32_t s_d[kMU][kMS + 1];   // transposed: [u][s], padded against bank conflicts
-    __shared__ uint64_t s_c[kMU][kMS + 1];
+    __shared__ int32_t s_d[kMU][kMS + 1];  // transposed: [u][s], padded against bank conflicts
+    __shared__ uint32_t s_lo[kMU][kMS + 1];
+    __shared__ uint32_t s_hi[kMU][kMS + 1];
     __shared__ int32_t s_w[kMU][kMV];
     const int s0 = blockIdx.y * kMS, v0 = blockIdx.x * kMV;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // target group, source group
-    int32_t best[4][4];
-    uint64_t cnt[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            best[i][j] = kMpInf;
-            cnt[i][j] = 0ull;
-        }
-    bool carry = false;
-    for (int u0 = 0; u0 < n; u0 += kMU) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < kMU * kMS; i += kMBlk) {
-            const int r = i / kMU, c = i % kMU;  // source r, vertex u0 + c (coalesced along u)
-            const int s = s0 + r, u = u0 + c;
-            const bool in = s < nb && u < n;
-            s_d[c][r] = in ? xd[(size_t)s * n + u] : kMpInf;
-            s_c[c][r] = in ? xc[(size_t)s * n + u] : 0ull;
-        }
+    auto load_w = [&](int u0) {
         for (int i = threadIdx.x; i < kMU * kMV; i += kMBlk) {
             const int r = i / kMV, c = i % kMV;
             const int u = u0 + r, v = v0 + c;
             s_w[r][c] = (u < n && v < n) ? wm[(size_t)u * n + v] : kMpInf;
         }
+    };
+    int32_t best[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) best[i][j] = kMpInf;
+    // pass 1: least walk weights
+    for (int u0 = 0; u0 < n; u0 += kMU) {
         __syncthreads();
-#pragma unroll 2
+        for (int i = threadIdx.x; i < kMU * kMS; i += kMBlk) {
+            const int r = i / kMU, c = i % kMU;  // source r, vertex u0 + c (coalesced along u)
+            const int s = s0 + r, u = u0 + c;
+            s_d[c][r] = (s < nb && u < n) ? xd[(size_t)s * n + u] : kMpInf;
+        }
+        load_w(u0);
+        __syncthreads();
+#pragma unroll 4
         for (int k = 0; k < kMU; ++k) {
             int32_t ad[4], wv[4];
-            uint64_t ac[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 ad[i] = s_d[k][ty + 16 * i];
-                ac[i] = s_c[k][ty + 16 * i];
                 wv[i] = s_w[k][tx + 16 * i];
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int32_t t = ad[i] + wv[j];  // both below 2^30: no overflow
-                    const uint64_t sum = cnt[i][j] + ac[i];
-                    carry |= t == best[i][j] && sum < ac[i];
-                    cnt[i][j] = t < best[i][j] ? ac[i] : (t == best[i][j] ? sum : cnt[i][j]);
-                    best[i][j] = min(best[i][j], t);
-                }
+                for (int j = 0; j < 4; ++j) best[i][j] = min(best[i][j], ad[i] + wv[j]);  // both below 2^30
+        }
+    }
+    // pass 2: counts of the walks of least weight
+    uint32_t lo[4][4], hi[4][4], ov[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        ov[i] = 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) lo[i][j] = hi[i][j] = 0u;
+    }
+    for (int u0 = 0; u0 < n; u0 += kMU) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < kMU * kMS; i += kMBlk) {
+            const int r = i / kMU, c = i % kMU;
+            const int s = s0 + r, u = u0 + c;
+            const bool in = s < nb && u < n;
+            const uint64_t x = in ? xc[(size_t)s * n + u] : 0ull;
+            s_d[c][r] = in ? xd[(size_t)s * n + u] : kMpInf;
+            s_lo[c][r] = (uint32_t)x;
+            s_hi[c][r] = (uint32_t)(x >> 32);
+        }
+        load_w(u0);
+        __syncthreads();
+#pragma unroll 2
+        for (int k = 0; k < kMU; ++k) {
+            int32_t ad[4], wv[4];
+            uint32_t alo[4], ahi[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                ad[i] = s_d[k][ty + 16 * i];
+                alo[i] = s_lo[k][ty + 16 * i];
+                ahi[i] = s_hi[k][ty + 16 * i];
+                wv[i] = s_w[k][tx + 16 * i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) add_if_equal(ad[i] + wv[j], best[i][j], alo[i], ahi[i], lo[i][j], hi[i][j], ov[i]);
         }
     }
     bool changed = false;
+    bool carry = false;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int s = s0 + ty + 16 * i;
@@ -112,7 +158,8 @@ __global__ void __launch_bounds__(kMBlk) k_mp_step(const int32_t *__restrict__ x
             const int v = v0 + tx + 16 * j;
             if (v >= n) continue;
             int32_t d = best[i][j] >= kMpInf ? kMpInf : best[i][j];
-            uint64_t c = d >= kMpInf ? 0ull : cnt[i][j];
+            uint64_t c = d >= kMpInf ? 0ull : (((uint64_t)hi[i][j] << 32) | lo[i][j]);
+            if (d < kMpInf) carry |= ov[i] != 0u;
             if (v == self) {  // the empty walk; every other walk back to s is longer
                 d = 0;
                 c = 1ull;
