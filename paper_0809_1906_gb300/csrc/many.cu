@@ -83,7 +83,8 @@ __global__ void __launch_bounds__(kMBlock, W >= 4 ? 3 : 4) k_many(const ManyPara
                 F[(size_t)s * W + (b >> 5)] |= 1u << (b & 31);  // one source per (s, b): no race
                 atomicOr(ufr + (s >> 5), 1u << (s & 31));
                 sigma[(size_t)s * B + b] = 1ull;
-                for (int k = 0; k < B; ++k) Sbuf[(size_t)s * B + k] = k == b ? 1 : 0;  // masked level-0 row
+                // masked level-0 row: the word holding b (the only word read)
+                for (int k = 32 * (b >> 5); k < 32 * (b >> 5) + 32; ++k) Sbuf[(size_t)s * B + k] = k == b ? 1 : 0;
             }
             __syncthreads();
             // forward levels
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(kMBlock, W >= 4 ? 3 : 4) k_many(const ManyPara
                         }
                         body::fwd_sum<W, false>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufl, Fl, Sl, sigma, wide, false, U,
                                                 s_u[wib], s_nz[wib], lane, acc, nf, ovf, arcs);
-                        produced |= body::store_next<W>(sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
+                        produced |= body::store_next<W, false>(sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
                     }
                 }
                 wide = __syncthreads_or(wide_next);
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(kMBlock, W >= 4 ? 3 : 4) k_many(const ManyPara
 #pragma unroll
                         for (int j = 0; j < W; ++j) S[j] = 0.0f;
                         body::bwd_sum<W, false>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufs, Fs, Cs, f, s_u[wib], s_nz[wib], lane, S);
-                        body::finalize_dep<W>(sigma, Cl, target, v, f, S, lane);
+                        body::finalize_dep<W, false>(sigma, Cl, target, v, f, S, lane);
                     }
                 }
                 __syncthreads();

@@ -184,9 +184,7 @@ __device__ __forceinline__ void unpack_lanes(T *p, const T (&x)[W], T (&out)[W],
 // One 32-arc chunk: lane k gets arc e (if e < end), its neighbour u_k (stored
 // in s_u[k]) and masks m_k[j] = frontier words of u_k AND want[j] (zero for
 // arcs that cannot contribute); s_nz[k] gets the W-bit set of non-zero words
-// of m_k, so the backward adder loads only the words that can contribute
-// (measured: a gain there, a loss in the forward adder, which loads whole
-// rows).
+// of m_k, so the adders load only the words that can contribute.
 // Returns the ballot of contributing lanes; u and nz are lane k's own
 // neighbour and word set.
 template <int W, bool NC>
@@ -313,9 +311,12 @@ __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg
                 acc[j] = y;
             }
         } else if (!wide) {
-            // two neighbours per step: 2W independent coalesced loads in flight.
-            // At most 32 values below 2^16 per chunk: 32-bit sums are exact and
-            // are folded into the 64-bit ones once per chunk.
+            // two neighbours per step: up to 2W independent coalesced loads in
+            // flight, only the words that can contribute (the many-graph kernel:
+            // its batch state does not fit L2, so every word skipped is DRAM
+            // traffic saved; 411 -> 382 ms on the 2000-graph set). At most 32
+            // values below 2^16 per chunk: 32-bit sums are exact and are folded
+            // into the 64-bit ones once per chunk.
             const uint16_t *base = Sl + lane;
             uint32_t a32[W];
 #pragma unroll
@@ -327,11 +328,12 @@ __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg
                 if (k1 >= 0) bal &= bal - 1;
                 const uint16_t *r0 = base + (size_t)s_u[k0] * B;
                 const uint16_t *r1 = base + (size_t)s_u[k1 >= 0 ? k1 : k0] * B;
+                const uint32_t z0 = s_nz[k0], z1 = k1 >= 0 ? s_nz[k1] : 0u;
                 uint32_t x0[W], x1[W];
 #pragma unroll
                 for (int j = 0; j < W; ++j) {
-                    x0[j] = (uint32_t)ldx<NC>(r0 + 32 * j);
-                    x1[j] = k1 >= 0 ? (uint32_t)ldx<NC>(r1 + 32 * j) : 0u;
+                    x0[j] = ((z0 >> j) & 1u) ? (uint32_t)ldx<NC>(r0 + 32 * j) : 0u;
+                    x1[j] = ((z1 >> j) & 1u) ? (uint32_t)ldx<NC>(r1 + 32 * j) : 0u;
                 }
 #pragma unroll
                 for (int j = 0; j < W; ++j) a32[j] += x0[j] + x1[j];
@@ -542,10 +544,13 @@ __device__ __forceinline__ void bwd_sum(const int32_t *__restrict__ col, int beg
 }
 
 // Store sigma and the new frontier words of v (its level-(l+1) sums are final).
-// Sn: the masked level-(l+1) uint16 row buffer, written in full (zeros for
-// the sources v is not new for) when v joins some frontier. Returns whether
-// v joined; wide is set when one of its new counts needs more than 16 bits.
-template <int W>
+// Sn: the masked level-(l+1) uint16 row buffer (zeros for the sources v is
+// not new for), written in full when v joins some frontier, or with
+// ALL_WORDS = false only in the words that hold a new source of v: every
+// adder reads word j of v's row only when v is in frontier l+1 for a source
+// of word j. Returns whether v joined; wide is set when one of its new counts
+// needs more than 16 bits.
+template <int W, bool ALL_WORDS = true>
 __device__ __forceinline__ bool store_next(uint64_t *sigma, uint16_t *Sn, uint32_t *Fn, uint32_t *ufn, int v,
                                            const uint64_t (&acc)[W], const uint32_t (&nf)[W], int lane,
                                            bool &wide) {
@@ -562,7 +567,7 @@ __device__ __forceinline__ bool store_next(uint64_t *sigma, uint16_t *Sn, uint32
         for (int j = 0; j < W; ++j) {
             const bool mine = (nf[j] >> lane) & 1u;
             wide |= mine && (acc[j] >> 16) != 0ull;
-            Sn[(size_t)v * B + 32 * j + lane] = mine ? (uint16_t)acc[j] : (uint16_t)0;
+            if (ALL_WORDS || nf[j] != 0u) Sn[(size_t)v * B + 32 * j + lane] = mine ? (uint16_t)acc[j] : (uint16_t)0;
         }
     }
     if (any != 0 && lane == 0) atomicOr(ufn + (v >> 5), 1u << (v & 31));
@@ -574,13 +579,15 @@ __device__ __forceinline__ float sigma_f32(uint64_t x) {
     return (x >> 32) ? __ull2float_rn(x) : __uint2float_rn((uint32_t)x);
 }
 
-// Cl: the masked level-l c buffer, written in full (zeros for the sources v
-// is not at level l for). For s with d(s,v) = l: delta_s(v) = sigma_s(v) * S
+// Cl: the masked level-l c buffer (zeros for the sources v is not at level l
+// for), written in full, or with ALL_WORDS = false only in the words that
+// hold a level-l source of v (every backward adder reads word j of v's row
+// only when v is at level l for a source of word j). For s with d(s,v) = l: delta_s(v) = sigma_s(v) * S
 // and c_s(v) = (1 + delta_s(v)) / sigma_s(v) = 1/sigma_s(v) + S. The batch's
 // delta values of v are all >= 0 and are added in FP32, 8 per lane in order
 // then a 5-step tree across the warp (relative error at most 12 * 2^-24), and
 // the vertex's total goes into bc[v] in FP64.
-template <int W>
+template <int W, bool ALL_WORDS = true>
 __device__ __forceinline__ void finalize_dep(const uint64_t *sigma, float *Cl, double *bc, int v,
                                              const uint32_t (&f)[W], const float (&S)[W], int lane) {
     constexpr int B = 32 * W;
@@ -595,7 +602,7 @@ __device__ __forceinline__ void finalize_dep(const uint64_t *sigma, float *Cl, d
             c = __fdividef(1.0f, sg) + S[j];     // c_s(v) for the level above
             sum += d;
         }
-        Cl[idx] = c;
+        if (ALL_WORDS || f[j] != 0u) Cl[idx] = c;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(kFull, sum, off);
