@@ -101,7 +101,7 @@ struct SweepLane {
     int dev = -1;  // device of the stream and buffers
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
-    int32_t W = 0, Lcap = 0, n = 0;
+    int32_t W = 0, Lcap = 0, n = 0, s_levels = 2;
     size_t slots = 0;
     DevBuf<uint64_t> sigma, part;
     DevBuf<float> cval;
@@ -185,6 +185,7 @@ struct bc_graph {
 
     // multi-source batch state for (W, Lcap)
     int32_t W = 0, Lcap = 0;
+    int32_t s_levels = 2;  // masked-row buffers: Lcap (one per level) or 2 (by parity)
     DevBuf<uint64_t> sigma, part;
     DevBuf<float> cval;
     DevBuf<uint16_t> Smask;
@@ -443,13 +444,22 @@ void use_plan(bcgb::MsParams &p, const ItemPlan &pl) {
     p.slot_nch = pl.slot_nch;
 }
 
+// One masked-row buffer per level lets the backward read each pair's count
+// as 2 bytes (instead of the 8-byte sigma); it costs Lcap rows per vertex, so
+// deep graphs (a large level capacity) keep the two parity buffers instead.
+constexpr double kSLevelsBudget = 1.5 * (1 << 30);
+int s_levels_for(size_t n, size_t B, int Lcap) {
+    return (double)Lcap * (double)n * (double)B * 2.0 <= kSLevelsBudget ? Lcap : 2;
+}
+
 int ensure_state(bc_graph *g, int W, int Lcap) {
     if (g->W == W && g->Lcap >= Lcap && g->sigma.p) return BC_OK;
     const size_t n = (size_t)std::max(g->n, 1);
     const size_t B = 32 * (size_t)W;
     const size_t nw32 = (n + 31) / 32;
     CK(g->sigma.ensure(n * B));
-    CK(g->Smask.ensure(2 * n * B));
+    g->s_levels = s_levels_for(n, B, Lcap);
+    CK(g->Smask.ensure((size_t)g->s_levels * n * B));
     CK(g->wideflags.ensure((size_t)Lcap));
     CK(g->cval.ensure(2 * n * B));
     CK(g->F.ensure((size_t)Lcap * n * W));
@@ -516,6 +526,7 @@ bcgb::MsParams make_params(bc_graph *g) {
     use_plan(p, g->fplan);
     p.sigma = g->sigma.p;
     p.S = g->Smask.p;
+    p.s_levels = g->s_levels;
     p.wide = g->wideflags.p;
     p.cval = g->cval.p;
     p.F = g->F.p;
@@ -554,7 +565,8 @@ int ensure_lane(bc_graph *g, SweepLane &ln, int W, int Lcap) {
     const size_t B = 32 * (size_t)W;
     const size_t nw32 = (n + 31) / 32;
     CK(ln.sigma.ensure(n * B));
-    CK(ln.Smask.ensure(2 * n * B));
+    ln.s_levels = s_levels_for(n, B, Lcap);
+    CK(ln.Smask.ensure((size_t)ln.s_levels * n * B));
     CK(ln.wideflags.ensure((size_t)Lcap));
     CK(ln.cval.ensure(2 * n * B));
     CK(ln.F.ensure((size_t)Lcap * n * W));
@@ -580,6 +592,7 @@ bcgb::MsParams lane_params(bc_graph *g, int k) {
     p.Lcap = ln.Lcap;
     p.sigma = ln.sigma.p;
     p.S = ln.Smask.p;
+    p.s_levels = ln.s_levels;
     p.wide = ln.wideflags.p;
     p.cval = ln.cval.p;
     p.F = ln.F.p;
@@ -770,6 +783,7 @@ int run_dense_group(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream
             p.seq = ++g->seq;
             p.sources = g->sources.p + b0;
             p.sigma = g->gsigma.p + b * sstr;
+            p.s_levels = 2;  // the dense levels write sigma only: the backward reads it there
             p.F = g->gF.p + b * fstr;
             p.V = g->gV.p + b * vstr;
             p.ufr = g->gufr.p + b * ustr;
@@ -1089,7 +1103,8 @@ int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStr
         // memory budget for the extra lanes' batch state. With BC_TIMING one
         // lane, so that every launch's event time is its own.
         const int32_t nbat = (nsrc + B - 1) / B;
-        const double lane_bytes = (double)std::max(g->n, 1) * ((double)B * 28.0 + (double)g->Lcap * W * 4.0 + 16.0);
+        const double lane_bytes = (double)std::max(g->n, 1) * ((double)B * 24.0 + (double)g->Lcap * W * 4.0 + 16.0) +
+                                  (double)g->s_levels * std::max(g->n, 1) * B * 2.0;
         int K = g->timing ? 1 : std::min<int32_t>(kSweepLanes, nbat);
         while (K > 1 && (K - 1) * lane_bytes > kLaneBudgetBytes) --K;
         if (K > 1) return run_lanes(g, nsrc, W, K, st, backward, hash, rows_sig, rows_dist, wait_ms);

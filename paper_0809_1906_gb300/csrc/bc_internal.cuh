@@ -4,8 +4,10 @@
 // vertices; every per-vertex row is contiguous so a warp reads a neighbour's
 // row in one coalesced access):
 //   sigma  uint64 [n][B]        exact path counts sigma_s(v)        (Section 1.1)
-//   S      uint16 [2][n][B]     masked rows by level parity: sigma_s(v) where
-//                               d(s,v) = l, 0 for the other sources
+//   S      uint16 [s_levels][n][B]  masked rows: sigma_s(v) where d(s,v) = l,
+//                               0 for the other sources; one buffer per level
+//                               (s_levels = Lcap), or two by level parity
+//                               (s_levels = 2)
 //   wide   uint32 [Lcap]        level l has a count >= 2^16 (S unusable there)
 //   cval   float  [2][n][B]     masked rows by level parity of
 //                               c_s(v) = (1 + delta_s*(v)) / sigma_s(v)
@@ -66,7 +68,10 @@ struct MsParams {
     const int32_t *slot_nch;    // number of chunks of that vertex
     const int32_t *sources;     // this batch's source ids [nb]
     uint64_t *sigma;
-    uint16_t *S;   // [2][n][B]
+    uint16_t *S;   // [s_levels][n][B]
+    int32_t s_levels;  // Lcap: level l in buffer l, which the backward reads for sigma; 2: by parity
+    const uint16_t *S_rd;  // set per forward launch: the buffer of level l (read)
+    uint16_t *S_wr;        // and of level l+1 (written)
     uint32_t *wide;  // [Lcap]
     float *cval;   // [2][n][B]
     uint32_t *F;

@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     const uint32_t *Vin = p.V + (size_t)(l & 1) * nW;
     uint32_t *Vout = p.V + (size_t)((l + 1) & 1) * nW;
     const size_t nB = (size_t)p.n * B;
-    const uint16_t *Sl = p.S + (size_t)(l & 1) * nB;
-    uint16_t *Sn = p.S + (size_t)((l + 1) & 1) * nB;
+    const uint16_t *Sl = p.S_rd;  // masked rows of level l and l+1 (set by the launcher)
+    uint16_t *Sn = p.S_wr;
     const bool wide = *(volatile uint32_t *)(p.wide + l) != 0u;
     const bool ones = l == 1 && p.first;  // level 1 written by k_first: all counts 1, no masked rows
     bool produced = false, ovf = false, wide_next = false;
@@ -348,9 +348,18 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
     body::WarpStage ws{s_stage + wib * stage::kBwdStageBytes, s_bar + wib, s_qz[wib], 0u, false};
     if (lane == 0) stage::bar_init(ws.bar);
     __syncwarp();
+    // where the finalize reads sigma_s(v) for the pairs at level l: none at
+    // level 1 from k_first (every count is 1), the level's masked uint16 row
+    // when each level has its own buffer and the level is narrow, else the
+    // uint64 array
+    const bool sig_ones = l == 1 && p.first;
+    const uint16_t *Sl = (!sig_ones && p.s_levels > 2 && *(volatile const uint32_t *)(p.wide + l) == 0u)
+                             ? p.S + (size_t)l * nB
+                             : nullptr;
     // sigma row span of item k of the group (its words at level l), brought
     // into L2 two items ahead of the step that reads it
     auto prefetch_sigma = [&](int k) {
+        if (sig_ones) return;
         uint32_t any = 0;
         int lo = W, hi = -1;
 #pragma unroll
@@ -362,8 +371,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
                 hi = j;
             }
         }
-        if (any != 0u)
-            stage::prefetch_l2(p.sigma + (size_t)s_v[wib][k] * B + 32 * lo, 256u * (uint32_t)(hi - lo + 1));
+        if (any != 0u) {
+            if (Sl)
+                stage::prefetch_l2(Sl + (size_t)s_v[wib][k] * B + 32 * lo, 64u * (uint32_t)(hi - lo + 1));
+            else
+                stage::prefetch_l2(p.sigma + (size_t)s_v[wib][k] * B + 32 * lo, 256u * (uint32_t)(hi - lo + 1));
+        }
     };
     // the forward pass's item striding; lane k of a warp checks whether its
     // k-th next item's vertex is at level l for any source (the same for all
@@ -410,7 +423,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
             for (int j = 0; j < W; ++j) S[j] = 0.0f;
             body::bwd_sum<W, true, true>(p.col, beg, end, ufs, Fs, Cs, f, s_u[wib], s_nz[wib], lane, S, &ws);
             if (slot < 0) {
-                body::finalize_dep<W>(p.sigma, Cl, p.bc, v, f, S, lane);
+                body::finalize_dep<W>(p.sigma, Sl, sig_ones, Cl, p.bc, v, f, S, lane);
                 continue;
             }
             float *pp = reinterpret_cast<float *>(p.part) + (size_t)slot * B + lane;
@@ -433,7 +446,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
 #pragma unroll
                 for (int j = 0; j < W; ++j) S[j] += __ldcg(q + 32 * j);
             }
-            body::finalize_dep<W>(p.sigma, Cl, p.bc, v, f, S, lane);
+            body::finalize_dep<W>(p.sigma, Sl, sig_ones, Cl, p.bc, v, f, S, lane);
             if (lane == 0) p.cnt[first] = 0u;
         }
     }
@@ -636,8 +649,12 @@ void ms_launch_first(int W, const MsParams &p, cudaStream_t st) {
     BCGB_DISPATCH_W(W, pdl::launch(k_first<kW>, 2 * sm_count(), kBlock, 0, st, p));
 }
 
-void ms_launch_forward(int W, const MsParams &p, int level, cudaStream_t st) {
-    if (p.nitems == 0) return;
+void ms_launch_forward(int W, const MsParams &p0, int level, cudaStream_t st) {
+    if (p0.nitems == 0) return;
+    MsParams p = p0;
+    const size_t nB = (size_t)p.n * 32 * W;
+    p.S_rd = p.S + (size_t)(level % p.s_levels) * nB;  // one buffer per level, or two by parity
+    p.S_wr = p.S + (size_t)((level + 1) % p.s_levels) * nB;
     BCGB_DISPATCH_W(W, (fwd_attr<kW>(),
                         pdl::launch(k_forward<kW>, item_blocks(p, k_forward<kW>, kFwdSmem), kBlock, kFwdSmem, st, p,
                                     level)));

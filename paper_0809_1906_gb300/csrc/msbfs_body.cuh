@@ -587,9 +587,13 @@ __device__ __forceinline__ float sigma_f32(uint64_t x) {
 // delta values of v are all >= 0 and are added in FP32, 8 per lane in order
 // then a 5-step tree across the warp (relative error at most 12 * 2^-24), and
 // the vertex's total goes into bc[v] in FP64.
+// sigma_s(v) comes from the level's masked uint16 row Sl when given (a
+// narrow level: every count below 2^16), is 1 when `ones` (level 1, reached
+// from the sources directly), else from the uint64 array.
 template <int W, bool ALL_WORDS = true>
-__device__ __forceinline__ void finalize_dep(const uint64_t *sigma, float *Cl, double *bc, int v,
-                                             const uint32_t (&f)[W], const float (&S)[W], int lane) {
+__device__ __forceinline__ void finalize_dep(const uint64_t *sigma, const uint16_t *Sl, bool ones, float *Cl,
+                                             double *bc, int v, const uint32_t (&f)[W], const float (&S)[W],
+                                             int lane) {
     constexpr int B = 32 * W;
     float sum = 0.0f;
 #pragma unroll
@@ -597,7 +601,7 @@ __device__ __forceinline__ void finalize_dep(const uint64_t *sigma, float *Cl, d
         const size_t idx = (size_t)v * B + 32 * j + lane;
         float c = 0.0f;
         if ((f[j] >> lane) & 1u) {
-            const float sg = sigma_f32(sigma[idx]);
+            const float sg = ones ? 1.0f : (Sl ? __uint2float_rn((uint32_t)Sl[idx]) : sigma_f32(sigma[idx]));
             const float d = sg * S[j];           // delta_s(v) = sigma_s(v) * sum_w c_s(w)
             c = __fdividef(1.0f, sg) + S[j];     // c_s(v) for the level above
             sum += d;
@@ -607,6 +611,12 @@ __device__ __forceinline__ void finalize_dep(const uint64_t *sigma, float *Cl, d
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(kFull, sum, off);
     if (lane == 0) bc[v] += (double)sum;
+}
+
+template <int W, bool ALL_WORDS = true>
+__device__ __forceinline__ void finalize_dep(const uint64_t *sigma, float *Cl, double *bc, int v,
+                                             const uint32_t (&f)[W], const float (&S)[W], int lane) {
+    finalize_dep<W, ALL_WORDS>(sigma, nullptr, false, Cl, bc, v, f, S, lane);
 }
 
 }  // namespace body

@@ -132,6 +132,7 @@ extern "C" int bc_run_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *
     p.slot_nch = dummy;
     p.sigma = reinterpret_cast<uint64_t *>(base + kOffSigma);
     p.S = reinterpret_cast<uint16_t *>(base + kOffS);
+    p.s_levels = 2;  // two masked-row buffers by level parity (the backward reads sigma)
     p.wide = reinterpret_cast<uint32_t *>(base + kOffWide);
     p.cval = reinterpret_cast<float *>(base + kOffCval);
     p.F = reinterpret_cast<uint32_t *>(base + kOffF);
