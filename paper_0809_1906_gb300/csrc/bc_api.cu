@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -623,6 +624,22 @@ int resolve_batch(const bc_options *opt, int *W) {
 // then by id; rank[v] is v's position. The distances come from one batched
 // forward pass on the device (ensure_rank); here, stable counting sorts,
 // last key first.
+// A barrier for the few host threads of rank_from_dist.
+struct SpinBarrier {
+    std::atomic<int> count{0}, gen{0};
+    int n;
+    explicit SpinBarrier(int n_) : n(n_) {}
+    void wait() {
+        const int g = gen.load(std::memory_order_acquire);
+        if (count.fetch_add(1, std::memory_order_acq_rel) == n - 1) {
+            count.store(0, std::memory_order_relaxed);
+            gen.fetch_add(1, std::memory_order_release);
+        } else {
+            while (gen.load(std::memory_order_acquire) == g) std::this_thread::yield();
+        }
+    }
+};
+
 void rank_from_dist(bc_graph *g, std::vector<int32_t> &dist, int k) {
     const int32_t n = g->n;
     // Each vertex's key: its distances to landmarks 0, 1, ... (unreachable
@@ -630,48 +647,98 @@ void rank_from_dist(bc_graph *g, std::vector<int32_t> &dist, int k) {
     // bits, each field just wide enough for its landmark's largest value;
     // landmarks that no longer fit are left out. A stable LSD radix sort on
     // the key (8-bit digits, digits every key shares skipped) orders the
-    // vertices lexicographically by their distance profiles, ties by id.
-    std::vector<uint64_t> hi((size_t)n, 0), lo((size_t)n, 0);
-    int used = 0;
-    for (int i = 0; i < k; ++i) {
-        int32_t *d = dist.data() + (size_t)i * n;
-        int32_t dmax = 0;
-        for (int32_t v = 0; v < n; ++v) dmax = std::max(dmax, d[v]);
-        const uint64_t unreached = (uint64_t)dmax + 1;
-        int b = 1;
-        while ((uint64_t{1} << b) <= unreached) ++b;
-        if (used + b > 128) break;
-        used += b;
-        for (int32_t v = 0; v < n; ++v) {
-            const uint64_t x = d[v] < 0 ? unreached : (uint64_t)d[v];
-            hi[v] = (hi[v] << b) | (lo[v] >> (64 - b));
-            lo[v] = (lo[v] << b) | x;
+    // vertices lexicographically by their distance profiles, ties by id. The
+    // host threads take contiguous ranges; the counts of a pass are laid out
+    // thread by thread within each digit value, which keeps the sort stable.
+    const int T = n < 16384 ? 1 : std::max(1, std::min<int>(8, (int)std::thread::hardware_concurrency()));
+    std::vector<uint64_t> key[2][2];  // [buffer][hi, lo]
+    for (auto &b : key)
+        for (auto &x : b) x.assign((size_t)n, 0);
+    std::vector<int32_t> ord[2];
+    ord[0].resize(n);
+    ord[1].resize(n);
+    std::vector<int32_t> dm((size_t)T * k, 0);
+    std::vector<size_t> cnt((size_t)T * 256);
+    int final_cur = 0;
+    bool skip = false;
+    SpinBarrier bar(T);
+    auto work = [&](int t) {
+        int cur = 0;  // which buffer holds the current order (the same in every thread)
+        const int32_t v0 = (int32_t)((int64_t)n * t / T), v1 = (int32_t)((int64_t)n * (t + 1) / T);
+        for (int i = 0; i < k; ++i) {
+            const int32_t *d = dist.data() + (size_t)i * n;
+            int32_t m = 0;
+            for (int32_t v = v0; v < v1; ++v) m = std::max(m, d[v]);
+            dm[(size_t)t * k + i] = m;
         }
-    }
-    std::vector<int32_t> ord(n), tmp(n);
-    std::vector<uint64_t> hi2((size_t)n), lo2((size_t)n);
-    std::iota(ord.begin(), ord.end(), 0);
-    for (int digit = 0; digit < 16; ++digit) {
-        const int sh = 8 * (digit & 7);
-        std::vector<uint64_t> &key = digit < 8 ? lo : hi;
-        size_t cnt[257] = {0};
-        for (int32_t t = 0; t < n; ++t) ++cnt[((key[t] >> sh) & 0xFF) + 1];
-        bool shared = false;
-        for (int x = 1; x <= 256; ++x) shared |= cnt[x] == (size_t)n;
-        if (shared) continue;
-        for (int x = 1; x <= 256; ++x) cnt[x] += cnt[x - 1];
-        for (int32_t t = 0; t < n; ++t) {
-            const size_t at = cnt[(key[t] >> sh) & 0xFF]++;
-            tmp[at] = ord[t];
-            hi2[at] = hi[t];
-            lo2[at] = lo[t];
+        bar.wait();
+        uint64_t *hi = key[0][0].data(), *lo = key[0][1].data();
+        int used = 0;
+        for (int i = 0; i < k; ++i) {
+            int32_t dmax = 0;
+            for (int q = 0; q < T; ++q) dmax = std::max(dmax, dm[(size_t)q * k + i]);
+            const uint64_t unreached = (uint64_t)dmax + 1;
+            int b = 1;
+            while ((uint64_t{1} << b) <= unreached) ++b;
+            if (used + b > 128) break;
+            used += b;
+            const int32_t *d = dist.data() + (size_t)i * n;
+            for (int32_t v = v0; v < v1; ++v) {
+                const uint64_t x = d[v] < 0 ? unreached : (uint64_t)d[v];
+                hi[v] = (hi[v] << b) | (lo[v] >> (64 - b));
+                lo[v] = (lo[v] << b) | x;
+            }
         }
-        ord.swap(tmp);
-        hi.swap(hi2);
-        lo.swap(lo2);
+        for (int32_t v = v0; v < v1; ++v) ord[0][v] = v;
+        bar.wait();
+        for (int digit = 0; digit < 16; ++digit) {
+            const int sh = 8 * (digit & 7);
+            const int part = digit < 8 ? 1 : 0;
+            const uint64_t *kk = key[cur][part].data();
+            size_t *c = cnt.data() + (size_t)t * 256;
+            std::fill(c, c + 256, 0);
+            for (int32_t x = v0; x < v1; ++x) ++c[(kk[x] >> sh) & 0xFF];
+            bar.wait();
+            if (t == 0) {  // offsets: digit value major, thread minor
+                size_t run = 0, top = 0;
+                for (int dv = 0; dv < 256; ++dv) {
+                    size_t tot = 0;
+                    for (int q = 0; q < T; ++q) {
+                        const size_t x = cnt[(size_t)q * 256 + dv];
+                        cnt[(size_t)q * 256 + dv] = run;
+                        run += x;
+                        tot += x;
+                    }
+                    top = std::max(top, tot);
+                }
+                skip = top == (size_t)n;  // every key has this digit: the pass changes nothing
+            }
+            bar.wait();
+            if (!skip) {
+                const int nx = cur ^ 1;
+                for (int32_t x = v0; x < v1; ++x) {
+                    const size_t at = c[(kk[x] >> sh) & 0xFF]++;
+                    ord[nx][at] = ord[cur][x];
+                    key[nx][0][at] = key[cur][0][x];
+                    key[nx][1][at] = key[cur][1][x];
+                }
+            }
+            const bool flipped = !skip;
+            bar.wait();  // skip is rewritten by the next pass only after every thread read it
+            if (flipped) cur ^= 1;
+        }
+        if (t == 0) final_cur = cur;
+    };
+    std::vector<std::thread> th;
+    if (T == 1) {
+        work(0);
+    } else {
+        for (int t = 1; t < T; ++t) th.emplace_back(work, t);
+        work(0);
+        for (auto &x : th) x.join();
     }
     g->rank.assign(n, 0);
-    for (int32_t t = 0; t < n; ++t) g->rank[ord[t]] = t;
+    for (int32_t t = 0; t < n; ++t) g->rank[ord[final_cur][t]] = t;
 }
 
 // Validate and upload the source list. With `order`, the sources are staged
