@@ -22,7 +22,7 @@ namespace stage {
 
 // per-warp stage sizes: forward rows (uint16) and backward rows (FP32); the
 // backward kernel trades stage depth for a fourth resident block per SM
-constexpr uint32_t kFwdStageBytes = 8192;
+constexpr uint32_t kFwdStageBytes = 4096;
 constexpr uint32_t kBwdStageBytes = 4096;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
 
