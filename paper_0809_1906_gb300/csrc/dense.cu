@@ -182,8 +182,11 @@ __global__ void __launch_bounds__(128, 1)
     }
     const int xrow0 = bb * p.xrows + xin;
     const int nk = p.npad / kKT;
+    // the backward keeps two accumulators: the hi part's products in one, the
+    // mid and lo parts' (both small) in the other
+    const int nacc = kBwd ? 2 : nl;
     uint32_t ncols = 32;
-    while (ncols < (uint32_t)(nl * kN)) ncols <<= 1;
+    while (ncols < (uint32_t)(nacc * kN)) ncols <<= 1;
 
     if (tid == 0) {
         s_err = 0u;
@@ -240,9 +243,12 @@ __global__ void __launch_bounds__(128, 1)
             for (int q = 0; q < nl; ++q) {
                 const uint32_t xbase = smem_u32(st + (size_t)q * kXTile);
 #pragma unroll
-                for (int kk = 0; kk < kKT / 16; ++kk)
-                    umma_bf16<kN>(tmem + (uint32_t)(q * kN), sw128_desc(xbase + kk * 32), sw128_desc(abase + kk * 32),
-                              (it > 0 || kk > 0) ? 1u : 0u);
+                for (int kk = 0; kk < kKT / 16; ++kk) {
+                    const int qa = kBwd && q > 1 ? 1 : q;  // accumulator of part q
+                    const bool first = it == 0 && kk == 0 && !(kBwd && q == 2);
+                    umma_bf16<kN>(tmem + (uint32_t)(qa * kN), sw128_desc(xbase + kk * 32), sw128_desc(abase + kk * 32),
+                                  first ? 0u : 1u);
+                }
             }
             umma_commit(empty + s);  // frees the stage once these MMAs have read it
         }
@@ -266,7 +272,7 @@ __global__ void __launch_bounds__(128, 1)
             float S[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) S[i] = 0.0f;
-            for (int q = 0; q < nl; ++q) {  // hi + mid + lo, in this order
+            for (int q = 0; q < 2; ++q) {  // hi, then mid + lo
                 uint32_t r[16];
                 tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * kN + c0), r);
                 tmem_wait_ld();
@@ -483,10 +489,11 @@ bool make_map(CUtensorMap *m, void *base, uint64_t inner, uint64_t rows, uint32_
 }  // namespace
 
 template <int kN>
-int dense_stages(int nl) {
+int dense_stages(int nl, bool bwd = false) {
     // accumulators of at most 256 TMEM columns: two CTAs per SM (half the
     // shared memory each), so one CTA's epilogue overlaps the other's MMAs
-    const int budget = nl * kN <= 256 ? 100 * 1024 : 200 * 1024;
+    const int nacc = bwd ? 2 : nl;
+    const int budget = nacc * kN <= 256 ? 100 * 1024 : 200 * 1024;
     const int s = budget / (nl * kXTile + a_tile<kN>());
     return s < 1 ? 1 : (s > 8 ? 8 : s);
 }
@@ -514,7 +521,7 @@ int dense_make_maps(DenseMaps *maps, __nv_bfloat16 *X, uint64_t xrows_total, __n
 // (nl * 128 <= 512 columns), else kNT = 64.
 template <bool kBwd, int kN>
 int launch_level_t(const DenseMaps &maps, const DenseParams &p, int l, int nl, int write_next, cudaStream_t st) {
-    const int stages = dense_stages<kN>(nl);
+    const int stages = dense_stages<kN>(nl, kBwd);
     const size_t smem = dense_smem_bytes<kN>(nl, stages);
     if (cudaFuncSetAttribute(k_dense_level<kBwd, kN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
