@@ -491,9 +491,10 @@ bool make_map(CUtensorMap *m, void *base, uint64_t inner, uint64_t rows, uint32_
 template <int kN>
 int dense_stages(int nl, bool bwd = false) {
     // accumulators of at most 256 TMEM columns: two CTAs per SM (half the
-    // shared memory each), so one CTA's epilogue overlaps the other's MMAs
+    // shared memory each), at most 128: three, so one CTA's epilogue overlaps
+    // the others' MMAs
     const int nacc = bwd ? 2 : nl;
-    const int budget = nacc * kN <= 256 ? 100 * 1024 : 200 * 1024;
+    const int budget = nacc * kN <= 128 ? 66 * 1024 : (nacc * kN <= 256 ? 100 * 1024 : 200 * 1024);
     const int s = budget / (nl * kXTile + a_tile<kN>());
     return s < 1 ? 1 : (s > 8 ? 8 : s);
 }
