@@ -6,18 +6,21 @@
 // words) is contiguous, lane i of a warp owns sources 32j + i (j < W). Beside
 // the permanent uint64 sigma array, each level keeps *masked rows*: row v of
 // level l holds sigma_s(v) (forward, as uint16) or c_s(v) (backward, FP32)
-// for the sources s with d(s,v) = l and 0 for every other source, in two
-// buffers alternating by level parity. A level whose counts do not all fit
-// in 16 bits is marked "wide"; the next level then reads the permanent uint64
-// sigma under per-source masks instead (exact either way). A warp owns a vertex v (or a chunk of its arcs) and walks v's
-// arcs 32 at a time:
+// for the sources s with d(s,v) = l and 0 for every other source: c rows in
+// two buffers alternating by level parity, sigma rows in one buffer per level
+// (or two by parity when that would take too much memory; the many-graph
+// kernel). A level whose counts do not all fit in 16 bits is marked "wide";
+// the next level then reads the permanent uint64 sigma under per-source masks
+// instead (exact either way). A warp owns a vertex v (or a chunk of its arcs)
+// and walks v's arcs 32 at a time:
 //   probe  lane k takes arc k of the chunk: neighbour u_k, one bit of the
 //          union-frontier bitmap (is u_k in any source's frontier?), then
 //          u_k's W frontier words ANDed with the sources v cares about; arcs
 //          whose AND is empty are dropped;
-//   add    for each remaining neighbour the warp adds its masked row to its
-//          W per-lane sums: W coalesced loads, no per-source test, because
-//          the masked row is already zero wherever u_k does not contribute.
+//   add    for each remaining neighbour the warp adds the words of its
+//          masked row that can contribute to its W per-lane sums, with no
+//          per-source test: within such a word the masked row is zero
+//          wherever u_k does not contribute.
 // The frontier words of v come from an OR-reduction of the probe masks.
 #pragma once
 
