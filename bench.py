@@ -102,14 +102,20 @@ SWEEP_SOURCES = ("msbfs.cu", "msbfs_body.cuh", "rowstage.cuh", "pdl.cuh", "bc_in
 
 
 def csrc_digest() -> str:
-    """SHA-256 over the sweep kernels' sources: DRAM counters taken from an
-    older build do not describe the current kernels."""
+    """SHA-256 over the sweep kernels' sources with comments and blank space
+    removed: DRAM counters taken from an older build do not describe the
+    current kernels, while a comment edit changes nothing they measure."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in SWEEP_SOURCES:
-        with open(os.path.join(ROOT, "paper_0809_1906_gb300", "csrc", name), "rb") as fh:
-            h.update(name.encode())
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_0809_1906_gb300", "csrc", name), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        text = "".join(text.split())
+        h.update(name.encode())
+        h.update(text.encode())
     return h.hexdigest()
 
 
