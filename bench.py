@@ -101,21 +101,24 @@ class ClockSampler:
 SWEEP_SOURCES = ("msbfs.cu", "msbfs_body.cuh", "rowstage.cuh", "pdl.cuh", "bc_internal.cuh")
 
 
+def code_text(text: str) -> str:
+    """A C/CUDA source with its comments and blank space removed."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "".join(text.split())
+
+
 def csrc_digest() -> str:
     """SHA-256 over the sweep kernels' sources with comments and blank space
     removed: DRAM counters taken from an older build do not describe the
     current kernels, while a comment edit changes nothing they measure."""
     import hashlib
-    import re
     h = hashlib.sha256()
     for name in SWEEP_SOURCES:
         with open(os.path.join(ROOT, "paper_0809_1906_gb300", "csrc", name), encoding="utf-8") as fh:
-            text = fh.read()
-        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        text = re.sub(r"//[^\n]*", "", text)
-        text = "".join(text.split())
-        h.update(name.encode())
-        h.update(text.encode())
+            h.update(name.encode())
+            h.update(code_text(fh.read()).encode())
     return h.hexdigest()
 
 
@@ -125,13 +128,13 @@ KIND_KERNELS = {"init": ("k_init",), "forward": ("k_first", "k_forward"), "backw
 TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic_rmat.json")
 
 
-def measured_traffic(kind: str, launches: int):
+def measured_traffic(kind: str, launches: int, path: str = TRAFFIC_JSON):
     """DRAM bytes (read + write) per launch of kernel kind `kind`: the bytes of
     one full pass from the committed ncu capture profiles/traffic_rmat.json,
     divided by this run's launch count of that kind; None when the capture
     was taken on other kernel sources."""
     try:
-        with open(TRAFFIC_JSON) as f:
+        with open(path) as f:
             tr = json.load(f)
         if tr.get("csrc_sha256") != csrc_digest():
             return None
@@ -140,7 +143,7 @@ def measured_traffic(kind: str, launches: int):
         return None
 
 
-def write_traffic(csv_path: str, command: str):
+def write_traffic(csv_path: str, command: str, out_path: str = TRAFFIC_JSON, echo: bool = True):
     """Turn an ncu capture of one full pass (metrics dram__bytes_read.sum,
     dram__bytes_write.sum, gpu__time_duration.sum; --csv) into
     profiles/traffic_rmat.json."""
@@ -168,9 +171,11 @@ def write_traffic(csv_path: str, command: str):
            "note": "one bc_run over every source of the R-MAT workload (batch 256); ncu replays each launch "
                    "with cold caches, so bytes are an upper bound of a warm run",
            "kinds": kinds}
-    with open(TRAFFIC_JSON, "w") as f:
+    with open(out_path, "w") as f:
         json.dump(out, f, indent=1)
-    print(json.dumps(out, indent=1))
+    if echo:
+        print(json.dumps(out, indent=1))
+    return out
 
 
 def workload():

@@ -1,0 +1,59 @@
+"""Host-side parts of bench.py that need no GPU: the algorithmic-bytes model
+(the roofline numerator), the ncu capture digest and the DRAM traffic table
+the roofline line reads."""
+import json
+
+import bench
+
+
+def test_algorithmic_bytes_follow_the_per_source_model():
+    # per source: 2m level probes + 8 B sigma per DAG arc + 9 B per vertex
+    # (forward); 2m + 4 B c per arc + 13 B per vertex (backward); plus the
+    # per-batch CSR and BC terms
+    n, m, a, nsrc, B = 1000, 5000, 30000, 256, 256
+    fwd, bwd = bench.algorithmic_bytes(n, m, a, nsrc, B)
+    assert fwd == nsrc * (2 * m + 9 * n) + 8 * a + 1 * (8 * m + 4 * n)
+    assert bwd == nsrc * (2 * m + 13 * n) + 4 * a + 1 * (8 * m + 4 * n + 16 * n)
+    fwd2, bwd2 = bench.algorithmic_bytes(n, m, a, 2 * nsrc, B)
+    assert fwd2 > fwd and bwd2 > bwd  # more sources, more bytes; two batches pay the CSR twice
+
+
+def test_code_text_ignores_comments_and_space():
+    a = "int x = 1; // one\n/* block\n comment */ float  y;\n"
+    b = "int x=1;\nfloat y;   // other words\n"
+    assert bench.code_text(a) == bench.code_text(b)
+    assert bench.code_text(a) != bench.code_text("int x = 2; float y;")
+
+
+def test_traffic_table_from_an_ncu_csv(tmp_path):
+    hdr = '"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"\n'
+    rows = [
+        ('0', 'void unnamed>::k_forward<8>(MsParams, int)', 'dram__bytes_read.sum', 'byte', '1000'),
+        ('0', 'void unnamed>::k_forward<8>(MsParams, int)', 'dram__bytes_write.sum', 'byte', '200'),
+        ('0', 'void unnamed>::k_forward<8>(MsParams, int)', 'gpu__time_duration.sum', 'ns', '5000'),
+        ('1', 'void unnamed>::k_first<8>(MsParams)', 'dram__bytes_read.sum', 'byte', '30'),
+        ('1', 'void unnamed>::k_first<8>(MsParams)', 'dram__bytes_write.sum', 'byte', '10'),
+        ('2', 'void unnamed>::k_backward<8>(MsParams, int)', 'dram__bytes_read.sum', 'byte', '700'),
+        ('2', 'void unnamed>::k_backward<8>(MsParams, int)', 'dram__bytes_write.sum', 'byte', '100'),
+    ]
+    csv_path = tmp_path / "t.csv"
+    csv_path.write_text("==PROF== noise\n" + hdr + "".join(",".join(f'"{x}"' for x in r) + "\n" for r in rows))
+    out_path = tmp_path / "traffic.json"
+    out = bench.write_traffic(str(csv_path), "cmd", out_path=str(out_path), echo=False)
+    assert out["kinds"]["forward"]["launches"] == 2
+    assert out["kinds"]["forward"]["dram_bytes_per_pass"] == 1240.0
+    assert out["kinds"]["backward"]["dram_bytes_per_pass"] == 800.0
+    assert abs(out["kinds"]["forward"]["ncu_time_ms"] - 0.005) < 1e-12
+    # per launch over this run's own launch count; stale digests give None
+    assert bench.measured_traffic("backward", 4, path=str(out_path)) == 200.0
+    doc = json.loads(out_path.read_text())
+    doc["csrc_sha256"] = "0" * 64
+    out_path.write_text(json.dumps(doc))
+    assert bench.measured_traffic("backward", 4, path=str(out_path)) is None
+
+
+def test_committed_traffic_matches_the_current_kernels():
+    with open(bench.TRAFFIC_JSON) as f:
+        doc = json.load(f)
+    assert doc["csrc_sha256"] == bench.csrc_digest()
+    assert set(doc["kinds"]) >= {"forward", "backward", "hash"}
