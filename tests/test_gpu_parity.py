@@ -281,3 +281,21 @@ def test_lanes_reused_across_graphs(nat):
         tol = np.maximum(1e-5 * np.abs(ref["bc"]), 1e-6 * g.n)
         assert np.all(np.abs(got - ref["bc"]) <= tol), g.name
         assert np.array_equal(hs["hash_sigma"], ref["hash_sigma"]), g.name
+
+
+def test_parity_row_buffers_on_a_large_graph(nat):
+    """n = 100,000 at 256 sources per batch: one masked-row buffer per level
+    would take more than the budget, so the sweep keeps two buffers by level
+    parity and the backward reads the uint64 sigma. Two batches (two lanes)
+    of seeded sources against the oracle, summaries included."""
+    g = G.er_hamiltonian(100_000, 400_000, 4343)
+    src = G.sample_sources(g.n, 512, 44)
+    ref = oracle.bc(g, src)
+    with nat.Graph.from_csr(g, trust_input=True) as h:
+        h.run(src, batch=256)
+        got, code, _ = h.result()
+        hs = h.source_hashes(src.size)
+    assert code == nat.BC_OK
+    tol = np.maximum(1e-5 * np.abs(ref["bc"]), 1e-6 * g.n)
+    assert np.all(np.abs(got - ref["bc"]) <= tol)
+    assert np.array_equal(hs["hash_sigma"], ref["hash_sigma"]) and np.array_equal(hs["hash_dist"], ref["hash_dist"])
