@@ -1906,7 +1906,7 @@ void free_many(bc_many *m) {
 // Work items of the many-graph launch: each graph's source batches, split
 // into several items when one graph alone is more than half a CTA's fair
 // share of the total, then sorted by decreasing cost (LPT).
-int build_many(bc_many *m, const bc_options *opt) {
+int build_many(bc_many *m) {
     const int B = 32 * m->W;
     struct GInfo {
         int nb;
@@ -2037,7 +2037,7 @@ int bc_many_create(bc_graph *const *graphs, int32_t k, const bc_options *opt, bc
         }
         m->graphs.push_back(graphs[i]);
     }
-    const int r = build_many(m, opt);
+    const int r = build_many(m);
     if (r) {
         free_many(m);
         return r;

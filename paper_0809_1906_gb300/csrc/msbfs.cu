@@ -177,7 +177,6 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     uint32_t *ufn = p.ufr + (size_t)(l + 1) * p.nw32;
     const uint32_t *Vin = p.V + (size_t)(l & 1) * nW;
     uint32_t *Vout = p.V + (size_t)((l + 1) & 1) * nW;
-    const size_t nB = (size_t)p.n * B;
     const uint16_t *Sl = p.S_rd;  // masked rows of level l and l+1 (set by the launcher)
     uint16_t *Sn = p.S_wr;
     const bool wide = *(volatile uint32_t *)(p.wide + l) != 0u;
