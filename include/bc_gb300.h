@@ -111,8 +111,8 @@ extern "C" {
  *                  32, 64, 128 or 256 (0 = 256; BC_DENSE uses 128). For
  *                  weighted graphs: sources per wave (0 = 4 per SM).
  *   flags          BC_* option bits above.
- *   chunk          arcs per work item for high-degree vertices (0 = 256 in the
- *                  forward sweep, 128 in the backward sweep).
+ *   chunk          arcs per work item for high-degree vertices (0 = 256 in both
+ *                  sweeps; a given value applies to both).
  *   wait_limit_ms  bound on every host-side wait for device progress
  *                  (0 = 600000). Expiry returns BC_ERR_TIMEOUT.
  */
