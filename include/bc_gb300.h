@@ -214,6 +214,16 @@ int bc_forward_rows(bc_graph *g, const int32_t *sources, int32_t k, uint64_t *si
 int bc_kernel_time(bc_graph *g, int32_t kind, int64_t *launches, double *total_ms);
 
 /*
+ * Per-launch trace of the last run made with BC_TIMING, in launch order:
+ * kind[i] (BC_KERNEL_*), level[i] (the sweep level of a forward or backward
+ * launch, -1 otherwise) and ms[i] (its CUDA-event duration). Fills at most
+ * cap entries (kind, level, ms: host arrays of cap entries) and sets *count
+ * (may be NULL) to the number of traced launches. Synchronises the stream.
+ * Errors: BC_ERR_ARG, BC_ERR_STATE.
+ */
+int bc_kernel_trace(bc_graph *g, int64_t cap, int32_t *kind, int32_t *level, float *ms, int64_t *count);
+
+/*
  * Work counters of the last bc_run (synchronises its stream):
  *   dag_arcs   sum over the run's sources s of the number of arcs (u,v) with
  *              u in P_s(v), i.e. the size of each shortest-path DAG (Section 1.1)
@@ -245,16 +255,19 @@ int bc_graph_size(const bc_graph *g, int32_t *n, int64_t *m, int32_t *weighted);
  *   sources      DEVICE int32[num_sources] (ids in [0, n), at most
  *                BC_NOALLOC_MAX_N of them), or NULL for all vertices.
  *   bc           DEVICE double[n]: receives the ordered-pair betweenness.
- * Runs on cuda_stream and synchronises it (it reads each batch's depth).
+ * Runs on cuda_stream and synchronises it several times (it checks the
+ * inputs and reads each batch's depth back to the host).
  * Returns BC_OK, BC_WARN_SIGMA_OVERFLOW, BC_ERR_ARG (sizes beyond the limits,
  * NULL pointers, ids out of range), BC_ERR_UNSUPPORTED (a BFS deeper than
- * BC_NOALLOC_MAX_LEVELS levels), BC_ERR_CUDA. No message is recorded for
- * bc_last_error (that would allocate); use bc_status_string.
+ * BC_NOALLOC_MAX_LEVELS levels), BC_ERR_TIMEOUT (a bounded device wait for
+ * staged row copies gave up: the result is incomplete), BC_ERR_CUDA. No
+ * message is recorded for bc_last_error (that would allocate); use
+ * bc_status_string.
  * The first call on a device looks up the array's device address for that
- * device; make that first call before any stream capture. Every call on a
- * device shares the one array and leaves its contents behind (each call
- * clears what must start at zero): calls that overlap on the GPU race and
- * must not be issued concurrently.
+ * device (cudaGetSymbolAddress); make that first call before any stream
+ * capture begins. Every call on a device shares the one array and leaves its
+ * contents behind (each call clears what must start at zero): calls that
+ * overlap on the GPU race and must not be issued concurrently.
  */
 #define BC_NOALLOC_MAX_N 16384
 #define BC_NOALLOC_MAX_LEVELS 62
@@ -274,9 +287,12 @@ int bc_run_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col, const 
  *                 graphs: k unweighted handles from bc_create_graph, owned by
  *                 the caller and kept alive while the plan exists.
  *                 opt->batch: sources per batch, 32, 64, 128 or 256 (0 = 32).
+ *                 opt->flags: BC_NO_HASH skips the per-source summaries.
  * bc_many_run     replays the captured graph on cuda_stream (asynchronous).
  *                 Each graph's BC lands in its own handle: read it with
- *                 bc_result(graphs[i], ...) after bc_many_result.
+ *                 bc_result(graphs[i], ...) after bc_many_result, and its
+ *                 per-source summaries (every vertex a source, in vertex
+ *                 order) with bc_source_hashes(graphs[i], ...).
  * bc_many_result  synchronises; a graph deeper than the launch's level
  *                 capacity (64 levels) is re-run with bc_run on the same
  *                 stream; *rerun (may be NULL) receives how many were.

@@ -214,6 +214,7 @@ struct bc_graph {
     struct Ev {
         cudaEvent_t a, b;
         int kind;
+        int level;  // sweep level of the launch (-1: none)
     };
     std::vector<Ev> evpool;
     size_t evused = 0;
@@ -477,7 +478,7 @@ int ensure_state(bc_graph *g, int W, int Lcap) {
     return BC_OK;
 }
 
-size_t timer_begin(bc_graph *g, cudaStream_t st, int kind) {
+size_t timer_begin(bc_graph *g, cudaStream_t st, int kind, int level = -1) {
     g->launches++;
     if (!g->timing) return SIZE_MAX;
     if (g->evused == g->evpool.size()) {
@@ -488,6 +489,7 @@ size_t timer_begin(bc_graph *g, cudaStream_t st, int kind) {
     }
     const size_t idx = g->evused++;
     g->evpool[idx].kind = kind;
+    g->evpool[idx].level = level;
     cudaEventRecord(g->evpool[idx].a, st);
     return idx;
 }
@@ -502,7 +504,7 @@ struct Timer {
     bc_graph *g;
     cudaStream_t st;
     size_t idx;
-    Timer(bc_graph *g_, cudaStream_t s, int k) : g(g_), st(s), idx(timer_begin(g_, s, k)) {}
+    Timer(bc_graph *g_, cudaStream_t s, int k, int level = -1) : g(g_), st(s), idx(timer_begin(g_, s, k, level)) {}
     ~Timer() { timer_end(g, st, idx); }
     Timer(const Timer &) = delete;
     Timer &operator=(const Timer &) = delete;
@@ -1069,7 +1071,7 @@ int run_lanes(bc_graph *g, int32_t nsrc, int W, int K, cudaStream_t st, bool bac
             int done_lv = 0;
             if (bcgb::load_acquire_u(&h->progress_seq) == j.p.seq) done_lv = bcgb::load_acquire_i(&h->progress);
             while (j.launched <= j.p.Lcap - 2 && j.launched < done_lv + bcgb::kLookahead) {
-                Timer t(g, ls, BC_KERNEL_FORWARD);
+                Timer t(g, ls, BC_KERNEL_FORWARD, j.launched);
                 if (j.launched == 0)
                     bcgb::ms_launch_first(W, j.p, ls);
                 else
@@ -1099,7 +1101,7 @@ int run_lanes(bc_graph *g, int32_t nsrc, int W, int K, cudaStream_t st, bool bac
                 bcgb::MsParams pb = j.p;
                 use_plan(pb, g->bplan);
                 for (int l = L; l >= 1; --l) {
-                    Timer t(g, ls, BC_KERNEL_BACKWARD);
+                    Timer t(g, ls, BC_KERNEL_BACKWARD, l);
                     bcgb::ms_launch_backward(W, pb, l, ls);
                 }
             }
@@ -1199,7 +1201,7 @@ int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStr
         int L = 0;
         {
             auto launch = [&](int level) {
-                Timer t(g, st, BC_KERNEL_FORWARD);
+                Timer t(g, st, BC_KERNEL_FORWARD, level);
                 if (level == 0)
                     bcgb::ms_launch_first(W, p, st);
                 else
@@ -1218,7 +1220,7 @@ int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStr
             bcgb::MsParams pb = p;
             use_plan(pb, g->bplan);
             for (int l = L; l >= 1; --l) {
-                Timer t(g, st, BC_KERNEL_BACKWARD);
+                Timer t(g, st, BC_KERNEL_BACKWARD, l);
                 bcgb::ms_launch_backward(W, pb, l, st);
             }
         }
@@ -1814,6 +1816,23 @@ int bc_kernel_time(bc_graph *g, int32_t kind, int64_t *launches, double *total_m
     return BC_OK;
 }
 
+int bc_kernel_trace(bc_graph *g, int64_t cap, int32_t *kind, int32_t *level, float *ms, int64_t *count) {
+    g_err.clear();
+    if (!g || cap < 0 || (cap > 0 && (!kind || !level || !ms))) return fail(BC_ERR_ARG, "bad arguments");
+    if (!g->has_run) return fail(BC_ERR_STATE, "no completed bc_run");
+    CK(cudaStreamSynchronize(g->last_stream));
+    const int64_t k = std::min<int64_t>(cap, (int64_t)g->evused);
+    for (int64_t i = 0; i < k; ++i) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, g->evpool[i].a, g->evpool[i].b));
+        kind[i] = g->evpool[i].kind;
+        level[i] = g->evpool[i].level;
+        ms[i] = t;
+    }
+    if (count) *count = (int64_t)g->evused;
+    return BC_OK;
+}
+
 int64_t bc_launch_count(const bc_graph *g) { return g ? g->launches : 0; }
 
 int bc_run_stats(bc_graph *g, int64_t *dag_arcs, int64_t *depth_sum, double *tensor_flops) {
@@ -1867,6 +1886,7 @@ const char *bc_last_error(void) { return g_err.c_str(); }
 struct bc_many {
     std::vector<bc_graph *> graphs;
     int W = 1, grid = 0, Lcap = 64;
+    bool hash = true;  // per-source summaries into each graph's handle
     int32_t nitems = 0;
     DevBuf<bcgb::ManyGraph> d_graphs;
     DevBuf<bcgb::ManyItem> d_items;
@@ -1943,6 +1963,19 @@ int build_many(bc_many *m) {
         gd[i].row_ptr = g->row_ptr.p;
         gd[i].col = g->col.p;
         gd[i].bc = g->bc.p;
+        gd[i].h_sigma = gd[i].h_dist = nullptr;
+        gd[i].dist_sum = gd[i].reach = nullptr;
+        if (m->hash && g->n > 0) {
+            bc_graph *gw = m->graphs[i];
+            CK(gw->h_sigma.ensure(g->n));
+            CK(gw->h_dist.ensure(g->n));
+            CK(gw->dist_sum.ensure(g->n));
+            CK(gw->reach.ensure(g->n));
+            gd[i].h_sigma = gw->h_sigma.p;
+            gd[i].h_dist = gw->h_dist.p;
+            gd[i].dist_sum = gw->dist_sum.p;
+            gd[i].reach = gw->reach.p;
+        }
         if (q > 1) part_off += (int64_t)q * g->n;
         for (int k = 0; k < q; ++k) {
             Item x;
@@ -2031,6 +2064,7 @@ int bc_many_create(bc_graph *const *graphs, int32_t k, const bc_options *opt, bc
     bc_many *m = new (std::nothrow) bc_many();
     if (!m) return fail(BC_ERR_OOM, "host allocation failed");
     m->W = b / 32;
+    m->hash = !(opt && (opt->flags & BC_NO_HASH));
     for (int32_t i = 0; i < k; ++i) {
         if (!graphs[i] || graphs[i]->weighted || graphs[i]->directed) {
             free_many(m);
@@ -2054,7 +2088,8 @@ int bc_many_run(bc_many *m, void *cuda_stream) {
     if (m->exec) CK(cudaGraphLaunch(m->exec, st));
     for (bc_graph *g : m->graphs) {
         g->has_run = true;
-        g->has_hash = false;
+        g->has_hash = m->hash;
+        g->reordered = false;
         g->last_stream = st;
         g->last_nsrc = g->n;
         g->launches = 0;

@@ -37,6 +37,8 @@ struct DevCtl {
     uint32_t pad[2];
     unsigned long long dag_arcs;  // sum over the run's sources of |{(u,v): u in P_s(v)}|
     unsigned long long depth_sum; // sum over batches (or sources) of the BFS depth
+    unsigned long long batch_arcs; // the running batch's arcs, added to dag_arcs when its forward
+                                   // pass ends (a batch restarted with more levels counts once)
 };
 
 // Host-mapped mirror the host polls while the level loop runs (pinned,

@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(kMBlock, W >= 4 ? 3 : 4) k_many(const ManyPara
     __shared__ int32_t s_u[kMWarps][32];
     __shared__ uint32_t s_nz[kMWarps][32];
     __shared__ uint32_t s_w[kMWarps][32][W];  // per-lane words of a warp's 32 vertices
+    __shared__ unsigned long long s_sum[4][B];  // per-source summaries of the running batch
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     uint64_t *sigma = p.sigma + (size_t)blockIdx.x * p.nmax * B;
     uint16_t *Sbuf = p.S + (size_t)blockIdx.x * 2 * p.nmax * B;
@@ -155,6 +156,50 @@ __global__ void __launch_bounds__(kMBlock, W >= 4 ? 3 : 4) k_many(const ManyPara
                 }
             }
             if (capped) break;
+            if (gd.h_sigma) {
+                // per-source summaries over tiles of 32 vertices x 32 sources:
+                // lane k loads word j of vertex v0+k (reached set, frontier of
+                // every level), a 32x32 bit transpose gives lane s the tile mask
+                // of source 32j+s; popcounts give the distance terms, and
+                // sigma_s(v) (v+1) is added over the reached vertices
+                for (int i = tid; i < 4 * B; i += kMBlock) (&s_sum[0][0])[i] = 0ull;
+                __syncthreads();
+                const uint32_t *Vr = V + (size_t)((L + 1) & 1) * nW;  // visited through level L
+                const int ntiles = (n + 31) / 32;
+                for (int u = wib; u < ntiles * W; u += kMWarps) {
+                    const int t = u / W, j = u % W;
+                    const int v0 = 32 * t, vk = v0 + lane;
+                    const bool in = vk < n;
+                    const size_t wk = (size_t)(in ? vk : 0) * W + j;
+                    unsigned long long hs = 0, hd = 0, ds = 0;
+                    const uint32_t R = body::transpose32(in ? Vr[wk] : 0u, lane);
+                    for (int l = 0; l <= L; ++l) {
+                        const uint32_t T = body::transpose32(in ? F[(size_t)l * nW + wk] : 0u, lane);
+                        const uint32_t c = (uint32_t)__popc(T);
+                        const uint32_t ks = (uint32_t)__popc(T & 0xAAAAAAAAu) + 2u * (uint32_t)__popc(T & 0xCCCCCCCCu) +
+                                            4u * (uint32_t)__popc(T & 0xF0F0F0F0u) +
+                                            8u * (uint32_t)__popc(T & 0xFF00FF00u) +
+                                            16u * (uint32_t)__popc(T & 0xFFFF0000u);
+                        const unsigned long long vsum = (unsigned long long)c * (unsigned long long)(v0 + 1) + ks;
+                        hd += (unsigned long long)(l + 1) * vsum;
+                        ds += (unsigned long long)l * c;
+                    }
+                    const uint64_t *sg = sigma + (size_t)v0 * B + 32 * j + lane;
+                    for (int k = 0; k < 32 && v0 + k < n; ++k)
+                        if ((R >> k) & 1u) hs += sg[(size_t)k * B] * (unsigned long long)(v0 + k + 1);
+                    atomicAdd(&s_sum[0][32 * j + lane], hs);
+                    atomicAdd(&s_sum[1][32 * j + lane], hd);
+                    atomicAdd(&s_sum[2][32 * j + lane], ds);
+                    atomicAdd(&s_sum[3][32 * j + lane], (unsigned long long)__popc(R));
+                }
+                __syncthreads();
+                for (int b = tid; b < nb; b += kMBlock) {  // one batch per source: plain stores
+                    gd.h_sigma[s0 + b] = s_sum[0][b];
+                    gd.h_dist[s0 + b] = s_sum[1][b];
+                    gd.dist_sum[s0 + b] = (int64_t)s_sum[2][b];
+                    gd.reach[s0 + b] = (int64_t)s_sum[3][b];
+                }
+            }
             // backward levels (Theorem 1.1), BC into this item's target
             for (int l = L; l >= 1; --l) {
                 const uint32_t *Fl = F + (size_t)l * nW;

@@ -16,6 +16,11 @@ struct ManyGraph {
     const int32_t *row_ptr;
     const int32_t *col;
     double *bc;  // the graph's result vector
+    // per-source summaries in source (= vertex) order, or null: for source s,
+    // sum_v sigma_s(v) (v+1), sum_v (d(s,v)+1) (v+1), sum_v d(s,v) and the
+    // number of vertices reached, v over the vertices reachable from s
+    uint64_t *h_sigma, *h_dist;
+    int64_t *dist_sum, *reach;
 };
 
 struct ManyItem {

@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
         p.ctl->fwd_done = 0u;
         p.ctl->nonempty = 0u;
         p.ctl->nlevels = 0;
+        p.ctl->batch_arcs = 0ull;
         p.ctl->seq = p.seq;
         atomicExch(&p.ctl->blocks_done, 0u);
     }
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kBlock) k_first(const MsParams p) {
     if (atomicAdd(&p.ctl->blocks_done, 1u) != gridDim.x - 1) return;
     __threadfence();
     atomicExch(&p.ctl->blocks_done, 0u);
-    atomicAdd(&p.ctl->dag_arcs, (unsigned long long)total);
+    atomicAdd(&p.ctl->batch_arcs, (unsigned long long)total);
     volatile HostCtl *h = p.hctl;
     if (total == 0) {  // every source isolated: depth 0
         p.ctl->fwd_done = 1u;
@@ -292,7 +293,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
-    if (s_arcs) atomicAdd(&p.ctl->dag_arcs, s_arcs);
+    if (s_arcs) atomicAdd(&p.ctl->batch_arcs, s_arcs);
     if (s_flags & 1u) atomicOr(&p.ctl->nonempty, 1u);
     if (s_flags & 2u) atomicOr(&p.ctl->status, BC_STATUS_SIGMA_OVERFLOW);
     if (s_flags & 8u) atomicOr(&p.ctl->status, BC_STATUS_COPY_TIMEOUT);
@@ -308,6 +309,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
         p.ctl->fwd_done = 1u;
         p.ctl->nlevels = l;
         p.ctl->depth_sum += (unsigned long long)l;
+        p.ctl->dag_arcs += atomicExch(&p.ctl->batch_arcs, 0ull);
         h->nlevels = l;
         __threadfence_system();
         h->done_seq = p.seq;

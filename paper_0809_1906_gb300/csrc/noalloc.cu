@@ -185,5 +185,8 @@ extern "C" int bc_run_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *
     if (cudaMemcpyAsync(&status, &p.ctl->status, sizeof(status), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return BC_ERR_CUDA;
+    // a wait for staged row copies that gave up leaves rows incomplete: the
+    // result cannot be trusted
+    if (status & BC_STATUS_COPY_TIMEOUT) return BC_ERR_TIMEOUT;
     return (status & BC_STATUS_SIGMA_OVERFLOW) ? BC_WARN_SIGMA_OVERFLOW : BC_OK;
 }

@@ -417,19 +417,26 @@ def barabasi_albert(n: int, m: int = 3, seed: int = BASE_SEED + 5) -> Graph:
     return csr_from_edges(n, us, vs, name=f"ba_n{n}_m{m}")
 
 
+def many_graph_sizes(count: int = 2000, nmin: int = 50, nmax: int = 5000,
+                     seed: int = BASE_SEED + 5) -> np.ndarray:
+    """Vertex counts of the many-graph set: n = round(exp(U(ln nmin, ln nmax)))."""
+    u = Stream(seed, 9).uniform(count)
+    return np.rint(np.exp(math.log(nmin) + u * (math.log(nmax) - math.log(nmin)))).astype(np.int64)
+
+
+def many_graph(i: int, n: int, seed: int = BASE_SEED + 5) -> Graph:
+    """Member i of the many-graph set with n vertices. Even index: G(n, 3n)
+    plus a Hamiltonian path; odd index: BA(m=3)."""
+    if i % 2 == 0:
+        return er_hamiltonian(n, min(3 * n, n * (n - 1) // 2 - n), seed * 7919 + i)
+    return barabasi_albert(n, 3, seed * 7919 + i)
+
+
 def many_graphs(count: int = 2000, nmin: int = 50, nmax: int = 5000,
                 seed: int = BASE_SEED + 5) -> list[Graph]:
-    """Even index: G(n, 3n) plus a Hamiltonian path; odd index: BA(m=3).
-    n = round(exp(U(ln nmin, ln nmax)))."""
-    u = Stream(seed, 9).uniform(count)
-    ns = np.rint(np.exp(math.log(nmin) + u * (math.log(nmax) - math.log(nmin)))).astype(np.int64)
-    out = []
-    for i, n in enumerate(ns.tolist()):
-        if i % 2 == 0:
-            out.append(er_hamiltonian(n, min(3 * n, n * (n - 1) // 2 - n), seed * 7919 + i))
-        else:
-            out.append(barabasi_albert(n, 3, seed * 7919 + i))
-    return out
+    """The many-graph set: member i is many_graph(i, n_i)."""
+    ns = many_graph_sizes(count, nmin, nmax, seed)
+    return [many_graph(i, n, seed) for i, n in enumerate(ns.tolist())]
 
 
 def sample_sources(n: int, k: int, seed: int) -> np.ndarray:

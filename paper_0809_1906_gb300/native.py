@@ -53,7 +53,7 @@ KERNEL_NAMES = {0: "init", 1: "forward", 2: "backward", 3: "hash", 4: "plain", 5
 
 # every entry point include/bc_gb300.h declares
 EXPORTS = ["bc_create_graph", "bc_run", "bc_result", "bc_source_hashes", "bc_forward_rows",
-           "bc_kernel_time", "bc_run_stats", "bc_launch_count", "bc_graph_size", "bc_destroy_graph",
+           "bc_kernel_time", "bc_kernel_trace", "bc_run_stats", "bc_launch_count", "bc_graph_size", "bc_destroy_graph",
            "bc_status_string", "bc_last_error", "bc_run_noalloc",
            "bc_many_create", "bc_many_run", "bc_many_result", "bc_many_destroy", "bc_run_many"]
 
@@ -98,6 +98,7 @@ def load(build_if_needed: bool = True, require_gpu: bool = True):
             "bc_source_hashes": (i32, [P, P, P, P, P]),
             "bc_forward_rows": (i32, [P, P, i32, P, P, P, P]),
             "bc_kernel_time": (i32, [P, i32, P, P]),
+            "bc_kernel_trace": (i32, [P, i64, P, P, P, P]),
             "bc_run_stats": (i32, [P, P, P, P]),
             "bc_launch_count": (i64, [P]),
             "bc_graph_size": (i32, [P, P, P, P]),
@@ -247,6 +248,18 @@ class Graph:
         t = ctypes.c_double(0.0)
         _check(self.lib.bc_kernel_time(self.handle, kind, ctypes.byref(n), ctypes.byref(t)), "bc_kernel_time")
         return n.value, t.value
+
+    def kernel_trace(self):
+        """bc_kernel_trace: (kind, level, ms) arrays of every launch of the last BC_TIMING run."""
+        cnt = ctypes.c_int64(0)
+        _check(self.lib.bc_kernel_trace(self.handle, 0, None, None, None, ctypes.byref(cnt)), "bc_kernel_trace")
+        k = cnt.value
+        kind = np.empty(k, np.int32)
+        level = np.empty(k, np.int32)
+        ms = np.empty(k, np.float32)
+        _check(self.lib.bc_kernel_trace(self.handle, k, _addr(kind), _addr(level), _addr(ms), ctypes.byref(cnt)),
+               "bc_kernel_trace")
+        return kind, level, ms
 
     def run_stats(self):
         a = ctypes.c_int64(0)

@@ -1,4 +1,6 @@
-"""GPU parity of the many-graph persistent launch against the oracle."""
+"""GPU parity of the many-graph persistent launch against the oracle: BC
+within max(1e-5 |ref|, 1e-6 n), and the per-source summaries of sigma and the
+distances (every vertex of every graph a source) bit for bit."""
 import numpy as np
 import pytest
 
@@ -20,24 +22,56 @@ def close(got, ref, n):
     return np.all(np.abs(got - ref) <= tol)
 
 
+def check_plan(nat, gs, batch, reps=1, expect_rerun=None):
+    hs = [nat.Graph.from_csr(g) for g in gs]
+    refs = [oracle.bc(g) for g in gs]
+    try:
+        with nat.ManyPlan(hs, batch=batch) as plan:
+            for rep in range(reps):  # replays of the captured graph
+                plan.run()
+                code, flags, rerun = plan.result()
+                assert code == nat.BC_OK
+                if expect_rerun is not None:
+                    assert rerun == expect_rerun
+                for g, h, ref in zip(gs, hs, refs):
+                    got, _, _ = h.result()
+                    assert close(got, ref["bc"], g.n), (g.name, rep)
+                    if g.n == 0:
+                        continue
+                    sm = h.source_hashes(g.n)
+                    for k in ("hash_sigma", "hash_dist", "dist_sum", "reach"):
+                        assert np.array_equal(sm[k], ref[k]), (g.name, rep, k)
+    finally:
+        for h in hs:
+            h.close()
+
+
 @pytest.mark.parametrize("batch", [32, 64, 128, 256])
 def test_many_small_graphs(nat, batch):
     gs = G.many_graphs(40, 20, 600, seed=77)
     gs.append(G.path_graph(100))  # deeper than the 64-level capacity: re-run path
     gs.append(G.csr_from_edges(1, [], []))
-    hs = [nat.Graph.from_csr(g) for g in gs]
-    try:
-        with nat.ManyPlan(hs, batch=batch) as plan:
-            for rep in range(2):  # replay of the captured graph
-                plan.run()
-                code, flags, rerun = plan.result()
-                assert code == nat.BC_OK and rerun == 1
-                for g, h in zip(gs, hs):
-                    got, _, _ = h.result()
-                    assert close(got, oracle.bc(g)["bc"], g.n), (g.name, rep)
-    finally:
-        for h in hs:
-            h.close()
+    check_plan(nat, gs, batch, reps=2, expect_rerun=1)
+
+
+@pytest.mark.parametrize("batch", [64, 256])
+def test_many_largest_members(nat, batch):
+    """Graphs at the top of the set's size range, n = 5000: one of each recipe
+    (G(n, 3n) + Hamiltonian path, and Barabasi-Albert m = 3), with small
+    members beside them so that the large ones are split over several items."""
+    gs = [G.many_graph(0, 5000), G.many_graph(1, 5000), G.many_graph(2, 4999), G.many_graph(3, 4800)]
+    gs += G.many_graphs(12, 50, 300, seed=78)
+    check_plan(nat, gs, batch)
+
+
+def test_many_seeded_sample_of_the_benchmark_set(nat):
+    """24 members of the 2000-graph set itself (seeded choice of indices, the
+    largest one included), at the batch width the benchmark uses."""
+    ns = G.many_graph_sizes()
+    rng = np.random.default_rng(20080919)
+    idx = sorted(set(rng.choice(len(ns), 23, replace=False).tolist()) | {int(np.argmax(ns))})
+    gs = [G.many_graph(i, int(ns[i])) for i in idx]
+    check_plan(nat, gs, 256)
 
 
 def test_many_split_graph_deterministic(nat):

@@ -349,3 +349,54 @@ def test_rejects_bad_input(oracle_lib):
     bad = G.Graph(2, np.array([0, 1, 2], np.int32), np.array([0, 0], np.int32), None)  # self-loop
     with pytest.raises(ValueError):
         oracle_lib.bc(bad)
+
+
+# ---- the shortest-path DAG size (arcs (u, v) with u in P_s(v), Section 1.1),
+# which the roofline's algorithmic bytes count: closed forms and a count from
+# Floyd-Warshall distances that shares nothing with the oracle's BFS/Dijkstra.
+
+def _dag_arcs_from_distances(g, s):
+    d = brute.floyd_warshall(g)[s]
+    adj = brute.adjacency(g)
+    return sum(1 for u in range(g.n) if d[u] != brute.INF
+               for v, w in adj[u] if d[v] != brute.INF and d[u] + w == d[v])
+
+
+@pytest.mark.parametrize("n", [2, 5, 17])
+def test_dag_arcs_path_star_complete(oracle_lib, n):
+    # every one of these is a shortest-path tree from any source: n - 1 arcs
+    for g, srcs in ((G.path_graph(n), (0, n // 2, n - 1)), (G.star_graph(n), (0, n - 1)),
+                    (G.complete_graph(n), (0, n - 1))):
+        for s in srcs:
+            assert oracle_lib.source(g, s, with_delta=False)["arcs"] == n - 1, (g.name, s)
+    # an odd cycle is a tree from every vertex; an even one adds the second
+    # arc into the antipode
+    assert oracle_lib.source(G.cycle_graph(2 * n + 1), 3, with_delta=False)["arcs"] == 2 * n
+    assert oracle_lib.source(G.cycle_graph(2 * n), 3, with_delta=False)["arcs"] == 2 * n
+
+
+@pytest.mark.parametrize("a,b", [(1, 4), (3, 5), (6, 2)])
+def test_dag_arcs_complete_bipartite(oracle_lib, a, b):
+    # from an A vertex: b arcs to the B side, then each of the other a - 1 A
+    # vertices has all b B vertices as predecessors; from a B vertex the roles swap
+    g = G.complete_bipartite(a, b)
+    assert oracle_lib.source(g, 0, with_delta=False)["arcs"] == b + (a - 1) * b
+    assert oracle_lib.source(g, a, with_delta=False)["arcs"] == a + (b - 1) * a
+
+
+@pytest.mark.parametrize("k", [2, 5, 9])
+def test_dag_arcs_grid_corner(oracle_lib, k):
+    # from a corner every vertex (i, j) has predecessors (i-1, j) and (i, j-1)
+    # where they exist: 2 k (k - 1) arcs; uniform weights change nothing
+    assert oracle_lib.source(G.grid_graph(k), 0, with_delta=False)["arcs"] == 2 * k * (k - 1)
+    assert oracle_lib.source(G.grid_graph(k, 7), 0, with_delta=False)["arcs"] == 2 * k * (k - 1)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_dag_arcs_against_distance_table(oracle_lib, seed):
+    for g in (G.random_small(11, 0.35, 600 + seed), G.random_small(10, 0.4, 700 + seed, wmax=3)):
+        out = oracle_lib.bc(g)
+        for s in range(g.n):
+            want = _dag_arcs_from_distances(g, s)
+            assert oracle_lib.source(g, s, with_delta=False)["arcs"] == want, (g.name, s)
+            assert out["arcs"][s] == want
