@@ -104,6 +104,16 @@ extern "C" {
                                 fetches fewer rows; BC differs only by FP64 summation order, and
                                 per-source summaries keep the caller's order. */
 
+/* Test hook for the device-side timeout path (not for production runs):
+   every staged-row wait of the level sweeps also expects 16 bytes that no
+   copy delivers, so the bounded device wait (bc_options.device_wait_us)
+   runs out; the warp then releases those bytes, waits for its own copies to
+   land, stops staging, and bc_result returns BC_ERR_TIMEOUT. Nothing faults
+   or hangs: the wait is bounded and the context stays usable. */
+#define BC_TEST_WAIT_EXPIRY 0x200u
+#define BC_FORCE_BOTTOMUP 0x400u /* level 0 -> 1 also by the bottom-up pull over every vertex instead of
+                                    the top-down push from the sources' arcs */
+
 /*
  * Run options. Zero-initialise and set what you need; bc_run(..., NULL, ...)
  * uses the same defaults.
@@ -113,16 +123,37 @@ extern "C" {
  *   flags          BC_* option bits above.
  *   chunk          arcs per work item for high-degree vertices (0 = 256 in both
  *                  sweeps; a given value applies to both).
+ *   delta          bucket width of the weighted path: 0 or 1 (exact distances
+ *                  settle one value at a time, which the tie-aware path counts
+ *                  need); any other value returns BC_ERR_UNSUPPORTED.
  *   wait_limit_ms  bound on every host-side wait for device progress
  *                  (0 = 600000). Expiry returns BC_ERR_TIMEOUT.
+ *   alpha          direction of the unweighted forward sweep at level 0 -> 1,
+ *                  the level whose frontier (the batch's sources) is known before
+ *                  it runs: top-down (a push over the sources' arcs) while those
+ *                  arcs number fewer than 2m / alpha, the arcs a bottom-up pull
+ *                  reads; else bottom-up (every vertex sums over its neighbours
+ *                  in the frontier), as every later level runs. 0 = 1.
+ *                  BC_FORCE_BOTTOMUP pulls regardless.
+ *   beta           tail of the forward pass: the host launches levels three
+ *                  ahead of the device, and one at a time once the newest
+ *                  frontier holds at most beta x n vertices and under half of
+ *                  the one before it (a launch past the last level still costs
+ *                  a grid's start-up). 0 = 1/64.
+ *   device_wait_us bound on each device-side wait for staged row copies
+ *                  (0 = 2 s). Expiry sets BC_STATUS_COPY_TIMEOUT.
  */
 typedef struct bc_options {
     int32_t batch;
     uint32_t flags;
     int32_t chunk;
-    int32_t reserved0;
+    int32_t delta;
     int64_t wait_limit_ms;
-    int64_t reserved1[4];
+    float alpha;
+    float beta;
+    int32_t device_wait_us;
+    int32_t reserved0;
+    int64_t reserved1[2];
 } bc_options;
 
 typedef struct bc_graph bc_graph;
@@ -151,7 +182,8 @@ int bc_create_graph(int32_t n, const int32_t *row_ptr, const int32_t *col, const
  *   sources      int32[num_sources] (host or device), NULL = all n vertices.
  *                Ids in [0, n); repeats are allowed and counted each time.
  *   num_sources  >= 0 (ignored when sources == NULL).
- *   opt          NULL = defaults.
+ *   opt          NULL = the handle's default options (bc_autotune,
+ *                bc_set_default_options), else the built-in defaults.
  * Without BC_ACCUMULATE the result starts from zero. Returns when all work is
  * enqueued on cuda_stream, except for the bounded host waits the level loop
  * needs to learn each batch's depth. Unweighted batches run on up to eight
@@ -234,6 +266,27 @@ int bc_kernel_trace(bc_graph *g, int64_t cap, int32_t *kind, int32_t *level, flo
  */
 int bc_run_stats(bc_graph *g, int64_t *dag_arcs, int64_t *depth_sum, double *tensor_flops);
 
+/*
+ * Launch parameters (the paper has no counterpart: these choose how the
+ * kernels are shaped, never what they compute).
+ * bc_autotune  times bc_run on `sample` sources spread over the vertex ids
+ *              (0 = 2048) with CUDA events on cuda_stream, for every
+ *              candidate: unweighted graphs, batch 64/128/256 x chunk
+ *              128/256/512, then beta 1/256, 1/64, 1/16; weighted graphs,
+ *              2/4/8 sources per SM per wave. The fastest becomes the
+ *              handle's default (bc_run with opt = NULL uses it) and is copied
+ *              to *out (may be NULL). The handle's previous result is
+ *              overwritten. Errors: those of bc_run.
+ * bc_set_default_options  installs *opt as what bc_run uses for opt = NULL
+ *              (a tuned choice kept from an earlier process); NULL restores
+ *              the built-in defaults.
+ * bc_last_options  the options the last bc_run ran with, after that
+ *              substitution (all zero for the built-in defaults).
+ */
+int bc_autotune(bc_graph *g, int32_t sample, bc_options *out, void *cuda_stream);
+int bc_set_default_options(bc_graph *g, const bc_options *opt);
+int bc_last_options(const bc_graph *g, bc_options *out);
+
 /* Number of kernel launches the last bc_run issued (all kinds). */
 int64_t bc_launch_count(const bc_graph *g);
 
@@ -297,6 +350,10 @@ int bc_run_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col, const 
  *                 capacity (64 levels) is re-run with bc_run on the same
  *                 stream; *rerun (may be NULL) receives how many were.
  *                 Returns BC_OK or BC_WARN_SIGMA_OVERFLOW, or an error.
+ * bc_many_stats   after bc_many_result: the shortest-path DAG arcs (Section
+ *                 1.1's P_s(v) relations) summed over every source of every
+ *                 graph the persistent launch completed (re-run graphs not
+ *                 included).
  * bc_run_many     create + run + result + destroy in one call.
  * Errors: BC_ERR_ARG, BC_ERR_UNSUPPORTED (a weighted handle), BC_ERR_OOM,
  * BC_ERR_CUDA, BC_ERR_STATE.
@@ -305,6 +362,7 @@ typedef struct bc_many bc_many;
 int bc_many_create(bc_graph *const *graphs, int32_t k, const bc_options *opt, bc_many **out);
 int bc_many_run(bc_many *plan, void *cuda_stream);
 int bc_many_result(bc_many *plan, uint32_t *status_flags, int32_t *rerun);
+int bc_many_stats(const bc_many *plan, int64_t *dag_arcs);
 void bc_many_destroy(bc_many *plan);
 int bc_run_many(bc_graph *const *graphs, int32_t k, const bc_options *opt, void *cuda_stream);
 

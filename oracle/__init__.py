@@ -13,8 +13,8 @@ Centrality: Algorithms and Lower Bounds"):
 * :mod:`oracle.brute` -- the definitions of Section 1.1 by enumeration of
   every shortest path (pure Python, exact fractions; tiny graphs).
 * :mod:`oracle.algebraic` -- Section 3.1's matrix forms (ComputePathCount,
-  ComputeDependency, read as corrected in DESIGN) and Algorithm 2's pair
-  formula (Section 4.2.1), in numpy.
+  ComputeDependency; the path-count mask read as "not reached yet") and
+  Algorithm 2's pair formula (Section 4.2.1), in numpy.
 """
 from __future__ import annotations
 

@@ -1,12 +1,17 @@
 """Autotuner for the launch parameters of the batched paths.
 
-For one graph it times bc_run on a small seeded sample of sources for every
-batch width (sources per batch: 64, 128, 256) and work-item chunk size
-(arcs per warp item before a high-degree vertex is split: 128, 256, 512),
-and keeps the fastest. For a many-graph plan it times the persistent launch
-for batch widths 32 and 64. Results are cached in a JSON file keyed by
-(n, m, degree-skew bucket, GPU name), so a graph of the same shape on the
-same GPU reuses them. Timing uses CUDA events on the launching stream.
+For one graph the library's own tuner (bc_autotune) times bc_run on a sample
+of sources with CUDA events: unweighted graphs, every batch width (sources
+per batch: 64, 128, 256) x work-item chunk size (arcs per warp item before a
+high-degree vertex is split: 128, 256, 512), then the look-ahead's tail
+threshold beta (1/256, 1/64, 1/16); weighted graphs, the wave size.
+The choice becomes the handle's default, which bc_run uses when it is given
+no options. Here it is also cached in a JSON file keyed by (n, m,
+degree-skew bucket, GPU name), so a graph of the same shape on the same GPU
+gets it installed (bc_set_default_options) without timing again.
+
+For a many-graph plan it times the persistent launch for batch widths 32, 64,
+128 and 256 and keeps the fastest.
 """
 from __future__ import annotations
 
@@ -65,34 +70,28 @@ def _time_ms(fn, reps=2):
     return statistics.median(ts)
 
 
-def tune_graph(g, handle=None, batches=(64, 128, 256), chunks=(128, 256, 512), sample=512, use_cache=True):
-    """Best (batch, chunk) for bc_run on graph g (unweighted). Returns a dict
-    with the choice and the per-candidate times (ms per sampled source)."""
+def tune_graph(g, handle=None, sample=2048, use_cache=True):
+    """Best launch options for bc_run on graph g, installed as the handle's
+    default. Returns a dict with batch, chunk, alpha, beta (and whether it
+    came from the cache)."""
     key = _key(g, "graph")
     cache = _load()
-    if use_cache and key in cache:
-        return cache[key]
     own = handle is None
     h = handle or native.Graph.from_csr(g, trust_input=True)
     try:
-        src = G.sample_sources(g.n, min(g.n, sample), 4242)
-        res = {}
-        for b in batches:
-            for c in chunks:
-                k = min(src.size, 2 * b)
-                s = src[:k]
-                ms = _time_ms(lambda: (h.run(s, batch=b, chunk=c, flags=native.BC_NO_HASH), h.result()))
-                res[f"{b}x{c}"] = ms / k
-        best = min(res, key=res.get)
-        b, c = (int(x) for x in best.split("x"))
-        out = {"batch": b, "chunk": c, "ms_per_source": res}
+        if use_cache and key in cache:
+            c = cache[key]
+            h.set_default_options(native.make_options(c["batch"], 0, c["chunk"], alpha=c["alpha"], beta=c["beta"]))
+            return dict(c, cached=True)
+        o = h.autotune(sample)
+        out = {"batch": int(o.batch), "chunk": int(o.chunk), "alpha": float(o.alpha), "beta": float(o.beta)}
     finally:
         if own:
             h.close()
     cache = _load()
     cache[key] = out
     _store(cache)
-    return out
+    return dict(out, cached=False)
 
 
 def tune_many(gs, handles, batches=(32, 64, 128, 256), use_cache=True):

@@ -191,6 +191,17 @@ struct bc_graph {
     DevBuf<float> cval;
     DevBuf<uint16_t> Smask;
     DevBuf<uint32_t> wideflags, F, ufr, V, pmask, cnt;
+    // direction of level 0 -> 1 (top-down while the batch's source arcs are
+    // fewer than 2m / alpha) and the look-ahead's tail threshold (one level
+    // ahead once a shrinking frontier holds at most beta x n vertices)
+    float alpha = 1.0f, beta = 1.0f / 64.0f;
+    uint64_t dev_wait_ns = 0;  // bound on each device wait (0: the kernels' default)
+    uint32_t test_hold = 0;    // BC_TEST_WAIT_EXPIRY
+    bool bottom_up0 = false;   // BC_FORCE_BOTTOMUP: level 0 -> 1 pulled too
+    // options bc_run uses when given NULL (bc_autotune / bc_set_default_options)
+    bool has_defaults = false;
+    bc_options defaults{};
+    bc_options last_opt{};  // what the last bc_run was given (after the NULL substitution)
 
     // results
     DevBuf<double> bc;
@@ -539,6 +550,8 @@ bcgb::MsParams make_params(bc_graph *g) {
     p.part = g->part.p;
     p.pmask = g->pmask.p;
     p.cnt = g->cnt.p;
+    p.wait_ns = g->dev_wait_ns;
+    p.test_hold = g->test_hold;
     p.bc = g->bc.p;
     p.ctl = g->ctl;
     p.hctl = g->hctl_d;
@@ -609,6 +622,15 @@ bcgb::MsParams lane_params(bc_graph *g, int k) {
     p.ctl = ln.ctl;
     p.hctl = ln.hctl_d;
     return p;
+}
+
+// Per-run settings of the level sweeps taken from the options (NULL: defaults).
+void set_run_options(bc_graph *g, const bc_options *opt) {
+    g->alpha = (opt && opt->alpha > 0.0f) ? opt->alpha : 1.0f;
+    g->beta = (opt && opt->beta > 0.0f) ? std::min(opt->beta, 1.0f) : 1.0f / 64.0f;
+    g->dev_wait_ns = (opt && opt->device_wait_us > 0) ? (uint64_t)opt->device_wait_us * 1000ull : 0ull;
+    g->test_hold = (opt && (opt->flags & BC_TEST_WAIT_EXPIRY)) ? 16u : 0u;
+    g->bottom_up0 = opt && (opt->flags & BC_FORCE_BOTTOMUP);
 }
 
 int resolve_batch(const bc_options *opt, int *W) {
@@ -994,6 +1016,23 @@ int run_dense_group(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream
     return BC_OK;
 }
 
+// A shrinking frontier of at most this many vertices is taken as the tail of the
+// BFS: the host then launches one level at a time instead of kLookahead ahead
+// (a launch past the last level still costs a grid's start-up).
+int32_t small_frontier_items(const bc_graph *g) { return std::max<int32_t>(32, (int32_t)(g->beta * (float)g->n)); }
+
+// Beamer's direction rule for level 0 -> 1, the one level whose frontier (the
+// batch's sources) is known on the host: top-down (k_first, a push over the
+// sources' arcs) while those arcs are fewer than the 2m arcs a bottom-up pull
+// reads divided by alpha, else bottom-up. BC_FORCE_BOTTOMUP always pulls.
+int first_level_top_down(const bc_graph *g, const int32_t *src_host, int32_t nb) {
+    if (g->bottom_up0) return 0;
+    if (!src_host || g->directed) return 1;  // (directed graphs: the pull runs over in-arcs)
+    int64_t arcs = 0;
+    for (int32_t b = 0; b < nb; ++b) arcs += g->h_row_ptr[src_host[b] + 1] - g->h_row_ptr[src_host[b]];
+    return (double)arcs * (double)g->alpha < (double)g->narcs ? 1 : 0;
+}
+
 // The multi-source driver shared by bc_run and bc_forward_rows.
 // Concurrent sweep over K lanes (K >= 2). Batch i runs on lane i % K, each
 // lane on its own stream with its own batch state and BC accumulator, so the
@@ -1032,6 +1071,7 @@ int run_lanes(bc_graph *g, int32_t nsrc, int W, int K, cudaStream_t st, bool bac
     };
     Job jobs[kSweepLanes];
     int32_t next[kSweepLanes];
+    const int32_t small_frontier = small_frontier_items(g);
     for (int k = 0; k < K; ++k) next[k] = k;
     using clock = std::chrono::steady_clock;
     for (long spins = 0;; ++spins) {
@@ -1045,7 +1085,7 @@ int run_lanes(bc_graph *g, int32_t nsrc, int W, int K, cudaStream_t st, bool bac
                 const int32_t b0 = j.bi * B;
                 j.p = lane_params(g, k);
                 j.p.nb = std::min<int32_t>(B, nsrc - b0);
-                j.p.first = 1;
+                j.p.first = first_level_top_down(g, g->h_sources.data() + b0, j.p.nb);
                 j.p.seq = ++g->seq;
                 j.p.sources = g->sources.p + b0;
                 if (hash) {
@@ -1068,19 +1108,19 @@ int run_lanes(bc_graph *g, int32_t nsrc, int W, int K, cudaStream_t st, bool bac
             if (j.phase != 1) continue;
             busy = true;
             const bcgb::HostCtl *h = lane_hctl(k);
-            int done_lv = 0;
-            if (bcgb::load_acquire_u(&h->progress_seq) == j.p.seq) done_lv = bcgb::load_acquire_i(&h->progress);
-            while (j.launched <= j.p.Lcap - 2 && j.launched < done_lv + bcgb::kLookahead) {
+            int done_lv = 0, ahead = bcgb::kLookahead;
+            if (bcgb::word_for(&h->progress, j.p.seq, &done_lv)) ahead = bcgb::lookahead(h, small_frontier);
+            while (j.launched <= j.p.Lcap - 2 && j.launched < done_lv + ahead) {
                 Timer t(g, ls, BC_KERNEL_FORWARD, j.launched);
-                if (j.launched == 0)
+                if (j.launched == 0 && j.p.first)
                     bcgb::ms_launch_first(W, j.p, ls);
                 else
                     bcgb::ms_launch_forward(W, j.p, j.launched, ls);
                 ++j.launched;
                 moved = true;
             }
-            if (bcgb::load_acquire_u(&h->done_seq) != j.p.seq) continue;
-            const int L = bcgb::load_acquire_i(&h->nlevels);
+            int L = 0;
+            if (!bcgb::word_for(&h->done, j.p.seq, &L)) continue;
             moved = true;
             if (L < 0) {
                 // deeper than the level capacity: grow it on every lane and
@@ -1134,7 +1174,8 @@ int run_lanes(bc_graph *g, int32_t nsrc, int W, int K, cudaStream_t st, bool bac
                 const cudaError_t e = cudaStreamQuery(lane_stream(k));
                 if (e != cudaSuccess && e != cudaErrorNotReady)
                     return fail(BC_ERR_CUDA, std::string("device error during a forward pass: ") + cudaGetErrorString(e));
-                if (e == cudaSuccess && bcgb::load_acquire_u(&lane_hctl(k)->done_seq) != jobs[k].p.seq &&
+                int dummy = 0;
+                if (e == cudaSuccess && !bcgb::word_for(&lane_hctl(k)->done, jobs[k].p.seq, &dummy) &&
                     jobs[k].launched > jobs[k].p.Lcap - 2)
                     return fail(BC_ERR_STATE, "forward pass ended without reporting its depth");
             }
@@ -1183,7 +1224,7 @@ int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStr
         const int32_t nb = std::min<int32_t>(B, nsrc - b0);
         bcgb::MsParams p = make_params(g);
         p.nb = nb;
-        p.first = 1;
+        p.first = first_level_top_down(g, g->h_sources.data() + b0, nb);
         p.seq = ++g->seq;
         p.sources = g->sources.p + b0;
         if (hash) {
@@ -1202,12 +1243,13 @@ int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStr
         {
             auto launch = [&](int level) {
                 Timer t(g, st, BC_KERNEL_FORWARD, level);
-                if (level == 0)
+                if (level == 0 && p.first)
                     bcgb::ms_launch_first(W, p, st);
                 else
                     bcgb::ms_launch_forward(W, p, level, st);
             };
-            r = bcgb::drive_forward(g->hctl, p.seq, g->Lcap - 2, launch, wait_ms, st, &g_err, &L);
+            r = bcgb::drive_forward(g->hctl, p.seq, g->Lcap - 2, launch, wait_ms, st, &g_err, &L,
+                                    small_frontier_items(g));
         }
         if (r) return r;
         if (L < 0) {  // deeper than the level capacity: grow it and redo this batch
@@ -1641,10 +1683,15 @@ int bc_run(bc_graph *g, const int32_t *sources, int32_t num_sources, const bc_op
     g_err.clear();
     if (!g) return fail(BC_ERR_ARG, "graph is NULL");
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (!opt && g->has_defaults) opt = &g->defaults;  // the tuned (or installed) choice
+    g->last_opt = opt ? *opt : bc_options{};
     const uint32_t flags = opt ? opt->flags : 0u;
     int W = 0;
     int r = g->weighted ? BC_OK : resolve_batch(opt, &W);
     if (r) return r;
+    if (opt && opt->delta != 0 && opt->delta != 1)
+        return fail(BC_ERR_UNSUPPORTED, "delta: only bucket width 1 (one distance value per bucket) is supported");
+    set_run_options(g, opt);
     if (g->weighted && (flags & BC_PLAIN)) return fail(BC_ERR_UNSUPPORTED, "the one-source path is unweighted only");
     int32_t nsrc = 0;
     if (g->weighted && (flags & BC_DENSE) && sources)
@@ -1760,6 +1807,7 @@ int bc_forward_rows(bc_graph *g, const int32_t *sources, int32_t k, uint64_t *si
     cudaStream_t st = (cudaStream_t)cuda_stream;
     int W = 0;
     int r = g->weighted ? BC_OK : resolve_batch(opt, &W);
+    if (!r) set_run_options(g, opt);
     if (r) return r;
     int32_t nsrc = 0;
     r = stage_sources(g, sources, k, &nsrc);
@@ -1848,6 +1896,108 @@ int bc_run_stats(bc_graph *g, int64_t *dag_arcs, int64_t *depth_sum, double *ten
     return BC_OK;
 }
 
+int bc_set_default_options(bc_graph *g, const bc_options *opt) {
+    g_err.clear();
+    if (!g) return fail(BC_ERR_ARG, "graph is NULL");
+    g->has_defaults = opt != nullptr;
+    g->defaults = opt ? *opt : bc_options{};
+    return BC_OK;
+}
+
+int bc_last_options(const bc_graph *g, bc_options *out) {
+    g_err.clear();
+    if (!g || !out) return fail(BC_ERR_ARG, "bad arguments");
+    *out = g->last_opt;
+    return BC_OK;
+}
+
+int bc_autotune(bc_graph *g, int32_t sample, bc_options *out, void *cuda_stream) {
+    g_err.clear();
+    if (!g) return fail(BC_ERR_ARG, "graph is NULL");
+    if (sample < 0) return fail(BC_ERR_ARG, "sample < 0");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int32_t n = g->n;
+    if (n == 0) {
+        g->has_defaults = false;
+        if (out) *out = bc_options{};
+        return BC_OK;
+    }
+    const int32_t k = std::min<int32_t>(n, sample > 0 ? sample : 2048);
+    std::vector<int32_t> src(k);
+    for (int32_t i = 0; i < k; ++i) src[i] = (int32_t)(((int64_t)i * n) / k);  // spread over the ids
+    ScopedBuf<int32_t> d_src;
+    CK(d_src.ensure(k));
+    CK(cudaMemcpy(d_src.p, src.data(), (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int err = BC_OK;
+    // the shorter of two timed runs after one warm-up
+    auto time_ms = [&](const bc_options &o, float *ms) -> int {
+        float best = 0.0f;
+        for (int rep = 0; rep < 3; ++rep) {
+            if (cudaEventRecord(e0, st) != cudaSuccess) return fail(BC_ERR_CUDA, "event record");
+            int r = bc_run(g, d_src.p, k, &o, st);
+            if (r < 0) return r;
+            r = bc_result(g, nullptr, nullptr);
+            if (r < 0) return r;
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                return fail(BC_ERR_CUDA, "event wait");
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep == 1 || (rep == 2 && t < best)) best = t;
+        }
+        *ms = best;
+        return BC_OK;
+    };
+    bc_options best{};
+    float best_ms = 0.0f;
+    auto consider = [&](const bc_options &o) -> int {
+        float ms = 0.0f;
+        const int r = time_ms(o, &ms);
+        if (r < 0) return r;
+        if (best_ms == 0.0f || ms < best_ms) {
+            best_ms = ms;
+            best = o;
+        }
+        return BC_OK;
+    };
+    if (g->weighted) {
+        // sources per wave of the bucket kernel: 2, 4 or 8 per SM
+        for (int per : {2, 4, 8}) {
+            bc_options o{};
+            o.flags = BC_NO_HASH;
+            o.batch = per * sm_count_host();
+            if ((err = consider(o)) < 0) break;
+        }
+    } else {
+        // batch width x work-item chunk, then the set thresholds of the sweeps
+        for (int b : {64, 128, 256})
+            for (int c : {128, 256, 512}) {
+                bc_options o{};
+                o.flags = BC_NO_HASH;
+                o.batch = b;
+                o.chunk = c;
+                if (err >= 0 && (err = consider(o)) < 0) break;
+            }
+        // then the look-ahead's tail threshold (the base's 1/64 is already timed)
+        const bc_options base = best;
+        for (float bt : {1.0f / 256.0f, 1.0f / 16.0f}) {
+            bc_options o = base;
+            o.beta = bt;
+            if (err >= 0 && (err = consider(o)) < 0) break;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err < 0) return err;
+    best.flags = 0;
+    g->has_defaults = true;
+    g->defaults = best;
+    if (out) *out = best;
+    return BC_OK;
+}
+
 int bc_graph_size(const bc_graph *g, int32_t *n, int64_t *m, int32_t *weighted) {
     if (!g) return fail(BC_ERR_ARG, "graph is NULL");
     if (n) *n = g->n;
@@ -1901,6 +2051,7 @@ struct bc_many {
     cudaGraphExec_t exec = nullptr;
     cudaStream_t last_stream = nullptr;
     bool ran = false;
+    int64_t arcs = 0;  // DAG arcs counted by the last persistent launch
 };
 
 namespace {
@@ -2104,11 +2255,14 @@ int bc_many_result(bc_many *m, uint32_t *status_flags, int32_t *rerun) {
     if (!m) return fail(BC_ERR_ARG, "plan is NULL");
     if (!m->ran) return fail(BC_ERR_STATE, "no bc_many_run");
     uint32_t status = 0;
+    unsigned long long arcs = 0;
     std::vector<unsigned> capped(m->graphs.size());
     CK(cudaMemcpyAsync(&status, &m->ctl->status, 4, cudaMemcpyDeviceToHost, m->last_stream));
+    CK(cudaMemcpyAsync(&arcs, &m->ctl->dag_arcs, 8, cudaMemcpyDeviceToHost, m->last_stream));
     if (!capped.empty())
         CK(cudaMemcpyAsync(capped.data(), m->capped.p, capped.size() * 4, cudaMemcpyDeviceToHost, m->last_stream));
     CK(cudaStreamSynchronize(m->last_stream));
+    m->arcs = (int64_t)arcs;
     int32_t nre = 0;
     for (size_t i = 0; i < capped.size(); ++i) {
         if (!capped[i]) continue;
@@ -2125,6 +2279,14 @@ int bc_many_result(bc_many *m, uint32_t *status_flags, int32_t *rerun) {
     if (rerun) *rerun = nre;
     if (status_flags) *status_flags = status;
     return (status & BC_STATUS_SIGMA_OVERFLOW) ? BC_WARN_SIGMA_OVERFLOW : BC_OK;
+}
+
+int bc_many_stats(const bc_many *m, int64_t *dag_arcs) {
+    g_err.clear();
+    if (!m) return fail(BC_ERR_ARG, "plan is NULL");
+    if (!m->ran) return fail(BC_ERR_STATE, "no bc_many_run");
+    if (dag_arcs) *dag_arcs = m->arcs;
+    return BC_OK;
 }
 
 void bc_many_destroy(bc_many *m) {

@@ -39,17 +39,29 @@ struct DevCtl {
     unsigned long long depth_sum; // sum over batches (or sources) of the BFS depth
     unsigned long long batch_arcs; // the running batch's arcs, added to dag_arcs when its forward
                                    // pass ends (a batch restarted with more levels counts once)
+    uint32_t front_new;   // vertices put into the next frontier so far (summed over blocks)
+    uint32_t front_last;  // vertices in the newest complete frontier
 };
 
-// Host-mapped mirror the host polls while the level loop runs (pinned,
-// written by the device with system-scope fences).
+// Host-mapped block the host polls while the level loop runs (pinned). Each
+// word is written with one 64-bit relaxed store at system scope, the batch
+// sequence number in its high half and the value in its low half, so the host
+// learns both from one read: nothing has to be ordered, and the last block of
+// a level does not wait for its writes to reach host memory.
 struct HostCtl {
-    uint32_t done_seq;      // == batch seq once its forward pass ended
-    int32_t nlevels;        // its depth L, or -1 when the level capacity was hit
-    uint32_t progress_seq;  // batch seq of the last completed forward level
-    int32_t progress;       // number of forward levels completed
-    uint32_t pad[4];
+    unsigned long long done;      // (seq << 32) | depth L once the forward pass ended (-1: level capacity hit)
+    unsigned long long progress;  // (seq << 32) | number of forward levels completed
+    unsigned long long counts;    // (vertices in the newest frontier << 32) | (in the one before), each
+                                  // -1 when not counted; a hint for the host's look-ahead only
+    unsigned long long pad;
 };
+
+#ifdef __CUDACC__
+__device__ __forceinline__ void host_word(unsigned long long *w, uint32_t hi, uint32_t lo) {
+    const unsigned long long x = ((unsigned long long)hi << 32) | lo;
+    asm volatile("st.relaxed.sys.global.u64 [%0], %1;" ::"l"(w), "l"(x) : "memory");
+}
+#endif
 
 struct MsParams {
     int32_t n;
@@ -82,6 +94,8 @@ struct MsParams {
     uint64_t *part;
     uint32_t *pmask;
     uint32_t *cnt;
+    uint64_t wait_ns;         // bound on each device wait for staged rows (0: 2 s)
+    uint32_t test_hold;       // bytes every staged round expects beyond its copies (timeout test hook)
     double *bc;
     uint64_t *h_sigma;  // per-source summaries, indexed from this batch's first source
     uint64_t *h_dist;

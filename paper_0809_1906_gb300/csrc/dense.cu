@@ -2,7 +2,8 @@
 // tensor cores (flag BC_DENSE).
 //
 // ComputePathCount multiplies by the adjacency matrix A once per level. In
-// frontier form (corrected mask, see DESIGN), for a batch of B = 128 sources:
+// frontier form (the mask read as "not reached yet" rather than the previous
+// level only), for a batch of B = 128 sources:
 //     C_l[s][u] = sigma_s(u) if d(s,u) = l, else 0,
 //     C_{l+1} = (C_l . A) masked to the (s, v) not reached yet,
 // and the non-zero entries of C_{l+1} are sigma_s(v) for d(s,v) = l+1.

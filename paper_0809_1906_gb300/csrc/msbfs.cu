@@ -80,6 +80,8 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
         p.ctl->nonempty = 0u;
         p.ctl->nlevels = 0;
         p.ctl->batch_arcs = 0ull;
+        p.ctl->front_new = 0u;
+        p.ctl->front_last = 0xffffffffu;  // level 0 (the sources) is not counted
         p.ctl->seq = p.seq;
         atomicExch(&p.ctl->blocks_done, 0u);
     }
@@ -135,18 +137,15 @@ __global__ void __launch_bounds__(kBlock) k_first(const MsParams p) {
     __threadfence();
     atomicExch(&p.ctl->blocks_done, 0u);
     atomicAdd(&p.ctl->batch_arcs, (unsigned long long)total);
-    volatile HostCtl *h = p.hctl;
     if (total == 0) {  // every source isolated: depth 0
         p.ctl->fwd_done = 1u;
         p.ctl->nlevels = 0;
-        h->nlevels = 0;
-        __threadfence_system();
-        h->done_seq = p.seq;
+        host_word(&p.hctl->done, p.seq, 0u);
     }
-    h->progress = 1;
-    __threadfence_system();
-    h->progress_seq = p.seq;
-    __threadfence_system();
+    // level 1 has at most `total` vertices (the arcs out of the sources)
+    p.ctl->front_last = (uint32_t)total;
+    host_word(&p.hctl->counts, (uint32_t)total, 0xffffffffu);
+    host_word(&p.hctl->progress, p.seq, 1u);
 }
 
 template <int W>
@@ -159,11 +158,13 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     extern __shared__ __align__(128) uint8_t s_stage[];
     __shared__ uint32_t s_flags;
     __shared__ unsigned long long s_arcs;
+    __shared__ uint32_t s_front;  // vertices this block put into frontier l+1
     __shared__ int32_t s_u[kWarps][32];
     __shared__ uint32_t s_nz[kWarps][32];
     if (threadIdx.x == 0) {
         s_flags = 0u;
         s_arcs = 0ull;
+        s_front = 0u;
     }
     __syncthreads();
     // speculative launches past the last level, and the level-capacity guard
@@ -183,8 +184,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     const bool wide = *(volatile uint32_t *)(p.wide + l) != 0u;
     const bool ones = l == 1 && p.first;  // level 1 written by k_first: all counts 1, no masked rows
     bool produced = false, ovf = false, wide_next = false;
-    uint32_t arcs = 0;  // predecessor relations counted by this lane
-    body::WarpStage ws{s_stage + wib * stage::kFwdStageBytes, s_bar + wib, s_qz[wib], 0u, false};
+    uint32_t arcs = 0;   // predecessor relations counted by this lane
+    uint32_t front = 0;  // vertices this warp put into frontier l+1 (counted by every lane alike)
+    body::WarpStage ws{s_stage + wib * stage::kFwdStageBytes, s_bar + wib, s_qz[wib], 0u, false,
+                       p.wait_ns ? p.wait_ns : stage::kWaitNs, p.test_hold};
     if (lane == 0) stage::bar_init(ws.bar);
     __syncwarp();
 
@@ -241,7 +244,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
             body::fwd_sum<W, true, true>(p.col_f, beg, end, ufl, Fl, Sl, p.sigma, wide, ones, U, s_u[wib], s_nz[wib], lane,
                                          acc, nf, ovf, arcs, &ws);
             if (slot < 0) {
-                produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
+                const bool joined = body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
+                produced |= joined;
+                front += joined ? 1u : 0u;
                 continue;
             }
             uint64_t *pp = p.part + (size_t)slot * B + lane;
@@ -276,7 +281,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
                     nf[j] |= __ldcg(qm + j);
                 }
             }
-            produced |= body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
+            const bool joined = body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
+            produced |= joined;
+            front += joined ? 1u : 0u;
             if (lane == 0) p.cnt[first] = 0u;
         }
     }
@@ -290,10 +297,12 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
         if (wwide) atomicOr(&s_flags, 4u);
         if (ws.fail) atomicOr(&s_flags, 8u);
         if (arcs) atomicAdd(&s_arcs, (unsigned long long)arcs);
+        if (front) atomicAdd(&s_front, front);
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
     if (s_arcs) atomicAdd(&p.ctl->batch_arcs, s_arcs);
+    if (s_front) atomicAdd(&p.ctl->front_new, s_front);
     if (s_flags & 1u) atomicOr(&p.ctl->nonempty, 1u);
     if (s_flags & 2u) atomicOr(&p.ctl->status, BC_STATUS_SIGMA_OVERFLOW);
     if (s_flags & 8u) atomicOr(&p.ctl->status, BC_STATUS_COPY_TIMEOUT);
@@ -304,26 +313,23 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     __threadfence();
     const unsigned ne = atomicExch(&p.ctl->nonempty, 0u);
     atomicExch(&p.ctl->blocks_done, 0u);
-    volatile HostCtl *h = p.hctl;
     if (ne == 0u) {
         p.ctl->fwd_done = 1u;
         p.ctl->nlevels = l;
         p.ctl->depth_sum += (unsigned long long)l;
         p.ctl->dag_arcs += atomicExch(&p.ctl->batch_arcs, 0ull);
-        h->nlevels = l;
-        __threadfence_system();
-        h->done_seq = p.seq;
+        host_word(&p.hctl->done, p.seq, (uint32_t)l);
     } else if (l + 2 >= p.Lcap) {
         p.ctl->fwd_done = 1u;
         p.ctl->nlevels = -1;
-        h->nlevels = -1;
-        __threadfence_system();
-        h->done_seq = p.seq;
+        host_word(&p.hctl->done, p.seq, 0xffffffffu);
     }
-    h->progress = l + 1;
-    __threadfence_system();
-    h->progress_seq = p.seq;
-    __threadfence_system();
+    // the sizes of frontiers l+1 and l (vertices), a hint for the host's look-ahead
+    const uint32_t nxt = atomicExch(&p.ctl->front_new, 0u);
+    const uint32_t cur = p.ctl->front_last;
+    p.ctl->front_last = nxt;
+    host_word(&p.hctl->counts, nxt, cur);
+    host_word(&p.hctl->progress, p.seq, (uint32_t)(l + 1));
 }
 
 template <int W>
@@ -346,7 +352,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
     const size_t nB = (size_t)p.n * B;
     float *Cl = p.cval + (size_t)(l & 1) * nB;
     const float *Cs = p.cval + (size_t)((l + 1) & 1) * nB;
-    body::WarpStage ws{s_stage + wib * stage::kBwdStageBytes, s_bar + wib, s_qz[wib], 0u, false};
+    body::WarpStage ws{s_stage + wib * stage::kBwdStageBytes, s_bar + wib, s_qz[wib], 0u, false,
+                       p.wait_ns ? p.wait_ns : stage::kWaitNs, p.test_hold};
     if (lane == 0) stage::bar_init(ws.bar);
     __syncwarp();
     // where the finalize reads sigma_s(v) for the pairs at level l: none at

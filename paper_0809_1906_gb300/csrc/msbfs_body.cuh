@@ -43,7 +43,20 @@ struct WarpStage {
     uint32_t *qz;
     uint32_t phase;
     bool fail;
+    uint64_t limit_ns;  // bound on each wait
+    uint32_t hold;      // extra bytes each round expects that no copy delivers (timeout test hook), else 0
 };
+
+// A staged round's wait gave up: release the held bytes, then wait (bounded)
+// for the copies this warp already issued, so that no copy lands in the stage
+// after the warp stops using it; the warp stages nothing more.
+__device__ __forceinline__ void give_up(WarpStage *ws, uint32_t parity, int lane) {
+    if (lane == 0 && ws->hold) stage::complete_tx(ws->bar, ws->hold);
+    __syncwarp();
+    stage::wait(ws->bar, parity);
+    __syncwarp();
+    ws->fail = true;
+}
 
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -276,13 +289,14 @@ __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg
                 const uint32_t bytes = go ? 64u * (uint32_t)(hi - lo + 1) : 0u;
                 const uint32_t tot = __reduce_add_sync(kFull, bytes);
                 if (go) ws->qz[rank] = nz;
-                if (lane == 0) stage::expect_tx(ws->bar, tot);
+                if (lane == 0) stage::expect_tx(ws->bar, tot + ws->hold);
                 __syncwarp();
                 if (go) stage::copy(ws->buf + rank * RB + 64 * lo, Sl + (size_t)u * B + 32 * lo, bytes, ws->bar);
-                const bool ok = stage::wait(ws->bar, ws->phase);
+                const uint32_t ph = ws->phase;
+                const bool ok = stage::wait(ws->bar, ph, ws->limit_ns);
                 ws->phase ^= 1u;
                 if (!__all_sync(kFull, ok)) {
-                    ws->fail = true;
+                    give_up(ws, ph, lane);
                     break;
                 }
 #pragma unroll 4
@@ -490,13 +504,14 @@ __device__ __forceinline__ void bwd_sum(const int32_t *__restrict__ col, int beg
                 const uint32_t bytes = go ? 128u * (uint32_t)(hi - lo + 1) : 0u;
                 const uint32_t tot = __reduce_add_sync(kFull, bytes);
                 if (go) ws->qz[rank] = nz;
-                if (lane == 0) stage::expect_tx(ws->bar, tot);
+                if (lane == 0) stage::expect_tx(ws->bar, tot + ws->hold);
                 __syncwarp();
                 if (go) stage::copy(ws->buf + rank * RB + 128 * lo, Cs + (size_t)u * B + 32 * lo, bytes, ws->bar);
-                const bool ok = stage::wait(ws->bar, ws->phase);
+                const uint32_t ph = ws->phase;
+                const bool ok = stage::wait(ws->bar, ph, ws->limit_ns);
                 ws->phase ^= 1u;
                 if (!__all_sync(kFull, ok)) {
-                    ws->fail = true;
+                    give_up(ws, ph, lane);
                     break;
                 }
 #pragma unroll 2

@@ -120,19 +120,13 @@ __global__ void __launch_bounds__(kBlock) p_forward(const PlainParams p, const i
     atomicExch(&p.ctl->blocks_done, 0u);
     const int nt = (int)atomicAdd(p.tail, 0u);
     p.level_off[l + 2] = nt;
-    volatile HostCtl *h = p.hctl;
     if (nt == qe) {
         p.ctl->fwd_done = 1u;
         p.ctl->nlevels = l;
         p.ctl->depth_sum += (unsigned long long)l;
-        h->nlevels = l;
-        __threadfence_system();
-        h->done_seq = p.seq;
+        host_word(&p.hctl->done, p.seq, (uint32_t)l);
     }
-    h->progress = l + 1;
-    __threadfence_system();
-    h->progress_seq = p.seq;
-    __threadfence_system();
+    host_word(&p.hctl->progress, p.seq, (uint32_t)(l + 1));
 }
 
 __global__ void __launch_bounds__(kBlock) p_backward(const PlainParams p, const int l) {

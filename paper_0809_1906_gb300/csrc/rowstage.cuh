@@ -64,13 +64,19 @@ __device__ __forceinline__ bool try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0u;
 }
 
-// Bounded wait for the phase with the given parity; false once kWaitNs passed.
-__device__ __forceinline__ bool wait(uint64_t *bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity; false once limit_ns passed.
+__device__ __forceinline__ bool wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns = kWaitNs) {
     if (try_wait(bar, parity)) return true;
     const uint64_t t0 = now_ns();
     while (!try_wait(bar, parity))
-        if (now_ns() - t0 > kWaitNs) return false;
+        if (now_ns() - t0 > limit_ns) return false;
     return true;
+}
+
+// Count `bytes` of the current phase's expected transactions as done without
+// a copy (releases bytes that were expected but will not arrive).
+__device__ __forceinline__ void complete_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
 
 // Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)

@@ -42,6 +42,8 @@ BC_DENSE = 0x20
 BC_SPARSE_BACKWARD = 0x40
 BC_KEEP_ORDER = 0x80
 BC_PAIRS = 0x100
+BC_TEST_WAIT_EXPIRY = 0x200
+BC_FORCE_BOTTOMUP = 0x400
 
 BC_KERNEL_INIT = 0
 BC_KERNEL_FORWARD = 1
@@ -54,8 +56,9 @@ KERNEL_NAMES = {0: "init", 1: "forward", 2: "backward", 3: "hash", 4: "plain", 5
 # every entry point include/bc_gb300.h declares
 EXPORTS = ["bc_create_graph", "bc_run", "bc_result", "bc_source_hashes", "bc_forward_rows",
            "bc_kernel_time", "bc_kernel_trace", "bc_run_stats", "bc_launch_count", "bc_graph_size", "bc_destroy_graph",
-           "bc_status_string", "bc_last_error", "bc_run_noalloc",
-           "bc_many_create", "bc_many_run", "bc_many_result", "bc_many_destroy", "bc_run_many"]
+           "bc_status_string", "bc_last_error", "bc_run_noalloc", "bc_autotune", "bc_set_default_options",
+           "bc_last_options",
+           "bc_many_create", "bc_many_run", "bc_many_result", "bc_many_stats", "bc_many_destroy", "bc_run_many"]
 
 
 class BcError(RuntimeError):
@@ -66,8 +69,9 @@ class BcError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int32), ("flags", ctypes.c_uint32), ("chunk", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("wait_limit_ms", ctypes.c_int64),
-                ("reserved1", ctypes.c_int64 * 4)]
+                ("delta", ctypes.c_int32), ("wait_limit_ms", ctypes.c_int64),
+                ("alpha", ctypes.c_float), ("beta", ctypes.c_float), ("device_wait_us", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("reserved1", ctypes.c_int64 * 2)]
 
 
 _lock = threading.Lock()
@@ -106,9 +110,13 @@ def load(build_if_needed: bool = True, require_gpu: bool = True):
             "bc_status_string": (ctypes.c_char_p, [i32]),
             "bc_last_error": (ctypes.c_char_p, []),
             "bc_run_noalloc": (i32, [i32, P, P, P, i32, P, P]),
+            "bc_autotune": (i32, [P, i32, P, P]),
+            "bc_set_default_options": (i32, [P, P]),
+            "bc_last_options": (i32, [P, P]),
             "bc_many_create": (i32, [P, i32, P, ctypes.POINTER(P)]),
             "bc_many_run": (i32, [P, P]),
             "bc_many_result": (i32, [P, P, P]),
+            "bc_many_stats": (i32, [P, P]),
             "bc_many_destroy": (None, [P]),
             "bc_run_many": (i32, [P, i32, P, P]),
         }
@@ -159,9 +167,11 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def make_options(batch=0, flags=0, chunk=0, wait_limit_ms=0) -> Options:
+def make_options(batch=0, flags=0, chunk=0, wait_limit_ms=0, alpha=0.0, beta=0.0, delta=0,
+                 device_wait_us=0) -> Options:
     o = Options()
     o.batch, o.flags, o.chunk, o.wait_limit_ms = batch, flags, chunk, wait_limit_ms
+    o.alpha, o.beta, o.delta, o.device_wait_us = alpha, beta, delta, device_wait_us
     return o
 
 
@@ -207,14 +217,16 @@ class Graph:
     def __exit__(self, *exc):
         self.close()
 
-    def run(self, sources=None, batch=0, flags=0, chunk=0, wait_limit_ms=0, stream=None) -> int:
-        """bc_run: sources None = all vertices; numpy int32 (host) or torch int32 (host/device)."""
-        opt = make_options(batch, flags, chunk, wait_limit_ms)
+    def run(self, sources=None, batch=0, flags=0, chunk=0, wait_limit_ms=0, stream=None, alpha=0.0, beta=0.0,
+            delta=0, device_wait_us=0, default_options=False) -> int:
+        """bc_run: sources None = all vertices; numpy int32 (host) or torch int32 (host/device).
+        default_options=True passes NULL options (the library's defaults or its tuned choice)."""
+        opt = make_options(batch, flags, chunk, wait_limit_ms, alpha, beta, delta, device_wait_us)
         if sources is not None and isinstance(sources, np.ndarray):
             sources = np.ascontiguousarray(sources, dtype=np.int32)
         ns = 0 if sources is None else int(len(sources))
-        return _check(self.lib.bc_run(self.handle, _addr(sources), ns, ctypes.byref(opt), _stream_ptr(stream)),
-                      "bc_run")
+        return _check(self.lib.bc_run(self.handle, _addr(sources), ns, None if default_options else ctypes.byref(opt),
+                                      _stream_ptr(stream)), "bc_run")
 
     def result(self, out=None):
         """bc_result into `out` (numpy float64 / torch float64 host or device); returns (out, status, flags)."""
@@ -233,12 +245,12 @@ class Graph:
                "bc_source_hashes")
         return dict(hash_sigma=hs, hash_dist=hd, dist_sum=ds, reach=rc)
 
-    def forward_rows(self, sources, batch=0, stream=None):
+    def forward_rows(self, sources, batch=0, stream=None, flags=0):
         src = np.ascontiguousarray(sources, dtype=np.int32)
         k = int(src.size)
         sig = np.empty((k, self.n), np.uint64)
         dist = np.empty((k, self.n), np.int32)
-        opt = make_options(batch)
+        opt = make_options(batch, flags)
         code = _check(self.lib.bc_forward_rows(self.handle, _addr(src), k, _addr(sig), _addr(dist),
                                                ctypes.byref(opt), _stream_ptr(stream)), "bc_forward_rows")
         return sig, dist, code
@@ -260,6 +272,22 @@ class Graph:
         _check(self.lib.bc_kernel_trace(self.handle, k, _addr(kind), _addr(level), _addr(ms), ctypes.byref(cnt)),
                "bc_kernel_trace")
         return kind, level, ms
+
+    def autotune(self, sample: int = 0, stream=None) -> Options:
+        """bc_autotune: time the candidates on `sample` sources; the choice
+        becomes this handle's default for run(default_options=True)."""
+        o = Options()
+        _check(self.lib.bc_autotune(self.handle, int(sample), ctypes.byref(o), _stream_ptr(stream)), "bc_autotune")
+        return o
+
+    def set_default_options(self, opt) -> None:
+        _check(self.lib.bc_set_default_options(self.handle, None if opt is None else ctypes.byref(opt)),
+               "bc_set_default_options")
+
+    def last_options(self) -> Options:
+        o = Options()
+        _check(self.lib.bc_last_options(self.handle, ctypes.byref(o)), "bc_last_options")
+        return o
 
     def run_stats(self):
         a = ctypes.c_int64(0)
@@ -299,6 +327,11 @@ class ManyPlan:
         rr = ctypes.c_int32(0)
         code = _check(self.lib.bc_many_result(self.handle, ctypes.byref(fl), ctypes.byref(rr)), "bc_many_result")
         return code, fl.value, rr.value
+
+    def dag_arcs(self) -> int:
+        a = ctypes.c_int64(0)
+        _check(self.lib.bc_many_stats(self.handle, ctypes.byref(a)), "bc_many_stats")
+        return a.value
 
     def close(self):
         if getattr(self, "handle", None):

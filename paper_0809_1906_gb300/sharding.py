@@ -23,17 +23,37 @@ def shard_sources(sources, rank: int, world: int, batch: int) -> np.ndarray:
 
 def reduce_partials(partial: np.ndarray, group=None) -> np.ndarray:
     """Sum every rank's partial BC vector in rank order (bit-reproducible for a
-    fixed world size): gather to all ranks, then add rank 0, 1, ... in turn."""
+    fixed world size): gather to all ranks, then add rank 0, 1, ... in turn.
+    Works on a gloo group (host tensors) and on an NCCL group (the vector goes
+    through the current CUDA device)."""
     import torch
     import torch.distributed as dist
     if not dist.is_initialized() or dist.get_world_size(group) == 1:
-        return partial.copy()
+        return np.array(partial, dtype=np.float64, copy=True)
     t = torch.from_numpy(np.ascontiguousarray(partial, dtype=np.float64))
+    if dist.get_backend(group) == "nccl":
+        return reduce_partials_device(t.cuda(), group).cpu().numpy()
     parts = [torch.empty_like(t) for _ in range(dist.get_world_size(group))]
     dist.all_gather(parts, t, group=group)
-    out = np.zeros_like(partial, dtype=np.float64)
-    for p in parts:
-        out += p.numpy()
+    out = parts[0].clone()
+    for p in parts[1:]:
+        out += p
+    return out.numpy()
+
+
+def reduce_partials_device(partial, group=None):
+    """The rank-ordered sum of a tensor held by every rank (on the device for
+    an NCCL group): one all-gather of the n-vectors, then rank 0, 1, ... added
+    in turn, so every rank gets the same bits."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized() or dist.get_world_size(group) == 1:
+        return partial.clone()
+    parts = [torch.empty_like(partial) for _ in range(dist.get_world_size(group))]
+    dist.all_gather(parts, partial.contiguous(), group=group)
+    out = parts[0].clone()
+    for p in parts[1:]:
+        out += p
     return out
 
 

@@ -243,14 +243,34 @@ def test_rmat_full_size_bench_configuration(nat):
 
 
 def test_autotuner_choice_runs_correctly(nat, tmp_path, monkeypatch):
+    """The library's tuner picks launch options and installs them as the
+    handle's default: bc_run with NULL options then runs with that choice
+    (bc_last_options), correctly; a second process-level call is served from
+    the JSON cache and installs the same choice on a fresh handle."""
     from paper_0809_1906_gb300 import autotune
     monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "tune.json"))
     g = G.er_hamiltonian(3000, 15000, 9)
-    choice = autotune.tune_graph(g, sample=256)
-    assert choice["batch"] in (64, 128, 256) and choice["chunk"] in (128, 256, 512)
+    ref = oracle.bc(g)
+    with nat.Graph.from_csr(g) as h:
+        choice = autotune.tune_graph(g, h, sample=512)
+        assert choice["batch"] in (64, 128, 256) and choice["chunk"] in (128, 256, 512) and not choice["cached"]
+        assert choice["beta"] in (0.0, pytest.approx(1 / 256), pytest.approx(1 / 16))  # 0: the default 1/64
+        h.run(default_options=True)
+        got, code, _ = h.result()
+        used = h.last_options()
+        assert (used.batch, used.chunk) == (choice["batch"], choice["chunk"])
+        assert_bc_close(got, ref["bc"], g.n, "tuned defaults")
+        hs = h.source_hashes(g.n)
+        assert np.array_equal(hs["hash_sigma"], ref["hash_sigma"])
+        h.set_default_options(None)  # back to the built-in defaults
+        h.run(default_options=True)
+        assert h.last_options().batch == 0
     assert (tmp_path / "tune.json").exists()
-    assert autotune.tune_graph(g)["batch"] == choice["batch"]  # served from the cache
-    check_graph(nat, g, batch=choice["batch"], chunk=choice["chunk"], rows=False)
+    with nat.Graph.from_csr(g) as h2:
+        again = autotune.tune_graph(g, h2)
+        assert again["cached"] and again["batch"] == choice["batch"]
+        h2.run(default_options=True)
+        assert h2.last_options().chunk == choice["chunk"]
 
 
 @pytest.mark.parametrize("batch", [32, 64])
@@ -305,3 +325,12 @@ def test_parity_row_buffers_on_a_large_graph(nat):
     tol = np.maximum(1e-5 * np.abs(ref["bc"]), 1e-6 * g.n)
     assert np.all(np.abs(got - ref["bc"]) <= tol)
     assert np.array_equal(hs["hash_sigma"], ref["hash_sigma"]) and np.array_equal(hs["hash_dist"], ref["hash_dist"])
+
+
+def test_sharded_run_single_rank_matches_oracle(nat):
+    """The multi-GPU entry (one shard per rank, then the rank-ordered sum) on
+    a world of one rank: the shard is every source."""
+    from paper_0809_1906_gb300.sharding import run_sharded_gpu
+    g = G.er_hamiltonian(1500, 6000, 71)
+    got = run_sharded_gpu(g, batch=128)
+    assert_bc_close(got, oracle.bc(g)["bc"], g.n, "sharded world 1")

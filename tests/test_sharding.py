@@ -31,6 +31,10 @@ def _worker(rank, world, port, q):
     mine = shard_sources(np.arange(g.n, dtype=np.int32), rank, world, 64)
     part = oracle.bc(g, mine, threads=1)["bc"]
     full = reduce_partials(part)
+    import torch
+    from paper_0809_1906_gb300.sharding import reduce_partials_device
+    again = reduce_partials_device(torch.from_numpy(part)).numpy()
+    assert np.array_equal(full, again)  # both sum the gathered vectors in rank order
     q.put((rank, full))
     dist.barrier()
     dist.destroy_process_group()
