@@ -555,7 +555,8 @@ def run_profile(args):
     elif wl == "gnp":
         g, desc, flags = G.gnp(8192, 0.05), "gnp8192 dense", native.BC_DENSE
     else:
-        gs = G.many_graphs(args.sources or 200)
+        # a capture-sized set: the per-CTA workspaces grow with the largest n
+        gs = G.many_graphs(args.sources or 200, 50, args.nmax)
         hs = [native.Graph.from_csr(x, trust_input=True) for x in gs]
         with native.ManyPlan(hs, batch=256) as plan:
             plan.run()
@@ -564,7 +565,12 @@ def run_profile(args):
         print(json.dumps({"profile_run": "many", "graphs": len(gs), "status": code}), flush=True)
         return
     k = min(args.sources or 256, g.n)
-    src = np.arange(k, dtype=np.int32) if wl != "grid" else G.sample_sources(g.n, k, 33)
+    if wl == "grid":
+        src = G.sample_sources(g.n, k, 33)
+    elif wl == "rmat" and k < g.n:
+        src = G.sample_sources(g.n, k, 34)  # a representative batch, not the hub-heavy first one
+    else:
+        src = np.arange(k, dtype=np.int32)
     with native.Graph.from_csr(g, trust_input=True) as hp:
         hp.run(src, batch=args.batch if wl == "rmat" else 0, flags=flags)
         out, code, _ = hp.result()
@@ -587,6 +593,7 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="profiling driver: one bc_run over the first --sources sources (default 256), nothing else")
     ap.add_argument("--sources", type=int, default=0)
+    ap.add_argument("--nmax", type=int, default=1000, help="--profile --workload many: largest graph")
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--workload", default="rmat", choices=["rmat"] + sorted(CONFIGS),
                     help="rmat (default, the reported line) or one of the other configurations alone")

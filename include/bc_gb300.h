@@ -35,6 +35,9 @@
  *     kept for the next graph created on the same device. Caller buffers stay
  *     owned by the caller.
  *   - A graph handle may be used by one thread at a time.
+ *   - With the environment variable BC_LOG=1, bc_result writes one JSON line
+ *     per completed run to stderr (sizes, options, launches, host wall time
+ *     from bc_run to bc_result, edges/s, status bits).
  */
 #ifndef BC_GB300_H
 #define BC_GB300_H

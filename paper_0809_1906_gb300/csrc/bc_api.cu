@@ -7,6 +7,7 @@
 #include <atomic>
 #include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -26,6 +27,15 @@
 namespace {
 
 thread_local std::string g_err;
+
+// BC_LOG=1 in the environment: bc_result writes one JSON line per run to stderr.
+bool log_enabled() {
+    static const bool on = [] {
+        const char *v = std::getenv("BC_LOG");
+        return v && *v && std::strcmp(v, "0") != 0;
+    }();
+    return on;
+}
 
 int fail(int code, const std::string &msg) {
     g_err = msg;
@@ -202,6 +212,7 @@ struct bc_graph {
     bool has_defaults = false;
     bc_options defaults{};
     bc_options last_opt{};  // what the last bc_run was given (after the NULL substitution)
+    std::chrono::steady_clock::time_point run_t0;  // host clock at the last bc_run's start (BC_LOG)
 
     // results
     DevBuf<double> bc;
@@ -1683,6 +1694,7 @@ int bc_run(bc_graph *g, const int32_t *sources, int32_t num_sources, const bc_op
     g_err.clear();
     if (!g) return fail(BC_ERR_ARG, "graph is NULL");
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    g->run_t0 = std::chrono::steady_clock::now();
     if (!opt && g->has_defaults) opt = &g->defaults;  // the tuned (or installed) choice
     g->last_opt = opt ? *opt : bc_options{};
     const uint32_t flags = opt ? opt->flags : 0u;
@@ -1776,6 +1788,19 @@ int bc_result(bc_graph *g, double *bc, uint32_t *status_flags) {
     CK(cudaMemcpyAsync(&status, &g->ctl->status, sizeof(uint32_t), cudaMemcpyDefault, g->last_stream));
     CK(cudaStreamSynchronize(g->last_stream));
     if (status_flags) *status_flags = status;
+    if (log_enabled()) {
+        // one JSON line per completed run on stderr (environment variable BC_LOG=1)
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - g->run_t0).count();
+        const bc_options &o = g->last_opt;
+        std::fprintf(stderr,
+                     "{\"bc_log\": \"run\", \"n\": %d, \"m\": %lld, \"weighted\": %d, \"directed\": %d, "
+                     "\"sources\": %d, \"batch\": %d, \"flags\": %u, \"chunk\": %d, \"alpha\": %g, \"beta\": %g, "
+                     "\"launches\": %lld, \"wall_ms\": %.3f, \"edges_per_s\": %.6g, \"status\": %u}\n",
+                     g->n, (long long)(g->directed ? g->narcs : g->narcs / 2), (int)g->weighted, (int)g->directed,
+                     g->last_nsrc, o.batch, o.flags, o.chunk, (double)o.alpha, (double)o.beta, (long long)g->launches,
+                     ms, ms > 0.0 ? (double)g->last_nsrc * (double)(g->directed ? g->narcs : g->narcs / 2) / (ms / 1e3) : 0.0,
+                     status);
+    }
     if (status & BC_STATUS_BOUNDS) return fail(BC_ERR_BOUNDS, "device bounds check fired");
     if (status & BC_STATUS_DENSE_TIMEOUT) return fail(BC_ERR_TIMEOUT, "tensor-core pipeline wait timed out");
     if (status & BC_STATUS_COPY_TIMEOUT) return fail(BC_ERR_TIMEOUT, "staged row copy wait timed out");

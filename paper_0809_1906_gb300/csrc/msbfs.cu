@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kBlock) k_first(const MsParams p) {
     host_word(&p.hctl->progress, p.seq, 1u);
 }
 
-template <int W>
+template <int W, bool HOOK>
 __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const int l) {
     constexpr int B = 32 * W;
     pdl::enter();
@@ -184,10 +184,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     const bool wide = *(volatile uint32_t *)(p.wide + l) != 0u;
     const bool ones = l == 1 && p.first;  // level 1 written by k_first: all counts 1, no masked rows
     bool produced = false, ovf = false, wide_next = false;
-    uint32_t arcs = 0;   // predecessor relations counted by this lane
-    uint32_t front = 0;  // vertices this warp put into frontier l+1 (counted by every lane alike)
+    uint32_t arcs = 0;  // predecessor relations counted by this lane
     body::WarpStage ws{s_stage + wib * stage::kFwdStageBytes, s_bar + wib, s_qz[wib], 0u, false,
-                       p.wait_ns ? p.wait_ns : stage::kWaitNs, p.test_hold};
+                       body::stage_wctl(p.wait_ns, p.test_hold)};
     if (lane == 0) stage::bar_init(ws.bar);
     __syncwarp();
 
@@ -241,12 +240,12 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
                 acc[j] = 0ull;
                 nf[j] = 0u;
             }
-            body::fwd_sum<W, true, true>(p.col_f, beg, end, ufl, Fl, Sl, p.sigma, wide, ones, U, s_u[wib], s_nz[wib], lane,
+            body::fwd_sum<W, true, true, HOOK>(p.col_f, beg, end, ufl, Fl, Sl, p.sigma, wide, ones, U, s_u[wib], s_nz[wib], lane,
                                          acc, nf, ovf, arcs, &ws);
             if (slot < 0) {
                 const bool joined = body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
                 produced |= joined;
-                front += joined ? 1u : 0u;
+                if (joined && lane == 0) atomicAdd(&s_front, 1u);
                 continue;
             }
             uint64_t *pp = p.part + (size_t)slot * B + lane;
@@ -283,7 +282,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
             }
             const bool joined = body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
             produced |= joined;
-            front += joined ? 1u : 0u;
+            if (joined && lane == 0) atomicAdd(&s_front, 1u);
             if (lane == 0) p.cnt[first] = 0u;
         }
     }
@@ -297,7 +296,6 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
         if (wwide) atomicOr(&s_flags, 4u);
         if (ws.fail) atomicOr(&s_flags, 8u);
         if (arcs) atomicAdd(&s_arcs, (unsigned long long)arcs);
-        if (front) atomicAdd(&s_front, front);
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
@@ -332,7 +330,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     host_word(&p.hctl->progress, p.seq, (uint32_t)(l + 1));
 }
 
-template <int W>
+template <int W, bool HOOK>
 __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const int l) {
     constexpr int B = 32 * W;
     pdl::enter();
@@ -353,7 +351,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
     float *Cl = p.cval + (size_t)(l & 1) * nB;
     const float *Cs = p.cval + (size_t)((l + 1) & 1) * nB;
     body::WarpStage ws{s_stage + wib * stage::kBwdStageBytes, s_bar + wib, s_qz[wib], 0u, false,
-                       p.wait_ns ? p.wait_ns : stage::kWaitNs, p.test_hold};
+                       body::stage_wctl(p.wait_ns, p.test_hold)};
     if (lane == 0) stage::bar_init(ws.bar);
     __syncwarp();
     // where the finalize reads sigma_s(v) for the pairs at level l: none at
@@ -429,7 +427,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
             float S[W];  // lane owns source 32j + lane
 #pragma unroll
             for (int j = 0; j < W; ++j) S[j] = 0.0f;
-            body::bwd_sum<W, true, true>(p.col, beg, end, ufs, Fs, Cs, f, s_u[wib], s_nz[wib], lane, S, &ws);
+            body::bwd_sum<W, true, true, HOOK>(p.col, beg, end, ufs, Fs, Cs, f, s_u[wib], s_nz[wib], lane, S, &ws);
             if (slot < 0) {
                 body::finalize_dep<W>(p.sigma, Sl, sig_ones, Cl, p.bc, v, f, S, lane);
                 continue;
@@ -604,19 +602,17 @@ void stage_attr(K kernel, size_t bytes, std::atomic<uint32_t> &done) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     done.fetch_or(bit, std::memory_order_acq_rel);
 }
-template <int W>
+template <int W, bool HOOK>
 void fwd_attr() {
     static std::atomic<uint32_t> done{0};
-    stage_attr(k_forward<W>, kFwdSmem, done);
+    stage_attr(k_forward<W, HOOK>, kFwdSmem, done);
 }
-template <int W>
+template <int W, bool HOOK>
 void bwd_attr() {
     static std::atomic<uint32_t> done{0};
-    stage_attr(k_backward<W>, kBwdSmem, done);
+    stage_attr(k_backward<W, HOOK>, kBwdSmem, done);
 }
 
-// Persistent grid: as many blocks as fit on the GPU at once (occupancy of
-// the kernel instance), never more than the items need.
 template <class K>
 int item_blocks(const MsParams &p, K kernel, size_t dyn_smem = 0) {
     int per_sm = 0;
@@ -627,6 +623,24 @@ int item_blocks(const MsParams &p, K kernel, size_t dyn_smem = 0) {
     return need < cap ? need : cap;
 }
 
+// The level kernels with the wait bound / test hook read (HOOK), for runs
+// that set either; the others carry neither in their staging loop.
+bool uses_hook(const MsParams &p) { return p.wait_ns != 0 || p.test_hold != 0; }
+
+template <int W, bool HOOK>
+void launch_forward_t(const MsParams &p, int level, cudaStream_t st) {
+    fwd_attr<W, HOOK>();
+    pdl::launch(k_forward<W, HOOK>, item_blocks(p, k_forward<W, HOOK>, kFwdSmem), kBlock, kFwdSmem, st, p, level);
+}
+template <int W, bool HOOK>
+void launch_backward_t(const MsParams &p, int level, cudaStream_t st) {
+    bwd_attr<W, HOOK>();
+    pdl::launch(k_backward<W, HOOK>, item_blocks(p, k_backward<W, HOOK>, kBwdSmem), kBlock, kBwdSmem, st, p,
+                level);
+}
+
+// Persistent grid: as many blocks as fit on the GPU at once (occupancy of
+// the kernel instance), never more than the items need.
 template <int W>
 void launch_init_t(const MsParams &p, cudaStream_t st) {
     const size_t work = (size_t)p.n * W;
@@ -663,16 +677,20 @@ void ms_launch_forward(int W, const MsParams &p0, int level, cudaStream_t st) {
     const size_t nB = (size_t)p.n * 32 * W;
     p.S_rd = p.S + (size_t)(level % p.s_levels) * nB;  // one buffer per level, or two by parity
     p.S_wr = p.S + (size_t)((level + 1) % p.s_levels) * nB;
-    BCGB_DISPATCH_W(W, (fwd_attr<kW>(),
-                        pdl::launch(k_forward<kW>, item_blocks(p, k_forward<kW>, kFwdSmem), kBlock, kFwdSmem, st, p,
-                                    level)));
+    if (uses_hook(p)) {
+        BCGB_DISPATCH_W(W, (launch_forward_t<kW, true>(p, level, st)));
+    } else {
+        BCGB_DISPATCH_W(W, (launch_forward_t<kW, false>(p, level, st)));
+    }
 }
 
 void ms_launch_backward(int W, const MsParams &p, int level, cudaStream_t st) {
     if (p.nitems == 0) return;
-    BCGB_DISPATCH_W(W, (bwd_attr<kW>(),
-                        pdl::launch(k_backward<kW>, item_blocks(p, k_backward<kW>, kBwdSmem), kBlock, kBwdSmem, st, p,
-                                    level)));
+    if (uses_hook(p)) {
+        BCGB_DISPATCH_W(W, (launch_backward_t<kW, true>(p, level, st)));
+    } else {
+        BCGB_DISPATCH_W(W, (launch_backward_t<kW, false>(p, level, st)));
+    }
 }
 
 void ms_launch_hash(int W, const MsParams &p, int nlevels, cudaStream_t st) {

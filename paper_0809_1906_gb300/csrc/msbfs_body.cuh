@@ -43,15 +43,28 @@ struct WarpStage {
     uint32_t *qz;
     uint32_t phase;
     bool fail;
-    uint64_t limit_ns;  // bound on each wait
-    uint32_t hold;      // extra bytes each round expects that no copy delivers (timeout test hook), else 0
+    // read only by the sweeps instantiated with HOOK (a run that sets a wait
+    // bound or the timeout test hook): bits 7..0, bytes each round expects
+    // beyond its copies, which no copy delivers (the test hook; 0 otherwise);
+    // bits 31..8, the bound on each wait in microseconds (0: stage::kWaitNs)
+    uint32_t wctl;
 };
+
+// wctl of a warp stage from a wait bound (ns, 0 = default) and held bytes.
+__host__ __device__ __forceinline__ uint32_t stage_wctl(uint64_t wait_ns, uint32_t hold) {
+    uint64_t us = wait_ns / 1000ull;
+    if (wait_ns && us == 0) us = 1;
+    if (us > 0xffffffull) us = 0xffffffull;
+    return (uint32_t)(us << 8) | (hold & 0xffu);
+}
+__device__ __forceinline__ uint32_t stage_hold(const WarpStage *ws) { return ws->wctl & 0xffu; }
+__device__ __forceinline__ uint32_t stage_limit_us(const WarpStage *ws) { return ws->wctl >> 8; }
 
 // A staged round's wait gave up: release the held bytes, then wait (bounded)
 // for the copies this warp already issued, so that no copy lands in the stage
 // after the warp stops using it; the warp stages nothing more.
-__device__ __forceinline__ void give_up(WarpStage *ws, uint32_t parity, int lane) {
-    if (lane == 0 && ws->hold) stage::complete_tx(ws->bar, ws->hold);
+__device__ __forceinline__ void give_up(WarpStage *ws, uint32_t parity, int lane, uint32_t hold) {
+    if (lane == 0 && hold) stage::complete_tx(ws->bar, hold);
     __syncwarp();
     stage::wait(ws->bar, parity);
     __syncwarp();
@@ -238,7 +251,7 @@ __device__ __forceinline__ unsigned probe_chunk(const int32_t *__restrict__ col,
 // whose counts are all 1 (ones) just counts predecessors. nf[j]
 // gets the sources reaching v; exact uint64 sums, ovf flags a carry out of
 // bit 63; arcs counts predecessor relations (lane-local).
-template <int W, bool NC = true, bool STAGED = false>
+template <int W, bool NC = true, bool STAGED = false, bool HOOK = false>
 __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg, int end,
                                         const uint32_t *__restrict__ ufl, const uint32_t *__restrict__ Fl,
                                         const uint16_t *__restrict__ Sl, const uint64_t *__restrict__ sigma,
@@ -289,14 +302,14 @@ __device__ __forceinline__ void fwd_sum(const int32_t *__restrict__ col, int beg
                 const uint32_t bytes = go ? 64u * (uint32_t)(hi - lo + 1) : 0u;
                 const uint32_t tot = __reduce_add_sync(kFull, bytes);
                 if (go) ws->qz[rank] = nz;
-                if (lane == 0) stage::expect_tx(ws->bar, tot + ws->hold);
+                if (lane == 0) stage::expect_tx(ws->bar, tot + (HOOK ? stage_hold(ws) : 0u));
                 __syncwarp();
                 if (go) stage::copy(ws->buf + rank * RB + 64 * lo, Sl + (size_t)u * B + 32 * lo, bytes, ws->bar);
                 const uint32_t ph = ws->phase;
-                const bool ok = stage::wait(ws->bar, ph, ws->limit_ns);
+                const bool ok = stage::wait(ws->bar, ph, HOOK ? stage_limit_us(ws) : 0u);
                 ws->phase ^= 1u;
                 if (!__all_sync(kFull, ok)) {
-                    give_up(ws, ph, lane);
+                    give_up(ws, ph, lane, HOOK ? stage_hold(ws) : 0u);
                     break;
                 }
 #pragma unroll 4
@@ -449,7 +462,7 @@ __device__ __forceinline__ void bwd_sum_sparse(const int32_t *__restrict__ col, 
     }
 }
 
-template <int W, bool NC = true, bool STAGED = false>
+template <int W, bool NC = true, bool STAGED = false, bool HOOK = false>
 __device__ __forceinline__ void bwd_sum(const int32_t *__restrict__ col, int beg, int end,
                                         const uint32_t *__restrict__ ufs, const uint32_t *__restrict__ Fs,
                                         const float *__restrict__ Cs, const uint32_t (&f)[W], int32_t *s_u,
@@ -504,14 +517,14 @@ __device__ __forceinline__ void bwd_sum(const int32_t *__restrict__ col, int beg
                 const uint32_t bytes = go ? 128u * (uint32_t)(hi - lo + 1) : 0u;
                 const uint32_t tot = __reduce_add_sync(kFull, bytes);
                 if (go) ws->qz[rank] = nz;
-                if (lane == 0) stage::expect_tx(ws->bar, tot + ws->hold);
+                if (lane == 0) stage::expect_tx(ws->bar, tot + (HOOK ? stage_hold(ws) : 0u));
                 __syncwarp();
                 if (go) stage::copy(ws->buf + rank * RB + 128 * lo, Cs + (size_t)u * B + 32 * lo, bytes, ws->bar);
                 const uint32_t ph = ws->phase;
-                const bool ok = stage::wait(ws->bar, ph, ws->limit_ns);
+                const bool ok = stage::wait(ws->bar, ph, HOOK ? stage_limit_us(ws) : 0u);
                 ws->phase ^= 1u;
                 if (!__all_sync(kFull, ok)) {
-                    give_up(ws, ph, lane);
+                    give_up(ws, ph, lane, HOOK ? stage_hold(ws) : 0u);
                     break;
                 }
 #pragma unroll 2
@@ -592,6 +605,20 @@ __device__ __forceinline__ bool store_next(uint64_t *sigma, uint16_t *Sn, uint32
     return any != 0;
 }
 
+// hi + lo += x with Knuth's two-sum: the rounding error of hi + x, which is
+// exact in FP32, goes into lo. For k terms, all >= 0, the sum's error stays
+// below about k^2 2^-48 of the sum (2^-32 for a 256-source batch; a plain FP32
+// sum's bound is k 2^-24), in FP32 arithmetic only: GB300's FP64 rate is a
+// small fraction of its FP32 rate, so the FP64 units take just the one add
+// into BC(v) per vertex and level.
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += err;
+}
+
 // sigma as FP32, correctly rounded; the 32-bit conversion when it fits.
 __device__ __forceinline__ float sigma_f32(uint64_t x) {
     return (x >> 32) ? __ull2float_rn(x) : __uint2float_rn((uint32_t)x);
@@ -601,10 +628,12 @@ __device__ __forceinline__ float sigma_f32(uint64_t x) {
 // for), written in full, or with ALL_WORDS = false only in the words that
 // hold a level-l source of v (every backward adder reads word j of v's row
 // only when v is at level l for a source of word j). For s with d(s,v) = l: delta_s(v) = sigma_s(v) * S
-// and c_s(v) = (1 + delta_s(v)) / sigma_s(v) = 1/sigma_s(v) + S. The batch's
-// delta values of v are all >= 0 and are added in FP32, 8 per lane in order
-// then a 5-step tree across the warp (relative error at most 12 * 2^-24), and
-// the vertex's total goes into bc[v] in FP64.
+// and c_s(v) = (1 + delta_s(v)) / sigma_s(v) = 1/sigma_s(v) + S (1/sigma_s(v)
+// by the fast reciprocal, within 2 ulp; the correctly rounded one measured
+// 1.2 ms slower per R-MAT step). The batch's FP32 delta values of v are summed as an
+// unevaluated pair of FP32 words (two_sum_add: W per lane in order, then a
+// 5-step tree across the warp, a fixed order) and the total goes into bc[v]
+// in FP64.
 // sigma_s(v) comes from the level's masked uint16 row Sl when given (a
 // narrow level: every count below 2^16), is 1 when `ones` (level 1, reached
 // from the sources directly), else from the uint64 array.
@@ -613,22 +642,27 @@ __device__ __forceinline__ void finalize_dep(const uint64_t *sigma, const uint16
                                              double *bc, int v, const uint32_t (&f)[W], const float (&S)[W],
                                              int lane) {
     constexpr int B = 32 * W;
-    float sum = 0.0f;
+    float hi = 0.0f, lo = 0.0f;  // the running sum hi + lo, carried without rounding loss
 #pragma unroll
     for (int j = 0; j < W; ++j) {
         const size_t idx = (size_t)v * B + 32 * j + lane;
         float c = 0.0f;
         if ((f[j] >> lane) & 1u) {
             const float sg = ones ? 1.0f : (Sl ? __uint2float_rn((uint32_t)Sl[idx]) : sigma_f32(sigma[idx]));
-            const float d = sg * S[j];           // delta_s(v) = sigma_s(v) * sum_w c_s(w)
-            c = __fdividef(1.0f, sg) + S[j];     // c_s(v) for the level above
-            sum += d;
+            const float d = sg * S[j];        // delta_s(v) = sigma_s(v) * sum_w c_s(w)
+            c = __fdividef(1.0f, sg) + S[j];  // c_s(v) for the level above (1/sigma within 2 ulp)
+            two_sum_add(hi, lo, d);
         }
         if (ALL_WORDS || f[j] != 0u) Cl[idx] = c;
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(kFull, sum, off);
-    if (lane == 0) bc[v] += (double)sum;
+    for (int off = 16; off > 0; off >>= 1) {
+        const float h2 = __shfl_xor_sync(kFull, hi, off);
+        const float l2 = __shfl_xor_sync(kFull, lo, off);
+        two_sum_add(hi, lo, h2);
+        lo += l2;
+    }
+    if (lane == 0) bc[v] += (double)hi + (double)lo;
 }
 
 template <int W, bool ALL_WORDS = true>

@@ -64,9 +64,11 @@ __device__ __forceinline__ bool try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0u;
 }
 
-// Bounded wait for the phase with the given parity; false once limit_ns passed.
-__device__ __forceinline__ bool wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns = kWaitNs) {
+// Bounded wait for the phase with the given parity; false once the bound
+// passed: limit_us microseconds, or kWaitNs when limit_us is 0.
+__device__ __forceinline__ bool wait(uint64_t *bar, uint32_t parity, uint32_t limit_us = 0) {
     if (try_wait(bar, parity)) return true;
+    const uint64_t limit_ns = limit_us ? (uint64_t)limit_us * 1000ull : kWaitNs;
     const uint64_t t0 = now_ns();
     while (!try_wait(bar, parity))
         if (now_ns() - t0 > limit_ns) return false;

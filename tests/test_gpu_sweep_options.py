@@ -109,3 +109,27 @@ def test_device_wait_expiry_reports_timeout_then_next_run_is_correct(nat):
         got, code, st = h.result()
         assert code == nat.BC_OK and st == 0
         assert _close(got, ref["bc"], g.n)
+
+
+def test_run_log_lines(nat, tmp_path):
+    """BC_LOG=1: every bc_result writes one JSON line with the run's sizes,
+    options and host wall time (a fresh process, since the library reads the
+    variable once)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_0809_1906_gb300 import graphs as G, native\n"
+            "g = G.er_hamiltonian(500, 2000, 95)\n"
+            "with native.Graph.from_csr(g) as h:\n"
+            "    h.run(batch=64); h.result(); h.run(batch=128, beta=0.25); h.result()\n") % root
+    r = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, BC_LOG="1"), capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr
+    lines = [json.loads(x) for x in r.stderr.splitlines() if x.startswith('{"bc_log"')]
+    assert len(lines) == 2
+    assert lines[0]["n"] == 500 and lines[0]["batch"] == 64 and lines[1]["batch"] == 128
+    assert abs(lines[1]["beta"] - 0.25) < 1e-6 and lines[1]["sources"] == 500 and lines[1]["status"] == 0
+    assert lines[0]["wall_ms"] > 0 and lines[0]["launches"] > 0
