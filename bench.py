@@ -126,29 +126,30 @@ def csrc_digest() -> str:
 
 # Kernel kinds of bc_kernel_time and the kernels each one times.
 KIND_KERNELS = {"init": ("k_init",), "forward": ("k_first", "k_forward"), "backward": ("k_backward",),
-                "hash": ("k_hash", "k_hash_sum")}
+                "hash": ("k_hash",)}
 TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic_rmat.json")
 
 
-def measured_traffic(kind: str, launches: int, path: str = TRAFFIC_JSON):
-    """DRAM bytes (read + write) per launch of kernel kind `kind`: the bytes of
-    one full pass from the committed ncu capture profiles/traffic_rmat.json,
-    divided by this run's launch count of that kind; None when the capture
-    was taken on other kernel sources."""
+def measured_traffic(kind: str, path: str = TRAFFIC_JSON):
+    """DRAM bytes (read + write) per launch of kernel kind `kind`, from the
+    committed ncu capture of one 256-source batch (profiles/traffic_rmat.json);
+    None when the capture was taken on other kernel sources."""
     try:
         with open(path) as f:
             tr = json.load(f)
         if tr.get("csrc_sha256") != csrc_digest():
             return None
-        return tr["kinds"][kind]["dram_bytes_per_pass"] / max(launches, 1)
+        return tr["kinds"][kind]["dram_bytes_per_launch"]
     except Exception:
         return None
 
 
 def write_traffic(csv_path: str, command: str, out_path: str = TRAFFIC_JSON, echo: bool = True):
-    """Turn an ncu capture of one full pass (metrics dram__bytes_read.sum,
-    dram__bytes_write.sum, gpu__time_duration.sum; --csv) into
-    profiles/traffic_rmat.json."""
+    """Turn an ncu capture (metrics dram__bytes_read.sum, dram__bytes_write.sum,
+    gpu__time_duration.sum; --csv) of one batch of the R-MAT workload into
+    profiles/traffic_rmat.json: per kernel kind, the DRAM bytes of that batch's
+    launches (the 256-wide kernels only; the landmark pass runs 32-wide) divided
+    by their number."""
     import collections
     import csv
     with open(csv_path) as f:
@@ -157,21 +158,23 @@ def write_traffic(csv_path: str, command: str, out_path: str = TRAFFIC_JSON, ech
     per = collections.defaultdict(dict)
     for r in rows[1:]:
         i = int(r[h.index("ID")])
-        per[i]["kernel"] = r[h.index("Kernel Name")].split("(")[0].split("::")[-1].split("<")[0]
-        per[i][r[h.index("Metric Name")]] = float(r[h.index("Metric Value")])
+        name = r[h.index("Kernel Name")].split("(")[0].split("::")[-1]
+        per[i]["kernel"] = name.split("<")[0]
+        per[i]["wide"] = name.startswith(per[i]["kernel"] + "<8")
+        per[i][r[h.index("Metric Name")]] = float(r[h.index("Metric Value")].replace(",", ""))
     kinds = {}
     for kind, names in KIND_KERNELS.items():
-        sel = [x for x in per.values() if x["kernel"] in names]
+        sel = [x for x in per.values() if x["kernel"] in names and x["wide"]]
         if not sel:
             continue
         rd = sum(x.get("dram__bytes_read.sum", 0.0) for x in sel)
         wr = sum(x.get("dram__bytes_write.sum", 0.0) for x in sel)
-        kinds[kind] = {"launches": len(sel), "dram_bytes_per_pass": rd + wr, "dram_read_bytes": rd,
+        kinds[kind] = {"launches": len(sel), "dram_bytes_per_launch": (rd + wr) / len(sel), "dram_read_bytes": rd,
                        "dram_write_bytes": wr,
                        "ncu_time_ms": sum(x.get("gpu__time_duration.sum", 0.0) for x in sel) / 1e6}
     out = {"csrc_sha256": csrc_digest(), "command": command,
-           "note": "one bc_run over every source of the R-MAT workload (batch 256); ncu replays each launch "
-                   "with cold caches, so bytes are an upper bound of a warm run",
+           "note": "one 256-source batch of the R-MAT workload (seeded sample, one lane); ncu replays each launch "
+                   "with cold caches, so bytes are an upper bound of a warm run; per launch of each kind",
            "kinds": kinds}
     with open(out_path, "w") as f:
         json.dump(out, f, indent=1)
@@ -690,7 +693,7 @@ def main():
     dom, dom_bytes, dom_ms, dom_cnt = ("backward", bwd_b, b_ms, ktime["backward"][0]) if b_ms >= f_ms else \
         ("forward", fwd_b, f_ms, ktime["forward"][0])
     achieved = dom_bytes / (dom_ms / 1000.0) / 1e9
-    traffic = measured_traffic(dom, dom_cnt)
+    traffic = measured_traffic(dom)
     other = "forward" if dom == "backward" else "backward"
     o_b, o_ms = (fwd_b, f_ms) if other == "forward" else (bwd_b, b_ms)
 

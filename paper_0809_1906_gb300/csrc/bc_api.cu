@@ -1036,11 +1036,15 @@ int32_t small_frontier_items(const bc_graph *g) { return std::max<int32_t>(32, (
 // batch's sources) is known on the host: top-down (k_first, a push over the
 // sources' arcs) while those arcs are fewer than the 2m arcs a bottom-up pull
 // reads divided by alpha, else bottom-up. BC_FORCE_BOTTOMUP always pulls.
-int first_level_top_down(const bc_graph *g, const int32_t *src_host, int32_t nb) {
-    if (g->bottom_up0) return 0;
-    if (!src_host || g->directed) return 1;  // (directed graphs: the pull runs over in-arcs)
+// *arcs receives the count (0 when not counted).
+int first_level_top_down(const bc_graph *g, const int32_t *src_host, int32_t nb, int64_t *arcs_out) {
+    *arcs_out = 0;
+    if (!src_host) return g->bottom_up0 ? 0 : 1;
     int64_t arcs = 0;
     for (int32_t b = 0; b < nb; ++b) arcs += g->h_row_ptr[src_host[b] + 1] - g->h_row_ptr[src_host[b]];
+    *arcs_out = arcs;
+    if (g->bottom_up0) return 0;
+    if (g->directed) return 1;  // (directed graphs: the pull runs over in-arcs)
     return (double)arcs * (double)g->alpha < (double)g->narcs ? 1 : 0;
 }
 
@@ -1096,7 +1100,7 @@ int run_lanes(bc_graph *g, int32_t nsrc, int W, int K, cudaStream_t st, bool bac
                 const int32_t b0 = j.bi * B;
                 j.p = lane_params(g, k);
                 j.p.nb = std::min<int32_t>(B, nsrc - b0);
-                j.p.first = first_level_top_down(g, g->h_sources.data() + b0, j.p.nb);
+                j.p.first = first_level_top_down(g, g->h_sources.data() + b0, j.p.nb, &j.p.first_arcs);
                 j.p.seq = ++g->seq;
                 j.p.sources = g->sources.p + b0;
                 if (hash) {
@@ -1235,7 +1239,7 @@ int run_batches(bc_graph *g, int32_t nsrc, int W, const bc_options *opt, cudaStr
         const int32_t nb = std::min<int32_t>(B, nsrc - b0);
         bcgb::MsParams p = make_params(g);
         p.nb = nb;
-        p.first = first_level_top_down(g, g->h_sources.data() + b0, nb);
+        p.first = first_level_top_down(g, g->h_sources.data() + b0, nb, &p.first_arcs);
         p.seq = ++g->seq;
         p.sources = g->sources.p + b0;
         if (hash) {

@@ -70,6 +70,7 @@ struct MsParams {
     int32_t Lcap;  // level slots in F / ufr
     int32_t nb;    // sources in this batch (<= B)
     int32_t first; // level 1 was produced by k_first (all its counts are 1)
+    int64_t first_arcs;  // arcs out of this batch's sources (0: not counted; sizes k_first's grid)
     uint32_t seq;
     const int32_t *row_ptr;  // out-arcs: level 0->1 and the backward sweep
     const int32_t *col;

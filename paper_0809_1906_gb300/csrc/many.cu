@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kMBlock, W >= 4 ? 3 : 4) k_many(const ManyPara
                 const uint32_t *Fl = F + (size_t)l * nW;
                 const uint32_t *Fs = F + (size_t)(l + 1) * nW;
                 const uint32_t *ufs = ufr + (size_t)(l + 1) * nw32;
-                float *Cl = cval + (size_t)(l & 1) * nB;
+                float *Cl = l > 1 ? cval + (size_t)(l & 1) * nB : nullptr;  // level-1 c values have no reader
                 const float *Cs = cval + (size_t)((l + 1) & 1) * nB;
                 for (int v0 = wib; v0 < n; v0 += 32 * kMWarps) {
                     const int vk = v0 + lane * kMWarps;

@@ -121,9 +121,13 @@ __global__ void __launch_bounds__(kBlock) k_first(const MsParams p) {
     uint32_t *F1 = p.F + nW;
     uint32_t *uf1 = p.ufr + p.nw32;
     const int total = s_off[p.nb];
-    int b = 0;
     for (int a = blockIdx.x * kBlock + t; a < total; a += gridDim.x * kBlock) {
-        while (s_off[b + 1] <= a) ++b;  // a only grows, so b only moves forward
+        int lo = 0, hi = p.nb - 1;  // the source b whose arcs hold position a: s_off[b] <= a < s_off[b + 1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= a) lo = mid; else hi = mid - 1;
+        }
+        const int b = lo;
         const int s = p.sources[b];
         const int v = p.col[p.row_ptr[s] + (a - s_off[b])];
         atomicOr(F1 + (size_t)v * W + (b >> 5), 1u << (b & 31));
@@ -348,7 +352,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
     const uint32_t *Fs = p.F + (size_t)(l + 1) * nW;
     const uint32_t *ufs = p.ufr + (size_t)(l + 1) * p.nw32;
     const size_t nB = (size_t)p.n * B;
-    float *Cl = p.cval + (size_t)(l & 1) * nB;
+    // level 1 is the last level the backward computes (the sources' own
+    // dependencies are not part of BC), so its c values have no reader
+    float *Cl = l > 1 ? p.cval + (size_t)(l & 1) * nB : nullptr;
     const float *Cs = p.cval + (size_t)((l + 1) & 1) * nB;
     body::WarpStage ws{s_stage + wib * stage::kBwdStageBytes, s_bar + wib, s_qz[wib], 0u, false,
                        body::stage_wctl(p.wait_ns, p.test_hold)};
@@ -668,7 +674,13 @@ void ms_launch_init(int W, const MsParams &p, cudaStream_t st) {
 
 void ms_launch_first(int W, const MsParams &p, cudaStream_t st) {
     if (p.nb == 0) return;
-    BCGB_DISPATCH_W(W, pdl::launch(k_first<kW>, 2 * sm_count(), kBlock, 0, st, p));
+    // one thread per arc out of the batch's sources when the host counted them
+    int g = 2 * sm_count();
+    if (p.first_arcs > 0) {
+        const int64_t need = (p.first_arcs + kBlock - 1) / kBlock;
+        g = need < g ? (int)need : g;
+    }
+    BCGB_DISPATCH_W(W, pdl::launch(k_first<kW>, g, kBlock, 0, st, p));
 }
 
 void ms_launch_forward(int W, const MsParams &p0, int level, cudaStream_t st) {

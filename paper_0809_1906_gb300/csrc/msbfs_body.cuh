@@ -625,7 +625,8 @@ __device__ __forceinline__ float sigma_f32(uint64_t x) {
 }
 
 // Cl: the masked level-l c buffer (zeros for the sources v is not at level l
-// for), written in full, or with ALL_WORDS = false only in the words that
+// for; null at level 1, whose c values no level reads), written in full, or
+// with ALL_WORDS = false only in the words that
 // hold a level-l source of v (every backward adder reads word j of v's row
 // only when v is at level l for a source of word j). For s with d(s,v) = l: delta_s(v) = sigma_s(v) * S
 // and c_s(v) = (1 + delta_s(v)) / sigma_s(v) = 1/sigma_s(v) + S (1/sigma_s(v)
@@ -653,7 +654,7 @@ __device__ __forceinline__ void finalize_dep(const uint64_t *sigma, const uint16
             c = __fdividef(1.0f, sg) + S[j];  // c_s(v) for the level above (1/sigma within 2 ulp)
             two_sum_add(hi, lo, d);
         }
-        if (ALL_WORDS || f[j] != 0u) Cl[idx] = c;
+        if (Cl && (ALL_WORDS || f[j] != 0u)) Cl[idx] = c;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {

@@ -28,28 +28,30 @@ def test_code_text_ignores_comments_and_space():
 def test_traffic_table_from_an_ncu_csv(tmp_path):
     hdr = '"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"\n'
     rows = [
-        ('0', 'void unnamed>::k_forward<8>(MsParams, int)', 'dram__bytes_read.sum', 'byte', '1000'),
-        ('0', 'void unnamed>::k_forward<8>(MsParams, int)', 'dram__bytes_write.sum', 'byte', '200'),
-        ('0', 'void unnamed>::k_forward<8>(MsParams, int)', 'gpu__time_duration.sum', 'ns', '5000'),
-        ('1', 'void unnamed>::k_first<8>(MsParams)', 'dram__bytes_read.sum', 'byte', '30'),
-        ('1', 'void unnamed>::k_first<8>(MsParams)', 'dram__bytes_write.sum', 'byte', '10'),
-        ('2', 'void unnamed>::k_backward<8>(MsParams, int)', 'dram__bytes_read.sum', 'byte', '700'),
-        ('2', 'void unnamed>::k_backward<8>(MsParams, int)', 'dram__bytes_write.sum', 'byte', '100'),
+        ('0', 'void unnamed>::k_forward<1, false>(MsParams, int)', 'dram__bytes_read.sum', 'byte', '5000'),
+        ('1', 'void unnamed>::k_forward<8, false>(MsParams, int)', 'dram__bytes_read.sum', 'byte', '1000'),
+        ('1', 'void unnamed>::k_forward<8, false>(MsParams, int)', 'dram__bytes_write.sum', 'byte', '200'),
+        ('1', 'void unnamed>::k_forward<8, false>(MsParams, int)', 'gpu__time_duration.sum', 'ns', '5000'),
+        ('2', 'void unnamed>::k_first<8>(MsParams)', 'dram__bytes_read.sum', 'byte', '30'),
+        ('2', 'void unnamed>::k_first<8>(MsParams)', 'dram__bytes_write.sum', 'byte', '10'),
+        ('3', 'void unnamed>::k_backward<8, false>(MsParams, int)', 'dram__bytes_read.sum', 'byte', '700'),
+        ('3', 'void unnamed>::k_backward<8, false>(MsParams, int)', 'dram__bytes_write.sum', 'byte', '100'),
+        ('4', 'void unnamed>::k_backward<8, false>(MsParams, int)', 'dram__bytes_read.sum', 'byte', '1,300'),
     ]
     csv_path = tmp_path / "t.csv"
     csv_path.write_text("==PROF== noise\n" + hdr + "".join(",".join(f'"{x}"' for x in r) + "\n" for r in rows))
     out_path = tmp_path / "traffic.json"
     out = bench.write_traffic(str(csv_path), "cmd", out_path=str(out_path), echo=False)
+    # the 32-wide landmark pass is left out; per launch of each kind
     assert out["kinds"]["forward"]["launches"] == 2
-    assert out["kinds"]["forward"]["dram_bytes_per_pass"] == 1240.0
-    assert out["kinds"]["backward"]["dram_bytes_per_pass"] == 800.0
+    assert out["kinds"]["forward"]["dram_bytes_per_launch"] == 620.0
+    assert out["kinds"]["backward"]["dram_bytes_per_launch"] == 1050.0
     assert abs(out["kinds"]["forward"]["ncu_time_ms"] - 0.005) < 1e-12
-    # per launch over this run's own launch count; stale digests give None
-    assert bench.measured_traffic("backward", 4, path=str(out_path)) == 200.0
+    assert bench.measured_traffic("backward", path=str(out_path)) == 1050.0
     doc = json.loads(out_path.read_text())
     doc["csrc_sha256"] = "0" * 64
     out_path.write_text(json.dumps(doc))
-    assert bench.measured_traffic("backward", 4, path=str(out_path)) is None
+    assert bench.measured_traffic("backward", path=str(out_path)) is None
 
 
 def test_committed_traffic_table_is_well_formed():
@@ -59,5 +61,5 @@ def test_committed_traffic_table_is_well_formed():
         doc = json.load(f)
     assert len(doc["csrc_sha256"]) == 64 and doc["command"]
     assert set(doc["kinds"]) >= {"forward", "backward", "hash"}
-    got = bench.measured_traffic("forward", 10)
+    got = bench.measured_traffic("forward")
     assert (got is None) == (doc["csrc_sha256"] != bench.csrc_digest())
