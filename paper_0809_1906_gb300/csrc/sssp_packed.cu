@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kPBlk, 4) k_wsssp_packed(const WParams p) {
             const float sg = __uint2float_rn(pl(xv));
             const float dl = sg * S;
             if (v != src) drow[v] = dl;
-            ds[v] = ((unsigned long long)dv << 32) | __float_as_uint(__frcp_rn(sg) + S);  // c_s(v)
+            ds[v] = ((unsigned long long)dv << 32) | __float_as_uint(__fdividef(1.0f, sg) + S);  // c_s(v)
         }
         __syncthreads();
     }
