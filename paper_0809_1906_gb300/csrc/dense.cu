@@ -45,11 +45,19 @@ constexpr int kDB = 128;          // sources per batch (GEMM M)
 constexpr int kDW = kDB / 32;     // frontier words per vertex
 constexpr int kNT = 64;           // target vertices per CTA (GEMM N) of the narrow tile
 constexpr int kNW = 128;          // of the wide tile
-constexpr int kKT = 64;           // K per pipeline stage (128 bytes of bf16)
-constexpr int kXTile = kDB * kKT * 2;  // 16 KiB: one limb's operand tile
-// adjacency tile of an N-vertex CTA: N rows of 128 bytes
-template <int kN>
-constexpr int a_tile() { return kN * kKT * 2; }
+// K per pipeline stage: 64 (rows of 128 bytes of bf16, 128-byte swizzle) or
+// 32 (rows of 64 bytes, 64-byte swizzle: half the bytes per stage, so twice
+// the stages fit the same shared memory)
+template <int kK>
+constexpr int x_tile() { return kDB * kK * 2; }  // one limb's (or part's) operand tile
+// TMEM accumulators of the backward's three parts: 2 keeps the hi products
+// apart from the mid and lo ones (their own FP32 sums lose nothing to hi's
+// magnitude); 1 sums all three in one, which rounds like the FP32 sum of the
+// c values themselves and needs half the TMEM columns (three CTAs per SM
+// instead of two: 714 against 659 TFLOP/s on the 8192-vertex G(n, p) case)
+constexpr int kBwdAcc = 1;
+template <int kN, int kK>
+constexpr int a_tile() { return kN * kK * 2; }  // adjacency tile of an N-vertex CTA
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -93,16 +101,20 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
-// Shared-memory matrix descriptor: K-major tile, rows of 128 bytes, 128-byte
-// swizzle (8-row atoms of 1024 bytes); start address, stride between atoms
-// (1024 B), descriptor version 1, layout SWIZZLE_128B.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major tile of rows of kK bf16 (128 or 64
+// bytes) with the matching swizzle (8-row atoms of 1024 or 512 bytes); start
+// address, stride between atoms (the atom's bytes), descriptor version 1,
+// layout SWIZZLE_128B (code 2) or SWIZZLE_64B (code 4).
+template <int kK>
+__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
+    static_assert(kK == 64 || kK == 32, "stage K is 64 or 32");
+    constexpr uint32_t atom = 8u * kK * 2u;
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)1u << 16;
-    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)(atom >> 4) << 32;
     d |= (uint64_t)1u << 46;
-    d |= (uint64_t)2u << 61;
+    d |= (uint64_t)(kK == 64 ? 2u : 4u) << 61;
     return d;
 }
 // Instruction descriptor, kind::f16: FP32 accumulator, bf16 A and B, both
@@ -143,13 +155,14 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 //               c for level l, adds the batch's delta to BC (FP64, fixed
 //               order) and, when write_next, writes the split c rows of level l
 //               at rows xout .. xout + 383.
-template <bool kBwd, int kN>
+template <bool kBwd, int kN, int kK>
 __global__ void __launch_bounds__(128, 1)
     k_dense_level(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmA, const DenseParams p,
                   const int l, const int nl, const int stages, const int write_next) {
     extern __shared__ unsigned char dsm_raw[];
     unsigned char *dsm = reinterpret_cast<unsigned char *>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
-    const int stage_bytes = nl * kXTile + a_tile<kN>();
+    constexpr int kXTile = x_tile<kK>();
+    const int stage_bytes = nl * kXTile + a_tile<kN, kK>();
     uint64_t *bars = reinterpret_cast<uint64_t *>(dsm + (size_t)stages * stage_bytes);
     uint64_t *full = bars;
     uint64_t *empty = bars + stages;
@@ -182,10 +195,9 @@ __global__ void __launch_bounds__(128, 1)
         xout = 3 * kDB - xin;
     }
     const int xrow0 = bb * p.xrows + xin;
-    const int nk = p.npad / kKT;
-    // the backward keeps two accumulators: the hi part's products in one, the
-    // mid and lo parts' (both small) in the other
-    const int nacc = kBwd ? 2 : nl;
+    const int nk = p.npad / kK;
+    // the backward keeps kBwdAcc accumulators for its three parts (see kBwdAcc)
+    const int nacc = kBwd ? kBwdAcc : nl;
     uint32_t ncols = 32;
     while (ncols < (uint32_t)(nacc * kN)) ncols <<= 1;
 
@@ -222,8 +234,8 @@ __global__ void __launch_bounds__(128, 1)
             unsigned char *st = dsm + (size_t)s * stage_bytes;
             mbar_expect_tx(full + s, (uint32_t)stage_bytes);
             for (int q = 0; q < nl; ++q)
-                tma_load_2d(st + (size_t)q * kXTile, &tmX, it * kKT, xrow0 + q * kDB, full + s);
-            tma_load_2d(st + (size_t)nl * kXTile, &tmA, it * kKT, v0, full + s);
+                tma_load_2d(st + (size_t)q * kXTile, &tmX, it * kK, xrow0 + q * kDB, full + s);
+            tma_load_2d(st + (size_t)nl * kXTile, &tmA, it * kK, v0, full + s);
             issued = it + 1;
         }
         // drain: every issued load must have landed before shared memory is released
@@ -244,10 +256,12 @@ __global__ void __launch_bounds__(128, 1)
             for (int q = 0; q < nl; ++q) {
                 const uint32_t xbase = smem_u32(st + (size_t)q * kXTile);
 #pragma unroll
-                for (int kk = 0; kk < kKT / 16; ++kk) {
-                    const int qa = kBwd && q > 1 ? 1 : q;  // accumulator of part q
-                    const bool first = it == 0 && kk == 0 && !(kBwd && q == 2);
-                    umma_bf16<kN>(tmem + (uint32_t)(qa * kN), sw128_desc(xbase + kk * 32), sw128_desc(abase + kk * 32),
+                for (int kk = 0; kk < kK / 16; ++kk) {
+                    // accumulator of part q: forward, one per limb; backward, hi
+                    // in the first and mid + lo in the second (or all three in one)
+                    const int qa = kBwd ? (kBwdAcc == 1 ? 0 : (q > 1 ? 1 : q)) : q;
+                    const bool first = it == 0 && kk == 0 && (!kBwd || q < kBwdAcc);
+                    umma_bf16<kN>(tmem + (uint32_t)(qa * kN), sw_desc<kK>(xbase + kk * 32), sw_desc<kK>(abase + kk * 32),
                                   first ? 0u : 1u);
                 }
             }
@@ -273,7 +287,7 @@ __global__ void __launch_bounds__(128, 1)
             float S[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) S[i] = 0.0f;
-            for (int q = 0; q < 2; ++q) {  // hi, then mid + lo
+            for (int q = 0; q < kBwdAcc; ++q) {  // all parts, or hi then mid + lo
                 uint32_t r[16];
                 tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * kN + c0), r);
                 tmem_wait_ld();
@@ -475,34 +489,35 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool make_map(CUtensorMap *m, void *base, uint64_t inner, uint64_t rows, uint32_t box_rows) {
+// Boxes of kK elements (the swizzle span: 128 or 64 bytes) by box_rows rows.
+bool make_map(CUtensorMap *m, void *base, uint64_t inner, uint64_t rows, uint32_t box_rows, int kK) {
     auto fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[2] = {inner, rows};
     const cuuint64_t strides[1] = {inner * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)kKT, box_rows};
+    const cuuint32_t box[2] = {(cuuint32_t)kK, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              kK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
 
-template <int kN>
+template <int kN, int kK>
 int dense_stages(int nl, bool bwd = false) {
     // accumulators of at most 256 TMEM columns: two CTAs per SM (half the
     // shared memory each), at most 128: three, so one CTA's epilogue overlaps
     // the others' MMAs
-    const int nacc = bwd ? 2 : nl;
+    const int nacc = bwd ? kBwdAcc : nl;
     const int budget = nacc * kN <= 128 ? 66 * 1024 : (nacc * kN <= 256 ? 100 * 1024 : 200 * 1024);
-    const int s = budget / (nl * kXTile + a_tile<kN>());
+    const int s = budget / (nl * x_tile<kK>() + a_tile<kN, kK>());
     return s < 1 ? 1 : (s > 8 ? 8 : s);
 }
 
-template <int kN>
+template <int kN, int kK>
 size_t dense_smem_bytes(int nl, int stages) {
-    return (size_t)stages * (nl * kXTile + a_tile<kN>()) + 1024 + (2 * stages + 2) * sizeof(uint64_t) + 64;
+    return (size_t)stages * (nl * x_tile<kK>() + a_tile<kN, kK>()) + 1024 + (2 * stages + 2) * sizeof(uint64_t) + 64;
 }
 
 int dense_build_adjacency(const int32_t *row_ptr, const int32_t *col, int32_t n, int32_t npad, __nv_bfloat16 *A,
@@ -513,31 +528,38 @@ int dense_build_adjacency(const int32_t *row_ptr, const int32_t *col, int32_t n,
 }
 
 int dense_make_maps(DenseMaps *maps, __nv_bfloat16 *X, uint64_t xrows_total, __nv_bfloat16 *A, int32_t npad) {
-    if (!make_map(&maps->x, X, (uint64_t)npad, xrows_total, kDB)) return -1;
-    if (!make_map(&maps->a, A, (uint64_t)npad, (uint64_t)npad, kNT)) return -1;
-    if (!make_map(&maps->a_wide, A, (uint64_t)npad, (uint64_t)npad, kNW)) return -1;
+    if (!make_map(&maps->x, X, (uint64_t)npad, xrows_total, kDB, 64)) return -1;
+    if (!make_map(&maps->a, A, (uint64_t)npad, (uint64_t)npad, kNT, 64)) return -1;
+    if (!make_map(&maps->a_wide, A, (uint64_t)npad, (uint64_t)npad, kNW, 64)) return -1;
+    if (!make_map(&maps->x32, X, (uint64_t)npad, xrows_total, kDB, 32)) return -1;
+    if (!make_map(&maps->a_wide32, A, (uint64_t)npad, (uint64_t)npad, kNW, 32)) return -1;
     return 0;
 }
 
+// Stage K of the forward and backward level kernels (the 128-vertex tile).
+constexpr int kFwdK = 64;
+constexpr int kBwdK = 32;
+
 // A CTA covers kNW = 128 vertices when the limb accumulators fit TMEM
 // (nl * 128 <= 512 columns), else kNT = 64.
-template <bool kBwd, int kN>
+template <bool kBwd, int kN, int kK>
 int launch_level_t(const DenseMaps &maps, const DenseParams &p, int l, int nl, int write_next, cudaStream_t st) {
-    const int stages = dense_stages<kN>(nl, kBwd);
-    const size_t smem = dense_smem_bytes<kN>(nl, stages);
-    if (cudaFuncSetAttribute(k_dense_level<kBwd, kN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    const int stages = dense_stages<kN, kK>(nl, kBwd);
+    const size_t smem = dense_smem_bytes<kN, kK>(nl, stages);
+    if (cudaFuncSetAttribute(k_dense_level<kBwd, kN, kK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return -1;
-    k_dense_level<kBwd, kN><<<p.nactive * (p.npad / kN), 128, smem, st>>>(maps.x, kN == kNW ? maps.a_wide : maps.a,
-                                                                          p, l, nl, stages, write_next);
+    const CUtensorMap &mx = kK == 64 ? maps.x : maps.x32;
+    const CUtensorMap &ma = kK == 64 ? (kN == kNW ? maps.a_wide : maps.a) : maps.a_wide32;
+    k_dense_level<kBwd, kN, kK><<<p.nactive * (p.npad / kN), 128, smem, st>>>(mx, ma, p, l, nl, stages, write_next);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int dense_launch_level(const DenseMaps &maps, const DenseParams &p, int l, int nl, cudaStream_t st) {
     if (p.nactive <= 0) return 0;
     k_dense_limbs<<<dim3((p.n + 31) / 32, p.nactive), 256, 0, st>>>(p, l, nl);
-    if (nl * kNW <= 512) return launch_level_t<false, kNW>(maps, p, l, nl, 0, st);
-    return launch_level_t<false, kNT>(maps, p, l, nl, 0, st);
+    if (nl * kNW <= 512) return launch_level_t<false, kNW, kFwdK>(maps, p, l, nl, 0, st);
+    return launch_level_t<false, kNT, 64>(maps, p, l, nl, 0, st);
 }
 
 int dense_launch_bwd_last(const DenseParams &p, int nbatch, cudaStream_t st) {
@@ -548,7 +570,7 @@ int dense_launch_bwd_last(const DenseParams &p, int nbatch, cudaStream_t st) {
 
 int dense_launch_bwd_level(const DenseMaps &maps, const DenseParams &p, int l, cudaStream_t st) {
     if (p.nactive <= 0) return 0;
-    return launch_level_t<true, kNW>(maps, p, l, 3, l > 1 ? 1 : 0, st);  // hi, mid, lo parts
+    return launch_level_t<true, kNW, kBwdK>(maps, p, l, 3, l > 1 ? 1 : 0, st);  // hi, mid, lo parts
 }
 
 int dense_reduce_bc(const double *bcpart, int nbatch, int n, double *bc, cudaStream_t st) {

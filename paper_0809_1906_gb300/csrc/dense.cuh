@@ -45,7 +45,8 @@ struct DenseParams {
 };
 
 struct DenseMaps {
-    CUtensorMap x, a, a_wide;  // adjacency boxes of 64 and 128 rows
+    CUtensorMap x, a, a_wide;  // K = 64 boxes (128-byte swizzle); adjacency boxes of 64 and 128 rows
+    CUtensorMap x32, a_wide32; // K = 32 boxes (64-byte swizzle)
 };
 
 constexpr int kDenseXRows = kDenseMaxLimbs * 128;  // X rows per batch (>= 2 x 3 x 128 for the backward)
