@@ -50,12 +50,15 @@ constexpr int kNW = 128;          // of the wide tile
 // the stages fit the same shared memory)
 template <int kK>
 constexpr int x_tile() { return kDB * kK * 2; }  // one limb's (or part's) operand tile
-// TMEM accumulators of the backward's three parts: 2 keeps the hi products
-// apart from the mid and lo ones (their own FP32 sums lose nothing to hi's
-// magnitude); 1 sums all three in one, which rounds like the FP32 sum of the
-// c values themselves and needs half the TMEM columns (three CTAs per SM
-// instead of two: 714 against 659 TFLOP/s on the 8192-vertex G(n, p) case)
-constexpr int kBwdAcc = 1;
+// TMEM accumulators of the backward's three parts. 2 keeps the hi products
+// apart from the mid and lo ones: sums of hi parts (8 significant bits each)
+// stay exact, and the mid + lo sum loses nothing to hi's magnitude. 1 sums all
+// three in one accumulator (half the TMEM columns, three CTAs per SM instead
+// of two, about 8% faster on G(8192, 0.05)), but the tensor core's FP32
+// accumulation then drops low bits of every lo and mid product against the
+// hi-sized total, a bias that pulls BC down (4.4e-6 relative over all sources
+// at n = 8192) and grows with n.
+constexpr int kBwdAcc = 2;
 template <int kN, int kK>
 constexpr int a_tile() { return kN * kK * 2; }  // adjacency tile of an N-vertex CTA
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
