@@ -61,6 +61,20 @@ __device__ __forceinline__ void host_word(unsigned long long *w, uint32_t hi, ui
     const unsigned long long x = ((unsigned long long)hi << 32) | lo;
     asm volatile("st.relaxed.sys.global.u64 [%0], %1;" ::"l"(w), "l"(x) : "memory");
 }
+
+// hi + lo += x with Knuth's two-sum: the rounding error of hi + x, which is
+// exact in FP32, goes into lo. For k terms, all >= 0, the sum's error stays
+// below about k^2 2^-48 of the sum (2^-32 for a 256-source batch; a plain FP32
+// sum's bound is k 2^-24), in FP32 arithmetic only: GB300's FP64 rate is a
+// small fraction of its FP32 rate, so the FP64 units take just the one add
+// into BC(v) per vertex and level.
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += err;
+}
 #endif
 
 struct MsParams {

@@ -17,11 +17,15 @@
 // Only the limbs that can be non-zero are multiplied: the previous level
 // reports its largest sigma, which fixes the limb count (up to 8).
 //
-// GEMM tile: one CTA owns 64 target vertices (columns of A) for all 128
-// sources and all limbs: accumulator q (128 lanes x 64 columns of FP32) sits
-// in TMEM columns [64q, 64q + 64). Operand tiles arrive by TMA (128-byte
-// swizzle, one copy per CTA) through an S-stage shared-memory ring guarded by
-// mbarriers; one thread issues tcgen05.mma; four warps read TMEM back.
+// GEMM tile: one CTA owns N target vertices (columns of A; N = 64, 128 or
+// 256) for all 128 sources and all limbs: accumulator q (128 lanes x N
+// columns of FP32) sits in TMEM columns [Nq, Nq + N). Operand tiles arrive by
+// TMA (128- or 64-byte swizzle, one copy per CTA) through an S-stage
+// shared-memory ring guarded by mbarriers; one thread issues tcgen05.mma; four
+// warps read TMEM back. The kernels are bound by the rate at which an SM takes
+// in operand bytes, so the tile is as wide as TMEM allows (more products per
+// byte), and the epilogue's loads that do not depend on the MMAs are issued
+// ahead of their use.
 // Every wait is bounded (global timer); on expiry the kernel records an error,
 // drains what it issued, frees its TMEM and returns.
 //
@@ -45,6 +49,7 @@ constexpr int kDB = 128;          // sources per batch (GEMM M)
 constexpr int kDW = kDB / 32;     // frontier words per vertex
 constexpr int kNT = 64;           // target vertices per CTA (GEMM N) of the narrow tile
 constexpr int kNW = 128;          // of the wide tile
+constexpr int kNX = 256;          // of the widest tile (one CTA per SM when its accumulators take all of TMEM)
 // K per pipeline stage: 64 (rows of 128 bytes of bf16, 128-byte swizzle) or
 // 32 (rows of 64 bytes, 64-byte swizzle: half the bytes per stage, so twice
 // the stages fit the same shared memory)
@@ -150,6 +155,29 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Epilogue inputs of 16 columns v0 .. v0 + 15 that do not depend on the MMAs:
+// the frontier word of each column for this thread's warp (forward: visited
+// or in frontier l; backward: in frontier l) and, backward, sigma_b(v). All
+// loads are issued before any is used; columns past n read nothing.
+template <bool kBwd>
+__device__ __forceinline__ void epi_prefetch(int n, const uint32_t *Fl, const uint32_t *Vin, const uint64_t *sigma,
+                                             int v0, int warp, int b, uint32_t (&fw)[16], uint64_t (&sv)[16]) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int v = v0 + i;
+        const bool in = v < n;
+        const size_t wi = (size_t)(in ? v : 0) * kDW + warp;
+        if constexpr (kBwd) {
+            fw[i] = in ? __ldg(Fl + wi) : 0u;
+            sv[i] = in ? __ldg(reinterpret_cast<const unsigned long long *>(sigma) + (size_t)(in ? v : 0) * kDB + b)
+                       : 0ull;
+        } else {
+            fw[i] = in ? (__ldg(Vin + wi) | __ldg(Fl + wi)) : 0u;
+            sv[i] = 0ull;
+        }
+    }
+}
 
 // kBwd = false: forward level l -> l+1 (limb sums -> exact counts).
 // kBwd = true:  backward level l: the three bf16 parts of the masked c rows of
@@ -274,19 +302,33 @@ __global__ void __launch_bounds__(128, 1)
     }
     __syncwarp();
 
-    // epilogue: every thread owns one source (TMEM lane = 32 * warp + lane)
+    // epilogue: every thread owns one source (TMEM lane = 32 * warp + lane);
+    // the first 16 columns' frontier words (and sigma values) are fetched
+    // while the MMAs run, and each chunk fetches the next one's before its own
+    // arithmetic
+    const int b = tid;
+    const size_t nW = (size_t)p.n * kDW;
+    const uint32_t *Fl = Fb + (size_t)l * nW;
+    const uint32_t *Vin = Vb + (size_t)(l & 1) * nW;
+    uint32_t fw[16];
+    uint64_t sv[16];
+    epi_prefetch<kBwd>(p.n, Fl, Vin, sigma, v0, warp, b, fw, sv);
+    // `good` is uniform across the block (the warp collectives below rely on it)
     const bool ok = mbar_wait(done, 0);
     tc_fence_after();
-    __syncthreads();
-    const bool good = ok && s_err == 0u;
+    const bool good = __syncthreads_and(ok) != 0 && s_err == 0u;
     if (!good && tid == 0) atomicOr(&p.ctl->status, BC_STATUS_DENSE_TIMEOUT);
     if constexpr (kBwd) {
-        __shared__ double s_red[4][16];
-        const int b = tid;
-        const size_t nW = (size_t)p.n * kDW;
-        const uint32_t *Fl = Fb + (size_t)l * nW;
+        // per column, the batch's delta values summed as unevaluated FP32 pairs
+        // (two-sum over the warp's 32 sources, a fixed tree), then the four
+        // warps' pairs in FP64, in warp order
+        __shared__ float2 s_red[4][kN];
         const bool valid_src = b < nbv;
+        const size_t xr = (size_t)bb * p.xrows + xout + b;  // this source's hi row; mid and lo follow at +128, +256
         for (int c0 = 0; good && c0 < kN; c0 += 16) {
+            uint32_t fwn[16];
+            uint64_t svn[16];
+            epi_prefetch<true>(p.n, Fl, Vin, sigma, v0 + c0 + 16, warp, b, fwn, svn);
             float S[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) S[i] = 0.0f;
@@ -297,52 +339,74 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
                 for (int i = 0; i < 16; ++i) S[i] += __uint_as_float(r[i]);
             }
+            uint32_t ph[8], pm[8], pl[8];  // the 16 split c values of this row, two bf16 per word
+#pragma unroll
+            for (int i = 0; i < 8; ++i) ph[i] = pm[i] = pl[i] = 0u;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const int v = v0 + c0 + i;
-                double dsum = 0.0;
-                if (v < p.n) {
-                    const bool at = valid_src && ((__ldg(Fl + (size_t)v * kDW + warp) >> lane) & 1u);
-                    float d = 0.0f, c = 0.0f;
-                    if (at) {
-                        const float sg = __ull2float_rn(sigma[(size_t)v * kDB + b]);
-                        d = sg * S[i];          // delta_s*(v) = sigma_s(v) * sum_w c_s(w)
-                        c = (1.0f + d) / sg;    // c_s(v) for the level above
-                    }
-                    dsum = (double)d;
-                    if (write_next) {
-                        const __nv_bfloat16 h = __float2bfloat16_rn(c);
-                        const float r1 = c - __bfloat162float(h);
-                        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-                        const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(m));
-                        const size_t xr = (size_t)bb * p.xrows + xout + b;
-                        p.X[xr * p.npad + v] = h;
-                        p.X[(xr + kDB) * p.npad + v] = m;
-                        p.X[(xr + 2 * kDB) * p.npad + v] = lo;
-                    }
+                float d = 0.0f, c = 0.0f;
+                if (v < p.n && valid_src && ((fw[i] >> lane) & 1u)) {
+                    const float sg = __ull2float_rn(sv[i]);
+                    d = sg * S[i];          // delta_s*(v) = sigma_s(v) * sum_w c_s(w)
+                    c = (1.0f + d) / sg;    // c_s(v) for the level above
                 }
+                float hi = d, lo = 0.0f;
 #pragma unroll
-                for (int off = 16; off > 0; off >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, off);
-                if (lane == 0) s_red[warp][i] = dsum;
+                for (int off = 16; off > 0; off >>= 1) {
+                    const float h2 = __shfl_xor_sync(0xffffffffu, hi, off);
+                    const float l2 = __shfl_xor_sync(0xffffffffu, lo, off);
+                    two_sum_add(hi, lo, h2);
+                    lo += l2;
+                }
+                if (lane == 0) s_red[warp][c0 + i] = make_float2(hi, lo);
+                const __nv_bfloat16 h = __float2bfloat16_rn(c);
+                const float r1 = c - __bfloat162float(h);
+                const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+                const __nv_bfloat16 lw = __float2bfloat16_rn(r1 - __bfloat162float(m));
+                const int sh = 16 * (i & 1);
+                ph[i >> 1] |= (uint32_t)__bfloat16_as_ushort(h) << sh;
+                pm[i >> 1] |= (uint32_t)__bfloat16_as_ushort(m) << sh;
+                pl[i >> 1] |= (uint32_t)__bfloat16_as_ushort(lw) << sh;
             }
-            __syncthreads();
-            if (tid < 16 && v0 + c0 + tid < p.n)
-                p.bcpart[(size_t)bb * p.n + v0 + c0 + tid] +=
-                    ((s_red[0][tid] + s_red[1][tid]) + s_red[2][tid]) + s_red[3][tid];
-            __syncthreads();
+            if (write_next) {
+                // 32 contiguous bytes per part (npad is a multiple of 128 and
+                // c0 of 16, so each store is 16-byte aligned); columns past n
+                // get zeros
+                uint4 *dh = reinterpret_cast<uint4 *>(p.X + xr * p.npad + v0 + c0);
+                uint4 *dm = reinterpret_cast<uint4 *>(p.X + (xr + kDB) * p.npad + v0 + c0);
+                uint4 *dl = reinterpret_cast<uint4 *>(p.X + (xr + 2 * kDB) * p.npad + v0 + c0);
+                dh[0] = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                dh[1] = make_uint4(ph[4], ph[5], ph[6], ph[7]);
+                dm[0] = make_uint4(pm[0], pm[1], pm[2], pm[3]);
+                dm[1] = make_uint4(pm[4], pm[5], pm[6], pm[7]);
+                dl[0] = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+                dl[1] = make_uint4(pl[4], pl[5], pl[6], pl[7]);
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                fw[i] = fwn[i];
+                sv[i] = svn[i];
+            }
+        }
+        __syncthreads();
+        for (int c = tid; good && c < kN && v0 + c < p.n; c += 128) {
+            double acc = 0.0;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc += (double)s_red[w][c].x + (double)s_red[w][c].y;
+            p.bcpart[(size_t)bb * p.n + v0 + c] += acc;
         }
     } else {
-        const int b = tid;  // source index in the batch
-        const size_t nW = (size_t)p.n * kDW;
-        const uint32_t *Fl = Fb + (size_t)l * nW;
         uint32_t *Fn = Fb + (size_t)(l + 1) * nW;
-        const uint32_t *Vin = Vb + (size_t)(l & 1) * nW;
         uint32_t *Vout = Vb + (size_t)((l + 1) & 1) * nW;
         uint32_t *ufn = ufb + (size_t)(l + 1) * p.nw32;
         const bool valid_src = b < nbv;
         bool ovf = false, produced = false;
         unsigned long long maxsig = 0, remaining = 0;
         for (int c0 = 0; good && c0 < kN; c0 += 16) {
+            uint32_t fwn[16];
+            uint64_t svn[16];
+            epi_prefetch<false>(p.n, Fl, Vin, sigma, v0 + c0 + 16, warp, b, fwn, svn);
             uint64_t lo[16];
             uint32_t hi[16];
     #pragma unroll
@@ -369,8 +433,8 @@ __global__ void __launch_bounds__(128, 1)
     #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const int v = v0 + c0 + i;
-                if (v >= p.n) break;  // padding columns (uniform across the block)
-                const uint32_t vis = __ldg(Vin + (size_t)v * kDW + warp) | __ldg(Fl + (size_t)v * kDW + warp);
+                if (v >= p.n) continue;  // padding columns (uniform across the block)
+                const uint32_t vis = fw[i];
                 const bool seen = (vis >> lane) & 1u;
                 const bool hit = valid_src && !seen && (lo[i] | hi[i]) != 0ull;
                 if (hit) {
@@ -387,6 +451,8 @@ __global__ void __launch_bounds__(128, 1)
                 }
                 produced |= word != 0u;
             }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) fw[i] = fwn[i];
         }
         if (good) {
             if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(&p.ctl->status, BC_STATUS_SIGMA_OVERFLOW);
@@ -437,27 +503,49 @@ __global__ void __launch_bounds__(256) k_dense_limbs(const DenseParams p, const 
 }
 
 // Split masked c rows of the deepest level L (c_s(v) = 1 / sigma_s(v) there:
-// nothing depends on the farthest vertices, Lemma 3.3): rows xout + q*128 + b
-// hold part q (hi, mid, lo) of c, 0 for the pairs not at level L.
+// nothing depends on the farthest vertices, Lemma 3.3): rows q*128 + b of the
+// batch's first block hold part q (hi, mid, lo) of c, 0 for the pairs not at
+// level L. Tiles of 64 vertices x 128 sources through shared memory: sigma is
+// read along the sources, the X rows are written along the vertices (two
+// columns per 4-byte store); columns past n get zeros.
 __global__ void __launch_bounds__(256) k_dense_bwd_last(const DenseParams p) {
-    const int v = blockIdx.x * 2 + (threadIdx.x >> 7);
-    const int b = threadIdx.x & 127;
+    __shared__ float tile[64][kDB + 1];
+    const int v0 = blockIdx.x * 64;
     const int bb = blockIdx.y;
     const int L = p.depth[bb];
-    if (v >= p.n || L < 1) return;
+    if (L < 1) return;
+    const int nbv = p.nbs[bb];
     const size_t nW = (size_t)p.n * kDW;
     const uint32_t *FL = p.F + (size_t)bb * p.f_stride + (size_t)L * nW;
-    float c = 0.0f;
-    if (b < p.nbs[bb] && ((FL[(size_t)v * kDW + (b >> 5)] >> (b & 31)) & 1u))
-        c = 1.0f / __ull2float_rn(p.sigma[(size_t)bb * p.sig_stride + (size_t)v * kDB + b]);
-    const __nv_bfloat16 h = __float2bfloat16_rn(c);
-    const float r1 = c - __bfloat162float(h);
-    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(m));
-    const size_t xr = (size_t)bb * p.xrows + b;  // block 0 holds level L
-    p.X[xr * p.npad + v] = h;
-    p.X[(xr + kDB) * p.npad + v] = m;
-    p.X[(xr + 2 * kDB) * p.npad + v] = lo;
+    const uint64_t *sigma = p.sigma + (size_t)bb * p.sig_stride;
+    for (int i = threadIdx.x; i < 64 * kDB; i += 256) {
+        const int vv = i / kDB, b = i % kDB;
+        const int v = v0 + vv;
+        float c = 0.0f;
+        if (v < p.n && b < nbv && ((__ldg(FL + (size_t)v * kDW + (b >> 5)) >> (b & 31)) & 1u))
+            c = 1.0f / __ull2float_rn(sigma[(size_t)v * kDB + b]);
+        tile[vv][b] = c;
+    }
+    __syncthreads();
+    __nv_bfloat16 *X = p.X + (size_t)bb * p.xrows * p.npad;  // block 0 holds level L
+    for (int i = threadIdx.x; i < kDB * 32; i += 256) {
+        const int b = i / 32, vv = 2 * (i % 32);
+        uint32_t w[3] = {0u, 0u, 0u};
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float c = tile[vv + k][b];
+            const __nv_bfloat16 h = __float2bfloat16_rn(c);
+            const float r1 = c - __bfloat162float(h);
+            const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(m));
+            w[0] |= (uint32_t)__bfloat16_as_ushort(h) << (16 * k);
+            w[1] |= (uint32_t)__bfloat16_as_ushort(m) << (16 * k);
+            w[2] |= (uint32_t)__bfloat16_as_ushort(lo) << (16 * k);
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            *reinterpret_cast<uint32_t *>(X + ((size_t)q * kDB + b) * p.npad + v0 + vv) = w[q];
+    }
 }
 
 // BC of a group: bc[v] += sum_b bcpart[b][v], batches in order.
@@ -536,12 +624,23 @@ int dense_make_maps(DenseMaps *maps, __nv_bfloat16 *X, uint64_t xrows_total, __n
     if (!make_map(&maps->a_wide, A, (uint64_t)npad, (uint64_t)npad, kNW, 64)) return -1;
     if (!make_map(&maps->x32, X, (uint64_t)npad, xrows_total, kDB, 32)) return -1;
     if (!make_map(&maps->a_wide32, A, (uint64_t)npad, (uint64_t)npad, kNW, 32)) return -1;
+    if (npad % kNX == 0) {
+        if (!make_map(&maps->a_x, A, (uint64_t)npad, (uint64_t)npad, kNX, 64)) return -1;
+        if (!make_map(&maps->a_x32, A, (uint64_t)npad, (uint64_t)npad, kNX, 32)) return -1;
+    }
     return 0;
 }
 
 // Stage K of the forward and backward level kernels (the 128-vertex tile).
 constexpr int kFwdK = 64;
 constexpr int kBwdK = 32;
+// Tile widths: the backward takes 256 vertices per CTA when npad allows (its
+// two accumulators fill TMEM: one CTA per SM, five K = 32 stages). The
+// one-limb forward measured the same at 256 as at 128, so it stays at 128
+// (kFwdX).
+constexpr bool kBwdX = true;
+constexpr bool kFwdX = false;
+constexpr int kFwdXK = 64;
 
 // A CTA covers kNW = 128 vertices when the limb accumulators fit TMEM
 // (nl * 128 <= 512 columns), else kNT = 64.
@@ -553,7 +652,8 @@ int launch_level_t(const DenseMaps &maps, const DenseParams &p, int l, int nl, i
         cudaSuccess)
         return -1;
     const CUtensorMap &mx = kK == 64 ? maps.x : maps.x32;
-    const CUtensorMap &ma = kK == 64 ? (kN == kNW ? maps.a_wide : maps.a) : maps.a_wide32;
+    const CUtensorMap &ma = kN == kNX ? (kK == 64 ? maps.a_x : maps.a_x32)
+                                      : (kK == 64 ? (kN == kNW ? maps.a_wide : maps.a) : maps.a_wide32);
     k_dense_level<kBwd, kN, kK><<<p.nactive * (p.npad / kN), 128, smem, st>>>(mx, ma, p, l, nl, stages, write_next);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -561,19 +661,22 @@ int launch_level_t(const DenseMaps &maps, const DenseParams &p, int l, int nl, i
 int dense_launch_level(const DenseMaps &maps, const DenseParams &p, int l, int nl, cudaStream_t st) {
     if (p.nactive <= 0) return 0;
     k_dense_limbs<<<dim3((p.n + 31) / 32, p.nactive), 256, 0, st>>>(p, l, nl);
+    if (kFwdX && nl == 1 && p.npad % kNX == 0) return launch_level_t<false, kNX, kFwdXK>(maps, p, l, nl, 0, st);
     if (nl * kNW <= 512) return launch_level_t<false, kNW, kFwdK>(maps, p, l, nl, 0, st);
     return launch_level_t<false, kNT, 64>(maps, p, l, nl, 0, st);
 }
 
 int dense_launch_bwd_last(const DenseParams &p, int nbatch, cudaStream_t st) {
     if (nbatch <= 0 || p.n <= 0) return 0;
-    k_dense_bwd_last<<<dim3((p.n + 1) / 2, nbatch), 256, 0, st>>>(p);
+    k_dense_bwd_last<<<dim3((p.n + 63) / 64, nbatch), 256, 0, st>>>(p);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int dense_launch_bwd_level(const DenseMaps &maps, const DenseParams &p, int l, cudaStream_t st) {
     if (p.nactive <= 0) return 0;
-    return launch_level_t<true, kNW, kBwdK>(maps, p, l, 3, l > 1 ? 1 : 0, st);  // hi, mid, lo parts
+    if (kBwdX && p.npad % kNX == 0)
+        return launch_level_t<true, kNX, kBwdK>(maps, p, l, 3, l > 1 ? 1 : 0, st);  // hi, mid, lo parts
+    return launch_level_t<true, kNW, kBwdK>(maps, p, l, 3, l > 1 ? 1 : 0, st);
 }
 
 int dense_reduce_bc(const double *bcpart, int nbatch, int n, double *bc, cudaStream_t st) {

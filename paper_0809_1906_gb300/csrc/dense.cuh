@@ -47,6 +47,7 @@ struct DenseParams {
 struct DenseMaps {
     CUtensorMap x, a, a_wide;  // K = 64 boxes (128-byte swizzle); adjacency boxes of 64 and 128 rows
     CUtensorMap x32, a_wide32; // K = 32 boxes (64-byte swizzle)
+    CUtensorMap a_x, a_x32;    // adjacency boxes of 256 rows, K = 64 and 32 (when npad is a multiple of 256)
 };
 
 constexpr int kDenseXRows = kDenseMaxLimbs * 128;  // X rows per batch (>= 2 x 3 x 128 for the backward)

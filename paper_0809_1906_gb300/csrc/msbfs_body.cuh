@@ -605,20 +605,6 @@ __device__ __forceinline__ bool store_next(uint64_t *sigma, uint16_t *Sn, uint32
     return any != 0;
 }
 
-// hi + lo += x with Knuth's two-sum: the rounding error of hi + x, which is
-// exact in FP32, goes into lo. For k terms, all >= 0, the sum's error stays
-// below about k^2 2^-48 of the sum (2^-32 for a 256-source batch; a plain FP32
-// sum's bound is k 2^-24), in FP32 arithmetic only: GB300's FP64 rate is a
-// small fraction of its FP32 rate, so the FP64 units take just the one add
-// into BC(v) per vertex and level.
-__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x) {
-    const float s = hi + x;
-    const float bp = s - hi;
-    const float err = (hi - (s - bp)) + (x - bp);
-    hi = s;
-    lo += err;
-}
-
 // sigma as FP32, correctly rounded; the 32-bit conversion when it fits.
 __device__ __forceinline__ float sigma_f32(uint64_t x) {
     return (x >> 32) ? __ull2float_rn(x) : __uint2float_rn((uint32_t)x);
