@@ -103,6 +103,7 @@ struct ItemPlan {
 };
 
 constexpr int kSweepLanes = 8;                    // concurrent batches of the unweighted sweep
+constexpr int kSideStreams = 4;                   // side streams of the dense path's per-batch summaries
 constexpr double kLaneBudgetBytes = 8.0 * (1 << 30);  // batch state of the extra lanes
 
 // An extra lane of the batched sweep: its own stream, batch state, control
@@ -231,6 +232,9 @@ struct bc_graph {
     uint32_t seq = 0;
     SweepLane lanes[kSweepLanes - 1];  // lanes 1.. of the concurrent sweep (lane 0 is the state above)
     cudaEvent_t ev0 = nullptr;        // lane 0's join / fork event
+    cudaStream_t side[kSideStreams] = {};     // independent per-batch launches of the dense path
+    cudaEvent_t side_ev[kSideStreams] = {};
+    cudaEvent_t side_fork = nullptr;
 
     // timing
     struct Ev {
@@ -311,6 +315,11 @@ void free_graph(bc_graph *g) {
         if (l.st) cudaStreamDestroy(l.st);
     }
     if (g->wev) cudaEventDestroy(g->wev);
+    for (int i = 0; i < kSideStreams; ++i) {
+        if (g->side_ev[i]) cudaEventDestroy(g->side_ev[i]);
+        if (g->side[i]) cudaStreamDestroy(g->side[i]);
+    }
+    if (g->side_fork) cudaEventDestroy(g->side_fork);
     g->wds.release();
     g->wredo.release();
     g->bc.release();
@@ -853,6 +862,28 @@ int ensure_dense_group(bc_graph *g, int nb, int Lcap, cudaStream_t st) {
 // Backward: from the deepest level of the group down, the split c rows times
 // A per level (or, with BC_SPARSE_BACKWARD, the sparse backward per batch);
 // BC partials of the group are added in batch order.
+// Side streams start after the work queued on st (fork) and st waits for
+// everything queued on them (join).
+int fork_side(bc_graph *g, cudaStream_t st) {
+    if (!g->side_fork) CK(cudaEventCreateWithFlags(&g->side_fork, cudaEventDisableTiming));
+    CK(cudaEventRecord(g->side_fork, st));
+    for (int i = 0; i < kSideStreams; ++i) {
+        if (!g->side[i]) {
+            CK(cudaStreamCreateWithFlags(&g->side[i], cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&g->side_ev[i], cudaEventDisableTiming));
+        }
+        CK(cudaStreamWaitEvent(g->side[i], g->side_fork, 0));
+    }
+    return BC_OK;
+}
+int join_side(bc_graph *g, cudaStream_t st) {
+    for (int i = 0; i < kSideStreams; ++i) {
+        CK(cudaEventRecord(g->side_ev[i], g->side[i]));
+        CK(cudaStreamWaitEvent(st, g->side_ev[i], 0));
+    }
+    return BC_OK;
+}
+
 constexpr size_t kDenseGroupBudget = 24ull << 30;
 constexpr int kDenseL2Group = 8;  // batches that share each adjacency tile in turn
 
@@ -898,14 +929,6 @@ int run_dense_group(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream
                 p.reach = g->reach.p + b0;
             }
             ps[b] = p;
-            {
-                Timer t(g, st, BC_KERNEL_INIT);
-                bcgb::ms_launch_init(W, p, st);
-            }
-            {
-                Timer t(g, st, BC_KERNEL_FORWARD);
-                bcgb::ms_launch_first(W, p, st);
-            }
         }
         int32_t *d_blist = g->gmeta.p, *d_nbs = g->gmeta.p + NB, *d_depth = g->gmeta.p + 2 * NB;
         CK(cudaMemcpyAsync(d_nbs, nbs.data(), NB * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -931,6 +954,12 @@ int run_dense_group(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream
         d.bcpart = g->gbcpart.p;
         d.ctl = g->ctl;
         d.dctl = g->dctl.p;
+        {
+            // levels 0 and 1 of the whole group in one launch
+            Timer t(g, st, BC_KERNEL_FORWARD);
+            if (bcgb::dense_launch_first(d, NB, g->sources.p + (size_t)gb0 * B, g->row_ptr.p, g->col.p, st))
+                return fail(BC_ERR_CUDA, std::string("dense first level: ") + cudaGetErrorString(cudaGetLastError()));
+        }
         // ---- forward, all batches in lockstep
         std::vector<int32_t> active(NB);
         std::iota(active.begin(), active.end(), 0);
@@ -1009,12 +1038,17 @@ int run_dense_group(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream
             }
             if (bcgb::dense_reduce_bc(g->gbcpart.p, NB, n, g->bc.p, st)) return fail(BC_ERR_CUDA, "BC reduction");
         }
+        if (hash) {
+            // the batches' summaries are independent: spread over side streams
+            Timer t(g, st, BC_KERNEL_HASH);
+            r = fork_side(g, st);
+            if (r) return r;
+            for (int b = 0; b < NB; ++b) bcgb::ms_launch_hash(W, ps[b], depth[b], g->side[b % kSideStreams]);
+            r = join_side(g, st);
+            if (r) return r;
+        }
         for (int b = 0; b < NB; ++b) {
             const int32_t b0 = (gb0 + b) * B;
-            if (hash) {
-                Timer t(g, st, BC_KERNEL_HASH);
-                bcgb::ms_launch_hash(W, ps[b], depth[b], st);
-            }
             if (rows_sig || rows_dist) {
                 Timer t(g, st, BC_KERNEL_HASH);
                 bcgb::ms_launch_rows(W, ps[b], depth[b], rows_sig ? rows_sig + (size_t)b0 * n : nullptr,

@@ -548,6 +548,42 @@ __global__ void __launch_bounds__(256) k_dense_bwd_last(const DenseParams p) {
     }
 }
 
+// Levels 0 and 1 of every batch of a group in one launch (blockIdx.y = batch):
+// d(s,s) = 0 and sigma_s(s) = 1, and each neighbour v of s has d(s,v) = 1 and
+// sigma_s(v) = 1, its one shortest path being the arc s-v (the CSR holds no
+// duplicate arcs and no self-loops; Section 1.1). The group's frontier words
+// of levels 0 and 1, its visited words and its union-frontier bits are zero
+// when the launch starts. One warp per source, its lanes over the arcs.
+__global__ void __launch_bounds__(256) k_dense_first(const DenseParams p, const int32_t *__restrict__ sources,
+                                                     const int32_t *__restrict__ row_ptr,
+                                                     const int32_t *__restrict__ col) {
+    const int bb = blockIdx.y;
+    const int nbv = p.nbs[bb];
+    const size_t nW = (size_t)p.n * kDW;
+    uint32_t *F = p.F + (size_t)bb * p.f_stride;
+    uint32_t *V = p.V + (size_t)bb * p.v_stride;
+    uint32_t *uf = p.ufr + (size_t)bb * p.u_stride;
+    uint64_t *sigma = p.sigma + (size_t)bb * p.sig_stride;
+    const int32_t *src = sources + (size_t)bb * kDB;
+    const int lane = threadIdx.x & 31;
+    for (int b = blockIdx.x * 8 + (threadIdx.x >> 5); b < nbv; b += gridDim.x * 8) {
+        const int s = src[b];
+        const uint32_t bit = 1u << (b & 31);
+        if (lane == 0) {
+            atomicOr(F + (size_t)s * kDW + (b >> 5), bit);           // frontier 0
+            atomicOr(V + nW + (size_t)s * kDW + (b >> 5), bit);      // visited through level 0
+            atomicOr(uf + (s >> 5), 1u << (s & 31));
+            sigma[(size_t)s * kDB + b] = 1ull;
+        }
+        for (int e = row_ptr[s] + lane; e < row_ptr[s + 1]; e += 32) {
+            const int v = col[e];
+            atomicOr(F + nW + (size_t)v * kDW + (b >> 5), bit);      // frontier 1
+            atomicOr(uf + p.nw32 + (v >> 5), 1u << (v & 31));
+            sigma[(size_t)v * kDB + b] = 1ull;
+        }
+    }
+}
+
 // BC of a group: bc[v] += sum_b bcpart[b][v], batches in order.
 __global__ void __launch_bounds__(256) k_dense_bc_reduce(const double *__restrict__ part, int nbatch, int n,
                                                          double *__restrict__ bc) {
@@ -664,6 +700,19 @@ int dense_launch_level(const DenseMaps &maps, const DenseParams &p, int l, int n
     if (kFwdX && nl == 1 && p.npad % kNX == 0) return launch_level_t<false, kNX, kFwdXK>(maps, p, l, nl, 0, st);
     if (nl * kNW <= 512) return launch_level_t<false, kNW, kFwdK>(maps, p, l, nl, 0, st);
     return launch_level_t<false, kNT, 64>(maps, p, l, nl, 0, st);
+}
+
+int dense_launch_first(const DenseParams &p, int nbatch, const int32_t *sources, const int32_t *row_ptr,
+                       const int32_t *col, cudaStream_t st) {
+    if (nbatch <= 0 || p.n <= 0) return 0;
+    // the group's level-0/1 frontier words, visited words and union bits start at zero
+    if (cudaMemset2DAsync(p.F, p.f_stride * sizeof(uint32_t), 0, (size_t)2 * p.n * kDW * sizeof(uint32_t), nbatch,
+                          st) != cudaSuccess)
+        return -1;
+    if (cudaMemsetAsync(p.V, 0, (size_t)nbatch * p.v_stride * sizeof(uint32_t), st) != cudaSuccess) return -1;
+    if (cudaMemsetAsync(p.ufr, 0, (size_t)nbatch * p.u_stride * sizeof(uint32_t), st) != cudaSuccess) return -1;
+    k_dense_first<<<dim3(kDB / 8, nbatch), 256, 0, st>>>(p, sources, row_ptr, col);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int dense_launch_bwd_last(const DenseParams &p, int nbatch, cudaStream_t st) {

@@ -58,6 +58,11 @@ int dense_build_adjacency(const int32_t *row_ptr, const int32_t *col, int32_t n,
 int dense_make_maps(DenseMaps *maps, __nv_bfloat16 *X, uint64_t xrows_total, __nv_bfloat16 *A, int32_t npad);
 // Forward level l -> l+1 for the p.nactive batches of p.blist (limbs, then the product).
 int dense_launch_level(const DenseMaps &maps, const DenseParams &p, int l, int nl, cudaStream_t st);
+// Levels 0 and 1 of batches 0 .. nbatch (sources: 128 per batch, in batch
+// order): zeroes the group's frontier, visited and union-frontier words, then
+// sets the sources and their neighbours.
+int dense_launch_first(const DenseParams &p, int nbatch, const int32_t *sources, const int32_t *row_ptr,
+                       const int32_t *col, cudaStream_t st);
 // Split c rows of each batch's deepest level (batches 0 .. nbatch).
 int dense_launch_bwd_last(const DenseParams &p, int nbatch, cudaStream_t st);
 // Backward level l for the p.nactive batches with depth > l (BC into p.bcpart).
