@@ -30,10 +30,12 @@
  *     before anything enqueued on it later: bc_run spreads the batches over
  *     internal streams (lanes) that fork from cuda_stream when it starts and
  *     join it before it returns.
- *   - The library allocates the device memory it needs (cudaMalloc) and frees
- *     it in bc_destroy_graph, except the lanes' streams and buffers, which are
- *     kept for the next graph created on the same device. Caller buffers stay
- *     owned by the caller.
+ *   - The library allocates the device memory it needs (cudaMalloc). When
+ *     bc_destroy_graph frees a handle (after the device has finished its
+ *     work), its device blocks, up to 24 GiB in all, and the lanes' streams and
+ *     buffers are kept for the next graphs created on the same device;
+ *     bc_release_cached_memory frees the cached blocks, and an allocation that
+ *     fails frees them and retries. Caller buffers stay owned by the caller.
  *   - A graph handle may be used by one thread at a time.
  *   - With the environment variable BC_LOG=1, bc_result writes one JSON line
  *     per completed run to stderr (sizes, options, launches, host wall time
@@ -369,8 +371,13 @@ int bc_many_stats(const bc_many *plan, int64_t *dag_arcs);
 void bc_many_destroy(bc_many *plan);
 int bc_run_many(bc_graph *const *graphs, int32_t k, const bc_options *opt, void *cuda_stream);
 
-/* Free the handle and its device memory. NULL is ignored. */
+/* Free the handle and its device memory (its device blocks go to the cache
+ * described at the top). Synchronises the device first. NULL is ignored. */
 void bc_destroy_graph(bc_graph *g);
+
+/* Free the device blocks cached from destroyed handles (every device). Call
+ * it with no library call in flight. */
+void bc_release_cached_memory(void);
 
 /* Static text for a status code. */
 const char *bc_status_string(int status);

@@ -50,21 +50,106 @@ int fail(int code, const std::string &msg) {
                         std::string(#call) + ": " + cudaGetErrorString(e_));                  \
     } while (0)
 
+// Device blocks of closed graph handles, kept for the next handles (per
+// device, best fit within twice the request): creating and closing handles
+// then pays neither cudaMalloc nor cudaFree's wait for the whole device. A
+// block enters the cache only from bc_destroy_graph, after the device has
+// finished all work; an allocation that fails empties the cache and retries.
+namespace devcache {
+std::mutex mu;
+struct Block {
+    int dev;
+    void *p;
+    size_t bytes;
+};
+std::vector<Block> blocks;
+size_t cached = 0;
+constexpr size_t kMaxBytes = 24ull << 30;
+thread_local bool t_recycle = false;  // set while bc_destroy_graph frees a handle
+
+void trim(int dev) {  // dev < 0: every device
+    std::lock_guard<std::mutex> lk(mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (size_t i = 0; i < blocks.size();) {
+        if (dev < 0 || blocks[i].dev == dev) {
+            cudaSetDevice(blocks[i].dev);
+            cudaFree(blocks[i].p);
+            cached -= blocks[i].bytes;
+            blocks.erase(blocks.begin() + (long)i);
+        } else {
+            ++i;
+        }
+    }
+    cudaSetDevice(cur);
+}
+cudaError_t alloc(void **p, size_t bytes, size_t *got) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        size_t best = SIZE_MAX;
+        for (size_t i = 0; i < blocks.size(); ++i)
+            if (blocks[i].dev == dev && blocks[i].bytes >= bytes && blocks[i].bytes / 2 <= bytes &&
+                (best == SIZE_MAX || blocks[i].bytes < blocks[best].bytes))
+                best = i;
+        if (best != SIZE_MAX) {
+            *p = blocks[best].p;
+            *got = blocks[best].bytes;
+            cached -= blocks[best].bytes;
+            blocks.erase(blocks.begin() + (long)best);
+            return cudaSuccess;
+        }
+    }
+    e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        trim(dev);
+        e = cudaMalloc(p, bytes);
+    }
+    if (e == cudaSuccess) *got = bytes;
+    return e;
+}
+void release(void *p, size_t bytes) {
+    if (!p) return;
+    if (t_recycle) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        std::lock_guard<std::mutex> lk(mu);
+        if (cached + bytes <= kMaxBytes) {
+            blocks.push_back({dev, p, bytes});
+            cached += bytes;
+            return;
+        }
+    }
+    cudaFree(p);
+}
+}  // namespace devcache
+
 template <class T>
 struct DevBuf {
     T *p = nullptr;
     size_t n = 0;
+    size_t bytes = 0;
     void release() {
-        if (p) cudaFree(p);
+        devcache::release(p, bytes);
         p = nullptr;
         n = 0;
+        bytes = 0;
     }
     cudaError_t ensure(size_t count) {
         if (count <= n && p) return cudaSuccess;
         release();
         size_t c = count ? count : 1;
-        cudaError_t e = cudaMalloc((void **)&p, c * sizeof(T));
-        if (e == cudaSuccess) n = c;
+        void *q = nullptr;
+        size_t got = 0;
+        cudaError_t e = devcache::alloc(&q, c * sizeof(T), &got);
+        if (e == cudaSuccess) {
+            p = static_cast<T *>(q);
+            n = got / sizeof(T);
+            bytes = got;
+        }
         return e;
     }
 };
@@ -2072,8 +2157,12 @@ int bc_graph_size(const bc_graph *g, int32_t *n, int64_t *m, int32_t *weighted) 
 void bc_destroy_graph(bc_graph *g) {
     if (!g) return;
     cudaDeviceSynchronize();
+    devcache::t_recycle = true;  // the device is idle: the handle's blocks may serve the next handles
     free_graph(g);
+    devcache::t_recycle = false;
 }
+
+void bc_release_cached_memory(void) { devcache::trim(-1); }
 
 const char *bc_status_string(int status) {
     switch (status) {

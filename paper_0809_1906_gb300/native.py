@@ -56,6 +56,7 @@ KERNEL_NAMES = {0: "init", 1: "forward", 2: "backward", 3: "hash", 4: "plain", 5
 # every entry point include/bc_gb300.h declares
 EXPORTS = ["bc_create_graph", "bc_run", "bc_result", "bc_source_hashes", "bc_forward_rows",
            "bc_kernel_time", "bc_kernel_trace", "bc_run_stats", "bc_launch_count", "bc_graph_size", "bc_destroy_graph",
+           "bc_release_cached_memory",
            "bc_status_string", "bc_last_error", "bc_run_noalloc", "bc_autotune", "bc_set_default_options",
            "bc_last_options",
            "bc_many_create", "bc_many_run", "bc_many_result", "bc_many_stats", "bc_many_destroy", "bc_run_many"]
@@ -107,6 +108,7 @@ def load(build_if_needed: bool = True, require_gpu: bool = True):
             "bc_launch_count": (i64, [P]),
             "bc_graph_size": (i32, [P, P, P, P]),
             "bc_destroy_graph": (None, [P]),
+            "bc_release_cached_memory": (None, []),
             "bc_status_string": (ctypes.c_char_p, [i32]),
             "bc_last_error": (ctypes.c_char_p, []),
             "bc_run_noalloc": (i32, [i32, P, P, P, i32, P, P]),
@@ -349,6 +351,11 @@ class ManyPlan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def release_cached_memory() -> None:
+    """Free the device blocks kept from destroyed graph handles."""
+    load().bc_release_cached_memory()
 
 
 def betweenness(g, sources=None, batch=0, flags=0, stream=None):
