@@ -334,3 +334,21 @@ def test_sharded_run_single_rank_matches_oracle(nat):
     g = G.er_hamiltonian(1500, 6000, 71)
     got = run_sharded_gpu(g, batch=128)
     assert_bc_close(got, oracle.bc(g)["bc"], g.n, "sharded world 1")
+
+
+def test_handles_reuse_cached_blocks(nat):
+    """Destroyed handles leave their device blocks for the next ones: graphs
+    of several sizes created and destroyed in turn (smaller after larger,
+    which reuses larger blocks, and larger after smaller), then again after
+    the cache is emptied, each against the oracle."""
+    gs = [G.random_small(300, 0.02, 5, connect=True), G.random_small(120, 0.05, 6, connect=True),
+          G.random_small(700, 0.006, 7, connect=True)]
+    refs = [oracle.bc(g)["bc"] for g in gs]
+    for rnd in range(2):
+        for g, ref in zip(gs + gs[::-1], refs + refs[::-1]):
+            with nat.Graph.from_csr(g) as h:
+                h.run()
+                got, code, _ = h.result()
+            assert code == nat.BC_OK
+            assert_bc_close(got, ref, g.n, f"{g.name} round {rnd}")
+        nat.release_cached_memory()
