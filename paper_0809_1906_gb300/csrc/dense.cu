@@ -397,6 +397,9 @@ __global__ void __launch_bounds__(128, 1)
             p.bcpart[(size_t)bb * p.n + v0 + c] += acc;
         }
     } else {
+        // the tile's new frontier and visited words, written after the last
+        // chunk as one 16-byte row per vertex (and one union word per 32)
+        __shared__ uint32_t s_Fw[kN][kDW], s_Vw[kN][kDW];
         uint32_t *Fn = Fb + (size_t)(l + 1) * nW;
         uint32_t *Vout = Vb + (size_t)((l + 1) & 1) * nW;
         uint32_t *ufn = ufb + (size_t)(l + 1) * p.nw32;
@@ -445,14 +448,27 @@ __global__ void __launch_bounds__(128, 1)
                 remaining += (valid_src && !seen && !hit) ? 1ull : 0ull;
                 const uint32_t word = __ballot_sync(0xffffffffu, hit);
                 if (lane == 0) {
-                    Fn[(size_t)v * kDW + warp] = word;
-                    Vout[(size_t)v * kDW + warp] = vis;
-                    if (word) atomicOr(ufn + (v >> 5), 1u << (v & 31));
+                    s_Fw[c0 + i][warp] = word;
+                    s_Vw[c0 + i][warp] = vis;
                 }
                 produced |= word != 0u;
             }
 #pragma unroll
             for (int i = 0; i < 16; ++i) fw[i] = fwn[i];
+        }
+        __syncthreads();
+        for (int c = tid; good && c < kN; c += 128) {  // kN is a multiple of 32: whole warps per pass
+            const int v = v0 + c;
+            bool joined = false;
+            if (v < p.n) {
+                const uint4 f4 = make_uint4(s_Fw[c][0], s_Fw[c][1], s_Fw[c][2], s_Fw[c][3]);
+                *reinterpret_cast<uint4 *>(Fn + (size_t)v * kDW) = f4;
+                *reinterpret_cast<uint4 *>(Vout + (size_t)v * kDW) =
+                    make_uint4(s_Vw[c][0], s_Vw[c][1], s_Vw[c][2], s_Vw[c][3]);
+                joined = (f4.x | f4.y | f4.z | f4.w) != 0u;
+            }
+            const uint32_t bits = __ballot_sync(0xffffffffu, joined);
+            if (lane == 0 && bits) atomicOr(ufn + (v >> 5), bits);
         }
         if (good) {
             if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(&p.ctl->status, BC_STATUS_SIGMA_OVERFLOW);
