@@ -186,8 +186,12 @@ __device__ __forceinline__ void epi_prefetch(int n, const uint32_t *Fl, const ui
 //               c for level l, adds the batch's delta to BC (FP64, fixed
 //               order) and, when write_next, writes the split c rows of level l
 //               at rows xout .. xout + 383.
-template <bool kBwd, int kN, int kK>
-__global__ void __launch_bounds__(128, 1)
+//
+// kT threads (128 or 256): warp w reads TMEM lanes 32 (w % 4) .. + 31 (the
+// sources of that quarter) and, with 256 threads, warps 0-3 take the first
+// half of the tile's columns in the epilogue and warps 4-7 the second half.
+template <bool kBwd, int kN, int kK, int kT>
+__global__ void __launch_bounds__(kT, 1)
     k_dense_level(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmA, const DenseParams p,
                   const int l, const int nl, const int stages, const int write_next) {
     extern __shared__ unsigned char dsm_raw[];
@@ -201,7 +205,11 @@ __global__ void __launch_bounds__(128, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 1);
     __shared__ uint32_t s_err;
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int warp = (tid >> 5) & 3;                  // TMEM lane quarter = source word
+    constexpr int kGroups = kT / 128;                 // column groups of the epilogue
+    constexpr int kCols = kN / kGroups;               // columns of each group
+    const int cbeg = (tid >> 7) * kCols;              // this thread's first column
     // CTA -> (batch, 64-vertex tile): groups of p.group batches walk the
     // vertex tiles together, so each adjacency tile is read by p.group
     // batches in turn while it is in L2, and each batch's limb rows stay hot
@@ -242,7 +250,7 @@ __global__ void __launch_bounds__(128, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 0) {
+    if (tid < 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(ncols)
                      : "memory");
@@ -306,13 +314,13 @@ __global__ void __launch_bounds__(128, 1)
     // the first 16 columns' frontier words (and sigma values) are fetched
     // while the MMAs run, and each chunk fetches the next one's before its own
     // arithmetic
-    const int b = tid;
+    const int b = tid & 127;
     const size_t nW = (size_t)p.n * kDW;
     const uint32_t *Fl = Fb + (size_t)l * nW;
     const uint32_t *Vin = Vb + (size_t)(l & 1) * nW;
     uint32_t fw[16];
     uint64_t sv[16];
-    epi_prefetch<kBwd>(p.n, Fl, Vin, sigma, v0, warp, b, fw, sv);
+    epi_prefetch<kBwd>(p.n, Fl, Vin, sigma, v0 + cbeg, warp, b, fw, sv);
     // `good` is uniform across the block (the warp collectives below rely on it)
     const bool ok = mbar_wait(done, 0);
     tc_fence_after();
@@ -325,7 +333,7 @@ __global__ void __launch_bounds__(128, 1)
         __shared__ float2 s_red[4][kN];
         const bool valid_src = b < nbv;
         const size_t xr = (size_t)bb * p.xrows + xout + b;  // this source's hi row; mid and lo follow at +128, +256
-        for (int c0 = 0; good && c0 < kN; c0 += 16) {
+        for (int c0 = cbeg; good && c0 < cbeg + kCols; c0 += 16) {
             uint32_t fwn[16];
             uint64_t svn[16];
             epi_prefetch<true>(p.n, Fl, Vin, sigma, v0 + c0 + 16, warp, b, fwn, svn);
@@ -390,7 +398,7 @@ __global__ void __launch_bounds__(128, 1)
             }
         }
         __syncthreads();
-        for (int c = tid; good && c < kN && v0 + c < p.n; c += 128) {
+        for (int c = tid; good && c < kN && v0 + c < p.n; c += kT) {
             double acc = 0.0;
 #pragma unroll
             for (int w = 0; w < 4; ++w) acc += (double)s_red[w][c].x + (double)s_red[w][c].y;
@@ -406,7 +414,7 @@ __global__ void __launch_bounds__(128, 1)
         const bool valid_src = b < nbv;
         bool ovf = false, produced = false;
         unsigned long long maxsig = 0, remaining = 0;
-        for (int c0 = 0; good && c0 < kN; c0 += 16) {
+        for (int c0 = cbeg; good && c0 < cbeg + kCols; c0 += 16) {
             uint32_t fwn[16];
             uint64_t svn[16];
             epi_prefetch<false>(p.n, Fl, Vin, sigma, v0 + c0 + 16, warp, b, fwn, svn);
@@ -457,7 +465,7 @@ __global__ void __launch_bounds__(128, 1)
             for (int i = 0; i < 16; ++i) fw[i] = fwn[i];
         }
         __syncthreads();
-        for (int c = tid; good && c < kN; c += 128) {  // kN is a multiple of 32: whole warps per pass
+        for (int c = tid; good && c < kN; c += kT) {  // kN is a multiple of 32: whole warps per pass
             const int v = v0 + c;
             bool joined = false;
             if (v < p.n) {
@@ -487,7 +495,7 @@ __global__ void __launch_bounds__(128, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
 // Limb matrix of level l: X[q*128 + b][u] = byte q of sigma_b(u) where
@@ -691,6 +699,7 @@ constexpr int kBwdK = 32;
 // one-limb forward measured the same at 256 as at 128, so it stays at 128
 // (kFwdX).
 constexpr bool kBwdX = true;
+constexpr int kBwdXThreads = 256;
 constexpr bool kFwdX = false;
 constexpr int kFwdXK = 64;
 
@@ -700,13 +709,15 @@ template <bool kBwd, int kN, int kK>
 int launch_level_t(const DenseMaps &maps, const DenseParams &p, int l, int nl, int write_next, cudaStream_t st) {
     const int stages = dense_stages<kN, kK>(nl, kBwd);
     const size_t smem = dense_smem_bytes<kN, kK>(nl, stages);
-    if (cudaFuncSetAttribute(k_dense_level<kBwd, kN, kK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    // the widest backward tile runs one CTA per SM: its epilogue gets 8 warps
+    constexpr int kT = (kBwd && kN == kNX) ? kBwdXThreads : 128;
+    if (cudaFuncSetAttribute(k_dense_level<kBwd, kN, kK, kT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return -1;
     const CUtensorMap &mx = kK == 64 ? maps.x : maps.x32;
     const CUtensorMap &ma = kN == kNX ? (kK == 64 ? maps.a_x : maps.a_x32)
                                       : (kK == 64 ? (kN == kNW ? maps.a_wide : maps.a) : maps.a_wide32);
-    k_dense_level<kBwd, kN, kK><<<p.nactive * (p.npad / kN), 128, smem, st>>>(mx, ma, p, l, nl, stages, write_next);
+    k_dense_level<kBwd, kN, kK, kT><<<p.nactive * (p.npad / kN), kT, smem, st>>>(mx, ma, p, l, nl, stages, write_next);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
