@@ -338,6 +338,7 @@ struct bc_graph {
     // maps, and the state of a group of batches run in lockstep
     int32_t npad = 0;
     DevBuf<__nv_bfloat16> dA, dX;
+    DevBuf<uint8_t> dA8;  // the adjacency in e4m3 (forward levels with 4-bit limbs)
     DevBuf<bcgb::DenseCtl> dctl;
     bcgb::DenseMaps maps{};
     double dense_flops = 0.0;
@@ -422,6 +423,7 @@ void free_graph(bc_graph *g) {
     }
     bcgb::plain_free(g->plain);
     g->dA.release();
+    g->dA8.release();
     g->dX.release();
     g->dctl.release();
     for (auto *b : {&g->wdist, &g->worder, &g->wgrp, &g->wslots}) b->release();
@@ -914,6 +916,9 @@ int ensure_dense(bc_graph *g, cudaStream_t st) {
     CK(g->dA.ensure((size_t)npad * npad));
     if (bcgb::dense_build_adjacency(g->row_ptr.p, g->col.p, g->n, npad, g->dA.p, st))
         return fail(BC_ERR_CUDA, "dense adjacency build failed");
+    CK(g->dA8.ensure((size_t)npad * npad));
+    if (bcgb::dense_build_adjacency8(g->row_ptr.p, g->col.p, g->n, npad, g->dA8.p, st))
+        return fail(BC_ERR_CUDA, "dense adjacency build failed");
     g->npad = npad;
     return BC_OK;
 }
@@ -932,7 +937,7 @@ int ensure_dense_group(bc_graph *g, int nb, int Lcap, cudaStream_t st) {
     CK(g->dctl.ensure((size_t)nb));
     CK(g->dX.ensure((size_t)nb * bcgb::kDenseXRows * g->npad));
     CK(cudaMemsetAsync(g->dX.p, 0, g->dX.n * sizeof(__nv_bfloat16), st));
-    if (bcgb::dense_make_maps(&g->maps, g->dX.p, (uint64_t)nb * bcgb::kDenseXRows, g->dA.p, g->npad))
+    if (bcgb::dense_make_maps(&g->maps, g->dX.p, (uint64_t)nb * bcgb::kDenseXRows, g->dA.p, g->dA8.p, g->npad))
         return fail(BC_ERR_CUDA, "cuTensorMapEncodeTiled failed for the dense operands");
     g->gNB = nb;
     g->gLcap = Lcap;
@@ -1049,7 +1054,7 @@ int run_dense_group(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream
         std::vector<int32_t> active(NB);
         std::iota(active.begin(), active.end(), 0);
         std::vector<bcgb::DenseCtl> res(NB);
-        int nl = 1;  // level-1 counts are all 1
+        int nl = 1, nq = 1;  // level-1 counts are all 1 (one 8-bit or one 4-bit limb)
         bool capped = false;
         for (int l = 1; !active.empty(); ++l) {
             if (l + 2 >= Lcap) {
@@ -1062,7 +1067,7 @@ int run_dense_group(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream
             g->dense_flops += 2.0 * B * nl * (double)g->npad * (double)g->npad * (double)active.size();
             {
                 Timer t(g, st, BC_KERNEL_DENSE);
-                if (bcgb::dense_launch_level(g->maps, d, l, nl, st))
+                if (bcgb::dense_launch_level(g->maps, d, l, nl, nq, st))
                     return fail(BC_ERR_CUDA, std::string("dense level launch: ") + cudaGetErrorString(cudaGetLastError()));
             }
             uint32_t status = 0;
@@ -1085,7 +1090,12 @@ int run_dense_group(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream
             active.swap(still);
             nl = 1;
             while (nl < bcgb::kDenseMaxLimbs && (maxsig >> (8 * nl)) != 0ull) ++nl;
-            if (status & BC_STATUS_SIGMA_OVERFLOW) nl = bcgb::kDenseMaxLimbs;
+            nq = 1;
+            while (nq < 2 * bcgb::kDenseMaxLimbs && (maxsig >> (4 * nq)) != 0ull) ++nq;
+            if (status & BC_STATUS_SIGMA_OVERFLOW) {
+                nl = bcgb::kDenseMaxLimbs;
+                nq = 2 * bcgb::kDenseMaxLimbs;
+            }
         }
         if (capped) {  // deeper than the level capacity: grow it and redo this group
             CK(cudaStreamSynchronize(st));

@@ -33,6 +33,7 @@
 // [n][128], frontier and visited words, union-frontier bits), so the sparse
 // backward sweep and summaries run unchanged afterwards.
 #include <cuda.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
@@ -53,8 +54,11 @@ constexpr int kNX = 256;          // of the widest tile (one CTA per SM when its
 // K per pipeline stage: 64 (rows of 128 bytes of bf16, 128-byte swizzle) or
 // 32 (rows of 64 bytes, 64-byte swizzle: half the bytes per stage, so twice
 // the stages fit the same shared memory)
-template <int kK>
-constexpr int x_tile() { return kDB * kK * 2; }  // one limb's (or part's) operand tile
+// kF8: operands in e4m3 (one byte per element, 4-bit limbs) instead of bf16.
+template <int kK, bool kF8 = false>
+constexpr int row_bytes() { return kF8 ? kK : 2 * kK; }
+template <int kK, bool kF8 = false>
+constexpr int x_tile() { return kDB * row_bytes<kK, kF8>(); }  // one limb's (or part's) operand tile
 // TMEM accumulators of the backward's three parts. 2 keeps the hi products
 // apart from the mid and lo ones: sums of hi parts (8 significant bits each)
 // stay exact, and the mid + lo sum loses nothing to hi's magnitude. 1 sums all
@@ -64,8 +68,8 @@ constexpr int x_tile() { return kDB * kK * 2; }  // one limb's (or part's) opera
 // hi-sized total, a bias that pulls BC down (4.4e-6 relative over all sources
 // at n = 8192) and grows with n.
 constexpr int kBwdAcc = 2;
-template <int kN, int kK>
-constexpr int a_tile() { return kN * kK * 2; }  // adjacency tile of an N-vertex CTA
+template <int kN, int kK, bool kF8 = false>
+constexpr int a_tile() { return kN * row_bytes<kK, kF8>(); }  // adjacency tile of an N-vertex CTA
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -109,37 +113,49 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
-// Shared-memory matrix descriptor: K-major tile of rows of kK bf16 (128 or 64
-// bytes) with the matching swizzle (8-row atoms of 1024 or 512 bytes); start
+// Shared-memory matrix descriptor: K-major tile of rows of kRB bytes (128 or
+// 64) with the matching swizzle (8-row atoms of 1024 or 512 bytes); start
 // address, stride between atoms (the atom's bytes), descriptor version 1,
 // layout SWIZZLE_128B (code 2) or SWIZZLE_64B (code 4).
-template <int kK>
+template <int kRB>
 __device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
-    static_assert(kK == 64 || kK == 32, "stage K is 64 or 32");
-    constexpr uint32_t atom = 8u * kK * 2u;
+    static_assert(kRB == 128 || kRB == 64, "stage rows are 128 or 64 bytes");
+    constexpr uint32_t atom = 8u * kRB;
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)1u << 16;
     d |= (uint64_t)(atom >> 4) << 32;
     d |= (uint64_t)1u << 46;
-    d |= (uint64_t)(kK == 64 ? 2u : 4u) << 61;
+    d |= (uint64_t)(kRB == 128 ? 2u : 4u) << 61;
     return d;
 }
-// Instruction descriptor, kind::f16: FP32 accumulator, bf16 A and B, both
-// K-major, M = 128, N = kN.
-template <int kN>
+// Instruction descriptor: FP32 accumulator (bits 4-5 = 1), A and B both
+// K-major, M = 128, N = kN; A and B bf16 (format 1 in bits 7-9 and 10-12, for
+// kind::f16) or both e4m3 (format 0, for kind::f8f6f4).
+template <int kN, bool kF8 = false>
 constexpr uint32_t idesc() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(kDB >> 4) << 24);
+    return (1u << 4) | ((kF8 ? 0u : 1u) << 7) | ((kF8 ? 0u : 1u) << 10) | ((uint32_t)(kN >> 3) << 17) |
+           ((uint32_t)(kDB >> 4) << 24);
 }
 
-template <int kN>
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc<kN>()), "r"(acc)
-        : "memory");
+// One MMA over 32 bytes of K (16 bf16 or 32 e4m3 elements).
+template <int kN, bool kF8 = false>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+    if constexpr (kF8) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc<kN, true>()), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc<kN, false>()), "r"(acc)
+            : "memory");
+    }
 }
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -190,14 +206,15 @@ __device__ __forceinline__ void epi_prefetch(int n, const uint32_t *Fl, const ui
 // kT threads (128 or 256): warp w reads TMEM lanes 32 (w % 4) .. + 31 (the
 // sources of that quarter) and, with 256 threads, warps 0-3 take the first
 // half of the tile's columns in the epilogue and warps 4-7 the second half.
-template <bool kBwd, int kN, int kK, int kT>
+template <bool kBwd, int kN, int kK, int kT, bool kF8 = false>
 __global__ void __launch_bounds__(kT, 1)
     k_dense_level(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmA, const DenseParams p,
                   const int l, const int nl, const int stages, const int write_next) {
     extern __shared__ unsigned char dsm_raw[];
     unsigned char *dsm = reinterpret_cast<unsigned char *>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
-    constexpr int kXTile = x_tile<kK>();
-    const int stage_bytes = nl * kXTile + a_tile<kN, kK>();
+    constexpr int kRB = row_bytes<kK, kF8>();
+    constexpr int kXTile = x_tile<kK, kF8>();
+    const int stage_bytes = nl * kXTile + a_tile<kN, kK, kF8>();
     uint64_t *bars = reinterpret_cast<uint64_t *>(dsm + (size_t)stages * stage_bytes);
     uint64_t *full = bars;
     uint64_t *empty = bars + stages;
@@ -233,7 +250,7 @@ __global__ void __launch_bounds__(kT, 1)
         xin = ((L - 1 - l) & 1) ? 3 * kDB : 0;
         xout = 3 * kDB - xin;
     }
-    const int xrow0 = bb * p.xrows + xin;
+    const int xrow0 = bb * (kF8 ? 2 * p.xrows : p.xrows) + xin;  // e4m3 rows: npad bytes, two per bf16 row
     const int nk = p.npad / kK;
     // the backward keeps kBwdAcc accumulators for its three parts (see kBwdAcc)
     const int nacc = kBwd ? kBwdAcc : nl;
@@ -295,12 +312,12 @@ __global__ void __launch_bounds__(kT, 1)
             for (int q = 0; q < nl; ++q) {
                 const uint32_t xbase = smem_u32(st + (size_t)q * kXTile);
 #pragma unroll
-                for (int kk = 0; kk < kK / 16; ++kk) {
+                for (int kk = 0; kk < kRB / 32; ++kk) {
                     // accumulator of part q: forward, one per limb; backward, hi
                     // in the first and mid + lo in the second (or all three in one)
                     const int qa = kBwd ? (kBwdAcc == 1 ? 0 : (q > 1 ? 1 : q)) : q;
                     const bool first = it == 0 && kk == 0 && (!kBwd || q < kBwdAcc);
-                    umma_bf16<kN>(tmem + (uint32_t)(qa * kN), sw_desc<kK>(xbase + kk * 32), sw_desc<kK>(abase + kk * 32),
+                    umma<kN, kF8>(tmem + (uint32_t)(qa * kN), sw_desc<kRB>(xbase + kk * 32), sw_desc<kRB>(abase + kk * 32),
                                   first ? 0u : 1u);
                 }
             }
@@ -433,7 +450,7 @@ __global__ void __launch_bounds__(kT, 1)
                 for (int i = 0; i < 16; ++i) {
                     // exact integer < 2^24 held in FP32; add 2^(8q) * a into (hi:lo)
                     const uint64_t a = (uint64_t)__float2uint_rn(__uint_as_float(r[i]));
-                    const int sh = 8 * q;
+                    const int sh = (kF8 ? 4 : 8) * q;
                     const uint64_t part = a << sh;
                     const uint64_t carry_bits = sh ? (a >> (64 - sh)) : 0ull;
                     const uint64_t y = lo[i] + part;
@@ -500,7 +517,9 @@ __global__ void __launch_bounds__(kT, 1)
 
 // Limb matrix of level l: X[q*128 + b][u] = byte q of sigma_b(u) where
 // d(s_b, u) = l, else 0 (bf16). Tiles of 32 vertices x 128 sources through
-// shared memory so both the sigma reads and the X writes are coalesced.
+// shared memory so both the sigma reads and the X writes are coalesced. The
+// grid covers all npad columns: the padding is written with zeros, since the
+// buffer holds other rows' values there (0 x NaN is NaN in the products).
 __global__ void __launch_bounds__(256) k_dense_limbs(const DenseParams p, const int l, const int nl) {
     __shared__ uint64_t tile[32][kDB + 1];
     const int u0 = blockIdx.x * 32;
@@ -522,6 +541,37 @@ __global__ void __launch_bounds__(256) k_dense_limbs(const DenseParams p, const 
             const int b = i / 32, uu = i % 32;
             const unsigned byte = (unsigned)((tile[uu][b] >> (8 * q)) & 0xFFu);
             X[((size_t)q * kDB + b) * p.npad + u0 + uu] = __float2bfloat16_rn((float)byte);
+        }
+    }
+}
+
+// The same for e4m3 operands: X8[q*128 + b][u] = nibble q (4 bits) of
+// sigma_b(u) where d(s_b, u) = l, else 0; every value 0..15 is exact in e4m3.
+// Rows of npad bytes; batch b's rows start at b * 2 * xrows. Here too every
+// column up to npad is written: the bytes there may belong to bf16 rows of an
+// earlier sweep and read as e4m3 NaN.
+__global__ void __launch_bounds__(256) k_dense_nibbles(const DenseParams p, const int l, const int nq) {
+    __shared__ uint64_t tile[32][kDB + 1];
+    const int u0 = blockIdx.x * 32;
+    const int bb = p.blist[blockIdx.y];
+    const uint64_t *sigma = p.sigma + (size_t)bb * p.sig_stride;
+    uint8_t *X8 = reinterpret_cast<uint8_t *>(p.X) + (size_t)bb * 2 * p.xrows * p.npad;
+    const size_t nW = (size_t)p.n * kDW;
+    const uint32_t *Fl = p.F + (size_t)bb * p.f_stride + (size_t)l * nW;
+    for (int i = threadIdx.x; i < 32 * kDB; i += 256) {
+        const int uu = i / kDB, b = i % kDB;
+        const int u = u0 + uu;
+        uint64_t s = 0;
+        if (u < p.n && ((__ldg(Fl + (size_t)u * kDW + (b >> 5)) >> (b & 31)) & 1u)) s = sigma[(size_t)u * kDB + b];
+        tile[uu][b] = s;
+    }
+    __syncthreads();
+    for (int q = 0; q < nq; ++q) {
+        for (int i = threadIdx.x; i < 32 * kDB; i += 256) {
+            const int b = i / 32, uu = i % 32;
+            const unsigned nib = (unsigned)((tile[uu][b] >> (4 * q)) & 0xFu);
+            X8[((size_t)q * kDB + b) * p.npad + u0 + uu] =
+                (uint8_t)__nv_cvt_float_to_fp8((float)nib, __NV_SATFINITE, __NV_E4M3);
         }
     }
 }
@@ -627,6 +677,14 @@ __global__ void k_dense_adjacency(const int32_t *__restrict__ row_ptr, const int
             A[(size_t)v * npad + col[e]] = __float2bfloat16_rn(1.0f);
 }
 
+// The same adjacency in e4m3 (1.0 = 0x38, 0 = 0x00), one byte per entry.
+__global__ void k_dense_adjacency8(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n,
+                                   int32_t npad, uint8_t *A8) {
+    const uint8_t one = (uint8_t)__nv_cvt_float_to_fp8(1.0f, __NV_SATFINITE, __NV_E4M3);
+    for (int v = blockIdx.x; v < n; v += gridDim.x)
+        for (int e = row_ptr[v] + threadIdx.x; e < row_ptr[v + 1]; e += blockDim.x) A8[(size_t)v * npad + col[e]] = one;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -640,35 +698,39 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// Boxes of kK elements (the swizzle span: 128 or 64 bytes) by box_rows rows.
-bool make_map(CUtensorMap *m, void *base, uint64_t inner, uint64_t rows, uint32_t box_rows, int kK) {
+// Boxes of kK elements (the swizzle span: 128 or 64 bytes) by box_rows rows;
+// bf16 elements, or bytes (e4m3) when f8.
+bool make_map(CUtensorMap *m, void *base, uint64_t inner, uint64_t rows, uint32_t box_rows, int kK, bool f8 = false) {
     auto fn = encode_fn();
     if (!fn) return false;
+    const uint64_t esz = f8 ? 1 : 2;
     const cuuint64_t dims[2] = {inner, rows};
-    const cuuint64_t strides[1] = {inner * 2};
+    const cuuint64_t strides[1] = {inner * esz};
     const cuuint32_t box[2] = {(cuuint32_t)kK, box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              kK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return fn(m, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              kK * esz == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
 
-template <int kN, int kK>
+template <int kN, int kK, bool kF8 = false>
 int dense_stages(int nl, bool bwd = false) {
     // accumulators of at most 256 TMEM columns: two CTAs per SM (half the
     // shared memory each), at most 128: three, so one CTA's epilogue overlaps
     // the others' MMAs
     const int nacc = bwd ? kBwdAcc : nl;
     const int budget = nacc * kN <= 128 ? 66 * 1024 : (nacc * kN <= 256 ? 100 * 1024 : 200 * 1024);
-    const int s = budget / (nl * x_tile<kK>() + a_tile<kN, kK>());
+    const int s = budget / (nl * x_tile<kK, kF8>() + a_tile<kN, kK, kF8>());
     return s < 1 ? 1 : (s > 8 ? 8 : s);
 }
 
-template <int kN, int kK>
+template <int kN, int kK, bool kF8 = false>
 size_t dense_smem_bytes(int nl, int stages) {
-    return (size_t)stages * (nl * x_tile<kK>() + a_tile<kN, kK>()) + 1024 + (2 * stages + 2) * sizeof(uint64_t) + 64;
+    return (size_t)stages * (nl * x_tile<kK, kF8>() + a_tile<kN, kK, kF8>()) + 1024 + (2 * stages + 2) * sizeof(uint64_t) +
+           64;
 }
 
 int dense_build_adjacency(const int32_t *row_ptr, const int32_t *col, int32_t n, int32_t npad, __nv_bfloat16 *A,
@@ -678,7 +740,21 @@ int dense_build_adjacency(const int32_t *row_ptr, const int32_t *col, int32_t n,
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int dense_make_maps(DenseMaps *maps, __nv_bfloat16 *X, uint64_t xrows_total, __nv_bfloat16 *A, int32_t npad) {
+int dense_build_adjacency8(const int32_t *row_ptr, const int32_t *col, int32_t n, int32_t npad, uint8_t *A8,
+                           cudaStream_t st) {
+    if (cudaMemsetAsync(A8, 0, (size_t)npad * npad, st) != cudaSuccess) return -1;
+    if (n > 0) k_dense_adjacency8<<<n < 4096 ? n : 4096, 128, 0, st>>>(row_ptr, col, n, npad, A8);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int dense_make_maps(DenseMaps *maps, __nv_bfloat16 *X, uint64_t xrows_total, __nv_bfloat16 *A, uint8_t *A8,
+                    int32_t npad) {
+    maps->has_f8 = false;
+    if (A8) {  // e4m3 operands: X rows of npad bytes (two per bf16 row), adjacency boxes of 128 rows
+        if (!make_map(&maps->x8, X, (uint64_t)npad, 2 * xrows_total, kDB, 128, true)) return -1;
+        if (!make_map(&maps->a8, A8, (uint64_t)npad, (uint64_t)npad, kNW, 128, true)) return -1;
+        maps->has_f8 = true;
+    }
     if (!make_map(&maps->x, X, (uint64_t)npad, xrows_total, kDB, 64)) return -1;
     if (!make_map(&maps->a, A, (uint64_t)npad, (uint64_t)npad, kNT, 64)) return -1;
     if (!make_map(&maps->a_wide, A, (uint64_t)npad, (uint64_t)npad, kNW, 64)) return -1;
@@ -699,31 +775,41 @@ constexpr int kBwdK = 32;
 // one-limb forward measured the same at 256 as at 128, so it stays at 128
 // (kFwdX).
 constexpr bool kBwdX = true;
+// The forward's limb products in e4m3 with 4-bit limbs (kind::f8f6f4: one
+// byte per operand element and twice the bf16 rate) while the level's counts
+// need at most four of them (below 2^16); bf16 8-bit limbs otherwise
+constexpr bool kFwdF8 = true;
 constexpr int kBwdXThreads = 256;
 constexpr bool kFwdX = false;
 constexpr int kFwdXK = 64;
 
 // A CTA covers kNW = 128 vertices when the limb accumulators fit TMEM
 // (nl * 128 <= 512 columns), else kNT = 64.
-template <bool kBwd, int kN, int kK>
+template <bool kBwd, int kN, int kK, bool kF8 = false>
 int launch_level_t(const DenseMaps &maps, const DenseParams &p, int l, int nl, int write_next, cudaStream_t st) {
-    const int stages = dense_stages<kN, kK>(nl, kBwd);
-    const size_t smem = dense_smem_bytes<kN, kK>(nl, stages);
+    const int stages = dense_stages<kN, kK, kF8>(nl, kBwd);
+    const size_t smem = dense_smem_bytes<kN, kK, kF8>(nl, stages);
     // the widest backward tile runs one CTA per SM: its epilogue gets 8 warps
     constexpr int kT = (kBwd && kN == kNX) ? kBwdXThreads : 128;
-    if (cudaFuncSetAttribute(k_dense_level<kBwd, kN, kK, kT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(k_dense_level<kBwd, kN, kK, kT, kF8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
         return -1;
-    const CUtensorMap &mx = kK == 64 ? maps.x : maps.x32;
-    const CUtensorMap &ma = kN == kNX ? (kK == 64 ? maps.a_x : maps.a_x32)
-                                      : (kK == 64 ? (kN == kNW ? maps.a_wide : maps.a) : maps.a_wide32);
-    k_dense_level<kBwd, kN, kK, kT><<<p.nactive * (p.npad / kN), kT, smem, st>>>(mx, ma, p, l, nl, stages, write_next);
+    const CUtensorMap &mx = kF8 ? maps.x8 : (kK == 64 ? maps.x : maps.x32);
+    const CUtensorMap &ma = kF8 ? maps.a8
+                                : (kN == kNX ? (kK == 64 ? maps.a_x : maps.a_x32)
+                                             : (kK == 64 ? (kN == kNW ? maps.a_wide : maps.a) : maps.a_wide32));
+    k_dense_level<kBwd, kN, kK, kT, kF8><<<p.nactive * (p.npad / kN), kT, smem, st>>>(mx, ma, p, l, nl, stages,
+                                                                                       write_next);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int dense_launch_level(const DenseMaps &maps, const DenseParams &p, int l, int nl, cudaStream_t st) {
+int dense_launch_level(const DenseMaps &maps, const DenseParams &p, int l, int nl, int nq, cudaStream_t st) {
     if (p.nactive <= 0) return 0;
-    k_dense_limbs<<<dim3((p.n + 31) / 32, p.nactive), 256, 0, st>>>(p, l, nl);
+    if (kFwdF8 && maps.has_f8 && nq >= 1 && nq <= 4) {  // 4-bit limbs in e4m3, 128-vertex tiles
+        k_dense_nibbles<<<dim3(p.npad / 32, p.nactive), 256, 0, st>>>(p, l, nq);
+        return launch_level_t<false, kNW, 128, true>(maps, p, l, nq, 0, st);
+    }
+    k_dense_limbs<<<dim3(p.npad / 32, p.nactive), 256, 0, st>>>(p, l, nl);
     if (kFwdX && nl == 1 && p.npad % kNX == 0) return launch_level_t<false, kNX, kFwdXK>(maps, p, l, nl, 0, st);
     if (nl * kNW <= 512) return launch_level_t<false, kNW, kFwdK>(maps, p, l, nl, 0, st);
     return launch_level_t<false, kNT, 64>(maps, p, l, nl, 0, st);

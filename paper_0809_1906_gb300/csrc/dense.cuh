@@ -48,16 +48,25 @@ struct DenseMaps {
     CUtensorMap x, a, a_wide;  // K = 64 boxes (128-byte swizzle); adjacency boxes of 64 and 128 rows
     CUtensorMap x32, a_wide32; // K = 32 boxes (64-byte swizzle)
     CUtensorMap a_x, a_x32;    // adjacency boxes of 256 rows, K = 64 and 32 (when npad is a multiple of 256)
+    CUtensorMap x8, a8;        // e4m3 operands: 128-byte rows, X (4-bit limbs) and adjacency boxes of 128 rows
+    bool has_f8;
 };
 
 constexpr int kDenseXRows = kDenseMaxLimbs * 128;  // X rows per batch (>= 2 x 3 x 128 for the backward)
 
 int dense_build_adjacency(const int32_t *row_ptr, const int32_t *col, int32_t n, int32_t npad, __nv_bfloat16 *A,
                           cudaStream_t st);
-// Maps for X ([xrows_total][npad]) and A ([npad][npad]).
-int dense_make_maps(DenseMaps *maps, __nv_bfloat16 *X, uint64_t xrows_total, __nv_bfloat16 *A, int32_t npad);
-// Forward level l -> l+1 for the p.nactive batches of p.blist (limbs, then the product).
-int dense_launch_level(const DenseMaps &maps, const DenseParams &p, int l, int nl, cudaStream_t st);
+// The adjacency in e4m3 (A8 [npad][npad] bytes, 1.0 where an arc is).
+int dense_build_adjacency8(const int32_t *row_ptr, const int32_t *col, int32_t n, int32_t npad, uint8_t *A8,
+                           cudaStream_t st);
+// Maps for X ([xrows_total][npad]), A ([npad][npad]) and, when A8 is not null,
+// the e4m3 views of X and A8.
+int dense_make_maps(DenseMaps *maps, __nv_bfloat16 *X, uint64_t xrows_total, __nv_bfloat16 *A, uint8_t *A8,
+                    int32_t npad);
+// Forward level l -> l+1 for the p.nactive batches of p.blist (limbs, then
+// the product): nl 8-bit limbs of the level's counts, or nq <= 4 4-bit ones
+// in e4m3 when the maps have that form.
+int dense_launch_level(const DenseMaps &maps, const DenseParams &p, int l, int nl, int nq, cudaStream_t st);
 // Levels 0 and 1 of batches 0 .. nbatch (sources: 128 per batch, in batch
 // order): zeroes the group's frontier, visited and union-frontier words, then
 // sets the sources and their neighbours.

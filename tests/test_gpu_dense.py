@@ -117,3 +117,20 @@ def test_dense_backward_tensor_vs_sparse(nat, n, p):
         b, _, _ = h.result()
     assert np.all(np.abs(a - ref) <= tol), float(np.max(np.abs(a - ref) / np.maximum(np.abs(ref), 1)))
     assert np.all(np.abs(b - ref) <= tol)
+
+
+def test_dense_limb_sums_stay_exact(nat):
+    """Source 0 -> 15 vertices -> 2000 vertices joined to all 15 (sigma 15 each)
+    -> one vertex joined to all 2000: its count 15 * 2000 = 30000 is one limb
+    product's sum of 2000 terms of 15, which needs about 15 significant bits
+    of the tensor core's accumulator (so does every 4-bit-limb or 8-bit-limb
+    level here). sigma and d bit-exact from every source, BC within bounds."""
+    a, b = 15, 2000
+    L1 = np.arange(1, 1 + a)
+    L2 = np.arange(1 + a, 1 + a + b)
+    top = 1 + a + b
+    us = [np.zeros(a, np.int64), np.repeat(L1, b), L2]
+    vs = [L1, np.tile(L2, a), np.full(b, top)]
+    g = G.csr_from_edges(top + 1, np.concatenate(us), np.concatenate(vs), name="fan_15_2000")
+    src = np.ascontiguousarray(np.arange(g.n, dtype=np.int32)[::7])  # includes source 0
+    check(nat, g, sources=src, rows=4)
