@@ -265,11 +265,14 @@ int bc_kernel_trace(bc_graph *g, int64_t cap, int32_t *kind, int32_t *level, flo
  *   dag_arcs   sum over the run's sources s of the number of arcs (u,v) with
  *              u in P_s(v), i.e. the size of each shortest-path DAG (Section 1.1)
  *   depth_sum  sum over batches (one-source path: over sources) of the BFS depth
- *   tensor_flops  multiply-add work issued to the tensor cores by BC_DENSE
- *              (2 * M * N * K summed over the level products), 0 otherwise
+ *   tensor_flops  multiply-add work issued to the tensor cores by BC_DENSE in
+ *              bf16 (2 * M * N * K summed over the level products), 0 otherwise
+ *   tensor_flops_f8  the same for the products in e4m3 (forward levels whose
+ *              counts fit four 4-bit limbs)
  * Any pointer may be NULL (host pointers). Errors: BC_ERR_ARG, BC_ERR_STATE.
  */
-int bc_run_stats(bc_graph *g, int64_t *dag_arcs, int64_t *depth_sum, double *tensor_flops);
+int bc_run_stats(bc_graph *g, int64_t *dag_arcs, int64_t *depth_sum, double *tensor_flops,
+                 double *tensor_flops_f8);
 
 /*
  * Launch parameters (the paper has no counterpart: these choose how the

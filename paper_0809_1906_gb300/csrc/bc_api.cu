@@ -341,7 +341,7 @@ struct bc_graph {
     DevBuf<uint8_t> dA8;  // the adjacency in e4m3 (forward levels with 4-bit limbs)
     DevBuf<bcgb::DenseCtl> dctl;
     bcgb::DenseMaps maps{};
-    double dense_flops = 0.0;
+    double dense_flops = 0.0, dense_flops_f8 = 0.0;  // tensor-core work: bf16 and e4m3 products
     int32_t gNB = 0, gLcap = 0;  // group capacity (batches) and its level capacity
     DevBuf<uint64_t> gsigma;
     DevBuf<uint32_t> gF, gV, gufr;
@@ -1064,7 +1064,10 @@ int run_dense_group(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream
             CK(cudaMemcpyAsync(d_blist, active.data(), active.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
             CK(cudaMemsetAsync(g->dctl.p, 0, NB * sizeof(bcgb::DenseCtl), st));
             d.nactive = (int32_t)active.size();
-            g->dense_flops += 2.0 * B * nl * (double)g->npad * (double)g->npad * (double)active.size();
+            if (bcgb::dense_level_f8(g->maps, nq))
+                g->dense_flops_f8 += 2.0 * B * nq * (double)g->npad * (double)g->npad * (double)active.size();
+            else
+                g->dense_flops += 2.0 * B * nl * (double)g->npad * (double)g->npad * (double)active.size();
             {
                 Timer t(g, st, BC_KERNEL_DENSE);
                 if (bcgb::dense_launch_level(g->maps, d, l, nl, nq, st))
@@ -1861,6 +1864,7 @@ int bc_run(bc_graph *g, const int32_t *sources, int32_t num_sources, const bc_op
     g->evused = 0;
     g->launches = 0;
     g->dense_flops = 0.0;
+    g->dense_flops_f8 = 0.0;
     g->has_run = false;
     const bool hash = !(flags & BC_NO_HASH);
     if (!(flags & BC_ACCUMULATE)) CK(cudaMemsetAsync(g->bc.p, 0, g->bc.n * sizeof(double), st));
@@ -2041,7 +2045,8 @@ int bc_kernel_trace(bc_graph *g, int64_t cap, int32_t *kind, int32_t *level, flo
 
 int64_t bc_launch_count(const bc_graph *g) { return g ? g->launches : 0; }
 
-int bc_run_stats(bc_graph *g, int64_t *dag_arcs, int64_t *depth_sum, double *tensor_flops) {
+int bc_run_stats(bc_graph *g, int64_t *dag_arcs, int64_t *depth_sum, double *tensor_flops,
+                 double *tensor_flops_f8) {
     g_err.clear();
     if (!g) return fail(BC_ERR_ARG, "graph is NULL");
     if (!g->has_run) return fail(BC_ERR_STATE, "no completed bc_run");
@@ -2051,6 +2056,7 @@ int bc_run_stats(bc_graph *g, int64_t *dag_arcs, int64_t *depth_sum, double *ten
     if (dag_arcs) *dag_arcs = (int64_t)v[0];
     if (depth_sum) *depth_sum = (int64_t)v[1];
     if (tensor_flops) *tensor_flops = g->dense_flops;
+    if (tensor_flops_f8) *tensor_flops_f8 = g->dense_flops_f8;
     return BC_OK;
 }
 

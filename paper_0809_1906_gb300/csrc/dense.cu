@@ -803,9 +803,11 @@ int launch_level_t(const DenseMaps &maps, const DenseParams &p, int l, int nl, i
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+bool dense_level_f8(const DenseMaps &maps, int nq) { return kFwdF8 && maps.has_f8 && nq >= 1 && nq <= 4; }
+
 int dense_launch_level(const DenseMaps &maps, const DenseParams &p, int l, int nl, int nq, cudaStream_t st) {
     if (p.nactive <= 0) return 0;
-    if (kFwdF8 && maps.has_f8 && nq >= 1 && nq <= 4) {  // 4-bit limbs in e4m3, 128-vertex tiles
+    if (dense_level_f8(maps, nq)) {  // 4-bit limbs in e4m3, 128-vertex tiles
         k_dense_nibbles<<<dim3(p.npad / 32, p.nactive), 256, 0, st>>>(p, l, nq);
         return launch_level_t<false, kNW, 128, true>(maps, p, l, nq, 0, st);
     }

@@ -67,6 +67,8 @@ int dense_make_maps(DenseMaps *maps, __nv_bfloat16 *X, uint64_t xrows_total, __n
 // the product): nl 8-bit limbs of the level's counts, or nq <= 4 4-bit ones
 // in e4m3 when the maps have that form.
 int dense_launch_level(const DenseMaps &maps, const DenseParams &p, int l, int nl, int nq, cudaStream_t st);
+// Whether dense_launch_level takes the e4m3 form for nq 4-bit limbs.
+bool dense_level_f8(const DenseMaps &maps, int nq);
 // Levels 0 and 1 of batches 0 .. nbatch (sources: 128 per batch, in batch
 // order): zeroes the group's frontier, visited and union-frontier words, then
 // sets the sources and their neighbours.

@@ -104,7 +104,7 @@ def load(build_if_needed: bool = True, require_gpu: bool = True):
             "bc_forward_rows": (i32, [P, P, i32, P, P, P, P]),
             "bc_kernel_time": (i32, [P, i32, P, P]),
             "bc_kernel_trace": (i32, [P, i64, P, P, P, P]),
-            "bc_run_stats": (i32, [P, P, P, P]),
+            "bc_run_stats": (i32, [P, P, P, P, P]),
             "bc_launch_count": (i64, [P]),
             "bc_graph_size": (i32, [P, P, P, P]),
             "bc_destroy_graph": (None, [P]),
@@ -294,13 +294,20 @@ class Graph:
     def run_stats(self):
         a = ctypes.c_int64(0)
         d = ctypes.c_int64(0)
-        _check(self.lib.bc_run_stats(self.handle, ctypes.byref(a), ctypes.byref(d), None), "bc_run_stats")
+        _check(self.lib.bc_run_stats(self.handle, ctypes.byref(a), ctypes.byref(d), None, None), "bc_run_stats")
         return a.value, d.value
 
     def dense_flops(self) -> float:
+        """Tensor-core work of the last BC_DENSE run, bf16 and e4m3 together."""
+        bf, f8 = self.dense_flops_by_type()
+        return bf + f8
+
+    def dense_flops_by_type(self):
+        """(bf16 flops, e4m3 flops) of the last BC_DENSE run."""
         f = ctypes.c_double(0.0)
-        _check(self.lib.bc_run_stats(self.handle, None, None, ctypes.byref(f)), "bc_run_stats")
-        return f.value
+        f8 = ctypes.c_double(0.0)
+        _check(self.lib.bc_run_stats(self.handle, None, None, ctypes.byref(f), ctypes.byref(f8)), "bc_run_stats")
+        return f.value, f8.value
 
     def launch_count(self) -> int:
         return int(self.lib.bc_launch_count(self.handle))
