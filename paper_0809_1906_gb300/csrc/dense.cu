@@ -549,29 +549,38 @@ __global__ void __launch_bounds__(256) k_dense_limbs(const DenseParams p, const 
 // sigma_b(u) where d(s_b, u) = l, else 0; every value 0..15 is exact in e4m3.
 // Rows of npad bytes; batch b's rows start at b * 2 * xrows. Here too every
 // column up to npad is written: the bytes there may belong to bf16 rows of an
-// earlier sweep and read as e4m3 NaN.
-__global__ void __launch_bounds__(256) k_dense_nibbles(const DenseParams p, const int l, const int nq) {
-    __shared__ uint64_t tile[32][kDB + 1];
-    const int u0 = blockIdx.x * 32;
+// earlier sweep and read as e4m3 NaN. Tiles of 64 vertices x 128 sources
+// (counts below 2^16 on this path, kept as 32-bit words); four columns per
+// 4-byte store. ones: every count of the level is 1 (level 1, set by
+// k_dense_first), so sigma is not read.
+__global__ void __launch_bounds__(256) k_dense_nibbles(const DenseParams p, const int l, const int nq,
+                                                       const int ones) {
+    __shared__ uint32_t tile[64][kDB + 1];
+    const int u0 = blockIdx.x * 64;
     const int bb = p.blist[blockIdx.y];
     const uint64_t *sigma = p.sigma + (size_t)bb * p.sig_stride;
     uint8_t *X8 = reinterpret_cast<uint8_t *>(p.X) + (size_t)bb * 2 * p.xrows * p.npad;
     const size_t nW = (size_t)p.n * kDW;
     const uint32_t *Fl = p.F + (size_t)bb * p.f_stride + (size_t)l * nW;
-    for (int i = threadIdx.x; i < 32 * kDB; i += 256) {
+    for (int i = threadIdx.x; i < 64 * kDB; i += 256) {
         const int uu = i / kDB, b = i % kDB;
         const int u = u0 + uu;
-        uint64_t s = 0;
-        if (u < p.n && ((__ldg(Fl + (size_t)u * kDW + (b >> 5)) >> (b & 31)) & 1u)) s = sigma[(size_t)u * kDB + b];
+        uint32_t s = 0;
+        if (u < p.n && ((__ldg(Fl + (size_t)u * kDW + (b >> 5)) >> (b & 31)) & 1u))
+            s = ones ? 1u : (uint32_t)sigma[(size_t)u * kDB + b];
         tile[uu][b] = s;
     }
     __syncthreads();
     for (int q = 0; q < nq; ++q) {
-        for (int i = threadIdx.x; i < 32 * kDB; i += 256) {
-            const int b = i / 32, uu = i % 32;
-            const unsigned nib = (unsigned)((tile[uu][b] >> (4 * q)) & 0xFu);
-            X8[((size_t)q * kDB + b) * p.npad + u0 + uu] =
-                (uint8_t)__nv_cvt_float_to_fp8((float)nib, __NV_SATFINITE, __NV_E4M3);
+        for (int i = threadIdx.x; i < kDB * 16; i += 256) {
+            const int b = i / 16, c4 = 4 * (i % 16);
+            uint32_t w = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const unsigned nib = (tile[c4 + k][b] >> (4 * q)) & 0xFu;
+                w |= (uint32_t)__nv_cvt_float_to_fp8((float)nib, __NV_SATFINITE, __NV_E4M3) << (8 * k);
+            }
+            *reinterpret_cast<uint32_t *>(X8 + ((size_t)q * kDB + b) * p.npad + u0 + c4) = w;
         }
     }
 }
@@ -808,7 +817,7 @@ bool dense_level_f8(const DenseMaps &maps, int nq) { return kFwdF8 && maps.has_f
 int dense_launch_level(const DenseMaps &maps, const DenseParams &p, int l, int nl, int nq, cudaStream_t st) {
     if (p.nactive <= 0) return 0;
     if (dense_level_f8(maps, nq)) {  // 4-bit limbs in e4m3, 128-vertex tiles
-        k_dense_nibbles<<<dim3(p.npad / 32, p.nactive), 256, 0, st>>>(p, l, nq);
+        k_dense_nibbles<<<dim3(p.npad / 64, p.nactive), 256, 0, st>>>(p, l, nq, l == 1 ? 1 : 0);
         return launch_level_t<false, kNW, 128, true>(maps, p, l, nq, 0, st);
     }
     k_dense_limbs<<<dim3(p.npad / 32, p.nactive), 256, 0, st>>>(p, l, nl);
