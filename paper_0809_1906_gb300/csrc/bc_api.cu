@@ -1044,6 +1044,15 @@ int run_dense_group(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream
         d.bcpart = g->gbcpart.p;
         d.ctl = g->ctl;
         d.dctl = g->dctl.p;
+        // with the tensor-core backward the summaries come from its levels
+        // (and the deepest level's split) instead of a pass over the batch state
+        const bool dense_hash = hash && backward && !sparse_bwd;
+        d.sources = g->sources.p + (size_t)gb0 * B;
+        d.src_base = gb0 * B;
+        d.h_sigma = dense_hash ? g->h_sigma.p : nullptr;
+        d.h_dist = dense_hash ? g->h_dist.p : nullptr;
+        d.dist_sum = dense_hash ? g->dist_sum.p : nullptr;
+        d.reach = dense_hash ? g->reach.p : nullptr;
         {
             // levels 0 and 1 of the whole group in one launch
             Timer t(g, st, BC_KERNEL_FORWARD);
@@ -1136,7 +1145,7 @@ int run_dense_group(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream
             }
             if (bcgb::dense_reduce_bc(g->gbcpart.p, NB, n, g->bc.p, st)) return fail(BC_ERR_CUDA, "BC reduction");
         }
-        if (hash) {
+        if (hash && !dense_hash) {
             // the batches' summaries are independent: spread over side streams
             Timer t(g, st, BC_KERNEL_HASH);
             r = fork_side(g, st);

@@ -350,6 +350,8 @@ __global__ void __launch_bounds__(kT, 1)
         __shared__ float2 s_red[4][kN];
         const bool valid_src = b < nbv;
         const size_t xr = (size_t)bb * p.xrows + xout + b;  // this source's hi row; mid and lo follow at +128, +256
+        // summary terms of this thread's pairs (level l, its columns)
+        unsigned long long t_hs = 0, t_vs = 0, t_cnt = 0;
         for (int c0 = cbeg; good && c0 < cbeg + kCols; c0 += 16) {
             uint32_t fwn[16];
             uint64_t svn[16];
@@ -372,6 +374,9 @@ __global__ void __launch_bounds__(kT, 1)
                 const int v = v0 + c0 + i;
                 float d = 0.0f, c = 0.0f;
                 if (v < p.n && valid_src && ((fw[i] >> lane) & 1u)) {
+                    t_hs += (unsigned long long)sv[i] * (unsigned long long)(v + 1);
+                    t_vs += (unsigned long long)(v + 1);
+                    ++t_cnt;
                     const float sg = __ull2float_rn(sv[i]);
                     d = sg * S[i];          // delta_s*(v) = sigma_s(v) * sum_w c_s(w)
                     c = (1.0f + d) / sg;    // c_s(v) for the level above
@@ -413,6 +418,13 @@ __global__ void __launch_bounds__(kT, 1)
                 fw[i] = fwn[i];
                 sv[i] = svn[i];
             }
+        }
+        if (good && p.h_sigma && t_cnt) {  // d = l for every pair here
+            const size_t o = (size_t)p.src_base + (size_t)bb * kDB + b;
+            atomicAdd(reinterpret_cast<unsigned long long *>(p.h_sigma + o), t_hs);
+            atomicAdd(reinterpret_cast<unsigned long long *>(p.h_dist + o), (unsigned long long)(l + 1) * t_vs);
+            atomicAdd(reinterpret_cast<unsigned long long *>(p.dist_sum + o), (unsigned long long)l * t_cnt);
+            atomicAdd(reinterpret_cast<unsigned long long *>(p.reach + o), t_cnt);
         }
         __syncthreads();
         for (int c = tid; good && c < kN && v0 + c < p.n; c += kT) {
@@ -596,18 +608,50 @@ __global__ void __launch_bounds__(256) k_dense_bwd_last(const DenseParams p) {
     const int v0 = blockIdx.x * 64;
     const int bb = blockIdx.y;
     const int L = p.depth[bb];
-    if (L < 1) return;
     const int nbv = p.nbs[bb];
+    if (L < 1) {  // no source of the batch has a neighbour: only their own summary terms
+        if (p.h_sigma && blockIdx.x == 0 && threadIdx.x < nbv) {
+            const size_t o = (size_t)p.src_base + (size_t)bb * kDB + threadIdx.x;
+            const unsigned long long h0 = (unsigned long long)p.sources[(size_t)bb * kDB + threadIdx.x] + 1ull;
+            atomicAdd(reinterpret_cast<unsigned long long *>(p.h_sigma + o), h0);
+            atomicAdd(reinterpret_cast<unsigned long long *>(p.h_dist + o), h0);
+            atomicAdd(reinterpret_cast<unsigned long long *>(p.reach + o), 1ull);
+        }
+        return;
+    }
     const size_t nW = (size_t)p.n * kDW;
     const uint32_t *FL = p.F + (size_t)bb * p.f_stride + (size_t)L * nW;
     const uint64_t *sigma = p.sigma + (size_t)bb * p.sig_stride;
+    const int bt = threadIdx.x % kDB;  // the source of every item of this thread
+    unsigned long long t_hs = 0, t_vs = 0, t_cnt = 0;
     for (int i = threadIdx.x; i < 64 * kDB; i += 256) {
         const int vv = i / kDB, b = i % kDB;
         const int v = v0 + vv;
         float c = 0.0f;
-        if (v < p.n && b < nbv && ((__ldg(FL + (size_t)v * kDW + (b >> 5)) >> (b & 31)) & 1u))
-            c = 1.0f / __ull2float_rn(sigma[(size_t)v * kDB + b]);
+        if (v < p.n && b < nbv && ((__ldg(FL + (size_t)v * kDW + (b >> 5)) >> (b & 31)) & 1u)) {
+            const uint64_t sg = sigma[(size_t)v * kDB + b];
+            c = 1.0f / __ull2float_rn(sg);
+            t_hs += (unsigned long long)sg * (unsigned long long)(v + 1);
+            t_vs += (unsigned long long)(v + 1);
+            ++t_cnt;
+        }
         tile[vv][b] = c;
+    }
+    if (p.h_sigma) {
+        // summaries: this thread's level-L pairs, and (first tile) the source
+        // itself, d = 0 and sigma = 1
+        unsigned long long h0 = 0, c0 = 0;
+        if (blockIdx.x == 0 && threadIdx.x < kDB && bt < nbv) {
+            h0 = (unsigned long long)p.sources[(size_t)bb * kDB + bt] + 1ull;
+            c0 = 1;
+        }
+        if (t_cnt || c0) {
+            const size_t o = (size_t)p.src_base + (size_t)bb * kDB + bt;
+            atomicAdd(reinterpret_cast<unsigned long long *>(p.h_sigma + o), t_hs + h0);
+            atomicAdd(reinterpret_cast<unsigned long long *>(p.h_dist + o), (unsigned long long)(L + 1) * t_vs + h0);
+            atomicAdd(reinterpret_cast<unsigned long long *>(p.dist_sum + o), (unsigned long long)L * t_cnt);
+            atomicAdd(reinterpret_cast<unsigned long long *>(p.reach + o), t_cnt + c0);
+        }
     }
     __syncthreads();
     __nv_bfloat16 *X = p.X + (size_t)bb * p.xrows * p.npad;  // block 0 holds level L

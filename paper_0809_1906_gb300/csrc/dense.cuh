@@ -42,6 +42,13 @@ struct DenseParams {
     double *bcpart;         // [batch][n] BC contributions of each batch (added in batch order later)
     DevCtl *ctl;
     DenseCtl *dctl;         // [batch]
+    // per-source summaries (may be null): the backward levels and the deepest
+    // level's split add the terms of the pairs they visit, the split also the
+    // sources' own (level 0); batch b's source j goes to index src_base + 128 b + j
+    const int32_t *sources;  // the group's sources, 128 per batch
+    int32_t src_base;
+    uint64_t *h_sigma, *h_dist;
+    int64_t *dist_sum, *reach;
 };
 
 struct DenseMaps {
