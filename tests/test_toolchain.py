@@ -1,7 +1,8 @@
 """What the toolchain allows on sm_103a for the algebraic path (no GPU: nvcc
 and ptxas only). The 8-bit-integer tensor-core form (tcgen05.mma kind::i8,
 u8 x u8 -> s32) assembles for sm_100a but not for sm_103a, so on GB300 the
-limb products of Section 3.1.1 run as bf16 x bf16 -> FP32 (kind::f16; exact
+limb products of Section 3.1.1 run as e4m3 x e4m3 -> FP32 (kind::f8f6f4; exact
+for 4-bit limbs while 15 n < 2^24) or bf16 x bf16 -> FP32 (kind::f16; exact
 for 8-bit limbs while 255 n < 2^24)."""
 import os
 import shutil
@@ -39,5 +40,7 @@ def test_integer_tensor_cores_are_not_available_on_sm103a(tmp_path):
     assert rc != 0 and "kind::i8" in out and "sm_103a" in out, out
     rc, out = _assemble(tmp_path, "i8", "100a")
     assert rc == 0, out
-    rc, out = _assemble(tmp_path, "f16", "103a")  # the form the dense path uses
+    rc, out = _assemble(tmp_path, "f16", "103a")  # the forms the dense path uses
+    assert rc == 0, out
+    rc, out = _assemble(tmp_path, "f8f6f4", "103a")
     assert rc == 0, out
