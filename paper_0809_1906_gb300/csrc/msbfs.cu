@@ -345,6 +345,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
     extern __shared__ __align__(128) uint8_t s_stage[];
     __shared__ int32_t s_u[kWarps][32];
     __shared__ uint32_t s_nz[kWarps][32];
+    __shared__ __align__(16) uint16_t s_sig[kWarps][W][32];  // the counts of the item being finalized
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const size_t nW = (size_t)p.n * W;
@@ -430,12 +431,33 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
 #pragma unroll
             for (int j = 0; j < W; ++j) f[j] = s_f[wib][kk][j];
 
+            // an unsplit vertex finalizes right after its scan: its counts
+            // (the words with a level-l source) are copied to shared memory
+            // while the neighbours are scanned (even lanes, 4 bytes each)
+            const bool early = slot < 0 && Sl != nullptr;
+            if (early) {
+#pragma unroll
+                for (int j = 0; j < W; ++j)
+                    if (f[j] != 0u && (lane & 1) == 0) {
+                        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_sig[wib][j][lane]);
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst),
+                                     "l"(Sl + (size_t)v * B + 32 * j + lane)
+                                     : "memory");
+                    }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            }
             float S[W];  // lane owns source 32j + lane
 #pragma unroll
             for (int j = 0; j < W; ++j) S[j] = 0.0f;
             body::bwd_sum<W, true, true, HOOK>(p.col, beg, end, ufs, Fs, Cs, f, s_u[wib], s_nz[wib], lane, S, &ws);
             if (slot < 0) {
-                body::finalize_dep<W>(p.sigma, Sl, sig_ones, Cl, p.bc, v, f, S, lane);
+                if (early) {
+                    asm volatile("cp.async.wait_group 0;" ::: "memory");
+                    __syncwarp();
+                }
+                body::finalize_dep<W>(p.sigma, Sl, sig_ones, Cl, p.bc, v, f, S, lane,
+                                      early ? &s_sig[wib][0][0] : nullptr);
+                __syncwarp();  // the next item's copies overwrite s_sig
                 continue;
             }
             float *pp = reinterpret_cast<float *>(p.part) + (size_t)slot * B + lane;

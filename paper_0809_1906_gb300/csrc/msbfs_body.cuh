@@ -623,11 +623,13 @@ __device__ __forceinline__ float sigma_f32(uint64_t x) {
 // in FP64.
 // sigma_s(v) comes from the level's masked uint16 row Sl when given (a
 // narrow level: every count below 2^16), is 1 when `ones` (level 1, reached
-// from the sources directly), else from the uint64 array.
+// from the sources directly), else from the uint64 array. Ssh: when not null,
+// v's words of Sl already copied to shared memory ([W][32], the words with a
+// level-l source), read there instead.
 template <int W, bool ALL_WORDS = true>
 __device__ __forceinline__ void finalize_dep(const uint64_t *sigma, const uint16_t *Sl, bool ones, float *Cl,
                                              double *bc, int v, const uint32_t (&f)[W], const float (&S)[W],
-                                             int lane) {
+                                             int lane, const uint16_t *Ssh = nullptr) {
     constexpr int B = 32 * W;
     float hi = 0.0f, lo = 0.0f;  // the running sum hi + lo, carried without rounding loss
 #pragma unroll
@@ -635,7 +637,9 @@ __device__ __forceinline__ void finalize_dep(const uint64_t *sigma, const uint16
         const size_t idx = (size_t)v * B + 32 * j + lane;
         float c = 0.0f;
         if ((f[j] >> lane) & 1u) {
-            const float sg = ones ? 1.0f : (Sl ? __uint2float_rn((uint32_t)Sl[idx]) : sigma_f32(sigma[idx]));
+            const float sg = ones ? 1.0f
+                                  : (Ssh ? __uint2float_rn((uint32_t)Ssh[32 * j + lane])
+                                         : (Sl ? __uint2float_rn((uint32_t)Sl[idx]) : sigma_f32(sigma[idx])));
             const float d = sg * S[j];        // delta_s(v) = sigma_s(v) * sum_w c_s(w)
             c = __fdividef(1.0f, sg) + S[j];  // c_s(v) for the level above (1/sigma within 2 ulp)
             two_sum_add(hi, lo, d);
