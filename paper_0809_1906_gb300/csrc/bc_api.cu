@@ -581,7 +581,7 @@ int ensure_state(bc_graph *g, int W, int Lcap) {
     CK(g->sigma.ensure(n * B));
     g->s_levels = s_levels_for(n, B, Lcap);
     CK(g->Smask.ensure((size_t)g->s_levels * n * B));
-    CK(g->wideflags.ensure((size_t)Lcap));
+    CK(g->wideflags.ensure((size_t)2 * Lcap));  // per-level flags, then the frontier sizes
     CK(g->cval.ensure(2 * n * B));
     CK(g->F.ensure((size_t)Lcap * n * W));
     CK(g->ufr.ensure((size_t)Lcap * nw32));
@@ -650,6 +650,7 @@ bcgb::MsParams make_params(bc_graph *g) {
     p.S = g->Smask.p;
     p.s_levels = g->s_levels;
     p.wide = g->wideflags.p;
+    p.lsize = g->wideflags.p + g->Lcap;
     p.cval = g->cval.p;
     p.F = g->F.p;
     p.ufr = g->ufr.p;
@@ -691,7 +692,7 @@ int ensure_lane(bc_graph *g, SweepLane &ln, int W, int Lcap) {
     CK(ln.sigma.ensure(n * B));
     ln.s_levels = s_levels_for(n, B, Lcap);
     CK(ln.Smask.ensure((size_t)ln.s_levels * n * B));
-    CK(ln.wideflags.ensure((size_t)Lcap));
+    CK(ln.wideflags.ensure((size_t)2 * Lcap));  // per-level flags, then the frontier sizes
     CK(ln.cval.ensure(2 * n * B));
     CK(ln.F.ensure((size_t)Lcap * n * W));
     CK(ln.ufr.ensure((size_t)Lcap * nw32));
@@ -718,6 +719,7 @@ bcgb::MsParams lane_params(bc_graph *g, int k) {
     p.S = ln.Smask.p;
     p.s_levels = ln.s_levels;
     p.wide = ln.wideflags.p;
+    p.lsize = ln.wideflags.p + ln.Lcap;
     p.cval = ln.cval.p;
     p.F = ln.F.p;
     p.ufr = ln.ufr.p;

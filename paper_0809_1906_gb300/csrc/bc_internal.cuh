@@ -102,6 +102,7 @@ struct MsParams {
     const uint16_t *S_rd;  // set per forward launch: the buffer of level l (read)
     uint16_t *S_wr;        // and of level l+1 (written)
     uint32_t *wide;  // [Lcap]
+    uint32_t *lsize;  // [Lcap] or null: vertices in frontier l (written as the forward reaches it)
     float *cval;   // [2][n][B]
     uint32_t *F;
     uint32_t *ufr;

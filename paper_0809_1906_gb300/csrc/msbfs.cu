@@ -40,6 +40,15 @@ using body::load_row;
 using body::valid_word;
 using body::transpose32;
 
+// A level's union-frontier filter pays when its frontier is narrow: a wide
+// one lets most neighbours through, and the filter's bit load is one more
+// dependent load per arc. Wide: at least n / kFilterRatio vertices (the size
+// the forward recorded; no record, always filter).
+constexpr uint32_t kFilterRatio = 32;
+__device__ __forceinline__ bool filter_level(const MsParams &p, int l) {
+    return p.lsize == nullptr || (uint64_t)p.lsize[l] * kFilterRatio < (uint64_t)p.n;
+}
+
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
     constexpr int B = 32 * W;
@@ -76,6 +85,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const MsParams p) {
         p.S[(size_t)s * B + b] = 1;
     }
     if (threadIdx.x == 0) {
+        if (p.lsize) p.lsize[0] = (uint32_t)p.nb;
         p.ctl->fwd_done = 0u;
         p.ctl->nonempty = 0u;
         p.ctl->nlevels = 0;
@@ -148,6 +158,7 @@ __global__ void __launch_bounds__(kBlock) k_first(const MsParams p) {
     }
     // level 1 has at most `total` vertices (the arcs out of the sources)
     p.ctl->front_last = (uint32_t)total;
+    if (p.lsize) p.lsize[1] = (uint32_t)total;
     host_word(&p.hctl->counts, (uint32_t)total, 0xffffffffu);
     host_word(&p.hctl->progress, p.seq, 1u);
 }
@@ -187,6 +198,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     uint16_t *Sn = p.S_wr;
     const bool wide = *(volatile uint32_t *)(p.wide + l) != 0u;
     const bool ones = l == 1 && p.first;  // level 1 written by k_first: all counts 1, no masked rows
+    const uint32_t *ufl_f = filter_level(p, l) ? ufl : nullptr;  // the union filter, on narrow frontiers only
     bool produced = false, ovf = false, wide_next = false;
     uint32_t arcs = 0;  // predecessor relations counted by this lane
     body::WarpStage ws{s_stage + wib * stage::kFwdStageBytes, s_bar + wib, s_qz[wib], 0u, false,
@@ -244,7 +256,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
                 acc[j] = 0ull;
                 nf[j] = 0u;
             }
-            body::fwd_sum<W, true, true, HOOK>(p.col_f, beg, end, ufl, Fl, Sl, p.sigma, wide, ones, U, s_u[wib], s_nz[wib], lane,
+            body::fwd_sum<W, true, true, HOOK>(p.col_f, beg, end, ufl_f, Fl, Sl, p.sigma, wide, ones, U, s_u[wib], s_nz[wib], lane,
                                          acc, nf, ovf, arcs, &ws);
             if (slot < 0) {
                 const bool joined = body::store_next<W>(p.sigma, Sn, Fn, ufn, v, acc, nf, lane, wide_next);
@@ -330,6 +342,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_forward(const MsParams p, const i
     const uint32_t nxt = atomicExch(&p.ctl->front_new, 0u);
     const uint32_t cur = p.ctl->front_last;
     p.ctl->front_last = nxt;
+    if (p.lsize) p.lsize[l + 1] = nxt;
     host_word(&p.hctl->counts, nxt, cur);
     host_word(&p.hctl->progress, p.seq, (uint32_t)(l + 1));
 }
@@ -357,6 +370,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
     // dependencies are not part of BC), so its c values have no reader
     float *Cl = l > 1 ? p.cval + (size_t)(l & 1) * nB : nullptr;
     const float *Cs = p.cval + (size_t)((l + 1) & 1) * nB;
+    const uint32_t *ufs_f = filter_level(p, l + 1) ? ufs : nullptr;  // the union filter, on narrow frontiers only
     body::WarpStage ws{s_stage + wib * stage::kBwdStageBytes, s_bar + wib, s_qz[wib], 0u, false,
                        body::stage_wctl(p.wait_ns, p.test_hold)};
     if (lane == 0) stage::bar_init(ws.bar);
@@ -449,7 +463,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_backward(const MsParams p, const 
             float S[W];  // lane owns source 32j + lane
 #pragma unroll
             for (int j = 0; j < W; ++j) S[j] = 0.0f;
-            body::bwd_sum<W, true, true, HOOK>(p.col, beg, end, ufs, Fs, Cs, f, s_u[wib], s_nz[wib], lane, S, &ws);
+            body::bwd_sum<W, true, true, HOOK>(p.col, beg, end, ufs_f, Fs, Cs, f, s_u[wib], s_nz[wib], lane, S, &ws);
             if (slot < 0) {
                 if (early) {
                     asm volatile("cp.async.wait_group 0;" ::: "memory");

@@ -215,7 +215,9 @@ __device__ __forceinline__ void unpack_lanes(T *p, const T (&x)[W], T (&out)[W],
 // arcs that cannot contribute); s_nz[k] gets the W-bit set of non-zero words
 // of m_k, so the adders load only the words that can contribute.
 // Returns the ballot of contributing lanes; u and nz are lane k's own
-// neighbour and word set.
+// neighbour and word set. ufr (the union of the level's frontiers, one bit
+// per vertex) skips the row loads of neighbours in no frontier; null when the
+// level's frontier is wide enough that most neighbours pass.
 template <int W, bool NC>
 __device__ __forceinline__ unsigned probe_chunk(const int32_t *__restrict__ col, int e, int end,
                                                 const uint32_t *__restrict__ ufr, const uint32_t *__restrict__ Fx,
@@ -227,7 +229,7 @@ __device__ __forceinline__ unsigned probe_chunk(const int32_t *__restrict__ col,
     for (int j = 0; j < W; ++j) m[j] = 0u;
     if (e < end) {
         u = __ldg(col + e);
-        if ((ldx<NC>(ufr + (u >> 5)) >> (u & 31)) & 1u) {
+        if (ufr == nullptr || ((ldx<NC>(ufr + (u >> 5)) >> (u & 31)) & 1u)) {
             uint32_t fu[W];
             load_row<W, NC>(Fx + (size_t)u * W, fu);
 #pragma unroll
