@@ -1006,6 +1006,11 @@ int run_dense_group(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream
             bcgb::MsParams p = make_params(g);
             p.nb = nbs[b];
             p.first = 1;
+            // no frontier sizes from the tensor-core forward: the sparse
+            // backward keeps the union filter on every level (it also hides
+            // the frontier row below the deepest, which a group whose pairs
+            // were all reached a level early never writes)
+            p.lsize = nullptr;
             p.seq = ++g->seq;
             p.sources = g->sources.p + b0;
             p.sigma = g->gsigma.p + b * sstr;
