@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(kMBlock, W >= 4 ? 3 : 4) k_many(const ManyPara
     __shared__ uint32_t s_nz[kMWarps][32];
     __shared__ uint32_t s_w[kMWarps][32][W];  // per-lane words of a warp's 32 vertices
     __shared__ unsigned long long s_sum[4][B];  // per-source summaries of the running batch
+    __shared__ __align__(16) uint64_t s_sig[kMWarps][W][32];  // counts of the vertex being finalized
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     uint64_t *sigma = p.sigma + (size_t)blockIdx.x * p.nmax * B;
     uint16_t *Sbuf = p.S + (size_t)blockIdx.x * 2 * p.nmax * B;
@@ -230,11 +231,25 @@ __global__ void __launch_bounds__(kMBlock, W >= 4 ? 3 : 4) k_many(const ManyPara
 #pragma unroll
                         for (int j = 0; j < W; ++j) f[j] = s_w[wib][__ffs(todo) - 1][j];
                         todo &= todo - 1;
+                        // v's counts (the words with a level-l source) go to
+                        // shared memory while its neighbours are scanned
+#pragma unroll
+                        for (int j = 0; j < W; ++j)
+                            if (f[j] != 0u) {
+                                const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_sig[wib][j][lane]);
+                                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst),
+                                             "l"(sigma + (size_t)v * B + 32 * j + lane)
+                                             : "memory");
+                            }
+                        asm volatile("cp.async.commit_group;" ::: "memory");
                         float S[W];
 #pragma unroll
                         for (int j = 0; j < W; ++j) S[j] = 0.0f;
                         body::bwd_sum<W, false>(gd.col, gd.row_ptr[v], gd.row_ptr[v + 1], ufs, Fs, Cs, f, s_u[wib], s_nz[wib], lane, S);
-                        body::finalize_dep<W, false>(sigma, Cl, target, v, f, S, lane);
+                        asm volatile("cp.async.wait_group 0;" ::: "memory");
+                        __syncwarp();
+                        body::finalize_dep<W, false>(sigma, Cl, target, v, f, S, lane, &s_sig[wib][0][0]);
+                        __syncwarp();  // the next vertex's copies overwrite s_sig
                     }
                 }
                 __syncthreads();

@@ -631,7 +631,8 @@ __device__ __forceinline__ float sigma_f32(uint64_t x) {
 template <int W, bool ALL_WORDS = true>
 __device__ __forceinline__ void finalize_dep(const uint64_t *sigma, const uint16_t *Sl, bool ones, float *Cl,
                                              double *bc, int v, const uint32_t (&f)[W], const float (&S)[W],
-                                             int lane, const uint16_t *Ssh = nullptr) {
+                                             int lane, const uint16_t *Ssh = nullptr,
+                                             const uint64_t *Ssig = nullptr) {
     constexpr int B = 32 * W;
     float hi = 0.0f, lo = 0.0f;  // the running sum hi + lo, carried without rounding loss
 #pragma unroll
@@ -641,7 +642,8 @@ __device__ __forceinline__ void finalize_dep(const uint64_t *sigma, const uint16
         if ((f[j] >> lane) & 1u) {
             const float sg = ones ? 1.0f
                                   : (Ssh ? __uint2float_rn((uint32_t)Ssh[32 * j + lane])
-                                         : (Sl ? __uint2float_rn((uint32_t)Sl[idx]) : sigma_f32(sigma[idx])));
+                                         : (Ssig ? sigma_f32(Ssig[32 * j + lane])
+                                                 : (Sl ? __uint2float_rn((uint32_t)Sl[idx]) : sigma_f32(sigma[idx]))));
             const float d = sg * S[j];        // delta_s(v) = sigma_s(v) * sum_w c_s(w)
             c = __fdividef(1.0f, sg) + S[j];  // c_s(v) for the level above (1/sigma within 2 ulp)
             two_sum_add(hi, lo, d);
@@ -660,8 +662,9 @@ __device__ __forceinline__ void finalize_dep(const uint64_t *sigma, const uint16
 
 template <int W, bool ALL_WORDS = true>
 __device__ __forceinline__ void finalize_dep(const uint64_t *sigma, float *Cl, double *bc, int v,
-                                             const uint32_t (&f)[W], const float (&S)[W], int lane) {
-    finalize_dep<W, ALL_WORDS>(sigma, nullptr, false, Cl, bc, v, f, S, lane);
+                                             const uint32_t (&f)[W], const float (&S)[W], int lane,
+                                             const uint64_t *Ssig = nullptr) {
+    finalize_dep<W, ALL_WORDS>(sigma, nullptr, false, Cl, bc, v, f, S, lane, nullptr, Ssig);
 }
 
 }  // namespace body
