@@ -134,3 +134,23 @@ def test_dense_limb_sums_stay_exact(nat):
     g = G.csr_from_edges(top + 1, np.concatenate(us), np.concatenate(vs), name="fan_15_2000")
     src = np.ascontiguousarray(np.arange(g.n, dtype=np.int32)[::7])  # includes source 0
     check(nat, g, sources=src, rows=4)
+
+
+def test_dense_tensor_work_by_operand_type(nat):
+    """The forward's limb products run in e4m3 while a level's counts fit four
+    4-bit limbs, the backward's in bf16: bc_run_stats reports each. Level 1
+    -> 2 of G(300, 0.05) has all counts 1 (one e4m3 limb); the sparse
+    backward issues no bf16 work."""
+    g = G.gnp(300, 0.05, seed=3)
+    with nat.Graph.from_csr(g) as h:
+        h.run(flags=nat.BC_DENSE)
+        h.result()
+        bf, f8 = h.dense_flops_by_type()
+        npad = 384
+        assert f8 >= 2.0 * 128 * npad * npad * 3  # at least one e4m3 level for each of the 3 batches
+        assert bf >= 2.0 * 128 * 3 * npad * npad  # at least one bf16 backward level (3 parts)
+        assert h.dense_flops() == bf + f8
+        h.run(flags=nat.BC_DENSE | nat.BC_SPARSE_BACKWARD)
+        h.result()
+        bf2, f82 = h.dense_flops_by_type()
+        assert bf2 == 0.0 and f82 == f8
