@@ -771,9 +771,9 @@ bool make_map(CUtensorMap *m, void *base, uint64_t inner, uint64_t rows, uint32_
 
 template <int kN, int kK, bool kF8 = false>
 int dense_stages(int nl, bool bwd = false) {
-    // accumulators of at most 256 TMEM columns: two CTAs per SM (half the
-    // shared memory each), at most 128: three, so one CTA's epilogue overlaps
-    // the others' MMAs
+    // accumulators of at most 128 TMEM columns: three CTAs per SM, at most
+    // 256: two (so one CTA's epilogue overlaps the others' MMAs), more: one
+    // CTA with most of the shared memory in stages
     const int nacc = bwd ? kBwdAcc : nl;
     const int budget = nacc * kN <= 128 ? 66 * 1024 : (nacc * kN <= 256 ? 100 * 1024 : 200 * 1024);
     const int s = budget / (nl * x_tile<kK, kF8>() + a_tile<kN, kK, kF8>());
@@ -820,19 +820,20 @@ int dense_make_maps(DenseMaps *maps, __nv_bfloat16 *X, uint64_t xrows_total, __n
     return 0;
 }
 
-// Stage K of the forward and backward level kernels (the 128-vertex tile).
+// Stage K (elements) of the bf16 forward and backward level kernels.
 constexpr int kFwdK = 64;
 constexpr int kBwdK = 32;
-// Tile widths: the backward takes 256 vertices per CTA when npad allows (its
-// two accumulators fill TMEM: one CTA per SM, five K = 32 stages). The
-// one-limb forward measured the same at 256 as at 128, so it stays at 128
-// (kFwdX).
+// Backward tiles of 256 vertices when npad allows: its two accumulators fill
+// TMEM (one CTA per SM, five K = 32 stages), and the CTA's 8 warps split the
+// epilogue's columns in two.
 constexpr bool kBwdX = true;
+constexpr int kBwdXThreads = 256;
 // The forward's limb products in e4m3 with 4-bit limbs (kind::f8f6f4: one
 // byte per operand element and twice the bf16 rate) while the level's counts
-// need at most four of them (below 2^16); bf16 8-bit limbs otherwise
+// need at most four of them (below 2^16); bf16 8-bit limbs otherwise.
 constexpr bool kFwdF8 = true;
-constexpr int kBwdXThreads = 256;
+// A bf16 one-limb forward on 256-vertex tiles (kFwdXK elements per stage)
+// measured the same as on 128, so it is off.
 constexpr bool kFwdX = false;
 constexpr int kFwdXK = 64;
 
