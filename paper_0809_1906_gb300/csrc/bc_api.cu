@@ -1485,8 +1485,9 @@ int sm_count_host() {
 }
 
 // Weighted path: waves of one CTA per source (csrc/sssp_weighted.cu).
-// opt->batch (if set) is the wave size; default 4 CTAs per SM, capped so the
-// wave state stays within 8 GiB.
+// opt->batch (if set) is the wave size; default one CTA per SM (more sources
+// in flight only add random DRAM sectors: measured 1 / 2 / 4 per SM 316 / 329
+// / 325 ms on the 512x512 grid), capped so the wave state stays within 8 GiB.
 // Weighted sweep: waves of G sources (one CTA each, packed state) on
 // kWeightedLanes lanes: wave k runs on lane k % lanes, each with its own stream,
 // state, delta rows and BC accumulator, so one wave's slowest sources overlap
@@ -1509,7 +1510,7 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
     int C = (int)std::min<int64_t>(std::max<int64_t>(1024, (4ll << 20) / K / 4), (int64_t)n + 1);
     C = std::max(C, 64);
     const size_t per_src = (size_t)n * (4 + 8 + 4 + 4 + 4 + 4 + 8) + 4 + (size_t)K * C * 4;
-    int G = (opt && opt->batch > 0) ? opt->batch : 4 * sm_count_host();
+    int G = (opt && opt->batch > 0) ? opt->batch : sm_count_host();
     G = (int)std::min<size_t>((size_t)G, std::max<size_t>(1, (8ull << 30) / per_src));
     G = std::max(1, std::min(G, std::max(nsrc, 1)));
     const int32_t nwaves = (nsrc + G - 1) / G;
@@ -2143,8 +2144,8 @@ int bc_autotune(bc_graph *g, int32_t sample, bc_options *out, void *cuda_stream)
         return BC_OK;
     };
     if (g->weighted) {
-        // sources per wave of the bucket kernel: 2, 4 or 8 per SM
-        for (int per : {2, 4, 8}) {
+        // sources per wave of the bucket kernel: 1, 2 or 4 per SM
+        for (int per : {1, 2, 4}) {
             bc_options o{};
             o.flags = BC_NO_HASH;
             o.batch = per * sm_count_host();

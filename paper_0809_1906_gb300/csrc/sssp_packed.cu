@@ -30,7 +30,7 @@ constexpr uint32_t kDInf = 0x7fffffffu;
 struct PSmem {
     int32_t cnt[kMaxRing];
     uint32_t ovf[kMaxRing / 32];
-    int32_t nset;
+    int32_t nset[2];  // vertices settled in the current step, by step parity
     int32_t pending;
     int32_t ngroups;
     uint32_t flags;  // 1: sigma overflowed 32 bits
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kPBlk, 4) k_wsssp_packed(const WParams p) {
     for (int b = tid; b < p.K; b += kPBlk) sm.cnt[b] = 0;
     for (int b = tid; b < kMaxRing / 32; b += kPBlk) sm.ovf[b] = 0u;
     if (tid == 0) {
-        sm.nset = 0;
+        sm.nset[0] = sm.nset[1] = 0;
         sm.pending = 0;
         sm.ngroups = 0;
         sm.flags = 0u;
@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(kPBlk, 4) k_wsssp_packed(const WParams p) {
     bool big = false;  // a count reached 2^32
     int32_t done = 0;
     int32_t d = 0;
+    int par = 0;  // parity of the non-empty steps (which settled counter is live)
     while (sm.pending > 0) {
         const int b = d % p.K;
         const int cnt = sm.cnt[b];
@@ -98,26 +99,12 @@ __global__ void __launch_bounds__(kPBlk, 4) k_wsssp_packed(const WParams p) {
             ++d;
             continue;
         }
-        __syncthreads();
-        if (!spill) {
-            for (int k = tid; k < cnt; k += kPBlk) {
-                const int v = __ldcg(slots + (size_t)b * p.C + k);
-                if (pd(__ldcg(ds + v)) == (uint32_t)d) order[done + atomicAdd(&sm.nset, 1)] = v;
-            }
-        } else {
-            for (int v = tid; v < n; v += kPBlk)
-                if (pd(__ldcg(ds + v)) == (uint32_t)d) order[done + atomicAdd(&sm.nset, 1)] = v;
-        }
-        __syncthreads();
-        const int k = sm.nset;
-        if (tid == 0) {
-            sm.cnt[b] = 0;
-            atomicAnd(&sm.ovf[b >> 5], ~(1u << (b & 31)));
-            atomicSub(&sm.pending, cnt);
-            if (k > 0) grp[sm.ngroups++] = done;
-        }
-        for (int t = tid; t < k; t += kPBlk) {
-            const int v = order[done + t];
+        // every settled vertex (tentative distance d is final) is relaxed by
+        // the thread that found it: the push only fires on a strict decrease,
+        // so a vertex sits once in its final bucket; its predecessors were all
+        // settled at smaller distances; pushes go to other buckets (w >= 1,
+        // the ring is wider than the largest weight)
+        auto settle = [&](const int v) {
             uint32_t s = v == src ? 1u : 0u;
             if (p.col_in) {
                 // directed: sigma over v's in-arcs (their tails below d are final)
@@ -176,10 +163,33 @@ __global__ void __launch_bounds__(kPBlk, 4) k_wsssp_packed(const WParams p) {
                 }
             }
             atomicOr(ds + v, (unsigned long long)s);  // settled: sigma into the low half
+        };
+        if (!spill) {
+            for (int k = tid; k < cnt; k += kPBlk) {
+                const int v = __ldcg(slots + (size_t)b * p.C + k);
+                if (pd(__ldcg(ds + v)) == (uint32_t)d) {
+                    order[done + atomicAdd(&sm.nset[par], 1)] = v;
+                    settle(v);
+                }
+            }
+        } else {
+            for (int v = tid; v < n; v += kPBlk)
+                if (pd(__ldcg(ds + v)) == (uint32_t)d) {
+                    order[done + atomicAdd(&sm.nset[par], 1)] = v;
+                    settle(v);
+                }
         }
         __syncthreads();
+        const int k = sm.nset[par];
+        if (tid == 0) {
+            sm.cnt[b] = 0;
+            atomicAnd(&sm.ovf[b >> 5], ~(1u << (b & 31)));
+            atomicSub(&sm.pending, cnt);
+            if (k > 0) grp[sm.ngroups++] = done;
+            sm.nset[par ^ 1] = 0;  // the next step's counter (nobody reads it in this one)
+        }
         done += k;
-        if (tid == 0) sm.nset = 0;
+        par ^= 1;
         ++d;
         __syncthreads();
     }
