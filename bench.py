@@ -532,13 +532,14 @@ def cfg_pairs(c):
 
 CONFIGS = {"er1024": cfg_er1024, "grid": cfg_grid, "gnp": cfg_gnp, "many": cfg_many,
            "directed": cfg_directed, "wdense": cfg_wdense, "pairs": cfg_pairs}
-# the configurations measured beside the R-MAT line by default (BASELINE's
-# other configurations); the others on request with --workload
+# the workloads measured beside the R-MAT line by default (ER n=1024, the
+# weighted grid, G(8192, 0.05), the 2000-graph set); the others on request
+# with --workload
 DEFAULT_EXTRA = ("er1024", "grid", "gnp", "many")
 
 
 def run_extra(args):
-    """One other configuration as its own JSON line (not the driver's line)."""
+    """One other configuration as its own JSON line (not the default line)."""
     c = Ctx(args, args.cpu_seconds)
     fn = CONFIGS[args.workload]
     line = fn(c, full=True) if args.workload == "gnp" else fn(c)
@@ -548,7 +549,7 @@ def run_extra(args):
 
 
 def run_profile(args):
-    """Profiling driver: one run of one workload's hot path on its first
+    """Profiling mode: one run of one workload's hot path on its first
     --sources sources (default one batch of 256 on one lane: a small case for
     ncu), nothing else."""
     import torch
@@ -601,7 +602,7 @@ def main():
     ap.add_argument("--err-sources", type=int, default=1024,
                     help="sources of the R-MAT sample compared with the FP64 oracle")
     ap.add_argument("--profile", action="store_true",
-                    help="profiling driver: one bc_run over the first --sources sources (default 256), nothing else")
+                    help="profiling mode: one bc_run over the first --sources sources (default 256), nothing else")
     ap.add_argument("--sources", type=int, default=0)
     ap.add_argument("--nmax", type=int, default=1000, help="--profile --workload many: largest graph")
     ap.add_argument("--batch", type=int, default=BATCH)
