@@ -36,7 +36,9 @@
  *     buffers are kept for the next graphs created on the same device;
  *     bc_release_cached_memory frees the cached blocks, and an allocation that
  *     fails frees them and retries. Caller buffers stay owned by the caller.
- *   - A graph handle may be used by one thread at a time.
+ *   - A graph handle may be used by one thread at a time. It lives on the
+ *     device that is current when it is created, and every call on it
+ *     (bc_destroy_graph included) must be made with that device current.
  *   - With the environment variable BC_LOG=1, bc_result writes one JSON line
  *     per completed run to stderr (sizes, options, launches, host wall time
  *     from bc_run to bc_result, edges/s, status bits).
