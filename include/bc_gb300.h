@@ -104,12 +104,17 @@ extern "C" {
                                 of lambda_sv lambda_vt / lambda_st. Needs sources = NULL, n <= 16384
                                 (12 n^2 bytes of rows plus 8 n^2 of scratch); unweighted or weighted,
                                 directed or not; not with BC_PLAIN / BC_DENSE. */
-#define BC_KEEP_ORDER 0x80u  /* batch the sources in the order given. By default (unweighted, batched,
-                                more than 32 sources) batches are formed from the sources sorted by
-                                their BFS distances to 32 landmark vertices, so the sources of one
-                                32-source word have similar distance profiles and the level sweep
-                                fetches fewer rows; BC differs only by FP64 summation order, and
-                                per-source summaries keep the caller's order. */
+#define BC_KEEP_ORDER 0x80u  /* run in the caller's source order and vertex numbering. By default
+                                (unweighted, batched, more than 32 sources) batches are formed from
+                                the sources sorted by their BFS distances to 32 landmark vertices, so
+                                the sources of one 32-source word have similar distance profiles and
+                                the level sweep fetches fewer rows; and the weighted sweep of an
+                                undirected graph runs on a copy of the graph renumbered by
+                                bc_vertex_order (built on first use, kept with the handle), so that
+                                neighbouring vertices share memory sectors. Either way BC differs
+                                only by floating-point summation order; distances, path counts,
+                                forward rows and per-source summaries are the same, in the caller's
+                                order and ids. */
 
 /* Test hook for the device-side timeout path (not for production runs):
    every staged-row wait of the level sweeps also expects 16 bytes that no
@@ -383,6 +388,21 @@ void bc_destroy_graph(bc_graph *g);
 /* Free the device blocks cached from destroyed handles (every device). Call
  * it with no library call in flight. */
 void bc_release_cached_memory(void);
+
+/* A vertex numbering with locality, from the CSR alone (host code; no GPU
+ * needed). Not part of the paper's method: it is the memory layout the
+ * weighted sweep uses for undirected graphs (see BC_KEEP_ORDER). Multilevel
+ * heavy-edge matching: each level matches every node, in id order, with the
+ * unmatched neighbour joined to it by the most edges; matched pairs become the
+ * next level's nodes. Vertices are then numbered by their ancestors, top level
+ * first, so each run of consecutive new ids is a connected cluster as a rule.
+ *   n                 vertices (>= 0)
+ *   row_ptr [n+1]     host, CSR row offsets (row_ptr[0] = 0, non-decreasing)
+ *   col [row_ptr[n]]  host, arc heads in [0, n)
+ *   perm [n]          host, written: perm[v] = the new id of v (a permutation)
+ * Deterministic. Returns BC_OK, or BC_ERR_ARG for a NULL pointer, n < 0, a
+ * malformed row_ptr or a head out of range (perm untouched). */
+int bc_vertex_order(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t *perm);
 
 /* Static text for a status code. */
 const char *bc_status_string(int status);

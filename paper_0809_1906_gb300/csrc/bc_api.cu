@@ -360,6 +360,13 @@ struct bc_graph {
     std::vector<int32_t> h_sources;  // host copy of the staged source list
     DevBuf<uint64_t> wsigma;
     DevBuf<float> wcval, wrows;
+    // the weighted sweep's relabelled copy of an undirected graph (built on
+    // first use): the CSR in a numbering with locality, old -> new ids
+    // (wperm, also on the host) and new -> old (wvid), and a run's sources
+    // in the new numbering
+    bool relabel_ok = false;
+    std::vector<int32_t> h_wperm;
+    DevBuf<int32_t> prow_ptr, pcol, pw, wperm, wvid, wpsrc;
     // lanes 1..3 of the weighted waves: stream, packed state, rows, BC accumulator
     struct WLane {
         cudaStream_t st = nullptr;
@@ -427,6 +434,7 @@ void free_graph(bc_graph *g) {
     g->dX.release();
     g->dctl.release();
     for (auto *b : {&g->wdist, &g->worder, &g->wgrp, &g->wslots}) b->release();
+    for (auto *b : {&g->prow_ptr, &g->pcol, &g->pw, &g->wperm, &g->wvid, &g->wpsrc}) b->release();
     g->wsigma.release();
     g->wcval.release();
     g->wrows.release();
@@ -1485,9 +1493,11 @@ int sm_count_host() {
 }
 
 // Weighted path: waves of one CTA per source (csrc/sssp_weighted.cu).
-// opt->batch (if set) is the wave size; default one CTA per SM (more sources
-// in flight only add random DRAM sectors: measured 1 / 2 / 4 per SM 316 / 329
-// / 325 ms on the 512x512 grid), capped so the wave state stays within 8 GiB.
+// opt->batch (if set) is the wave size; default two CTAs per SM (on the
+// relabelled 512x512 grid, 1 / 2 / 4 per SM measured 274 / 256 / 255 ms; on
+// the caller's row-major numbering 316 / 329 / 325 ms, where more sources in
+// flight only add random DRAM sectors), capped so the wave state stays within
+// 8 GiB.
 // Weighted sweep: waves of G sources (one CTA each, packed state) on
 // kWeightedLanes lanes: wave k runs on lane k % lanes, each with its own stream,
 // state, delta rows and BC accumulator, so one wave's slowest sources overlap
@@ -1498,6 +1508,50 @@ int sm_count_host() {
 // they are flagged and computed again at the end by the 64-bit kernel, whose
 // delta rows are added in the order of the flagged sources.
 constexpr int kWeightedLanes = 2;  // measured: 3 or 4 lanes no faster on the 512x512 grid
+
+// The relabelled copy of an undirected weighted graph (relabel.cu's
+// numbering): vertex v becomes wperm[v]; its arcs keep their weights, heads
+// renumbered and sorted. Built once per handle; host code plus uploads.
+int ensure_relabel(bc_graph *g) {
+    if (g->relabel_ok) return BC_OK;
+    const int32_t n = g->n;
+    const int64_t m2 = g->narcs;
+    std::vector<int32_t> cl, ww;
+    CK(fetch(cl, (const int32_t *)g->col.p, (size_t)m2));
+    CK(fetch(ww, (const int32_t *)g->w.p, (size_t)m2));
+    const std::vector<int32_t> &rp = g->h_row_ptr;
+    std::vector<int32_t> perm((size_t)n), vid((size_t)n);
+    bcgb::locality_order(n, rp.data(), cl.data(), perm.data());
+    for (int32_t v = 0; v < n; ++v) vid[(size_t)perm[v]] = v;
+    std::vector<int32_t> prp((size_t)n + 1, 0), pcl((size_t)m2), pww((size_t)m2);
+    std::vector<std::pair<int32_t, int32_t>> row;
+    for (int32_t x = 0; x < n; ++x) {
+        const int32_t v = vid[(size_t)x];
+        row.clear();
+        for (int64_t e = rp[v]; e < rp[(size_t)v + 1]; ++e) row.emplace_back(perm[(size_t)cl[(size_t)e]], ww[(size_t)e]);
+        std::sort(row.begin(), row.end());
+        const int32_t at = prp[(size_t)x];
+        for (size_t i = 0; i < row.size(); ++i) {
+            pcl[(size_t)at + i] = row[i].first;
+            pww[(size_t)at + i] = row[i].second;
+        }
+        prp[(size_t)x + 1] = at + (int32_t)row.size();
+    }
+    auto up = [&](DevBuf<int32_t> &d, const std::vector<int32_t> &h) -> int {
+        CK(d.ensure(h.size()));
+        if (!h.empty()) CK(cudaMemcpy(d.p, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        return BC_OK;
+    };
+    int r = up(g->prow_ptr, prp);
+    if (!r) r = up(g->pcol, pcl);
+    if (!r) r = up(g->pw, pww);
+    if (!r) r = up(g->wperm, perm);
+    if (!r) r = up(g->wvid, vid);
+    if (r) return r;
+    g->h_wperm.swap(perm);
+    g->relabel_ok = true;
+    return BC_OK;
+}
 constexpr double kWeightedLaneBudget = 24.0 * (1 << 30);  // packed wave state of all lanes
 
 int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t st, bool backward, bool hash,
@@ -1510,7 +1564,7 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
     int C = (int)std::min<int64_t>(std::max<int64_t>(1024, (4ll << 20) / K / 4), (int64_t)n + 1);
     C = std::max(C, 64);
     const size_t per_src = (size_t)n * (4 + 8 + 4 + 4 + 4 + 4 + 8) + 4 + (size_t)K * C * 4;
-    int G = (opt && opt->batch > 0) ? opt->batch : sm_count_host();
+    int G = (opt && opt->batch > 0) ? opt->batch : 2 * sm_count_host();
     G = (int)std::min<size_t>((size_t)G, std::max<size_t>(1, (8ull << 30) / per_src));
     G = std::max(1, std::min(G, std::max(nsrc, 1)));
     const int32_t nwaves = (nsrc + G - 1) / G;
@@ -1536,6 +1590,19 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
     }
     CK(g->wredo.ensure((size_t)std::max(nsrc, 1)));
     CK(cudaMemsetAsync(g->wredo.p, 0, (size_t)std::max(nsrc, 1), st));
+    // undirected graphs run on the relabelled copy (BC_KEEP_ORDER: on the
+    // caller's numbering): sources mapped in, summaries, rows and BC mapped
+    // back to the caller's ids by the kernels
+    const bool relabel = !g->directed && n > 1 && !(opt && (opt->flags & BC_KEEP_ORDER));
+    if (relabel) {
+        int r = ensure_relabel(g);
+        if (r) return r;
+        CK(g->wpsrc.ensure((size_t)std::max(nsrc, 1)));
+        Timer t(g, st, BC_KERNEL_INIT);
+        bcgb::launch_map_ids(g->wperm.p, g->sources.p, g->wpsrc.p, nsrc, st);
+    }
+    const int32_t *vid = relabel ? g->wvid.p : nullptr;
+    const int32_t *srcs = relabel ? g->wpsrc.p : g->sources.p;
     if (lanes > 1 && !g->wev) CK(cudaEventCreateWithFlags(&g->wev, cudaEventDisableTiming));
     if (lanes > 1) CK(cudaEventRecord(g->wev, st));
     for (int k = 1; k < lanes; ++k) {
@@ -1558,9 +1625,10 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
     base.K = K;
     base.C = C;
     base.dmax = (int32_t)std::min<int64_t>((int64_t)n * g->maxw, INT32_MAX - 1);
-    base.row_ptr = g->row_ptr.p;
-    base.col = g->col.p;
-    base.w = g->w.p;
+    base.row_ptr = relabel ? g->prow_ptr.p : g->row_ptr.p;
+    base.col = relabel ? g->pcol.p : g->col.p;
+    base.w = relabel ? g->pw.p : g->w.p;
+    base.vid = vid;
     if (g->directed) {
         base.row_ptr_in = g->row_ptr_in.p;
         base.col_in = g->col_in.p;
@@ -1574,7 +1642,7 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
         bc_graph::WLane *l = ln == 0 ? nullptr : &g->wl[ln - 1];
         const cudaStream_t ls = l ? l->st : st;
         bcgb::WParams p = base;
-        p.sources = g->sources.p + w0;
+        p.sources = srcs + w0;
         p.order = l ? l->order.p : g->worder.p;
         p.grp = l ? l->grp.p : g->wgrp.p;
         p.slots = l ? l->slots.p : g->wslots.p;
@@ -1596,7 +1664,7 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
         }
         if (backward) {
             Timer t(g, ls, BC_KERNEL_BACKWARD);
-            bcgb::w_launch_reduce(rows, nw, n, l ? l->bc.p : g->bc.p, sm_count_host(), ls);
+            bcgb::w_launch_reduce(rows, nw, n, vid, l ? l->bc.p : g->bc.p, sm_count_host(), ls);
         }
         CK(cudaGetLastError());
     }
@@ -1614,7 +1682,7 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
     for (int32_t i = 0; i < nsrc; ++i)
         if (redo[i]) {
             rpos.push_back(i);
-            rsrc.push_back(g->h_sources[(size_t)i]);
+            rsrc.push_back(relabel ? g->h_wperm[(size_t)g->h_sources[(size_t)i]] : g->h_sources[(size_t)i]);
         }
     for (size_t r0 = 0; r0 < rpos.size(); r0 += (size_t)G) {
         const int nr = (int)std::min<size_t>((size_t)G, rpos.size() - r0);
@@ -1644,7 +1712,7 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
         }
         if (backward) {
             Timer t(g, st, BC_KERNEL_BACKWARD);
-            bcgb::w_launch_reduce(g->wrows.p, nr, n, g->bc.p, sm_count_host(), st);
+            bcgb::w_launch_reduce(g->wrows.p, nr, n, vid, g->bc.p, sm_count_host(), st);
         }
         CK(cudaGetLastError());
     }
@@ -2196,6 +2264,20 @@ void bc_destroy_graph(bc_graph *g) {
 }
 
 void bc_release_cached_memory(void) { devcache::trim(-1); }
+
+int bc_vertex_order(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t *perm) {
+    g_err.clear();
+    if (n < 0) return fail(BC_ERR_ARG, "n < 0");
+    if (!row_ptr || !perm) return fail(BC_ERR_ARG, "row_ptr or perm is NULL");
+    if (row_ptr[0] != 0) return fail(BC_ERR_ARG, "row_ptr[0] != 0");
+    for (int32_t v = 0; v < n; ++v)
+        if (row_ptr[v + 1] < row_ptr[v]) return fail(BC_ERR_ARG, "row_ptr decreases");
+    if (row_ptr[n] > 0 && !col) return fail(BC_ERR_ARG, "col is NULL");
+    for (int64_t e = 0; e < row_ptr[n]; ++e)
+        if (col[e] < 0 || col[e] >= n) return fail(BC_ERR_ARG, "arc head out of range");
+    bcgb::locality_order(n, row_ptr, col, perm);
+    return BC_OK;
+}
 
 const char *bc_status_string(int status) {
     switch (status) {

@@ -205,8 +205,9 @@ __global__ void __launch_bounds__(kPBlk, 4) k_wsssp_packed(const WParams p) {
     for (int t = tid; t < done; t += kPBlk) {
         const int v = order[t];
         const unsigned long long x = ds[v];
-        hs += (unsigned long long)pl(x) * (unsigned long long)(v + 1);
-        hd += (unsigned long long)(pd(x) + 1) * (unsigned long long)(v + 1);
+        const unsigned long long id1 = (unsigned long long)(p.vid ? p.vid[v] : v) + 1ull;  // the caller's id + 1
+        hs += (unsigned long long)pl(x) * id1;
+        hd += (unsigned long long)(pd(x) + 1) * id1;
         dsum += pd(x);
         rc += 1ull;
     }
@@ -214,8 +215,9 @@ __global__ void __launch_bounds__(kPBlk, 4) k_wsssp_packed(const WParams p) {
         for (int v = tid; v < n; v += kPBlk) {
             const unsigned long long x = ds[v];
             const bool r = pd(x) != kDInf;
-            if (p.rows_dist) p.rows_dist[(size_t)o * n + v] = r ? (int32_t)pd(x) : -1;
-            if (p.rows_sigma) p.rows_sigma[(size_t)o * n + v] = r ? (unsigned long long)pl(x) : 0ull;
+            const size_t at = (size_t)o * n + (size_t)(p.vid ? p.vid[v] : v);
+            if (p.rows_dist) p.rows_dist[at] = r ? (int32_t)pd(x) : -1;
+            if (p.rows_sigma) p.rows_sigma[at] = r ? (unsigned long long)pl(x) : 0ull;
         }
     }
 #pragma unroll

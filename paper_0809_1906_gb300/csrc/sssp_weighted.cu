@@ -211,16 +211,18 @@ __global__ void __launch_bounds__(kWBlock, 4) k_wsssp(const WParams p) {
         const int v = order[t];
         const int dv = dist[v];
         const uint64_t sg = sigma[v];
-        hs += sg * (unsigned long long)(v + 1);
-        hd += (unsigned long long)(dv + 1) * (unsigned long long)(v + 1);
+        const unsigned long long id1 = (unsigned long long)(p.vid ? p.vid[v] : v) + 1ull;  // the caller's id + 1
+        hs += sg * id1;
+        hd += (unsigned long long)(dv + 1) * id1;
         ds += (unsigned long long)dv;
         rc += 1ull;
     }
     if (p.rows_dist || p.rows_sigma) {
         for (int v = tid; v < n; v += kWBlock) {
             const int dv = dist[v];
-            if (p.rows_dist) p.rows_dist[(size_t)o * n + v] = dv == kInf ? -1 : dv;
-            if (p.rows_sigma) p.rows_sigma[(size_t)o * n + v] = dv == kInf ? 0ull : sigma[v];
+            const size_t at = (size_t)o * n + (size_t)(p.vid ? p.vid[v] : v);
+            if (p.rows_dist) p.rows_dist[at] = dv == kInf ? -1 : dv;
+            if (p.rows_sigma) p.rows_sigma[at] = dv == kInf ? 0ull : sigma[v];
         }
     }
 #pragma unroll
@@ -292,11 +294,11 @@ __global__ void __launch_bounds__(kWBlock, 4) k_wsssp(const WParams p) {
 
 // BC(v) += sum over the wave's rows in row order (FP64).
 __global__ void __launch_bounds__(256) k_wreduce(const float *__restrict__ rows, int32_t nrows, int32_t n,
-                                                 double *__restrict__ bc) {
+                                                 const int32_t *__restrict__ vid, double *__restrict__ bc) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         double acc = 0.0;
         for (int r = 0; r < nrows; ++r) acc += (double)rows[(size_t)r * n + v];
-        bc[v] += acc;
+        bc[vid ? vid[v] : v] += acc;
     }
 }
 
@@ -306,10 +308,11 @@ void w_launch_wave(const WParams &p, int nsrc, cudaStream_t st) {
     k_wsssp<<<nsrc, kWBlock, 0, st>>>(p);
 }
 
-void w_launch_reduce(const float *rows, int nrows, int n, double *bc, int sms, cudaStream_t st) {
+void w_launch_reduce(const float *rows, int nrows, int n, const int32_t *vid, double *bc, int sms,
+                     cudaStream_t st) {
     int g = (n + 255) / 256;
     g = g > 4 * sms ? 4 * sms : (g < 1 ? 1 : g);
-    k_wreduce<<<g, 256, 0, st>>>(rows, nrows, n, bc);
+    k_wreduce<<<g, 256, 0, st>>>(rows, nrows, n, vid, bc);
 }
 
 }  // namespace bcgb

@@ -23,6 +23,8 @@ struct WParams {
     const int32_t *w_in;
     const int32_t *w;
     const int32_t *sources;  // this wave's sources
+    const int32_t *vid;      // the caller's id of each vertex when the graph was relabelled (null: the same);
+                             // summaries and rows use the caller's ids
     const int32_t *pos;      // position of each CTA's source in the summaries and rows (null: its index);
                              // delta rows are always at the CTA's index
     uint64_t *ds;            // [wave][n] packed state (distance << 32 | sigma or c bits)
@@ -45,6 +47,8 @@ struct WParams {
 
 void w_launch_wave(const WParams &p, int nsrc, cudaStream_t st);         // 64-bit counts
 void w_launch_wave_packed(const WParams &p, int nsrc, cudaStream_t st);  // packed state, 32-bit counts
-void w_launch_reduce(const float *rows, int nrows, int n, double *bc, int sms, cudaStream_t st);
+// bc[vid[v]] += the FP64 sum over r < nrows of rows[r][v], rows in order (vid null: bc[v])
+void w_launch_reduce(const float *rows, int nrows, int n, const int32_t *vid, double *bc, int sms,
+                     cudaStream_t st);
 
 }  // namespace bcgb

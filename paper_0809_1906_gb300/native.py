@@ -56,7 +56,7 @@ KERNEL_NAMES = {0: "init", 1: "forward", 2: "backward", 3: "hash", 4: "plain", 5
 # every entry point include/bc_gb300.h declares
 EXPORTS = ["bc_create_graph", "bc_run", "bc_result", "bc_source_hashes", "bc_forward_rows",
            "bc_kernel_time", "bc_kernel_trace", "bc_run_stats", "bc_launch_count", "bc_graph_size", "bc_destroy_graph",
-           "bc_release_cached_memory",
+           "bc_release_cached_memory", "bc_vertex_order",
            "bc_status_string", "bc_last_error", "bc_run_noalloc", "bc_autotune", "bc_set_default_options",
            "bc_last_options",
            "bc_many_create", "bc_many_run", "bc_many_result", "bc_many_stats", "bc_many_destroy", "bc_run_many"]
@@ -109,6 +109,7 @@ def load(build_if_needed: bool = True, require_gpu: bool = True):
             "bc_graph_size": (i32, [P, P, P, P]),
             "bc_destroy_graph": (None, [P]),
             "bc_release_cached_memory": (None, []),
+            "bc_vertex_order": (i32, [i32, P, P, P]),
             "bc_status_string": (ctypes.c_char_p, [i32]),
             "bc_last_error": (ctypes.c_char_p, []),
             "bc_run_noalloc": (i32, [i32, P, P, P, i32, P, P]),
@@ -363,6 +364,23 @@ class ManyPlan:
 def release_cached_memory() -> None:
     """Free the device blocks kept from destroyed graph handles."""
     load().bc_release_cached_memory()
+
+
+def vertex_order(n: int, row_ptr, col) -> np.ndarray:
+    """bc_vertex_order: perm[v] = v's id in the numbering with locality that the
+    weighted sweep runs on (host code; no GPU needed)."""
+    _build.build()
+    lib = ctypes.CDLL(_build.LIB)  # a host-only call: not the cached handle, which demands a GPU
+    lib.bc_vertex_order.restype = ctypes.c_int32
+    lib.bc_vertex_order.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    perm = np.empty(max(n, 0), dtype=np.int32)
+    code = lib.bc_vertex_order(int(n), _addr(rp), _addr(cl) if cl.size else None, _addr(perm))
+    if code != BC_OK:
+        lib.bc_last_error.restype = ctypes.c_char_p
+        raise BcError(code, "bc_vertex_order", lib.bc_last_error().decode())
+    return perm
 
 
 def betweenness(g, sources=None, batch=0, flags=0, stream=None):

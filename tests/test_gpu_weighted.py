@@ -26,10 +26,12 @@ def assert_bc_close(got, ref, n, what=""):
     return float(np.max(err / np.maximum(np.abs(ref), 1.0)))
 
 
-def check(nat, g, sources=None, batch=0, rows=8):
+def check(nat, g, sources=None, batch=0, rows=8, flags=0):
+    """The default run (an undirected graph runs on its relabelled copy) or,
+    with BC_KEEP_ORDER, the caller's numbering: against the oracle."""
     ref = oracle.bc(g, sources)
     with nat.Graph.from_csr(g) as h:
-        h.run(sources, batch=batch)
+        h.run(sources, batch=batch, flags=flags)
         got, code, _ = h.result()
         ns = g.n if sources is None else len(sources)
         hs = h.source_hashes(ns)
@@ -41,7 +43,7 @@ def check(nat, g, sources=None, batch=0, rows=8):
         if rows:
             src = np.arange(g.n, dtype=np.int32) if sources is None else np.asarray(sources, np.int32)
             pick = src[:rows]
-            sig, dist, _ = h.forward_rows(pick)
+            sig, dist, _ = h.forward_rows(pick, flags=flags)
             for i, s in enumerate(pick.tolist()):
                 o = oracle.source(g, s, with_delta=False)
                 assert np.array_equal(dist[i], o["dist"].astype(np.int32)), (g.name, s)
@@ -54,6 +56,36 @@ def test_small_weighted_ties(nat, seed):
     n = [9, 20, 50, 120, 333, 600, 1000, 64][seed]
     g = G.random_small(n, min(0.5, 4.0 / n), 1200 + seed, wmax=3, connect=seed % 3 != 0)
     check(nat, g, batch=[0, 1, 7, 64][seed % 4])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_caller_numbering_matches_oracle(nat, seed):
+    """BC_KEEP_ORDER keeps the caller's vertex ids on the weighted sweep."""
+    n = [50, 333, 1000, 64][seed]
+    g = G.random_small(n, min(0.5, 4.0 / n), 1300 + seed, wmax=3, connect=seed % 2 == 0)
+    check(nat, g, batch=[0, 7][seed % 2], flags=nat.BC_KEEP_ORDER)
+
+
+def test_relabelled_and_caller_numbering_agree(nat):
+    """Both numberings give the same rows and summaries bit for bit; BC only
+    differs by summation order."""
+    big = G.grid_longrange(side=96, frac=0.05, wmax=100, seed=77)
+    src = G.sample_sources(big.n, 300, 5)
+    with nat.Graph.from_csr(big) as h:
+        out = {}
+        for fl in (0, nat.BC_KEEP_ORDER):
+            h.run(src, flags=fl)
+            bc, code, _ = h.result()
+            hs = h.source_hashes(len(src))
+            sig, dist, _ = h.forward_rows(src[:16], flags=fl)
+            out[fl] = (bc, hs, sig, dist)
+        a, b = out[0], out[nat.BC_KEEP_ORDER]
+        for k in ("hash_sigma", "hash_dist", "reach"):
+            assert np.array_equal(a[1][k], b[1][k]), k
+        assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
+        assert_bc_close(a[0], b[0], big.n, "relabelled vs caller numbering")
+    ref = oracle.bc(big, src)
+    assert_bc_close(a[0], ref["bc"], big.n, "relabelled vs oracle")
 
 
 def test_uniform_weight_equals_unweighted(nat):
