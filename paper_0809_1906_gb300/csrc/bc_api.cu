@@ -1493,11 +1493,11 @@ int sm_count_host() {
 }
 
 // Weighted path: waves of one CTA per source (csrc/sssp_weighted.cu).
-// opt->batch (if set) is the wave size; default two CTAs per SM (on the
-// relabelled 512x512 grid, 1 / 2 / 4 per SM measured 274 / 256 / 255 ms; on
-// the caller's row-major numbering 316 / 329 / 325 ms, where more sources in
-// flight only add random DRAM sectors), capped so the wave state stays within
-// 8 GiB.
+// opt->batch (if set) is the wave size; default three sources per SM, two of
+// them resident (512-thread CTAs: on the relabelled 512x512 grid 1 / 2 / 3 / 4
+// per SM measured 258 / 257 / 241 / 252 ms, with 256-thread CTAs 274 / 255 /
+// 253 / 256; on the caller's row-major numbering more sources in flight only
+// added random DRAM sectors), capped so the wave state stays within 8 GiB.
 // Weighted sweep: waves of G sources (one CTA each, packed state) on
 // kWeightedLanes lanes: wave k runs on lane k % lanes, each with its own stream,
 // state, delta rows and BC accumulator, so one wave's slowest sources overlap
@@ -1564,7 +1564,7 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
     int C = (int)std::min<int64_t>(std::max<int64_t>(1024, (4ll << 20) / K / 4), (int64_t)n + 1);
     C = std::max(C, 64);
     const size_t per_src = (size_t)n * (4 + 8 + 4 + 4 + 4 + 4 + 8) + 4 + (size_t)K * C * 4;
-    int G = (opt && opt->batch > 0) ? opt->batch : 2 * sm_count_host();
+    int G = (opt && opt->batch > 0) ? opt->batch : 3 * sm_count_host();
     G = (int)std::min<size_t>((size_t)G, std::max<size_t>(1, (8ull << 30) / per_src));
     G = std::max(1, std::min(G, std::max(nsrc, 1)));
     const int32_t nwaves = (nsrc + G - 1) / G;
@@ -2212,8 +2212,8 @@ int bc_autotune(bc_graph *g, int32_t sample, bc_options *out, void *cuda_stream)
         return BC_OK;
     };
     if (g->weighted) {
-        // sources per wave of the bucket kernel: 1, 2 or 4 per SM
-        for (int per : {1, 2, 4}) {
+        // sources per wave of the bucket kernel: 1 to 4 per SM
+        for (int per : {1, 2, 3, 4}) {
             bc_options o{};
             o.flags = BC_NO_HASH;
             o.batch = per * sm_count_host();

@@ -23,7 +23,7 @@
 namespace bcgb {
 namespace {
 
-constexpr int kPBlk = 256;
+constexpr int kPBlk = 512;  // threads per source: faster than 128 or 256 on the relabelled 512x512 grid
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kDInf = 0x7fffffffu;
 
@@ -50,7 +50,7 @@ __device__ __forceinline__ void push(const WParams &p, PSmem &sm, int32_t *slots
         atomicOr(&sm.ovf[b >> 5], 1u << (b & 31));
 }
 
-__global__ void __launch_bounds__(kPBlk, 4) k_wsssp_packed(const WParams p) {
+__global__ void __launch_bounds__(kPBlk, 2) k_wsssp_packed(const WParams p) {
     __shared__ PSmem sm;
     const int i = blockIdx.x;
     const int o = p.pos ? p.pos[i] : i;  // output position
