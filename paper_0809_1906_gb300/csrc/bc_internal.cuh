@@ -132,11 +132,6 @@ void ms_launch_hash(int W, const MsParams &p, int nlevels, cudaStream_t st);
 void ms_launch_rows(int W, const MsParams &p, int nlevels, uint64_t *sig_out, int32_t *dist_out,
                     cudaStream_t st);
 void launch_scale(double *x, int32_t n, double f, cudaStream_t st);
-// relabel.cu: perm[v] = v's id in a numbering with locality (multilevel
-// heavy-edge matching over the CSR; host code), and out[i] = perm[in[i]]
-// for i < k on the device.
-void locality_order(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t *perm);
-void launch_map_ids(const int32_t *perm, const int32_t *in, int32_t *out, int32_t k, cudaStream_t st);
 // dst[i] += src[i] for i < n; unless from is null, to's status |= from's and
 // its arc and depth sums += from's
 void ms_launch_merge(const double *src, double *dst, int32_t n, const DevCtl *from, DevCtl *to, cudaStream_t st);

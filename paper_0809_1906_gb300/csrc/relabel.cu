@@ -26,7 +26,7 @@
 #include <cstdint>
 #include <vector>
 
-#include "bc_internal.cuh"
+#include "weighted.cuh"
 
 namespace bcgb {
 

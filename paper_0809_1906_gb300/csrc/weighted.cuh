@@ -45,6 +45,12 @@ struct WParams {
     DevCtl *ctl;
 };
 
+// relabel.cu: perm[v] = v's id in a numbering with locality (multilevel
+// heavy-edge matching over the CSR; host code), and out[i] = perm[in[i]]
+// for i < k on the device.
+void locality_order(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t *perm);
+void launch_map_ids(const int32_t *perm, const int32_t *in, int32_t *out, int32_t k, cudaStream_t st);
+
 void w_launch_wave(const WParams &p, int nsrc, cudaStream_t st);         // 64-bit counts
 void w_launch_wave_packed(const WParams &p, int nsrc, cudaStream_t st);  // packed state, 32-bit counts
 // bc[vid[v]] += the FP64 sum over r < nrows of rows[r][v], rows in order (vid null: bc[v])
