@@ -131,7 +131,8 @@ extern "C" {
  * uses the same defaults.
  *   batch          sources per batch for the unweighted multi-source path:
  *                  32, 64, 128 or 256 (0 = 256; BC_DENSE uses 128). For
- *                  weighted graphs: sources per wave (0 = 3 per SM).
+ *                  weighted graphs: sources per wave (0 = 8 per SM below
+ *                  131072 vertices, else 3 per SM).
  *   flags          BC_* option bits above.
  *   chunk          arcs per work item for high-degree vertices (0 = 256 in both
  *                  sweeps; a given value applies to both).
@@ -288,7 +289,7 @@ int bc_run_stats(bc_graph *g, int64_t *dag_arcs, int64_t *depth_sum, double *ten
  *              (0 = 2048) with CUDA events on cuda_stream, for every
  *              candidate: unweighted graphs, batch 64/128/256 x chunk
  *              128/256/512, then beta 1/256, 1/64, 1/16; weighted graphs,
- *              1/2/3/4 sources per SM per wave. The fastest becomes the
+ *              1/2/3/4/8 sources per SM per wave. The fastest becomes the
  *              handle's default (bc_run with opt = NULL uses it) and is copied
  *              to *out (may be NULL). The handle's previous result is
  *              overwritten. Errors: those of bc_run.

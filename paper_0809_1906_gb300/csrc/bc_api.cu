@@ -1493,11 +1493,12 @@ int sm_count_host() {
 }
 
 // Weighted path: waves of one CTA per source (csrc/sssp_weighted.cu).
-// opt->batch (if set) is the wave size; default three sources per SM, two of
-// them resident (512-thread CTAs: on the relabelled 512x512 grid 1 / 2 / 3 / 4
-// per SM measured 258 / 257 / 241 / 252 ms, with 256-thread CTAs 274 / 255 /
-// 253 / 256; on the caller's row-major numbering more sources in flight only
-// added random DRAM sectors), capped so the wave state stays within 8 GiB.
+// opt->batch (if set) is the wave size; default kWSmallPerSm sources per SM
+// for the 128-thread CTAs of small graphs, else three per SM, two of them
+// resident (512-thread CTAs: on the relabelled 512x512 grid 1 / 2 / 3 / 4 per
+// SM measured 258 / 257 / 241 / 252 ms, with 256-thread CTAs 274 / 255 / 253 /
+// 256; on the caller's row-major numbering more sources in flight only added
+// random DRAM sectors), capped so the wave state stays within 8 GiB.
 // Weighted sweep: waves of G sources (one CTA each, packed state) on
 // kWeightedLanes lanes: wave k runs on lane k % lanes, each with its own stream,
 // state, delta rows and BC accumulator, so one wave's slowest sources overlap
@@ -1508,6 +1509,7 @@ int sm_count_host() {
 // they are flagged and computed again at the end by the 64-bit kernel, whose
 // delta rows are added in the order of the flagged sources.
 constexpr int kWeightedLanes = 2;  // measured: 3 or 4 lanes no faster on the 512x512 grid
+constexpr int kWSmallPerSm = 8;    // wave of the 128-thread CTAs (small graphs), per SM: all resident
 
 // The relabelled copy of an undirected weighted graph (relabel.cu's
 // numbering): vertex v becomes wperm[v]; its arcs keep their weights, heads
@@ -1564,7 +1566,8 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
     int C = (int)std::min<int64_t>(std::max<int64_t>(1024, (4ll << 20) / K / 4), (int64_t)n + 1);
     C = std::max(C, 64);
     const size_t per_src = (size_t)n * (4 + 8 + 4 + 4 + 4 + 4 + 8) + 4 + (size_t)K * C * 4;
-    int G = (opt && opt->batch > 0) ? opt->batch : 3 * sm_count_host();
+    const int per_sm = bcgb::w_packed_threads(n) == 128 ? kWSmallPerSm : 3;
+    int G = (opt && opt->batch > 0) ? opt->batch : per_sm * sm_count_host();
     G = (int)std::min<size_t>((size_t)G, std::max<size_t>(1, (8ull << 30) / per_src));
     G = std::max(1, std::min(G, std::max(nsrc, 1)));
     const int32_t nwaves = (nsrc + G - 1) / G;
@@ -2212,8 +2215,8 @@ int bc_autotune(bc_graph *g, int32_t sample, bc_options *out, void *cuda_stream)
         return BC_OK;
     };
     if (g->weighted) {
-        // sources per wave of the bucket kernel: 1 to 4 per SM
-        for (int per : {1, 2, 3, 4}) {
+        // sources per wave of the bucket kernel: 1 to 4 or 8 per SM
+        for (int per : {1, 2, 3, 4, 8}) {
             bc_options o{};
             o.flags = BC_NO_HASH;
             o.batch = per * sm_count_host();

@@ -23,7 +23,6 @@
 namespace bcgb {
 namespace {
 
-constexpr int kPBlk = 512;  // threads per source: faster than 128 or 256 on the relabelled 512x512 grid
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kDInf = 0x7fffffffu;
 
@@ -34,7 +33,7 @@ struct PSmem {
     int32_t pending;
     int32_t ngroups;
     uint32_t flags;  // 1: sigma overflowed 32 bits
-    unsigned long long red[4][kPBlk / 32];
+    unsigned long long red[4][32];  // one slot per warp (up to 1024 threads)
 };
 
 __device__ __forceinline__ uint32_t pd(uint64_t x) { return (uint32_t)(x >> 32); }
@@ -50,7 +49,9 @@ __device__ __forceinline__ void push(const WParams &p, PSmem &sm, int32_t *slots
         atomicOr(&sm.ovf[b >> 5], 1u << (b & 31));
 }
 
-__global__ void __launch_bounds__(kPBlk, 2) k_wsssp_packed(const WParams p) {
+// kPBlk threads per source (w_packed_threads)
+template <int kPBlk>
+__global__ void __launch_bounds__(kPBlk, 1024 / kPBlk) k_wsssp_packed(const WParams p) {
     __shared__ PSmem sm;
     const int i = blockIdx.x;
     const int o = p.pos ? p.pos[i] : i;  // output position
@@ -286,8 +287,13 @@ __global__ void __launch_bounds__(kPBlk, 2) k_wsssp_packed(const WParams p) {
 
 }  // namespace
 
+int w_packed_threads(int32_t n) { return n < kWSmallN ? 128 : 512; }
+
 void w_launch_wave_packed(const WParams &p, int nsrc, cudaStream_t st) {
-    k_wsssp_packed<<<nsrc, kPBlk, 0, st>>>(p);
+    if (w_packed_threads(p.n) == 128)
+        k_wsssp_packed<128><<<nsrc, 128, 0, st>>>(p);
+    else
+        k_wsssp_packed<512><<<nsrc, 512, 0, st>>>(p);
 }
 
 }  // namespace bcgb

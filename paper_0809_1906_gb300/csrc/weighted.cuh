@@ -53,6 +53,14 @@ void launch_map_ids(const int32_t *perm, const int32_t *in, int32_t *out, int32_
 
 void w_launch_wave(const WParams &p, int nsrc, cudaStream_t st);         // 64-bit counts
 void w_launch_wave_packed(const WParams &p, int nsrc, cudaStream_t st);  // packed state, 32-bit counts
+// Threads per source of the packed kernel: a distance step settles about n /
+// (distinct distances) vertices, so small graphs leave wide CTAs idle at every
+// barrier while large ones need the threads. Square grids with 5% long-range
+// edges, best wave of each (ms): n = 4096 (all sources) 128 threads 18.1, 512
+// threads 58.2; n = 16384 (2048 sources) 11.8 / 35.0; n = 65536 30.5 / 41.0;
+// n = 262144 146.4 / 123.4. The switch sits between the last two sizes.
+constexpr int32_t kWSmallN = 131072;
+int w_packed_threads(int32_t n);
 // bc[vid[v]] += the FP64 sum over r < nrows of rows[r][v], rows in order (vid null: bc[v])
 void w_launch_reduce(const float *rows, int nrows, int n, const int32_t *vid, double *bc, int sms,
                      cudaStream_t st);
