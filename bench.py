@@ -111,13 +111,17 @@ def code_text(text: str) -> str:
     return "".join(text.split())
 
 
-def csrc_digest() -> str:
-    """SHA-256 over the sweep kernels' sources with comments and blank space
+# Sources of the weighted kernel whose DRAM bytes profiles/traffic_grid.json holds.
+GRID_SOURCES = ("sssp_packed.cu", "weighted.cuh", "relabel.cu")
+
+
+def csrc_digest(names=SWEEP_SOURCES) -> str:
+    """SHA-256 over the kernels' sources with comments and blank space
     removed: DRAM counters taken from an older build do not describe the
     current kernels, while a comment edit changes nothing they measure."""
     import hashlib
     h = hashlib.sha256()
-    for name in SWEEP_SOURCES:
+    for name in names:
         with open(os.path.join(ROOT, "paper_0809_1906_gb300", "csrc", name), encoding="utf-8") as fh:
             h.update(name.encode())
             h.update(code_text(fh.read()).encode())
@@ -180,6 +184,52 @@ def write_traffic(csv_path: str, command: str, out_path: str = TRAFFIC_JSON, ech
         json.dump(out, f, indent=1)
     if echo:
         print(json.dumps(out, indent=1))
+    return out
+
+
+TRAFFIC_GRID_JSON = os.path.join(ROOT, "profiles", "traffic_grid.json")
+
+
+def measured_traffic_grid(path: str = TRAFFIC_GRID_JSON):
+    """DRAM bytes (read + write) per source of k_wsssp_packed on the weighted
+    grid, from the committed ncu capture of one wave
+    (profiles/traffic_grid.json); None when taken on other kernel sources."""
+    try:
+        with open(path) as f:
+            tr = json.load(f)
+        if tr.get("csrc_sha256") != csrc_digest(GRID_SOURCES):
+            return None
+        return tr["dram_bytes_per_source"]
+    except Exception:
+        return None
+
+
+def write_traffic_grid(csv_path: str, sources: int, command: str, out_path: str = TRAFFIC_GRID_JSON):
+    """Turn an ncu capture (dram__bytes_read.sum, dram__bytes_write.sum,
+    gpu__time_duration.sum; --csv) of k_wsssp_packed launches over `sources`
+    sources of the weighted grid into profiles/traffic_grid.json."""
+    import csv
+    with open(csv_path) as f:
+        rows = list(csv.reader(line for line in f if line.startswith('"')))
+    h = rows[0]
+    tot = {}
+    ids = set()
+    for r in rows[1:]:
+        if "k_wsssp_packed" not in r[h.index("Kernel Name")]:
+            continue
+        ids.add(r[h.index("ID")])
+        k = r[h.index("Metric Name")]
+        tot[k] = tot.get(k, 0.0) + float(r[h.index("Metric Value")].replace(",", ""))
+    rd, wr = tot.get("dram__bytes_read.sum", 0.0), tot.get("dram__bytes_write.sum", 0.0)
+    out = {"csrc_sha256": csrc_digest(GRID_SOURCES), "command": command,
+           "note": "k_wsssp_packed over one wave of the weighted grid's seeded sources (relabelled graph); ncu "
+                   "replays the launch with cold caches; bytes per source = (read + write) / sources",
+           "launches": len(ids), "sources": sources, "dram_read_bytes": rd, "dram_write_bytes": wr,
+           "dram_bytes_per_source": (rd + wr) / max(sources, 1),
+           "ncu_time_ms": tot.get("gpu__time_duration.sum", 0.0) / 1e6}
+    with open(out_path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out, indent=1))
     return out
 
 
@@ -363,6 +413,8 @@ def cfg_grid(c):
     n, m = g.n, g.m
     alg = 4096 * (16 * m + 32 * n) + 12 * arcs  # per source: 2 passes x 2m x 4 B, 12 B per DAG arc, 32 B per vertex
     achieved = alg / (fms / 1e3) / 1e9
+    tps = measured_traffic_grid()  # DRAM bytes per source, scaled to the sources of an average launch
+    traffic = tps * 4096 / max(fl, 1) if tps is not None else None
     return {"metric": METRIC, "unit": UNIT, "value": 4096 * m / (ms / 1e3), "ms_per_step": ms,
             "config": {"workload": f"512x512 grid + 5% long-range, w~U[1,100] (n={n}, m={m}), 4096 sampled sources",
                        "dag_arcs_per_source": arcs / 4096,
@@ -370,7 +422,8 @@ def cfg_grid(c):
                                                  "value": sub.n * sub.m / (ms_sub / 1e3),
                                                  "error_vs_oracle": err_sub}},
             "roofline": {"bound": "hbm", "kernel": "k_wsssp_packed", "achieved": achieved, "peak": c.hbm,
-                         "unit": "GB/s", "frac": achieved / c.hbm, "peak_source": c.hbm_kind, "traffic": None,
+                         "unit": "GB/s", "frac": achieved / c.hbm, "peak_source": c.hbm_kind, "traffic": traffic,
+                         "traffic_note": "profiles/traffic_grid.json: DRAM bytes per source x sources per launch",
                          "algorithmic_bytes": alg, "kernel_ms": fms, "launches": fl},
             "error_vs_oracle": err,
             "cpu_baseline": _oracle_rate(g, srcn, c.cpu_seconds)}
@@ -613,9 +666,14 @@ def main():
     ap.add_argument("--write-traffic", metavar="CSV", default=None,
                     help="write profiles/traffic_rmat.json from an ncu CSV capture of --profile, then exit")
     ap.add_argument("--traffic-command", default="", help="the ncu command line recorded with --write-traffic")
+    ap.add_argument("--write-traffic-grid", metavar="CSV", default=None,
+                    help="write profiles/traffic_grid.json from an ncu CSV capture of --profile --workload grid "
+                         "over --sources sources, then exit")
     args = ap.parse_args()
     if args.write_traffic:
         return write_traffic(args.write_traffic, args.traffic_command)
+    if args.write_traffic_grid:
+        return write_traffic_grid(args.write_traffic_grid, args.sources, args.traffic_command)
     args.warmup = max(args.warmup, 3)
     if args.profile:
         return run_profile(args)

@@ -63,3 +63,24 @@ def test_committed_traffic_table_is_well_formed():
     assert set(doc["kinds"]) >= {"forward", "backward", "hash"}
     got = bench.measured_traffic("forward")
     assert (got is None) == (doc["csrc_sha256"] != bench.csrc_digest())
+
+
+def test_grid_traffic_table_from_an_ncu_csv(tmp_path):
+    hdr = '"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"\n'
+    rows = [
+        ('0', 'void unnamed>::k_map_ids(const int *, const int *, int *, int)', 'dram__bytes_read.sum', 'byte', '99'),
+        ('1', 'void unnamed>::k_wsssp_packed<512>(WParams)', 'dram__bytes_read.sum', 'byte', '3,000'),
+        ('1', 'void unnamed>::k_wsssp_packed<512>(WParams)', 'dram__bytes_write.sum', 'byte', '1000'),
+        ('1', 'void unnamed>::k_wsssp_packed<512>(WParams)', 'gpu__time_duration.sum', 'ns', '2000000'),
+    ]
+    csv_path = tmp_path / "g.csv"
+    csv_path.write_text(hdr + "".join(",".join(f'"{x}"' for x in r) + "\n" for r in rows))
+    out_path = tmp_path / "grid.json"
+    out = bench.write_traffic_grid(str(csv_path), 8, "cmd", out_path=str(out_path))
+    assert out["launches"] == 1 and out["dram_bytes_per_source"] == 500.0
+    assert abs(out["ncu_time_ms"] - 2.0) < 1e-12
+    assert bench.measured_traffic_grid(path=str(out_path)) == 500.0
+    doc = json.loads(out_path.read_text())
+    doc["csrc_sha256"] = "0" * 64
+    out_path.write_text(json.dumps(doc))
+    assert bench.measured_traffic_grid(path=str(out_path)) is None
