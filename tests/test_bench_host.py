@@ -84,3 +84,12 @@ def test_grid_traffic_table_from_an_ncu_csv(tmp_path):
     doc["csrc_sha256"] = "0" * 64
     out_path.write_text(json.dumps(doc))
     assert bench.measured_traffic_grid(path=str(out_path)) is None
+
+
+def test_committed_grid_traffic_is_well_formed():
+    with open(bench.TRAFFIC_GRID_JSON) as f:
+        doc = json.load(f)
+    assert len(doc["csrc_sha256"]) == 64 and doc["command"] and doc["sources"] > 0
+    assert doc["dram_bytes_per_source"] == (doc["dram_read_bytes"] + doc["dram_write_bytes"]) / doc["sources"]
+    got = bench.measured_traffic_grid()
+    assert (got is None) == (doc["csrc_sha256"] != bench.csrc_digest(bench.GRID_SOURCES))
