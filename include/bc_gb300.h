@@ -108,9 +108,9 @@ extern "C" {
                                 (unweighted, batched, more than 32 sources) batches are formed from
                                 the sources sorted by their BFS distances to 32 landmark vertices, so
                                 the sources of one 32-source word have similar distance profiles and
-                                the level sweep fetches fewer rows; and the weighted sweep of an
-                                undirected graph runs on a copy of the graph renumbered by
-                                bc_vertex_order (built on first use, kept with the handle), so that
+                                the level sweep fetches fewer rows; and the weighted sweep runs on
+                                a copy of the graph renumbered by bc_vertex_order (built on first
+                                use, kept with the handle; a directed graph by its out-arcs), so that
                                 neighbouring vertices share memory sectors. Either way BC differs
                                 only by floating-point summation order; distances, path counts,
                                 forward rows and per-source summaries are the same, in the caller's
@@ -392,7 +392,7 @@ void bc_release_cached_memory(void);
 
 /* A vertex numbering with locality, from the CSR alone (host code; no GPU
  * needed). Not part of the paper's method: it is the memory layout the
- * weighted sweep uses for undirected graphs (see BC_KEEP_ORDER). Multilevel
+ * weighted sweep runs on (see BC_KEEP_ORDER). Multilevel
  * heavy-edge matching: each level matches every node, in id order, with the
  * unmatched neighbour joined to it by the most edges; matched pairs become the
  * next level's nodes. Vertices are then numbered by their ancestors, top level

@@ -360,13 +360,13 @@ struct bc_graph {
     std::vector<int32_t> h_sources;  // host copy of the staged source list
     DevBuf<uint64_t> wsigma;
     DevBuf<float> wcval, wrows;
-    // the weighted sweep's relabelled copy of an undirected graph (built on
-    // first use): the CSR in a numbering with locality, old -> new ids
-    // (wperm, also on the host) and new -> old (wvid), and a run's sources
-    // in the new numbering
+    // the weighted sweep's relabelled copy of the graph (built on first
+    // use): the CSR (and a directed graph's in-arc CSR) in a numbering with
+    // locality, old -> new ids (wperm, also on the host) and new -> old
+    // (wvid), and a run's sources in the new numbering
     bool relabel_ok = false;
     std::vector<int32_t> h_wperm;
-    DevBuf<int32_t> prow_ptr, pcol, pw, wperm, wvid, wpsrc;
+    DevBuf<int32_t> prow_ptr, pcol, pw, prow_ptr_in, pcol_in, pw_in, wperm, wvid, wpsrc;
     // lanes 1..3 of the weighted waves: stream, packed state, rows, BC accumulator
     struct WLane {
         cudaStream_t st = nullptr;
@@ -434,7 +434,9 @@ void free_graph(bc_graph *g) {
     g->dX.release();
     g->dctl.release();
     for (auto *b : {&g->wdist, &g->worder, &g->wgrp, &g->wslots}) b->release();
-    for (auto *b : {&g->prow_ptr, &g->pcol, &g->pw, &g->wperm, &g->wvid, &g->wpsrc}) b->release();
+    for (auto *b : {&g->prow_ptr, &g->pcol, &g->pw, &g->prow_ptr_in, &g->pcol_in, &g->pw_in, &g->wperm, &g->wvid,
+                    &g->wpsrc})
+        b->release();
     g->wsigma.release();
     g->wcval.release();
     g->wrows.release();
@@ -1492,6 +1494,68 @@ int sm_count_host() {
     return c;
 }
 
+// The relabelled copy of a weighted graph (relabel.cu's numbering of the
+// out-arc CSR): vertex v becomes wperm[v]; each row keeps its arcs' weights,
+// with the heads renumbered and sorted; a directed graph's in-arc CSR is
+// renumbered the same way. Built once per handle; host code plus uploads.
+int ensure_relabel(bc_graph *g) {
+    if (g->relabel_ok) return BC_OK;
+    const int32_t n = g->n;
+    const int64_t m2 = g->narcs;
+    std::vector<int32_t> cl, ww;
+    CK(fetch(cl, (const int32_t *)g->col.p, (size_t)m2));
+    CK(fetch(ww, (const int32_t *)g->w.p, (size_t)m2));
+    std::vector<int32_t> perm((size_t)n), vid((size_t)n);
+    bcgb::locality_order(n, g->h_row_ptr.data(), cl.data(), perm.data());
+    for (int32_t v = 0; v < n; ++v) vid[(size_t)perm[v]] = v;
+    // row x of the result holds row vid[x] of (rp, col, w), heads renumbered
+    auto permute = [&](const std::vector<int32_t> &rp, const std::vector<int32_t> &col,
+                       const std::vector<int32_t> &w, std::vector<int32_t> &prp, std::vector<int32_t> &pcl,
+                       std::vector<int32_t> &pww) {
+        prp.assign((size_t)n + 1, 0);
+        pcl.resize(col.size());
+        pww.resize(col.size());
+        std::vector<std::pair<int32_t, int32_t>> row;
+        for (int32_t x = 0; x < n; ++x) {
+            const int32_t v = vid[(size_t)x];
+            row.clear();
+            for (int64_t e = rp[(size_t)v]; e < rp[(size_t)v + 1]; ++e)
+                row.emplace_back(perm[(size_t)col[(size_t)e]], w[(size_t)e]);
+            std::sort(row.begin(), row.end());
+            const int32_t at = prp[(size_t)x];
+            for (size_t i = 0; i < row.size(); ++i) {
+                pcl[(size_t)at + i] = row[i].first;
+                pww[(size_t)at + i] = row[i].second;
+            }
+            prp[(size_t)x + 1] = at + (int32_t)row.size();
+        }
+    };
+    auto up = [&](DevBuf<int32_t> &d, const std::vector<int32_t> &h) -> int {
+        CK(d.ensure(h.size()));
+        if (!h.empty()) CK(cudaMemcpy(d.p, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        return BC_OK;
+    };
+    std::vector<int32_t> prp, pcl, pww;
+    permute(g->h_row_ptr, cl, ww, prp, pcl, pww);
+    int r = up(g->prow_ptr, prp);
+    if (!r) r = up(g->pcol, pcl);
+    if (!r) r = up(g->pw, pww);
+    if (!r && g->directed) {
+        CK(fetch(cl, (const int32_t *)g->col_in.p, (size_t)m2));
+        CK(fetch(ww, (const int32_t *)g->w_in.p, (size_t)m2));
+        permute(g->h_row_ptr_in, cl, ww, prp, pcl, pww);
+        r = up(g->prow_ptr_in, prp);
+        if (!r) r = up(g->pcol_in, pcl);
+        if (!r) r = up(g->pw_in, pww);
+    }
+    if (!r) r = up(g->wperm, perm);
+    if (!r) r = up(g->wvid, vid);
+    if (r) return r;
+    g->h_wperm.swap(perm);
+    g->relabel_ok = true;
+    return BC_OK;
+}
+
 // Weighted path: waves of one CTA per source (csrc/sssp_weighted.cu).
 // opt->batch (if set) is the wave size; default kWSmallPerSm sources per SM
 // for the 128-thread CTAs of small graphs, else three per SM, two of them
@@ -1511,49 +1575,6 @@ int sm_count_host() {
 constexpr int kWeightedLanes = 2;  // measured: 3 or 4 lanes no faster on the 512x512 grid
 constexpr int kWSmallPerSm = 8;    // wave of the 128-thread CTAs (small graphs), per SM: all resident
 
-// The relabelled copy of an undirected weighted graph (relabel.cu's
-// numbering): vertex v becomes wperm[v]; its arcs keep their weights, heads
-// renumbered and sorted. Built once per handle; host code plus uploads.
-int ensure_relabel(bc_graph *g) {
-    if (g->relabel_ok) return BC_OK;
-    const int32_t n = g->n;
-    const int64_t m2 = g->narcs;
-    std::vector<int32_t> cl, ww;
-    CK(fetch(cl, (const int32_t *)g->col.p, (size_t)m2));
-    CK(fetch(ww, (const int32_t *)g->w.p, (size_t)m2));
-    const std::vector<int32_t> &rp = g->h_row_ptr;
-    std::vector<int32_t> perm((size_t)n), vid((size_t)n);
-    bcgb::locality_order(n, rp.data(), cl.data(), perm.data());
-    for (int32_t v = 0; v < n; ++v) vid[(size_t)perm[v]] = v;
-    std::vector<int32_t> prp((size_t)n + 1, 0), pcl((size_t)m2), pww((size_t)m2);
-    std::vector<std::pair<int32_t, int32_t>> row;
-    for (int32_t x = 0; x < n; ++x) {
-        const int32_t v = vid[(size_t)x];
-        row.clear();
-        for (int64_t e = rp[v]; e < rp[(size_t)v + 1]; ++e) row.emplace_back(perm[(size_t)cl[(size_t)e]], ww[(size_t)e]);
-        std::sort(row.begin(), row.end());
-        const int32_t at = prp[(size_t)x];
-        for (size_t i = 0; i < row.size(); ++i) {
-            pcl[(size_t)at + i] = row[i].first;
-            pww[(size_t)at + i] = row[i].second;
-        }
-        prp[(size_t)x + 1] = at + (int32_t)row.size();
-    }
-    auto up = [&](DevBuf<int32_t> &d, const std::vector<int32_t> &h) -> int {
-        CK(d.ensure(h.size()));
-        if (!h.empty()) CK(cudaMemcpy(d.p, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-        return BC_OK;
-    };
-    int r = up(g->prow_ptr, prp);
-    if (!r) r = up(g->pcol, pcl);
-    if (!r) r = up(g->pw, pww);
-    if (!r) r = up(g->wperm, perm);
-    if (!r) r = up(g->wvid, vid);
-    if (r) return r;
-    g->h_wperm.swap(perm);
-    g->relabel_ok = true;
-    return BC_OK;
-}
 constexpr double kWeightedLaneBudget = 24.0 * (1 << 30);  // packed wave state of all lanes
 
 int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t st, bool backward, bool hash,
@@ -1593,10 +1614,10 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
     }
     CK(g->wredo.ensure((size_t)std::max(nsrc, 1)));
     CK(cudaMemsetAsync(g->wredo.p, 0, (size_t)std::max(nsrc, 1), st));
-    // undirected graphs run on the relabelled copy (BC_KEEP_ORDER: on the
-    // caller's numbering): sources mapped in, summaries, rows and BC mapped
-    // back to the caller's ids by the kernels
-    const bool relabel = !g->directed && n > 1 && !(opt && (opt->flags & BC_KEEP_ORDER));
+    // the sweep runs on the relabelled copy (BC_KEEP_ORDER: on the caller's
+    // numbering): sources mapped in, summaries, rows and BC mapped back to
+    // the caller's ids by the kernels
+    const bool relabel = n > 1 && !(opt && (opt->flags & BC_KEEP_ORDER));
     if (relabel) {
         int r = ensure_relabel(g);
         if (r) return r;
@@ -1633,9 +1654,9 @@ int run_weighted(bc_graph *g, int32_t nsrc, const bc_options *opt, cudaStream_t 
     base.w = relabel ? g->pw.p : g->w.p;
     base.vid = vid;
     if (g->directed) {
-        base.row_ptr_in = g->row_ptr_in.p;
-        base.col_in = g->col_in.p;
-        base.w_in = g->w_in.p;
+        base.row_ptr_in = relabel ? g->prow_ptr_in.p : g->row_ptr_in.p;
+        base.col_in = relabel ? g->pcol_in.p : g->col_in.p;
+        base.w_in = relabel ? g->pw_in.p : g->w_in.p;
     }
     base.ctl = g->ctl;
     for (int32_t k = 0; k < nwaves; ++k) {

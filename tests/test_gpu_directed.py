@@ -83,9 +83,12 @@ def test_kkp_tripartite_weighted(nat, n):
 
 
 @pytest.mark.parametrize("seed", range(3))
-def test_directed_random_weighted(nat, seed):
+@pytest.mark.parametrize("numbering", ["relabelled", "caller"])
+def test_directed_random_weighted(nat, seed, numbering):
+    """The weighted sweep on its renumbered copy (out- and in-arc CSRs) and,
+    with BC_KEEP_ORDER, on the caller's numbering."""
     g = G.directed_random(400, 0.02, 1030 + seed, wmax=5)
-    check(nat, g)
+    check(nat, g, flags=nat.BC_KEEP_ORDER if numbering == "caller" else 0)
 
 
 def test_directed_rejected_where_unsupported(nat):

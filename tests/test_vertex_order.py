@@ -1,5 +1,5 @@
 """CPU checks of bc_vertex_order, the numbering with locality that the weighted
-sweep of an undirected graph runs on (host code, no GPU)."""
+sweep runs on (host code, no GPU)."""
 import numpy as np
 import pytest
 
