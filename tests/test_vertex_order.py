@@ -98,3 +98,15 @@ def test_rejects_malformed_input(bad):
     with pytest.raises(native.BcError) as e:
         native.vertex_order(n, rp, col)
     assert e.value.code == native.BC_ERR_ARG
+
+
+def test_directed_and_irregular_csr():
+    # the weighted sweep orders a directed graph by its out-arcs; self-loops
+    # and repeated heads are accepted here (bc_create_graph rejects them)
+    g = G.directed_random(300, 0.02, 7, wmax=3)
+    p = order(g)
+    assert is_perm(p, g.n) and np.array_equal(p, order(g))
+    rp = np.array([0, 3, 4, 4, 6], np.int32)
+    col = np.array([0, 1, 1, 0, 3, 3], np.int32)
+    p = native.vertex_order(4, rp, col)
+    assert is_perm(p, 4)
