@@ -1556,14 +1556,14 @@ int ensure_relabel(bc_graph *g) {
     return BC_OK;
 }
 
-// Weighted path: waves of one CTA per source (csrc/sssp_weighted.cu).
-// opt->batch (if set) is the wave size; default kWSmallPerSm sources per SM
-// for the 128-thread CTAs of small graphs, else three per SM, two of them
-// resident (512-thread CTAs: on the relabelled 512x512 grid 1 / 2 / 3 / 4 per
-// SM measured 258 / 257 / 241 / 252 ms, with 256-thread CTAs 274 / 255 / 253 /
-// 256; on the caller's row-major numbering more sources in flight only added
-// random DRAM sectors), capped so the wave state stays within 8 GiB.
-// Weighted sweep: waves of G sources (one CTA each, packed state) on
+// Weighted sweep (csrc/sssp_packed.cu; csrc/sssp_weighted.cu for 64-bit
+// counts): waves of G sources, one CTA each. G is opt->batch if set, else
+// kWSmallPerSm sources per SM for the 128-thread CTAs of small graphs, else
+// three per SM, two of them resident (512-thread CTAs: on the relabelled
+// 512x512 grid 1 / 2 / 3 / 4 per SM measured 258 / 257 / 241 / 252 ms, with
+// 256-thread CTAs 274 / 255 / 253 / 256; on the caller's row-major numbering
+// more sources in flight only added random DRAM sectors), capped so the wave
+// state stays within 8 GiB. Waves run on
 // kWeightedLanes lanes: wave k runs on lane k % lanes, each with its own stream,
 // state, delta rows and BC accumulator, so one wave's slowest sources overlap
 // the next waves. The delta rows of a wave are added to its lane's BC in
