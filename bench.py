@@ -673,6 +673,8 @@ def main():
     if args.write_traffic:
         return write_traffic(args.write_traffic, args.traffic_command)
     if args.write_traffic_grid:
+        if args.sources <= 0:
+            ap.error("--write-traffic-grid needs --sources: the sources the captured launches covered")
         return write_traffic_grid(args.write_traffic_grid, args.sources, args.traffic_command)
     args.warmup = max(args.warmup, 3)
     if args.profile:
